@@ -1,0 +1,1126 @@
+/*
+ * mcrt_oracle.c -- plain, slow, FP64 CPU oracle of the null-collision path
+ * tracer (Villefranque et al. 2019, "Path-tracing Monte Carlo library for 3D
+ * radiative transfer in highly resolved cloudy atmospheres").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the tests, the package's smoke check and the bench's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA library; the only thing both sides see is the seeded scene data.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - Philox4x32-10 (Salmon et al., SC'11), written from the published round
+ *     definition; the method's random numbers come from it.
+ *   - The majorant pyramid: exact max over 8^3 children, level by level
+ *     (Sec. 3.1.1 "Construction": merged voxels store the max extinction).
+ *   - The leaf criterion of the hierarchical grid: a cell is used for tracking
+ *     when the vertical optical depth bound M * h_z of the merged region is
+ *     below the threshold tau~ (Sec. 4.2, list after the coarse-graining text).
+ *   - An FP32 traversal "spec" (bit-exact cell sequences) and an FP64
+ *     brute-force ray/voxel-face intersection that pins it.
+ *   - The null-collision free-path sampler (Sec. 2.3, steps 1-5 and Eq. 2),
+ *     ratio / delta tracking toward the sun, the backward local-estimate
+ *     radiance and ground-flux estimators with HG scattering and a Lambertian
+ *     ground (Sec. 4.1), and a forward analog flux estimator (Sec. 5.2: a
+ *     path is diffuse once it has been scattered).
+ *
+ * Everything floating point is double unless a function says it reproduces
+ * the FP32 traversal spec.  Build with -ffp-contract=off so that the FP32
+ * spec is not altered by fused multiply-adds.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ===================================================================== */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 4 "Philox").    */
+/* Round: two 32x32->64 products of counter words with fixed multipliers, */
+/* xor of the high halves with the other counter words and the key; the   */
+/* key is bumped by the Weyl constants between rounds.                    */
+/* ===================================================================== */
+#define PHILOX_MUL0 0xD2511F53u
+#define PHILOX_MUL1 0xCD9E8D57u
+#define PHILOX_WEYL0 0x9E3779B9u
+#define PHILOX_WEYL1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += PHILOX_WEYL0; k1 += PHILOX_WEYL1; }
+        uint64_t p0 = (uint64_t)PHILOX_MUL0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_MUL1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void orc_philox_batch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* Random stream of one (path, event, stream) triple.  Counter words:
+ *   c0 = path id low 32 bits, c1 = path id high 32 bits,
+ *   c2 = (event << 2) | stream, c3 = index of the 4-word block.
+ * Draw n is word (n & 3) of block (n >> 2).  Key = (seed low, seed high). */
+typedef struct {
+    uint32_t key[2];
+    uint32_t c0, c1, c2;
+    uint32_t n;
+    uint32_t buf[4];
+} rng_t;
+
+static void rng_init(rng_t* r, uint64_t seed, uint64_t path, uint32_t event, uint32_t stream)
+{
+    r->key[0] = (uint32_t)seed;
+    r->key[1] = (uint32_t)(seed >> 32);
+    r->c0 = (uint32_t)path;
+    r->c1 = (uint32_t)(path >> 32);
+    r->c2 = (event << 2) | (stream & 3u);
+    r->n = 0;
+}
+
+static uint32_t rng_u32(rng_t* r)
+{
+    if ((r->n & 3u) == 0) {
+        uint32_t ctr[4] = {r->c0, r->c1, r->c2, r->n >> 2};
+        orc_philox4x32_10(ctr, r->key, r->buf);
+    }
+    return r->buf[r->n++ & 3u];
+}
+
+/* Uniform in (0, 1]: ((x >> 8) + 1) * 2^-24, exact in float and double. */
+static double rng_u(rng_t* r)
+{
+    return (double)((rng_u32(r) >> 8) + 1u) * (1.0 / 16777216.0);
+}
+
+double orc_u01_from_u32(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+
+/* ===================================================================== */
+/* BF16 rounding of a finite, non-negative float (used for the optional    */
+/* BF16 storage of the extinction field).                                 */
+/* ===================================================================== */
+static uint32_t f2u(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
+static float u2f(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
+
+/* Round to nearest-even to the 8-bit mantissa of bfloat16. */
+float orc_bf16_round_nearest(float x)
+{
+    if (isnan(x) || isinf(x)) return x;
+    uint32_t u = f2u(x);
+    uint32_t lsb = (u >> 16) & 1u;
+    u = u + 0x7FFFu + lsb;
+    return u2f(u & 0xFFFF0000u);
+}
+
+/* Smallest bfloat16 value >= x, for x >= 0 (majorants must stay bounds). */
+float orc_bf16_round_up(float x)
+{
+    if (isnan(x) || isinf(x) || x <= 0.0f) return x <= 0.0f ? 0.0f : x;
+    uint32_t u = f2u(x);
+    if (u & 0xFFFFu) u = (u & 0xFFFF0000u) + 0x10000u;
+    return u2f(u);
+}
+
+/* ===================================================================== */
+/* Majorant pyramid (Sec. 3.1.1, "Construction"; Sec. 2.4: the majorant   */
+/* is piecewise uniform over the cells of a coarser grid).  Level 0 is   */
+/* the voxel field; a level-L cell covers 8^L voxels per axis and stores  */
+/* the exact max over its existing children.                             */
+/* ===================================================================== */
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+void orc_level_dims(int nx, int ny, int nz, int level, int out[3])
+{
+    int f = 1;
+    for (int l = 0; l < level; ++l) f *= 8;
+    out[0] = ceil_div(nx, f); out[1] = ceil_div(ny, f); out[2] = ceil_div(nz, f);
+}
+
+int64_t orc_pyramid_size(int nx, int ny, int nz, int levels)
+{
+    int64_t tot = 0;
+    for (int l = 1; l <= levels; ++l) {
+        int d[3]; orc_level_dims(nx, ny, nz, l, d);
+        tot += (int64_t)d[0] * d[1] * d[2];
+    }
+    return tot;
+}
+
+/* out: levels 1..levels concatenated, each x fastest.  round_up_bf16 != 0
+ * stores RU_bf16 of each max (the bound of a field stored as RN_bf16). */
+int orc_build_pyramid(const float* k, int nx, int ny, int nz, int levels, int round_up_bf16, float* out)
+{
+    if (levels < 1) return -1;
+    const float* prev = k;
+    int pd[3] = {nx, ny, nz};
+    float* cur = out;
+    for (int l = 1; l <= levels; ++l) {
+        int d[3]; orc_level_dims(nx, ny, nz, l, d);
+        for (int cz = 0; cz < d[2]; ++cz)
+            for (int cy = 0; cy < d[1]; ++cy)
+                for (int cx = 0; cx < d[0]; ++cx) {
+                    float m = 0.0f;
+                    for (int z = 8 * cz; z < 8 * cz + 8 && z < pd[2]; ++z)
+                        for (int y = 8 * cy; y < 8 * cy + 8 && y < pd[1]; ++y)
+                            for (int x = 8 * cx; x < 8 * cx + 8 && x < pd[0]; ++x) {
+                                float v = prev[((int64_t)z * pd[1] + y) * pd[0] + x];
+                                if (l == 1 && round_up_bf16) v = orc_bf16_round_up(v);
+                                if (v > m) m = v;
+                            }
+                    cur[((int64_t)cz * d[1] + cy) * d[0] + cx] = m;
+                }
+        prev = cur;
+        pd[0] = d[0]; pd[1] = d[1]; pd[2] = d[2];
+        cur += (int64_t)d[0] * d[1] * d[2];
+    }
+    return 0;
+}
+
+/* ===================================================================== */
+/* Scene description shared by the traversal and the estimators.          */
+/* ===================================================================== */
+typedef struct {
+    int32_t nx, ny, nz;
+    float dx, dy, dz;          /* voxel size [km] (FP32, used exactly)    */
+    const float* k;            /* extinction [km^-1], x fastest           */
+    int32_t levels;            /* pyramid levels above the voxels         */
+    const float* pyr;          /* concatenated levels 1..levels           */
+    float tau_merge;           /* leaf threshold tau~ (INFINITY allowed)  */
+    int32_t finest_level;      /* finest level used for tracking (0 or 1) */
+    double k_clear;            /* uniform clear-sky extinction            */
+    double ssa_clear, ssa_cloud;
+    double g;                  /* HG asymmetry                            */
+    double ground_albedo;
+    double sun[3];             /* unit vector toward the sun              */
+    int32_t sun_mode;          /* 0 ratio tracking, 1 delta tracking      */
+    int32_t max_order;         /* 0: all orders; n: score orders <= n     */
+    double k_gas;              /* extra uniform pure absorber             */
+    int64_t max_steps;         /* traversal guard per ray                 */
+} orc_scene;
+
+static const float* level_ptr(const orc_scene* S, int level, int dims[3])
+{
+    const float* p = S->pyr;
+    for (int l = 1; l < level; ++l) {
+        int d[3]; orc_level_dims(S->nx, S->ny, S->nz, l, d);
+        p += (int64_t)d[0] * d[1] * d[2];
+    }
+    orc_level_dims(S->nx, S->ny, S->nz, level, dims);
+    return p;
+}
+
+static float kvox(const orc_scene* S, const int v[3])
+{
+    return S->k[((int64_t)v[2] * S->ny + v[1]) * S->nx + v[0]];
+}
+
+/* Leaf containing voxel v: the coarsest cell at a level > finest_level
+ * whose bound on the vertical optical depth, M * h_z (FP32 product), is
+ * <= tau~; otherwise the cell of level finest_level.  (Sec. 4.2: cells are
+ * merged while the merged vertical optical depth stays below tau~; the
+ * merged cell stores the max, Sec. 3.1.1.) */
+static void leaf_of(const orc_scene* S, const int v[3], int* lev_out, float* M_out)
+{
+    for (int L = S->levels; L > S->finest_level; --L) {
+        int d[3];
+        const float* P = level_ptr(S, L, d);
+        int c[3] = {v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L)};
+        float M = P[((int64_t)c[2] * d[1] + c[1]) * d[0] + c[0]];
+        float hz = S->dz * (float)(1 << (3 * L));
+        float tz = M * hz;
+        if (tz <= S->tau_merge) { *lev_out = L; *M_out = M; return; }
+    }
+    int L = S->finest_level;
+    if (L == 0) { *lev_out = 0; *M_out = kvox(S, v); return; }
+    int d[3];
+    const float* P = level_ptr(S, L, d);
+    int c[3] = {v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L)};
+    *lev_out = L;
+    *M_out = P[((int64_t)c[2] * d[1] + c[1]) * d[0] + c[0]];
+}
+
+/* Voxel range [lo, hi] covered by the level-L cell containing voxel v. */
+static void cell_range(const orc_scene* S, int L, const int v[3], int lo[3], int hi[3])
+{
+    const int n[3] = {S->nx, S->ny, S->nz};
+    for (int a = 0; a < 3; ++a) {
+        int c = v[a] >> (3 * L);
+        lo[a] = c << (3 * L);
+        int e = (c + 1) << (3 * L);
+        hi[a] = (e < n[a] ? e : n[a]) - 1;
+    }
+}
+
+/* ===================================================================== */
+/* FP32 traversal spec.  The CUDA traversal is required to produce the    */
+/* same leaf sequence and the same t values bit for bit.  Every operation */
+/* is a single IEEE-754 binary32 operation with round-to-nearest; fmaf is */
+/* the correctly rounded fused multiply-add.                              */
+/*                                                                        */
+/* State: voxel index v of the current point, leaf (level, majorant),     */
+/* segment origin o, distance t along d.  Exit distance on axis a:        */
+/*   B = hi+1 (d>0) or lo (d<0) in voxel units,                           */
+/*   t_a = ((float)B * dx_a - o_a) * (1/d_a)       (three roundings),     */
+/*   +inf when d_a == 0;  exit axis = first minimum in x, y, z order;     */
+/*   t_exit = max(min_a t_a, t).                                          */
+/* Step: on the exit axis v_a = hi+1 or lo-1.  On the other axes          */
+/*   p_b = fmaf(t_exit, d_b, o_b), v_b = floor(p_b * (1/dx_b)), minus one */
+/*   when d_b < 0 and (float)v_b * dx_b == p_b, clamped into the old      */
+/*   leaf's voxel range.  z below 0 is the ground, z >= nz the top.       */
+/*   x, y wrap periodically; on a wrap the segment restarts at the exit   */
+/*   point (o_a set to 0 or L_a exactly) with t = 0.                      */
+/* Recorded per leaf: level, leaf index (3), t_in, t_out measured from    */
+/* the ray origin (tbase + t, one FP32 addition).                         */
+/* ===================================================================== */
+static int locate_f32(float p, float d, float dxa, float inv_dxa, int lo, int hi)
+{
+    int i = (int)floorf(p * inv_dxa);
+    if (d < 0.0f && (float)i * dxa == p) i -= 1;
+    if (i < lo) i = lo;
+    if (i > hi) i = hi;
+    return i;
+}
+
+/* Returns the number of leaves written; *status: 1 top, 2 ground,
+ * 3 capacity reached, 4 step guard, -1 bad input. */
+int orc_dda_spec(const orc_scene* S, const float o_in[3], const float d[3], int cap,
+                 int32_t* cells, float* tio, int32_t* status)
+{
+    const int n[3] = {S->nx, S->ny, S->nz};
+    const float h[3] = {S->dx, S->dy, S->dz};
+    float inv_h[3], inv_d[3], Lper[2];
+    float o[3] = {o_in[0], o_in[1], o_in[2]};
+    for (int a = 0; a < 3; ++a) {
+        inv_h[a] = 1.0f / h[a];
+        inv_d[a] = (d[a] != 0.0f) ? 1.0f / d[a] : 0.0f;
+    }
+    Lper[0] = (float)n[0] * h[0];
+    Lper[1] = (float)n[1] * h[1];
+    if (d[0] == 0.0f && d[1] == 0.0f && d[2] == 0.0f) { *status = -1; return 0; }
+    int v[3];
+    for (int a = 0; a < 3; ++a) v[a] = locate_f32(o[a], d[a], h[a], inv_h[a], 0, n[a] - 1);
+    float t = 0.0f, tbase = 0.0f;
+    int count = 0;
+    for (int64_t step = 0;; ++step) {
+        if (step >= S->max_steps) { *status = 4; return count; }
+        int L; float M;
+        leaf_of(S, v, &L, &M);
+        int lo[3], hi[3];
+        cell_range(S, L, v, lo, hi);
+        float ta[3];
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] == 0.0f) { ta[a] = INFINITY; continue; }
+            int B = d[a] > 0.0f ? hi[a] + 1 : lo[a];
+            float bnd = (float)B * h[a];
+            float diff = bnd - o[a];
+            ta[a] = diff * inv_d[a];
+        }
+        int ax = 0;
+        if (ta[1] < ta[ax]) ax = 1;
+        if (ta[2] < ta[ax]) ax = 2;
+        float texit = ta[ax] > t ? ta[ax] : t;
+        if (count >= cap) { *status = 3; return count; }
+        cells[4 * count + 0] = L;
+        cells[4 * count + 1] = v[0] >> (3 * L);
+        cells[4 * count + 2] = v[1] >> (3 * L);
+        cells[4 * count + 3] = v[2] >> (3 * L);
+        tio[2 * count + 0] = tbase + t;
+        tio[2 * count + 1] = tbase + texit;
+        ++count;
+        (void)M;
+        /* step across the face on axis ax */
+        float p[3];
+        for (int b = 0; b < 3; ++b) p[b] = fmaf(texit, d[b], o[b]);
+        int nv[3];
+        for (int b = 0; b < 3; ++b) {
+            if (b == ax) continue;
+            nv[b] = locate_f32(p[b], d[b], h[b], inv_h[b], lo[b], hi[b]);
+        }
+        nv[ax] = d[ax] > 0.0f ? hi[ax] + 1 : lo[ax] - 1;
+        if (ax == 2) {
+            if (nv[2] < 0) { *status = 2; return count; }
+            if (nv[2] >= n[2]) { *status = 1; return count; }
+            v[0] = nv[0]; v[1] = nv[1]; v[2] = nv[2];
+            t = texit;
+        } else {
+            int wrapped = 0;
+            if (nv[ax] < 0) { nv[ax] = n[ax] - 1; wrapped = 1; }
+            else if (nv[ax] >= n[ax]) { nv[ax] = 0; wrapped = 2; }
+            v[0] = nv[0]; v[1] = nv[1]; v[2] = nv[2];
+            if (wrapped) {
+                tbase = tbase + texit;
+                for (int b = 0; b < 3; ++b) o[b] = p[b];
+                o[ax] = (wrapped == 1) ? Lper[ax] : 0.0f;
+                t = 0.0f;
+            } else {
+                t = texit;
+            }
+        }
+    }
+}
+
+/* ===================================================================== */
+/* Brute-force FP64 leaf sequence along a ray: every voxel face crossed   */
+/* up to the top/ground (or tmax), sorted by distance, each voxel mapped  */
+/* to its leaf, consecutive equal leaves merged.  No incremental state.   */
+/* Used to pin the FP32 spec on small grids (away from near-ties).        */
+/* ===================================================================== */
+typedef struct { double t; } tcross;
+static int cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+int orc_dda_bruteforce(const orc_scene* S, const double o[3], const double d[3], double tmax, int cap,
+                       int32_t* cells, double* tio, int32_t* status)
+{
+    const int n[3] = {S->nx, S->ny, S->nz};
+    const double h[3] = {S->dx, S->dy, S->dz};
+    const double Lz = (double)n[2] * h[2];
+    /* distance to the top or ground */
+    double tend = tmax;
+    int end_status = 3;
+    if (d[2] > 0.0) { double tt = (Lz - o[2]) / d[2]; if (tt < tend) { tend = tt; end_status = 1; } }
+    else if (d[2] < 0.0) { double tt = (0.0 - o[2]) / d[2]; if (tt < tend) { tend = tt; end_status = 2; } }
+    /* all face crossings (x, y faces are unbounded because of periodicity) */
+    int64_t cnt = 0, capx = 1024;
+    double* ts = (double*)malloc(sizeof(double) * capx);
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        /* faces j*h; crossing t = (j*h - o)/d for j in range */
+        double t0 = 0.0, t1 = tend;
+        double p0 = o[a], p1 = o[a] + tend * d[a];
+        double lo = p0 < p1 ? p0 : p1, hi = p0 < p1 ? p1 : p0;
+        int64_t j0 = (int64_t)floor(lo / h[a]) - 1, j1 = (int64_t)ceil(hi / h[a]) + 1;
+        for (int64_t j = j0; j <= j1; ++j) {
+            double tc = ((double)j * h[a] - o[a]) / d[a];
+            if (tc > t0 && tc < t1) {
+                if (cnt == capx) { capx *= 2; ts = (double*)realloc(ts, sizeof(double) * capx); }
+                ts[cnt++] = tc;
+            }
+        }
+    }
+    qsort(ts, (size_t)cnt, sizeof(double), cmp_double);
+    int count = 0;
+    double prev_t = 0.0;
+    int prev_leaf[6] = {-1, -1, -1, -1, 0, 0};
+    for (int64_t i = 0; i <= cnt; ++i) {
+        double tb = (i < cnt) ? ts[i] : tend;
+        double tm = 0.5 * (prev_t + tb);
+        if (tb - prev_t <= 0.0) { prev_t = tb; continue; }
+        int v[3];
+        int image[2] = {0, 0};   /* periodic copy of the domain holding the point */
+        for (int a = 0; a < 3; ++a) {
+            double p = o[a] + tm * d[a];
+            if (a < 2) {
+                double L = (double)n[a] * h[a];
+                image[a] = (int)floor(p / L);
+                p = p - floor(p / L) * L;
+            }
+            int vi = (int)floor(p / h[a]);
+            if (vi < 0) vi = 0;
+            if (vi > n[a] - 1) vi = n[a] - 1;
+            v[a] = vi;
+        }
+        int L; float M;
+        leaf_of(S, v, &L, &M);
+        /* a new record starts at every leaf change and at every periodic
+         * wrap (the traversal restarts its segment there) */
+        int leaf[6] = {L, v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L), image[0], image[1]};
+        if (count > 0 && memcmp(leaf, prev_leaf, sizeof(leaf)) == 0) {
+            tio[2 * (count - 1) + 1] = tb;
+        } else {
+            if (count >= cap) { free(ts); *status = 3; return count; }
+            memcpy(cells + 4 * count, leaf, 4 * sizeof(int));
+            tio[2 * count + 0] = prev_t;
+            tio[2 * count + 1] = tb;
+            memcpy(prev_leaf, leaf, sizeof(leaf));
+            ++count;
+        }
+        prev_t = tb;
+    }
+    free(ts);
+    *status = end_status;
+    return count;
+}
+
+/* ===================================================================== */
+/* FP64 traversal used by the estimators.  It works on the current point  */
+/* p directly: find the leaf holding p (direction decides points on a     */
+/* face), the distance to that leaf's exit face, then move p there with   */
+/* the exit coordinate set exactly on the face.                           */
+/* ===================================================================== */
+typedef struct {
+    double p[3];     /* current point, x,y in [0, L) */
+    double d[3];
+    int v[3];        /* voxel of p for the current leaf */
+    int lev;         /* leaf level */
+    double M;        /* leaf majorant (+ k_gas) */
+    int lo[3], hi[3];
+    double seg;      /* distance from p to the leaf exit */
+    int exit_axis;
+    int64_t steps;
+} trav64;
+
+static int locate64(const orc_scene* S, double p, double d, int a)
+{
+    const int n[3] = {S->nx, S->ny, S->nz};
+    const double h[3] = {S->dx, S->dy, S->dz};
+    int i = (int)floor(p / h[a]);
+    if (d < 0.0 && (double)i * h[a] == p) i -= 1;
+    if (i < 0) i = 0;
+    if (i > n[a] - 1) i = n[a] - 1;
+    return i;
+}
+
+static void trav_setup_leaf(const orc_scene* S, trav64* T)
+{
+    const double h[3] = {S->dx, S->dy, S->dz};
+    float Mf;
+    leaf_of(S, T->v, &T->lev, &Mf);
+    T->M = (double)Mf + S->k_gas;
+    cell_range(S, T->lev, T->v, T->lo, T->hi);
+    double best = INFINITY;
+    int ax = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (T->d[a] == 0.0) continue;
+        double bnd = (T->d[a] > 0.0 ? (double)(T->hi[a] + 1) : (double)T->lo[a]) * h[a];
+        double ta = (bnd - T->p[a]) / T->d[a];
+        if (ta < 0.0) ta = 0.0;
+        if (ta < best) { best = ta; ax = a; }
+    }
+    T->seg = best;
+    T->exit_axis = ax;
+}
+
+static void trav_begin(const orc_scene* S, trav64* T, const double p[3], const double d[3])
+{
+    for (int a = 0; a < 3; ++a) { T->p[a] = p[a]; T->d[a] = d[a]; }
+    for (int a = 0; a < 3; ++a) T->v[a] = locate64(S, T->p[a], T->d[a], a);
+    T->steps = 0;
+    trav_setup_leaf(S, T);
+}
+
+/* Advance p by s < seg inside the current leaf (a tentative collision). */
+static void trav_move_inside(const orc_scene* S, trav64* T, double s)
+{
+    (void)S;
+    for (int a = 0; a < 3; ++a) T->p[a] += s * T->d[a];
+    T->seg -= s;
+    if (T->seg < 0.0) T->seg = 0.0;
+}
+
+/* Voxel holding p, clamped into the current leaf (so k <= M holds). */
+static double trav_k_here(const orc_scene* S, const trav64* T, int vox[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        int i = locate64(S, T->p[a], T->d[a], a);
+        if (i < T->lo[a]) i = T->lo[a];
+        if (i > T->hi[a]) i = T->hi[a];
+        vox[a] = i;
+    }
+    return (double)kvox(S, vox) + S->k_gas;
+}
+
+/* Move to the exit face of the current leaf and enter the next one.
+ * Returns 0 inside, 1 top of atmosphere, 2 ground, 4 step guard. */
+static int trav_next_leaf(const orc_scene* S, trav64* T)
+{
+    const int n[3] = {S->nx, S->ny, S->nz};
+    const double h[3] = {S->dx, S->dy, S->dz};
+    if (++T->steps > S->max_steps) return 4;
+    int ax = T->exit_axis;
+    double s = T->seg;
+    double bnd = (T->d[ax] > 0.0 ? (double)(T->hi[ax] + 1) : (double)T->lo[ax]) * h[ax];
+    for (int a = 0; a < 3; ++a) T->p[a] += s * T->d[a];
+    T->p[ax] = bnd;
+    int nv_ax = T->d[ax] > 0.0 ? T->hi[ax] + 1 : T->lo[ax] - 1;
+    if (ax == 2) {
+        if (nv_ax < 0) { T->p[2] = 0.0; return 2; }
+        if (nv_ax >= n[2]) { T->p[2] = (double)n[2] * h[2]; return 1; }
+    } else {
+        double L = (double)n[ax] * h[ax];
+        if (nv_ax < 0) T->p[ax] = L;
+        else if (nv_ax >= n[ax]) T->p[ax] = 0.0;
+    }
+    for (int a = 0; a < 3; ++a) T->v[a] = locate64(S, T->p[a], T->d[a], a);
+    trav_setup_leaf(S, T);
+    return 0;
+}
+
+/* ===================================================================== */
+/* Phase functions and directions.                                        */
+/* ===================================================================== */
+/* HG phase function normalised to 1 over 4 pi sr. */
+double orc_hg_pdf(double g, double mu)
+{
+    double den = 1.0 + g * g - 2.0 * g * mu;
+    return (1.0 - g * g) / (4.0 * ORC_PI * den * sqrt(den));
+}
+
+/* Inverse-CDF cosine of the HG distribution for xi in (0, 1]. */
+double orc_hg_sample_mu(double g, double xi)
+{
+    if (fabs(g) < 1e-4) return 1.0 - 2.0 * xi;
+    double s = (1.0 - g * g) / (1.0 - g + 2.0 * g * xi);
+    double mu = (1.0 + g * g - s * s) / (2.0 * g);
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    return mu;
+}
+
+/* Orthonormal basis around a unit vector n (Duff et al., "Building an
+ * orthonormal basis, revisited", JCGT 2017). */
+static void onb(const double n[3], double b1[3], double b2[3])
+{
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sign * n[0] * n[0] * a; b1[1] = sign * b; b1[2] = -sign * n[0];
+    b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* Direction making cosine mu with d, azimuth phi in the basis of d. */
+static void rotate_dir(const double d[3], double mu, double phi, double out[3])
+{
+    double b1[3], b2[3];
+    onb(d, b1, b2);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double c = st * cos(phi), s = st * sin(phi);
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = c * b1[a] + s * b2[a] + mu * d[a];
+    double nn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) out[a] = r[a] / nn;
+}
+
+/* Cosine-weighted direction about +z: cos(theta) = sqrt(xi1) > 0. */
+static void cosine_up(double xi1, double xi2, double out[3])
+{
+    double st = sqrt(fmax(0.0, 1.0 - xi1));
+    double phi = 2.0 * ORC_PI * xi2;
+    out[0] = st * cos(phi); out[1] = st * sin(phi); out[2] = sqrt(xi1);
+}
+
+void orc_hg_sample_dirs(double g, const double* d_in, const double* xi, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double mu = orc_hg_sample_mu(g, xi[2 * i]);
+        rotate_dir(d_in + 3 * i, mu, 2.0 * ORC_PI * xi[2 * i + 1], out + 3 * i);
+    }
+}
+
+/* ===================================================================== */
+/* Free flight with null collisions (Sec. 2.3, steps 4a-4g; Eq. 2): the   */
+/* optical depth -ln(u) is spent across leaves of uniform majorant M;     */
+/* at a tentative collision the true extinction k is read and the         */
+/* collision is real with probability k / M, else null and the flight    */
+/* goes on with a fresh optical depth.                                    */
+/* ===================================================================== */
+enum { EV_ESCAPE = 1, EV_GROUND = 2, EV_VOLUME = 3, EV_ABORT = 4 };
+
+typedef struct { int64_t tentative, real, leaves; } orc_counts;
+
+static int free_flight(const orc_scene* S, double p[3], const double d[3], rng_t* r,
+                       double* k_at, orc_counts* C)
+{
+    trav64 T;
+    trav_begin(S, &T, p, d);
+    double tau = -log(rng_u(r));
+    for (;;) {
+        if (T.M > 0.0 && tau < T.M * T.seg) {
+            double s = tau / T.M;
+            trav_move_inside(S, &T, s);
+            int vox[3];
+            double k = trav_k_here(S, &T, vox);
+            if (C) C->tentative++;
+            if (rng_u(r) * T.M <= k) {
+                for (int a = 0; a < 3; ++a) p[a] = T.p[a];
+                *k_at = k;
+                if (C) C->real++;
+                return EV_VOLUME;
+            }
+            tau = -log(rng_u(r));
+        } else {
+            tau -= T.M * T.seg;
+            int st = trav_next_leaf(S, &T);
+            if (C) C->leaves++;
+            if (st == 1) { for (int a = 0; a < 3; ++a) p[a] = T.p[a]; return EV_ESCAPE; }
+            if (st == 2) { for (int a = 0; a < 3; ++a) p[a] = T.p[a]; return EV_GROUND; }
+            if (st == 4) return EV_ABORT;
+        }
+    }
+}
+
+/* Transmissivity from p toward direction s up to the top of atmosphere.
+ * sun_mode 0: ratio tracking, t *= 1 - k/M at each tentative collision,
+ * with Russian roulette below 0.1 (survive with prob t/0.1, t <- 0.1).
+ * sun_mode 1: the 0/1 estimator of Sec. 2.3 (delta tracking). */
+static double transmissivity(const orc_scene* S, const double p[3], const double s[3], rng_t* r, orc_counts* C)
+{
+    trav64 T;
+    trav_begin(S, &T, p, s);
+    double t = 1.0;
+    double tau = -log(rng_u(r));
+    for (;;) {
+        if (T.M > 0.0 && tau < T.M * T.seg) {
+            trav_move_inside(S, &T, tau / T.M);
+            int vox[3];
+            double k = trav_k_here(S, &T, vox);
+            if (C) C->tentative++;
+            if (S->sun_mode == 1) {
+                if (rng_u(r) * T.M <= k) return 0.0;
+            } else {
+                t *= 1.0 - k / T.M;
+                if (t <= 0.0) return 0.0;
+                if (t < 0.1) {
+                    if (rng_u(r) * 0.1 <= t) t = 0.1;
+                    else return 0.0;
+                }
+            }
+            tau = -log(rng_u(r));
+        } else {
+            tau -= T.M * T.seg;
+            int st = trav_next_leaf(S, &T);
+            if (C) C->leaves++;
+            if (st == 1) return t;
+            if (st == 2 || st == 4) return 0.0;
+        }
+    }
+}
+
+double orc_transmissivity(const orc_scene* S, const double p[3], const double s[3], uint64_t seed, uint64_t path)
+{
+    rng_t r;
+    rng_init(&r, seed, path, 0, 1);
+    return transmissivity(S, p, s, &r, NULL);
+}
+
+/* Distance to the first real collision (for the mean-free-path pin). */
+double orc_first_collision_distance(const orc_scene* S, const double p[3], const double d[3], uint64_t seed, uint64_t path)
+{
+    rng_t r;
+    rng_init(&r, seed, path, 0, 0);
+    double q[3] = {p[0], p[1], p[2]};
+    double k;
+    /* unwrap: track the distance travelled along d */
+    trav64 T;
+    trav_begin(S, &T, q, d);
+    double dist = 0.0;
+    double tau = -log(rng_u(&r));
+    for (;;) {
+        if (T.M > 0.0 && tau < T.M * T.seg) {
+            double s = tau / T.M;
+            trav_move_inside(S, &T, s);
+            dist += s;
+            int vox[3];
+            k = trav_k_here(S, &T, vox);
+            if (rng_u(&r) * T.M <= k) return dist;
+            tau = -log(rng_u(&r));
+        } else {
+            tau -= T.M * T.seg;
+            dist += T.seg;
+            int st = trav_next_leaf(S, &T);
+            if (st != 0) return -dist;
+        }
+    }
+}
+
+/* ===================================================================== */
+/* Backward path with local estimates toward the sun (Sec. 4.1).          */
+/* Volume event at x: contribution w * omega(x) * p_HG(d . s) * T_sun(x); */
+/* ground event: w * (rho / pi) * max(s_z, 0) * T_sun(x).  Then w *=      */
+/* omega (or rho), a new direction is sampled (HG about d, or cosine      */
+/* about +z), and Russian roulette applies below w = 0.01.  The path ends */
+/* at the top of atmosphere.  Draw order in stream (event e, 0): the      */
+/* flight's draws, two direction draws, then the roulette draw.  The sun  */
+/* ray of event e uses stream (e, 1).                                     */
+/* ===================================================================== */
+static double omega_at(const orc_scene* S, double k_total)
+{
+    double k = k_total - S->k_gas;          /* cloud + clear */
+    double kc = k - S->k_clear;
+    if (kc < 0.0) kc = 0.0;
+    double kcl = k - kc;                    /* clear part actually present */
+    if (k_total <= 0.0) return 0.0;
+    return (kc * S->ssa_cloud + kcl * S->ssa_clear) / k_total;
+}
+
+static double trace_backward(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
+                             orc_counts* C, int64_t* aborted)
+{
+    double w = 1.0, score = 0.0;
+    const double* s = S->sun;
+    for (uint32_t e = 0;; ++e) {
+        rng_t r;
+        rng_init(&r, seed, path, e, 0);
+        double k;
+        int ev = free_flight(S, p, d, &r, &k, C);
+        if (ev == EV_ESCAPE) break;
+        if (ev == EV_ABORT) { if (aborted) (*aborted)++; break; }
+        int order = (int)e + 1;
+        int score_it = (S->max_order == 0 || order <= S->max_order);
+        rng_t rs;
+        rng_init(&rs, seed, path, e, 1);
+        if (ev == EV_VOLUME) {
+            double om = omega_at(S, k);
+            if (score_it) {
+                double Ts = transmissivity(S, p, s, &rs, C);
+                double mu = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
+                score += w * om * orc_hg_pdf(S->g, mu) * Ts;
+            }
+            w *= om;
+            double mu = orc_hg_sample_mu(S->g, rng_u(&r));
+            double phi = 2.0 * ORC_PI * rng_u(&r);
+            double nd[3];
+            rotate_dir(d, mu, phi, nd);
+            d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+        } else { /* ground */
+            if (score_it) {
+                double Ts = transmissivity(S, p, s, &rs, C);
+                score += w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
+            }
+            w *= S->ground_albedo;
+            double xi1 = rng_u(&r), xi2 = rng_u(&r);
+            cosine_up(xi1, xi2, d);
+        }
+        if (S->max_order > 0 && order >= S->max_order) break;
+        if (w < 0.01) {
+            if (rng_u(&r) * 0.01 <= w) w = 0.01;
+            else break;
+        }
+    }
+    return score;
+}
+
+/* ===================================================================== */
+/* Sensors.                                                               */
+/* ===================================================================== */
+typedef struct {
+    double pos[3], target[3], up[3];
+    double fov_deg;                 /* horizontal field of view */
+    int32_t width, height;
+} orc_camera;
+
+static void cam_basis(const orc_camera* C, double f[3], double rt[3], double u[3])
+{
+    double n;
+    for (int a = 0; a < 3; ++a) f[a] = C->target[a] - C->pos[a];
+    n = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] /= n;
+    rt[0] = f[1] * C->up[2] - f[2] * C->up[1];
+    rt[1] = f[2] * C->up[0] - f[0] * C->up[2];
+    rt[2] = f[0] * C->up[1] - f[1] * C->up[0];
+    n = sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+    for (int a = 0; a < 3; ++a) rt[a] /= n;
+    u[0] = rt[1] * f[2] - rt[2] * f[1];
+    u[1] = rt[2] * f[0] - rt[0] * f[2];
+    u[2] = rt[0] * f[1] - rt[1] * f[0];
+}
+
+/* Wrap x, y into [0, L). */
+static void wrap_xy(const orc_scene* S, double p[3])
+{
+    double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy;
+    p[0] -= floor(p[0] / Lx) * Lx;
+    p[1] -= floor(p[1] / Ly) * Ly;
+    if (p[0] >= Lx) p[0] = 0.0;
+    if (p[1] >= Ly) p[1] = 0.0;
+}
+
+/* One camera path (Sec. 4.1: pinhole camera, direction jittered in the
+ * pixel).  Stream (0, 2) gives the two jitter draws. */
+static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed, uint64_t path,
+                          orc_counts* cnt, int64_t* aborted)
+{
+    uint64_t pix = path / spp;
+    int px = (int)(pix % (uint64_t)C->width), py = (int)(pix / (uint64_t)C->width);
+    rng_t r;
+    rng_init(&r, seed, path, 0, 2);
+    double jx = 1.0 - rng_u(&r), jy = 1.0 - rng_u(&r);
+    double f[3], rt[3], u[3];
+    cam_basis(C, f, rt, u);
+    double tanh_ = tan(0.5 * C->fov_deg * ORC_PI / 180.0);
+    double sx = (2.0 * (px + jx) / C->width - 1.0) * tanh_;
+    double sy = (2.0 * (py + jy) / C->height - 1.0) * tanh_ * (double)C->height / (double)C->width;
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = f[a] + sx * rt[a] + sy * u[a];
+    double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] /= n;
+    double p[3] = {C->pos[0], C->pos[1], C->pos[2]};
+    double Lz = (double)S->nz * S->dz;
+    if (p[2] > Lz) {
+        if (d[2] >= 0.0) return 0.0;
+        double t = (Lz - p[2]) / d[2];
+        for (int a = 0; a < 2; ++a) p[a] += t * d[a];
+        p[2] = Lz;
+    } else if (p[2] < 0.0) {
+        return 0.0;
+    }
+    wrap_xy(S, p);
+    return trace_backward(S, p, d, seed, path, cnt, aborted);
+}
+
+/* One ground-flux path: uniform ground point, cosine-weighted upward
+ * direction (stream (0, 2): four draws); direct part from stream (0, 3).
+ * out[0] = T_dir, out[1] = T_dif = pi / mu0 * sum of local estimates. */
+static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[2],
+                      orc_counts* cnt, int64_t* aborted)
+{
+    rng_t r;
+    rng_init(&r, seed, path, 0, 2);
+    double u0 = rng_u(&r), u1 = rng_u(&r), u2 = rng_u(&r), u3 = rng_u(&r);
+    double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy;
+    double p[3] = {(1.0 - u0) * Lx, (1.0 - u1) * Ly, 0.0};
+    double d[3];
+    cosine_up(u2, u3, d);
+    rng_t rd;
+    rng_init(&rd, seed, path, 0, 3);
+    double q[3] = {p[0], p[1], p[2]};
+    double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
+    double score = trace_backward(S, p, d, seed, path, cnt, aborted);
+    double mu0 = S->sun[2];
+    out[0] = Tdir;
+    out[1] = ORC_PI / mu0 * score;
+}
+
+/* ===================================================================== */
+/* Forward analog flux (Sec. 5.2): photons enter uniformly at the top     */
+/* along -s; weights carry absorption (w *= omega, w *= rho); arrivals    */
+/* at the ground are direct until the photon has been scattered or        */
+/* reflected once.  Used as an independent cross-check of the backward   */
+/* estimator and for the energy balance R + T_abs + A = 1.                */
+/* out per photon: [0] R (escape weight), [1] T_dir arrivals,             */
+/* [2] T_dif arrivals, [3] volume absorption, [4] ground absorption,      */
+/* [5] weight left at cutoff.                                             */
+/* ===================================================================== */
+static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, double out[6], int64_t* aborted)
+{
+    for (int i = 0; i < 6; ++i) out[i] = 0.0;
+    rng_t r0;
+    rng_init(&r0, seed, path, 0, 2);
+    double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy, Lz = (double)S->nz * S->dz;
+    double p[3] = {(1.0 - rng_u(&r0)) * Lx, (1.0 - rng_u(&r0)) * Ly, Lz};
+    double d[3] = {-S->sun[0], -S->sun[1], -S->sun[2]};
+    double w = 1.0;
+    int scattered = 0;
+    for (uint32_t e = 0;; ++e) {
+        rng_t r;
+        rng_init(&r, seed, path, e, 0);
+        double k;
+        int ev = free_flight(S, p, d, &r, &k, NULL);
+        if (ev == EV_ESCAPE) { out[0] += w; return; }
+        if (ev == EV_ABORT) { if (aborted) (*aborted)++; out[5] += w; return; }
+        if (ev == EV_VOLUME) {
+            double om = omega_at(S, k);
+            out[3] += w * (1.0 - om);
+            w *= om;
+            double mu = orc_hg_sample_mu(S->g, rng_u(&r));
+            double phi = 2.0 * ORC_PI * rng_u(&r);
+            double nd[3];
+            rotate_dir(d, mu, phi, nd);
+            d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
+            scattered = 1;
+        } else {
+            if (scattered) out[2] += w; else out[1] += w;
+            out[4] += w * (1.0 - S->ground_albedo);
+            w *= S->ground_albedo;
+            double xi1 = rng_u(&r), xi2 = rng_u(&r);
+            cosine_up(xi1, xi2, d);
+            scattered = 1;
+        }
+        if (w < 1e-6) { out[5] += w; return; }
+    }
+}
+
+/* ===================================================================== */
+/* Parallel drivers (pthreads).  Work is cut into fixed blocks whose       */
+/* partial sums are combined in block order, so results do not depend on  */
+/* the number of threads.                                                 */
+/* ===================================================================== */
+typedef struct {
+    const orc_scene* S;
+    const orc_camera* C;
+    int kind;             /* 0 camera, 1 flux, 2 forward */
+    uint32_t spp;
+    uint64_t seed;
+    uint64_t begin, end;  /* path ids */
+    uint64_t block;       /* paths per block */
+    int64_t nblocks;
+    double* out;          /* per block partial sums (kind-dependent)  */
+    int64_t* aborted;     /* per block */
+    orc_counts* counts;   /* per block */
+    int64_t next;         /* next block (protected by mu) */
+    pthread_mutex_t mu;
+} job_t;
+
+static void run_block(job_t* J, int64_t b)
+{
+    uint64_t p0 = J->begin + (uint64_t)b * J->block;
+    uint64_t p1 = p0 + J->block;
+    if (p1 > J->end) p1 = J->end;
+    int64_t ab = 0;
+    orc_counts cnt = {0, 0, 0};
+    if (J->kind == 0) {
+        /* camera: the block is a set of whole pixels; out is per pixel */
+        for (uint64_t path = p0; path < p1; ++path) {
+            uint64_t pix = path / J->spp;
+            double sc = camera_path(J->S, J->C, J->spp, J->seed, path, &cnt, &ab);
+            J->out[2 * pix + 0] += sc;
+            J->out[2 * pix + 1] += sc * sc;
+        }
+    } else if (J->kind == 1) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (uint64_t path = p0; path < p1; ++path) {
+            double o[2];
+            flux_path(J->S, J->seed, path, o, &cnt, &ab);
+            double tot = o[0] + o[1];
+            acc[0] += o[0]; acc[1] += o[0] * o[0];
+            acc[2] += o[1]; acc[3] += o[1] * o[1];
+            acc[4] += tot;  acc[5] += tot * tot;
+        }
+        for (int i = 0; i < 6; ++i) J->out[6 * b + i] = acc[i];
+    } else {
+        double acc[12];
+        for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+        for (uint64_t path = p0; path < p1; ++path) {
+            double o[6];
+            forward_photon(J->S, J->seed, path, o, &ab);
+            for (int i = 0; i < 6; ++i) { acc[2 * i] += o[i]; acc[2 * i + 1] += o[i] * o[i]; }
+        }
+        for (int i = 0; i < 12; ++i) J->out[12 * b + i] = acc[i];
+    }
+    J->aborted[b] = ab;
+    J->counts[b] = cnt;
+}
+
+static void* worker(void* arg)
+{
+    job_t* J = (job_t*)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t b = J->next++;
+        pthread_mutex_unlock(&J->mu);
+        if (b >= J->nblocks) return NULL;
+        run_block(J, b);
+    }
+}
+
+static void run_job(job_t* J, int nthreads)
+{
+    pthread_mutex_init(&J->mu, NULL);
+    J->next = 0;
+    if (nthreads < 1) nthreads = 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, worker, J);
+    for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+    free(th);
+    pthread_mutex_destroy(&J->mu);
+}
+
+/* Camera: paths [pix_begin*spp, pix_end*spp); sums (2 per pixel of the
+ * whole image, only the range is touched); stats[0] aborted paths,
+ * stats[1..3] tentative collisions, real collisions, leaf steps. */
+int orc_trace_camera(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed,
+                     int64_t pix_begin, int64_t pix_end, double* sums, int nthreads, int64_t* stats)
+{
+    if (spp == 0 || pix_end < pix_begin) return -1;
+    job_t J;
+    memset(&J, 0, sizeof(J));
+    J.S = S; J.C = C; J.kind = 0; J.spp = spp; J.seed = seed;
+    J.begin = (uint64_t)pix_begin * spp; J.end = (uint64_t)pix_end * spp;
+    J.block = spp;                      /* one pixel per block */
+    J.nblocks = pix_end - pix_begin;
+    J.out = sums;
+    J.aborted = (int64_t*)calloc((size_t)(J.nblocks + 1), sizeof(int64_t));
+    J.counts = (orc_counts*)calloc((size_t)(J.nblocks + 1), sizeof(orc_counts));
+    run_job(&J, nthreads);
+    int64_t ab = 0; orc_counts tot = {0, 0, 0};
+    for (int64_t b = 0; b < J.nblocks; ++b) {
+        ab += J.aborted[b];
+        tot.tentative += J.counts[b].tentative; tot.real += J.counts[b].real; tot.leaves += J.counts[b].leaves;
+    }
+    if (stats) { stats[0] = ab; stats[1] = tot.tentative; stats[2] = tot.real; stats[3] = tot.leaves; }
+    free(J.aborted); free(J.counts);
+    return 0;
+}
+
+/* Flux: paths [begin, end); sums[6] = (sum, sum^2) of T_dir, T_dif, T_tot. */
+int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end, double* sums,
+                   int nthreads, int64_t* stats)
+{
+    if (end < begin) return -1;
+    job_t J;
+    memset(&J, 0, sizeof(J));
+    J.S = S; J.kind = 1; J.seed = seed; J.begin = begin; J.end = end;
+    J.block = 1024;
+    J.nblocks = (int64_t)((end - begin + J.block - 1) / J.block);
+    J.out = (double*)calloc((size_t)(6 * J.nblocks + 6), sizeof(double));
+    J.aborted = (int64_t*)calloc((size_t)(J.nblocks + 1), sizeof(int64_t));
+    J.counts = (orc_counts*)calloc((size_t)(J.nblocks + 1), sizeof(orc_counts));
+    run_job(&J, nthreads);
+    for (int i = 0; i < 6; ++i) sums[i] = 0.0;
+    int64_t ab = 0; orc_counts tot = {0, 0, 0};
+    for (int64_t b = 0; b < J.nblocks; ++b) {
+        for (int i = 0; i < 6; ++i) sums[i] += J.out[6 * b + i];
+        ab += J.aborted[b];
+        tot.tentative += J.counts[b].tentative; tot.real += J.counts[b].real; tot.leaves += J.counts[b].leaves;
+    }
+    if (stats) { stats[0] = ab; stats[1] = tot.tentative; stats[2] = tot.real; stats[3] = tot.leaves; }
+    free(J.out); free(J.aborted); free(J.counts);
+    return 0;
+}
+
+/* Forward analog: sums[12] = (sum, sum^2) of R, T_dir, T_dif, A_vol,
+ * A_ground, cutoff weight, per photon. */
+int orc_trace_forward(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end, double* sums,
+                      int nthreads, int64_t* stats)
+{
+    if (end < begin) return -1;
+    job_t J;
+    memset(&J, 0, sizeof(J));
+    J.S = S; J.kind = 2; J.seed = seed; J.begin = begin; J.end = end;
+    J.block = 1024;
+    J.nblocks = (int64_t)((end - begin + J.block - 1) / J.block);
+    J.out = (double*)calloc((size_t)(12 * J.nblocks + 12), sizeof(double));
+    J.aborted = (int64_t*)calloc((size_t)(J.nblocks + 1), sizeof(int64_t));
+    J.counts = (orc_counts*)calloc((size_t)(J.nblocks + 1), sizeof(orc_counts));
+    run_job(&J, nthreads);
+    for (int i = 0; i < 12; ++i) sums[i] = 0.0;
+    int64_t ab = 0;
+    for (int64_t b = 0; b < J.nblocks; ++b) {
+        for (int i = 0; i < 12; ++i) sums[i] += J.out[12 * b + i];
+        ab += J.aborted[b];
+    }
+    if (stats) stats[0] = ab;
+    free(J.out); free(J.aborted); free(J.counts);
+    return 0;
+}
+
+/* Per-photon energy balance check: returns max over photons of
+ * |R + A_vol + A_ground + T_abs_part... - 1|, where the ground arrival
+ * weight splits into absorbed and reflected parts.  Used by the
+ * R + T + A = 1 pin (weights are exact, so the residual is rounding). */
+double orc_forward_balance_residual(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end)
+{
+    double worst = 0.0;
+    for (uint64_t p = begin; p < end; ++p) {
+        double o[6];
+        forward_photon(S, seed, p, o, NULL);
+        double res = fabs(o[0] + o[3] + o[4] + o[5] - 1.0);
+        if (res > worst) worst = res;
+    }
+    return worst;
+}

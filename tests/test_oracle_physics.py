@@ -1,0 +1,241 @@
+"""Oracle pins against what the physics and the mathematics fix.
+
+* Beer's law through homogeneous and layered slabs (Sec. 2.2; Sec. 2.3
+  algorithm, whose expectation Eq. 2 is exp(-tau)).
+* Heterogeneous voxels along fixed rays: exp(-sum k_v l_v) with the lengths
+  from the brute-force face list (ratio and delta tracking unbiased).
+* Majorant invariance (Sec. 2.3-2.4: any valid majorant gives the same
+  expectation): global, pyramid at several tau~, voxel-exact tracking.
+* Black-sky Lambertian ground: radiance rho mu0 / pi with zero variance.
+* Single scattering in a homogeneous slab: closed forms (reflected and
+  transmitted radiance, order-1 tally only).
+* Energy balance of the forward analog estimator, per photon; R + T = 1 for
+  a conservative medium over a black ground, forward vs backward.
+* Reciprocity: backward local-estimate ground flux = forward analog flux.
+* Henyey-Greenstein moments and normalisation; exponential free paths.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenes
+
+
+def _oscene(orc, sp, **kw):
+    args = dict(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear,
+                ssa_clear=sp.ssa_clear, ssa_cloud=sp.ssa_cloud, g=sp.g, ground_albedo=sp.ground_albedo,
+                sun_zenith_deg=sp.sun_zenith_deg, sun_azimuth_deg=sp.sun_azimuth_deg)
+    args.update(kw)
+    return orc.Scene(**args)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_beer_homogeneous_slab(orc, mode):
+    k, H, th = 1.7, 1.6, 40.0
+    sp = scenes.homogeneous(16, 16, 16, 0.1, k, levels=2, sun_zenith_deg=th)
+    sc = _oscene(orc, sp, sun_mode=mode)
+    T, _ = orc.trace_flux(sc, 40000, seed=5)
+    want = math.exp(-k * H / math.cos(math.radians(th)))
+    assert abs(T.mean[0] - want) < 3.0 * T.se[0], (T.mean[0], want, T.se[0])
+
+
+def test_beer_layered_slabs(orc):
+    """Layers whose interfaces fall inside level-1 cells (not multiples of 8)."""
+    nz = 40
+    kz = np.zeros(nz, dtype=np.float32)
+    kz[0:3] = 0.5
+    kz[3:11] = 2.0
+    kz[11:13] = 0.0
+    kz[13:29] = 0.25
+    kz[29:40] = 1.1
+    k = np.broadcast_to(kz[:, None, None], (nz, 16, 16)).astype(np.float32).copy()
+    th = 25.0
+    sp = scenes.SceneSpec("layers", k, 0.05, 0.05, 0.05, 2, 0.0, 1.0, 1.0, 0.85, 0.0, th)
+    for tau, fin in [(1.0, 1), (0.0, 0), (float("inf"), 1)]:
+        sc = _oscene(orc, sp, tau_merge=tau, finest_level=fin)
+        T, _ = orc.trace_flux(sc, 30000, seed=9)
+        tau_v = float(np.sum(kz.astype(np.float64) * 0.05))
+        want = math.exp(-tau_v / math.cos(math.radians(th)))
+        assert abs(T.mean[0] - want) < 3.0 * T.se[0], (tau, T.mean[0], want, T.se[0])
+
+
+def _exact_optical_depth(orc, sp, o, d):
+    """Brute-force optical depth: voxel-level leaves (tau~ = 0, finest 0)."""
+    sc = orc.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, tau_merge=0.0, finest_level=0)
+    cells, tio, st = orc.dda_bruteforce(sc, np.asarray(o, np.float64), np.asarray(d, np.float64))
+    assert st == 1
+    tau = 0.0
+    for (lev, ix, iy, iz), (t0, t1) in zip(cells, tio):
+        if lev == 0:
+            tau += float(sp.k[iz, iy, ix]) * (t1 - t0)
+        else:
+            assert sp.k[iz * 8 ** lev:(iz + 1) * 8 ** lev, iy * 8 ** lev:(iy + 1) * 8 ** lev,
+                         ix * 8 ** lev:(ix + 1) * 8 ** lev].max() == 0.0
+    return tau
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_heterogeneous_ray_transmissivity(orc, mode):
+    sp = scenes.random_voxels(32, 32, 24, 0.1, 4.0, seed=21, levels=2, sparsity=0.6)
+    r = np.random.default_rng(7)
+    for j in range(3):
+        o = np.array([r.uniform(0, 3.2), r.uniform(0, 3.2), r.uniform(0, 1.0)])
+        v = np.array([r.normal(), r.normal(), abs(r.normal()) + 0.3])
+        v /= np.linalg.norm(v)
+        tau = _exact_optical_depth(orc, sp, o, v)
+        sc = orc.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=2, tau_merge=1.0, sun_mode=mode)
+        t = orc.transmissivity_many(sc, o, v, seed=1000 + j, n=100000)
+        want = math.exp(-tau)
+        se = t.std(ddof=1) / math.sqrt(t.size)
+        assert abs(t.mean() - want) < 3.0 * se + 1e-12, (j, t.mean(), want, se, tau)
+
+
+def test_majorant_invariance(orc):
+    """Same flux tallies whatever valid majorant is used."""
+    sp = scenes.blobs_small(0)
+    res = []
+    for tau, fin in [(0.1, 1), (1.0, 1), (10.0, 1), (float("inf"), 1), (0.0, 0)]:
+        sc = _oscene(orc, sp, tau_merge=tau, finest_level=fin)
+        T, _ = orc.trace_flux(sc, 40000, seed=3 + int(min(tau, 100)) + 7 * fin)
+        res.append(T)
+    for i in range(len(res)):
+        for j in range(i + 1, len(res)):
+            for q in range(3):
+                d = abs(res[i].mean[q] - res[j].mean[q])
+                s = math.hypot(res[i].se[q], res[j].se[q])
+                assert d < 4.0 * s, (i, j, q, d, s)
+
+
+def test_black_sky_lambertian_ground(orc):
+    rho, th = 0.3, 35.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, 0.0, levels=1, ground_albedo=rho, sun_zenith_deg=th)
+    sc = _oscene(orc, sp)
+    cam = scenes.nadir_camera(sp, 8, 8)
+    I, _ = orc.trace_camera(sc, orc.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, 8, 8), 64, seed=2)
+    want = rho * math.cos(math.radians(th)) / math.pi
+    assert np.max(np.abs(I.mean - want)) <= 1e-12 * want
+    assert np.max(I.se) <= 1e-12 * want
+
+
+def _hg(g, mu):
+    return (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * mu) ** 1.5)
+
+
+def test_single_scattering_reflected(orc):
+    k, H, g, om, th0 = 2.0, 0.8, 0.7, 0.9, 30.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, k, levels=1, g=g, ssa_cloud=om, ssa_clear=om,
+                            sun_zenith_deg=th0, sun_azimuth_deg=0.0)
+    sc = _oscene(orc, sp, max_order=1)
+    thv = 50.0          # viewing zenith (camera looks down along -d)
+    d = np.array([math.sin(math.radians(thv)), 0.0, -math.cos(math.radians(thv))])
+    pos = np.array([0.8, 0.8, 0.8]) - 20.0 * d
+    cam = orc.Camera(tuple(pos), (0.8, 0.8, 0.8), (0.0, 0.0, 1.0), 1e-3, 1, 1)
+    I, _ = orc.trace_camera(sc, cam, 200000, seed=4)
+    mu0, mu = math.cos(math.radians(th0)), math.cos(math.radians(thv))
+    s = np.array([math.sin(math.radians(th0)), 0.0, mu0])
+    tau = k * H
+    want = om * _hg(g, float(d @ s)) * mu0 / (mu0 + mu) * (1 - math.exp(-tau * (1 / mu0 + 1 / mu)))
+    assert abs(I.mean[0, 0] - want) < 3.0 * I.se[0, 0], (I.mean[0, 0], want, I.se[0, 0])
+
+
+def test_single_scattering_transmitted(orc):
+    """Slab between z = 0.4 and 1.2 km over clear air; camera below looks up."""
+    g, om, th0, kk = 0.6, 1.0, 20.0, 1.5
+    k = np.zeros((12, 16, 16), dtype=np.float32)
+    k[4:12] = kk
+    sp = scenes.SceneSpec("slab", k, 0.1, 0.1, 0.1, 1, 0.0, om, om, g, 0.0, th0)
+    sc = _oscene(orc, sp, max_order=1)
+    thv = 45.0
+    d = np.array([math.sin(math.radians(thv)) * math.cos(0.7), math.sin(math.radians(thv)) * math.sin(0.7),
+                  math.cos(math.radians(thv))])
+    pos = (0.8, 0.8, 0.05)
+    tgt = tuple(np.array(pos) + d)
+    cam = orc.Camera(pos, tgt, (1.0, 0.0, 0.0), 1e-3, 1, 1)
+    I, _ = orc.trace_camera(sc, cam, 200000, seed=6)
+    mu0, mu = math.cos(math.radians(th0)), math.cos(math.radians(thv))
+    s = np.array([math.sin(math.radians(th0)), 0.0, mu0])
+    tau = kk * 0.8
+    want = om * _hg(g, float(d @ s)) * mu0 / (mu0 - mu) * (math.exp(-tau / mu0) - math.exp(-tau / mu))
+    assert abs(I.mean[0, 0] - want) < 3.0 * I.se[0, 0], (I.mean[0, 0], want, I.se[0, 0])
+
+
+def test_forward_energy_balance_per_photon(orc):
+    sp = scenes.blobs_small(0)
+    sc = _oscene(orc, sp)
+    assert orc.forward_balance_residual(sc, seed=1, nphotons=3000) < 1e-12
+
+
+def test_conservative_R_plus_T(orc):
+    """omega = 1, black ground: every photon escapes or reaches the ground
+    once, so R_forward + T_backward = 1."""
+    sp = scenes.blobs_small(0)
+    sc = _oscene(orc, sp, ssa_clear=1.0, ssa_cloud=1.0, ground_albedo=0.0)
+    F, _ = orc.trace_forward(sc, 60000, seed=8)
+    B, _ = orc.trace_flux(sc, 60000, seed=9)
+    R = F.mean[0]
+    assert F.mean[3] == 0.0 and F.mean[4] == pytest.approx(F.mean[1] + F.mean[2])
+    d = abs(R + B.mean[2] - 1.0)
+    s = math.hypot(F.se[0], B.se[2])
+    assert d < 4.0 * s, (R, B.mean[2], s)
+
+
+def test_reciprocity_backward_vs_forward(orc):
+    sp = scenes.blobs_small(0)
+    sc = _oscene(orc, sp)
+    F, _ = orc.trace_forward(sc, 80000, seed=10)
+    B, _ = orc.trace_flux(sc, 80000, seed=11)
+    for qb, qf in [(0, 1), (1, 2)]:
+        d = abs(B.mean[qb] - F.mean[qf])
+        s = math.hypot(B.se[qb], F.se[qf])
+        assert d < 4.0 * s, (qb, B.mean[qb], F.mean[qf], s)
+
+
+@pytest.mark.parametrize("g", [0.0, 0.3, 0.85, -0.5])
+def test_hg_moments_and_normalisation(orc, g):
+    from scipy import integrate
+    r = np.random.default_rng(12)
+    xi = 1.0 - r.uniform(size=200000)           # (0, 1]
+    mu = np.array([orc.hg_sample_mu(g, x) for x in xi])
+    m1, m2 = mu.mean(), (mu * mu).mean()
+    se1 = mu.std() / math.sqrt(mu.size)
+    se2 = (mu * mu).std() / math.sqrt(mu.size)
+    assert abs(m1 - g) < 3 * se1 + 1e-12
+    assert abs(m2 - (1 + 2 * g * g) / 3) < 3 * se2 + 1e-12
+    total, _ = integrate.quad(lambda m: 2 * math.pi * orc.hg_pdf(g, m), -1, 1, epsabs=1e-12, points=[1.0])
+    assert total == pytest.approx(1.0, abs=1e-8)
+    # sampled cosines follow the pdf: compare binned frequencies
+    edges = np.linspace(-1, 1, 41)
+    h, _ = np.histogram(mu, bins=edges)
+    p = np.array([integrate.quad(lambda m: 2 * math.pi * orc.hg_pdf(g, m), a, b)[0]
+                  for a, b in zip(edges[:-1], edges[1:])])
+    e = p * mu.size
+    mask = e > 20
+    chi2 = float(((h[mask] - e[mask]) ** 2 / e[mask]).sum())
+    assert chi2 < 90.0, chi2
+
+
+def test_hg_rotation(orc):
+    r = np.random.default_rng(13)
+    d = r.normal(size=(5000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d[0] = (0, 0, 1)
+    d[1] = (0, 0, -1)
+    xi = 1.0 - r.uniform(size=(5000, 2))
+    out = orc.hg_sample_dirs(0.8, d, xi)
+    assert np.allclose(np.linalg.norm(out, axis=1), 1.0, atol=1e-12)
+    mu = np.array([orc.hg_sample_mu(0.8, x) for x in xi[:, 0]])
+    assert np.allclose((out * d).sum(axis=1), mu, atol=1e-9)
+
+
+def test_free_path_exponential(orc):
+    from scipy import stats
+    k = 3.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, k, levels=2)
+    sc = orc.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=2, tau_merge=1.0)
+    a = 0.3
+    dist = orc.first_collision_distances(sc, (0.33, 0.71, 0.45), (math.cos(a), math.sin(a), 0.0), seed=3, n=20000)
+    assert np.all(dist > 0)
+    se = dist.std() / math.sqrt(dist.size)
+    assert abs(dist.mean() - 1.0 / k) < 3 * se
+    assert stats.kstest(dist, "expon", args=(0, 1.0 / k)).pvalue > 1e-3
