@@ -1,0 +1,271 @@
+/*
+ * mcrt.h -- C ABI of the GB300 null-collision Monte Carlo radiative-transfer
+ * library (sm_103a).
+ *
+ * The library traces many independent photon paths through a voxelised
+ * extinction field above a ground, sampling free paths by null collisions
+ * over a pyramid of max-majorants, and scores radiance or ground-flux tallies
+ * by local estimates toward the sun (Villefranque et al. 2019, "Path-tracing
+ * Monte Carlo library for 3D radiative transfer in highly resolved cloudy
+ * atmospheres"; Sec. 2.3, Eq. 2, Sec. 2.4, Sec. 3.1, Sec. 4.1).
+ *
+ * Conventions shared by every call
+ *  - Units: km for lengths, km^-1 for extinction.  Axes x, y are periodic,
+ *    z runs from the ground (z = 0) to the top of the field (z = nz * dz);
+ *    above it the atmosphere is empty.
+ *  - Arrays are row-major with x fastest: index ((z * ny) + y) * nx + x.
+ *  - Handles are opaque and created/destroyed in pairs.  The library owns
+ *    every device allocation it makes; caller buffers are borrowed for the
+ *    duration of the call only and never freed by the library.
+ *  - Every call returns an mcrt_status (0 = success, < 0 = error).  Nothing
+ *    is thrown across the ABI and no device assert or trap is used; the text
+ *    of the last error of a context is returned by mcrt_last_error().
+ *  - Work is issued on the context's stream in call order.  Calls that
+ *    return data to host memory synchronise that stream before returning.
+ *  - Results depend only on the inputs and the seed, not on launch shape:
+ *    path i draws its random numbers from Philox4x32-10 counters derived
+ *    from (seed, i, event, stream).
+ *  - A NULL handle or pointer where one is required gives MCRT_ERR_ARG.
+ */
+#ifndef MCRT_H
+#define MCRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCRT_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define MCRT_API __attribute__((visibility("default")))
+#else
+#define MCRT_API
+#endif
+
+typedef struct mcrt_ctx mcrt_ctx;
+typedef struct mcrt_scene mcrt_scene;
+typedef struct mcrt_tally mcrt_tally;
+
+typedef enum {
+    MCRT_OK = 0,
+    MCRT_ERR_ARG = -1,        /* invalid argument (message says which)        */
+    MCRT_ERR_OOM = -2,        /* device or host allocation failed             */
+    MCRT_ERR_CUDA = -3,       /* a CUDA runtime call failed                   */
+    MCRT_ERR_TIMEOUT = -4,    /* the trace deadline expired; tallies partial  */
+    MCRT_ERR_CANCELLED = -5,  /* the cancel flag was raised; tallies partial  */
+    MCRT_ERR_STATE = -6,      /* call out of order (e.g. no majorants yet)    */
+    MCRT_ERR_BOUNDS = -7,     /* an output buffer is too small                */
+    MCRT_ERR_UNSUPPORTED = -8 /* valid request this build does not handle     */
+} mcrt_status;
+
+enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };
+enum { MCRT_STORAGE_F32 = 0, MCRT_STORAGE_BF16 = 1 };
+enum { MCRT_SUN_RATIO = 0, MCRT_SUN_DELTA = 1 };
+
+/* Library version and the ABI version it was built with. */
+MCRT_API int mcrt_version(int32_t* abi_version);
+
+/* Text for a status code (static storage, never NULL). */
+MCRT_API const char* mcrt_status_string(int status);
+
+/* --------------------------------------------------------------------- */
+/* Context                                                                */
+/* --------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t borrowed from the caller (it may be a framework's current
+ * stream) or NULL for the legacy default stream; it must outlive the
+ * context.  Errors: MCRT_ERR_ARG (bad device or NULL out), MCRT_ERR_CUDA. */
+MCRT_API int mcrt_create(mcrt_ctx** out, int device, void* cuda_stream);
+
+/* Destroy a context after its scenes and tallies.  Synchronises its stream. */
+MCRT_API int mcrt_destroy(mcrt_ctx* ctx);
+
+/* Last error message of the context ("" if none); valid until the next call
+ * on the context. */
+MCRT_API const char* mcrt_last_error(const mcrt_ctx* ctx);
+
+/* Number of kernels this context has launched so far (all calls). */
+MCRT_API int mcrt_launch_count(const mcrt_ctx* ctx, uint64_t* count);
+
+/* --------------------------------------------------------------------- */
+/* Scene: the extinction field, its majorant pyramid, ground and sun.     */
+/* --------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t nx, ny, nz;        /* voxels per axis, each >= 1                   */
+    float dx, dy, dz;          /* voxel size [km], > 0                          */
+    const float* ext;          /* total extinction k [km^-1], nx*ny*nz values,  */
+                               /* finite and >= 0, x fastest                    */
+    int32_t ext_mem;           /* MCRT_MEM_HOST or MCRT_MEM_DEVICE              */
+    float k_clear;             /* uniform clear-sky part of k [km^-1]           */
+    float ssa_clear;           /* single-scattering albedo of the clear part    */
+    float ssa_cloud;           /* single-scattering albedo of k - k_clear       */
+    float hg_g;                /* Henyey-Greenstein asymmetry, |g| < 1          */
+    int32_t storage;           /* MCRT_STORAGE_F32, or MCRT_STORAGE_BF16:       */
+                               /* voxels rounded to nearest bf16, majorants     */
+                               /* rounded up so they stay bounds               */
+} mcrt_field_desc;
+
+/* Create a scene from a field description.  The field is copied (from host
+ * or device memory) into the library's brick-major layout: 8x8x8 voxel
+ * bricks, 2 KiB each (Sec. 3.1.2: fixed-size blocks of spatially coherent
+ * voxels).  Single-scattering albedo at a voxel is
+ *   omega = ((k - k_clear) * ssa_cloud + k_clear * ssa_clear) / k
+ * (cloud droplets and clear air mixed in proportion to their extinction,
+ * Sec. 4.1 species sampling in expectation).  The ground is black and the
+ * sun at zenith until set.  Errors: MCRT_ERR_ARG, MCRT_ERR_OOM,
+ * MCRT_ERR_CUDA. */
+MCRT_API int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* desc, mcrt_scene** out);
+
+/* Destroy a scene (synchronises the context stream). */
+MCRT_API int mcrt_scene_destroy(mcrt_scene* scene);
+
+/* Build the majorant pyramid: level 0 is the voxel field, a level-L cell
+ * covers 8^L voxels per axis (clipped at the field edges) and holds the
+ * exact max of its children (Sec. 3.1.1: merged voxels keep the max
+ * extinction; Sec. 2.4: the majorant is uniform by parts).  `levels` >= 1
+ * levels are built above the voxels; 0 builds up to the first level with
+ * one cell.  Errors: MCRT_ERR_ARG (levels < 0 or > 8). */
+MCRT_API int mcrt_scene_build_majorants(mcrt_scene* scene, int32_t levels);
+
+/* Number of majorant levels built (0 if none). */
+MCRT_API int mcrt_scene_levels(const mcrt_scene* scene, int32_t* levels);
+
+/* Cells per axis of level `level` (1..levels). */
+MCRT_API int mcrt_scene_majorant_dims(const mcrt_scene* scene, int32_t level, int32_t dims[3]);
+
+/* Copy level `level` of the pyramid (x fastest) into host memory.
+ * `n` must be at least the level's cell count (else MCRT_ERR_BOUNDS);
+ * MCRT_ERR_STATE before mcrt_scene_build_majorants. */
+MCRT_API int mcrt_scene_read_majorants(const mcrt_scene* scene, int32_t level, float* host_out, size_t n);
+
+/* Flat Lambertian ground of albedo in [0, 1] (Sec. 4.1). */
+MCRT_API int mcrt_scene_set_ground_flat(mcrt_scene* scene, float albedo);
+
+/* Collimated sun; zenith in [0, 90) degrees, azimuth measured from +x
+ * toward +y (App. C scene table convention).  Direction toward the sun:
+ * (sin z cos a, sin z sin a, cos z). */
+MCRT_API int mcrt_scene_set_sun(mcrt_scene* scene, float zenith_deg, float azimuth_deg);
+
+/* --------------------------------------------------------------------- */
+/* Tracing                                                                */
+/* --------------------------------------------------------------------- */
+
+/* Pinhole camera (Sec. 4.1, App. C table of camera set-ups): position,
+ * target point, up vector, horizontal field of view and image size.  Pixel
+ * (px, py) spans image-plane coordinates
+ *   sx = (2 (px + jx) / width - 1) tan(fov / 2),
+ *   sy = (2 (py + jy) / height - 1) tan(fov / 2) height / width,
+ * jx, jy uniform jitter; direction = normalise(f + sx r + sy u) with
+ * f = normalise(target - pos), r = normalise(f x up), u = r x f.
+ * Image rows are py, columns px. */
+typedef struct {
+    float pos[3];
+    float target[3];
+    float up[3];
+    float fov_deg;
+    int32_t width, height;
+} mcrt_camera_desc;
+
+typedef struct {
+    float tau_merge;           /* leaf threshold tau~ (Sec. 4.2): a cell of     */
+                               /* level > finest_level is tracked whole when   */
+                               /* its majorant times its height is <= tau~;    */
+                               /* INFINITY = coarsest level.  Default 1.        */
+    int32_t finest_level;      /* finest level tracked: 1 (default), or 0 to    */
+                               /* track voxels where no coarser cell qualifies  */
+    int32_t max_order;         /* 0: all scattering orders; n: score events of  */
+                               /* order <= n and stop after order n             */
+    int32_t sun_mode;          /* MCRT_SUN_RATIO (default) or MCRT_SUN_DELTA    */
+    int32_t chunk;             /* paths a GPU thread claims at once; 0 = auto   */
+    int32_t block_size;        /* threads per block; 0 = auto                   */
+    int32_t grid_size;         /* blocks; 0 = SMs x resident blocks             */
+    int32_t count_events;      /* 1: also count collisions and leaf steps       */
+    double deadline_ms;        /* > 0: stop and report MCRT_ERR_TIMEOUT after   */
+                               /* this much device time                         */
+    const volatile int32_t* cancel_flag; /* NULL, or a flag in host-mapped or   */
+                               /* device memory; non-zero stops the trace with  */
+                               /* MCRT_ERR_CANCELLED                            */
+} mcrt_trace_opts;
+
+/* Fill `opts` with the defaults listed above. */
+MCRT_API int mcrt_trace_opts_default(mcrt_trace_opts* opts);
+
+/* Backward radiance image (Sec. 4.1): for each pixel, `spp` paths start at
+ * the camera; path p of pixel q has global id q * spp + p.  At every volume
+ * collision x the path scores  w * omega(x) * p_HG(d . s) * T_sun(x)  and at
+ * every ground hit  w * (albedo / pi) * max(s_z, 0) * T_sun(x), where w is
+ * the product of albedos met so far, d the path direction and s the sun
+ * direction; T_sun is estimated by ratio (or delta) tracking through the
+ * same majorants (Sec. 2.3).  Directions are resampled from HG or the
+ * cosine law; Russian roulette below w = 0.01.  Radiance is in units of the
+ * solar irradiance per sr.  The tally has width*height cells, 1 quantity.
+ * *tally_inout: NULL to create a new tally, or an existing tally of the same
+ * shape to reuse (its sums are reset).  Requires majorants.  Errors:
+ * MCRT_ERR_ARG, MCRT_ERR_STATE, MCRT_ERR_TIMEOUT, MCRT_ERR_CANCELLED,
+ * MCRT_ERR_CUDA, MCRT_ERR_OOM. */
+MCRT_API int mcrt_trace_camera(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
+                      const mcrt_trace_opts* opts, mcrt_tally** tally_inout);
+
+/* Domain-mean ground transmittance (Sec. 5.1, 5.2): `npaths` paths start at
+ * uniform ground points with cosine-distributed upward directions.  The tally
+ * has 1 cell and 3 quantities: T_dir = sun transmissivity from the ground
+ * point, T_dif = (pi / mu0) * sum of local estimates, T_tot = T_dir + T_dif;
+ * all normalised by mu0 times the solar irradiance. */
+MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, const mcrt_trace_opts* opts,
+                    mcrt_tally** tally_inout);
+
+/* --------------------------------------------------------------------- */
+/* Tallies                                                                */
+/* --------------------------------------------------------------------- */
+
+/* Cells and quantities of a tally. */
+MCRT_API int mcrt_tally_shape(const mcrt_tally* tally, int32_t* ncells, int32_t* nquant);
+
+/* Mean, standard error of the mean and path count per (cell, quantity), cell
+ * major; computed on the device from FP64 sums s1 = sum x, s2 = sum x^2:
+ * mean = s1 / N, se = sqrt((s2 / N - mean^2) / (N - 1)).  Any output may be
+ * NULL.  `count` must be >= ncells * nquant (else MCRT_ERR_BOUNDS). */
+MCRT_API int mcrt_tally_read(const mcrt_tally* tally, double* mean, double* stderr_out, uint64_t* n, size_t count);
+
+/* Raw FP64 sums (s1, s2) per (cell, quantity). */
+MCRT_API int mcrt_tally_read_sums(const mcrt_tally* tally, double* s1, double* s2, size_t count);
+
+/* Event counters of the trace that filled the tally (zeros unless
+ * count_events was set): [0] paths, [1] tentative collisions on paths,
+ * [2] real collisions, [3] ground hits, [4] leaf steps on paths,
+ * [5] tentative collisions on sun rays, [6] leaf steps on sun rays,
+ * [7] sun rays, [8] aborted paths (step guard), [9] free flights started.
+ * n >= 10. */
+MCRT_API int mcrt_tally_counters(const mcrt_tally* tally, uint64_t* counters, size_t n);
+
+/* Device time of the trace kernel that filled the tally, in ms. */
+MCRT_API int mcrt_tally_kernel_ms(const mcrt_tally* tally, float* ms);
+
+MCRT_API int mcrt_tally_destroy(mcrt_tally* tally);
+
+/* --------------------------------------------------------------------- */
+/* Checks (used by the tests; not on the hot path)                        */
+/* --------------------------------------------------------------------- */
+
+/* Leaves crossed by one ray, computed on the device with the tracer's own
+ * traversal code: for each leaf (level, ix, iy, iz) in `cells` (4 int32 each)
+ * and (t_in, t_out) in `t_in_out` (2 floats each, distances from o).
+ * *status: 1 top reached, 2 ground reached, 3 capacity reached, 4 step
+ * guard.  Host buffers.  Requires majorants. */
+MCRT_API int mcrt_debug_dda(const mcrt_scene* scene, const float o[3], const float d[3], float tau_merge,
+                   int32_t finest_level, int32_t* cells, float* t_in_out, int32_t cap, int32_t* count,
+                   int32_t* status);
+
+/* Philox4x32-10 evaluated on the device for n (counter[4], key[2]) pairs
+ * (host arrays); out receives 4 words per pair. */
+MCRT_API int mcrt_debug_philox(mcrt_ctx* ctx, const uint32_t* counters, const uint32_t* keys, uint32_t* out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCRT_H */

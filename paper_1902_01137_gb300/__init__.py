@@ -1,0 +1,423 @@
+"""Python binding of the GB300 null-collision radiative-transfer library.
+
+Thin ctypes marshalling around ``libmcrt.so`` (the C ABI of
+``include/mcrt.h``): every step of the method runs in the library's CUDA
+kernels.  PyTorch is used only for device memory and streams (a CUDA tensor
+can be passed as the extinction field; the context can run on torch's current
+stream).  Importing this package fails loudly when the library has not been
+built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+MCRT_OK = 0
+MCRT_ERR_ARG = -1
+MCRT_ERR_OOM = -2
+MCRT_ERR_CUDA = -3
+MCRT_ERR_TIMEOUT = -4
+MCRT_ERR_CANCELLED = -5
+MCRT_ERR_STATE = -6
+MCRT_ERR_BOUNDS = -7
+MCRT_ERR_UNSUPPORTED = -8
+MCRT_MEM_HOST = 0
+MCRT_MEM_DEVICE = 1
+MCRT_STORAGE_F32 = 0
+MCRT_STORAGE_BF16 = 1
+MCRT_SUN_RATIO = 0
+MCRT_SUN_DELTA = 1
+
+COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
+                 "sun_rays", "aborted", "flights")
+
+
+class McrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (_status_name(status), status, msg))
+        self.status = status
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_float), ("dy", C.c_float), ("dz", C.c_float),
+                ("ext", C.c_void_p), ("ext_mem", C.c_int32),
+                ("k_clear", C.c_float), ("ssa_clear", C.c_float), ("ssa_cloud", C.c_float),
+                ("hg_g", C.c_float), ("storage", C.c_int32)]
+
+
+class CameraDesc(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("fov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class TraceOpts(C.Structure):
+    _fields_ = [("tau_merge", C.c_float), ("finest_level", C.c_int32), ("max_order", C.c_int32),
+                ("sun_mode", C.c_int32), ("chunk", C.c_int32), ("block_size", C.c_int32),
+                ("grid_size", C.c_int32), ("count_events", C.c_int32), ("deadline_ms", C.c_double),
+                ("cancel_flag", C.c_void_p)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmcrt.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_1902_01137_gb300.build" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, i32, u32, u64, f32, f64 = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_float, C.c_double
+    P = C.POINTER
+    sig = {
+        "mcrt_version": [P(i32)],
+        "mcrt_status_string": [C.c_int],
+        "mcrt_create": [P(vp), C.c_int, vp],
+        "mcrt_destroy": [vp],
+        "mcrt_last_error": [vp],
+        "mcrt_launch_count": [vp, P(u64)],
+        "mcrt_scene_create": [vp, P(FieldDesc), P(vp)],
+        "mcrt_scene_destroy": [vp],
+        "mcrt_scene_build_majorants": [vp, i32],
+        "mcrt_scene_levels": [vp, P(i32)],
+        "mcrt_scene_majorant_dims": [vp, i32, P(i32)],
+        "mcrt_scene_read_majorants": [vp, i32, P(f32), C.c_size_t],
+        "mcrt_scene_set_ground_flat": [vp, f32],
+        "mcrt_scene_set_sun": [vp, f32, f32],
+        "mcrt_trace_opts_default": [P(TraceOpts)],
+        "mcrt_trace_camera": [vp, P(CameraDesc), u32, u64, P(TraceOpts), P(vp)],
+        "mcrt_trace_flux": [vp, u64, u64, P(TraceOpts), P(vp)],
+        "mcrt_tally_shape": [vp, P(i32), P(i32)],
+        "mcrt_tally_read": [vp, P(f64), P(f64), P(u64), C.c_size_t],
+        "mcrt_tally_read_sums": [vp, P(f64), P(f64), C.c_size_t],
+        "mcrt_tally_counters": [vp, P(u64), C.c_size_t],
+        "mcrt_tally_kernel_ms": [vp, P(f32)],
+        "mcrt_tally_destroy": [vp],
+        "mcrt_debug_dda": [vp, P(f32), P(f32), f32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
+        "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.mcrt_status_string.restype = C.c_char_p
+    L.mcrt_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def exported_names():
+    """Names of the C entry points the binding uses."""
+    _load()
+    return sorted(n for n in dir(_lib) if n.startswith("mcrt_"))
+
+
+def _status_name(s):
+    try:
+        return _load().mcrt_status_string(int(s)).decode()
+    except Exception:  # pragma: no cover
+        return "status"
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C entry points (argument marshalling only)
+# ---------------------------------------------------------------------------
+def _check(rc, ctx=None):
+    if rc != MCRT_OK:
+        msg = _load().mcrt_last_error(ctx).decode() if ctx is not None else _load().mcrt_last_error(None).decode()
+        raise McrtError(rc, msg)
+
+
+def mcrt_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        except Exception:
+            stream = 0
+    _check(_load().mcrt_create(C.byref(h), device, C.c_void_p(int(stream) if stream else None)))
+    return h
+
+
+def mcrt_destroy(ctx):
+    _check(_load().mcrt_destroy(ctx))
+
+
+def mcrt_launch_count(ctx) -> int:
+    v = C.c_uint64()
+    _check(_load().mcrt_launch_count(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def mcrt_scene_create(ctx, desc: FieldDesc):
+    h = C.c_void_p()
+    _check(_load().mcrt_scene_create(ctx, C.byref(desc), C.byref(h)), ctx)
+    return h
+
+
+def mcrt_scene_destroy(scene):
+    _check(_load().mcrt_scene_destroy(scene))
+
+
+def mcrt_scene_build_majorants(ctx, scene, levels: int):
+    _check(_load().mcrt_scene_build_majorants(scene, levels), ctx)
+
+
+def mcrt_scene_levels(scene) -> int:
+    v = C.c_int32()
+    _check(_load().mcrt_scene_levels(scene, C.byref(v)))
+    return v.value
+
+
+def mcrt_scene_majorant_dims(ctx, scene, level: int):
+    d = (C.c_int32 * 3)()
+    _check(_load().mcrt_scene_majorant_dims(scene, level, d), ctx)
+    return (d[0], d[1], d[2])
+
+
+def mcrt_scene_read_majorants(ctx, scene, level: int) -> np.ndarray:
+    dx, dy, dz = mcrt_scene_majorant_dims(ctx, scene, level)
+    out = np.zeros(dx * dy * dz, dtype=np.float32)
+    _check(_load().mcrt_scene_read_majorants(scene, level, _ptr(out, C.c_float), out.size), ctx)
+    return out.reshape(dz, dy, dx)
+
+
+def mcrt_scene_set_ground_flat(ctx, scene, albedo: float):
+    _check(_load().mcrt_scene_set_ground_flat(scene, albedo), ctx)
+
+
+def mcrt_scene_set_sun(ctx, scene, zenith_deg: float, azimuth_deg: float):
+    _check(_load().mcrt_scene_set_sun(scene, zenith_deg, azimuth_deg), ctx)
+
+
+def mcrt_trace_opts_default() -> TraceOpts:
+    o = TraceOpts()
+    _check(_load().mcrt_trace_opts_default(C.byref(o)))
+    return o
+
+
+def mcrt_trace_camera(ctx, scene, cam: CameraDesc, spp: int, seed: int, opts: TraceOpts, tally=None):
+    h = tally if tally is not None else C.c_void_p()
+    _check(_load().mcrt_trace_camera(scene, C.byref(cam), spp, seed, C.byref(opts), C.byref(h)), ctx)
+    return h
+
+
+def mcrt_trace_flux(ctx, scene, npaths: int, seed: int, opts: TraceOpts, tally=None):
+    h = tally if tally is not None else C.c_void_p()
+    _check(_load().mcrt_trace_flux(scene, npaths, seed, C.byref(opts), C.byref(h)), ctx)
+    return h
+
+
+def mcrt_tally_shape(ctx, tally):
+    a, b = C.c_int32(), C.c_int32()
+    _check(_load().mcrt_tally_shape(tally, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def mcrt_tally_read(ctx, tally):
+    nc, nq = mcrt_tally_shape(ctx, tally)
+    m = nc * nq
+    mean = np.zeros(m)
+    se = np.zeros(m)
+    n = np.zeros(m, dtype=np.uint64)
+    _check(_load().mcrt_tally_read(tally, _ptr(mean, C.c_double), _ptr(se, C.c_double), _ptr(n, C.c_uint64), m), ctx)
+    return mean.reshape(nc, nq), se.reshape(nc, nq), n.reshape(nc, nq)
+
+
+def mcrt_tally_read_sums(ctx, tally):
+    nc, nq = mcrt_tally_shape(ctx, tally)
+    m = nc * nq
+    s1 = np.zeros(m)
+    s2 = np.zeros(m)
+    _check(_load().mcrt_tally_read_sums(tally, _ptr(s1, C.c_double), _ptr(s2, C.c_double), m), ctx)
+    return s1.reshape(nc, nq), s2.reshape(nc, nq)
+
+
+def mcrt_tally_counters(ctx, tally) -> dict:
+    c = np.zeros(len(COUNTER_NAMES), dtype=np.uint64)
+    _check(_load().mcrt_tally_counters(tally, _ptr(c, C.c_uint64), c.size), ctx)
+    return {k: int(v) for k, v in zip(COUNTER_NAMES, c)}
+
+
+def mcrt_tally_kernel_ms(ctx, tally) -> float:
+    v = C.c_float()
+    _check(_load().mcrt_tally_kernel_ms(tally, C.byref(v)), ctx)
+    return v.value
+
+
+def mcrt_tally_destroy(tally):
+    _check(_load().mcrt_tally_destroy(tally))
+
+
+def mcrt_debug_dda(ctx, scene, o, d, tau_merge=1.0, finest_level=1, cap=4096):
+    o32 = np.ascontiguousarray(o, dtype=np.float32)
+    d32 = np.ascontiguousarray(d, dtype=np.float32)
+    cells = np.zeros((cap, 4), dtype=np.int32)
+    tio = np.zeros((cap, 2), dtype=np.float32)
+    n, st = C.c_int32(), C.c_int32()
+    _check(_load().mcrt_debug_dda(scene, _ptr(o32, C.c_float), _ptr(d32, C.c_float), tau_merge, finest_level,
+                                  _ptr(cells, C.c_int32), _ptr(tio, C.c_float), cap, C.byref(n), C.byref(st)), ctx)
+    return cells[:n.value].copy(), tio[:n.value].copy(), st.value
+
+
+def mcrt_debug_philox(ctx, ctr, key) -> np.ndarray:
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    out = np.zeros_like(ctr)
+    _check(_load().mcrt_debug_philox(ctx, _ptr(ctr, C.c_uint32), _ptr(key, C.c_uint32), _ptr(out, C.c_uint32),
+                                     ctr.shape[0]), ctx)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Convenience objects
+# ---------------------------------------------------------------------------
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        self.h = mcrt_create(device, stream)
+
+    def close(self):
+        if self.h:
+            mcrt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def launches(self) -> int:
+        return mcrt_launch_count(self.h)
+
+
+@dataclass
+class Result:
+    mean: np.ndarray
+    se: np.ndarray
+    n: np.ndarray
+    kernel_ms: float
+    counters: dict
+
+
+class Scene:
+    """A field on the device with its majorant pyramid."""
+
+    def __init__(self, ctx: Context, k, dx, dy, dz, k_clear=0.0, ssa_clear=1.0, ssa_cloud=1.0, g=0.85,
+                 storage=MCRT_STORAGE_F32, levels=0, albedo=0.0, sun_zenith_deg=0.0, sun_azimuth_deg=0.0):
+        self.ctx = ctx
+        desc = FieldDesc()
+        if hasattr(k, "is_cuda") and k.is_cuda:
+            import torch
+            kk = k.contiguous().to(torch.float32)
+            nz, ny, nx = kk.shape
+            desc.ext = C.c_void_p(kk.data_ptr())
+            desc.ext_mem = MCRT_MEM_DEVICE
+            self._keep = kk
+        else:
+            if hasattr(k, "numpy"):
+                k = k.numpy()
+            kk = np.ascontiguousarray(k, dtype=np.float32)
+            nz, ny, nx = kk.shape
+            desc.ext = C.c_void_p(kk.ctypes.data)
+            desc.ext_mem = MCRT_MEM_HOST
+            self._keep = kk
+        desc.nx, desc.ny, desc.nz = nx, ny, nz
+        desc.dx, desc.dy, desc.dz = dx, dy, dz
+        desc.k_clear, desc.ssa_clear, desc.ssa_cloud, desc.hg_g = k_clear, ssa_clear, ssa_cloud, g
+        desc.storage = storage
+        self.shape_xyz = (nx, ny, nz)
+        self.h = mcrt_scene_create(ctx.h, desc)
+        self._keep = None
+        mcrt_scene_build_majorants(ctx.h, self.h, levels)
+        mcrt_scene_set_ground_flat(ctx.h, self.h, albedo)
+        mcrt_scene_set_sun(ctx.h, self.h, sun_zenith_deg, sun_azimuth_deg)
+
+    @classmethod
+    def from_spec(cls, ctx: Context, spec, storage=MCRT_STORAGE_F32, k=None):
+        return cls(ctx, spec.k if k is None else k, spec.dx, spec.dy, spec.dz, k_clear=spec.k_clear,
+                   ssa_clear=spec.ssa_clear, ssa_cloud=spec.ssa_cloud, g=spec.g, storage=storage,
+                   levels=spec.levels, albedo=spec.ground_albedo, sun_zenith_deg=spec.sun_zenith_deg,
+                   sun_azimuth_deg=spec.sun_azimuth_deg)
+
+    def close(self):
+        if self.h:
+            mcrt_scene_destroy(self.h)
+            self.h = None
+
+    @property
+    def levels(self):
+        return mcrt_scene_levels(self.h)
+
+    def majorants(self, level):
+        return mcrt_scene_read_majorants(self.ctx.h, self.h, level)
+
+    def dda(self, o, d, tau_merge=1.0, finest_level=1, cap=4096):
+        return mcrt_debug_dda(self.ctx.h, self.h, o, d, tau_merge, finest_level, cap)
+
+    @staticmethod
+    def _opts(**kw):
+        o = mcrt_trace_opts_default()
+        for k, v in kw.items():
+            if k == "cancel_flag":
+                o.cancel_flag = C.c_void_p(v)
+            else:
+                setattr(o, k, v)
+        return o
+
+    def _result(self, t, read_counters):
+        mean, se, n = mcrt_tally_read(self.ctx.h, t)
+        ms = mcrt_tally_kernel_ms(self.ctx.h, t)
+        cnt = mcrt_tally_counters(self.ctx.h, t) if read_counters else {}
+        return Result(mean, se, n, ms, cnt)
+
+    def trace_camera(self, cam, spp, seed, tally=None, **opts):
+        cd = CameraDesc()
+        for i in range(3):
+            cd.pos[i], cd.target[i], cd.up[i] = cam.pos[i], cam.target[i], cam.up[i]
+        cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
+        o = self._opts(**opts)
+        t = mcrt_trace_camera(self.ctx.h, self.h, cd, spp, seed, o, tally)
+        try:
+            r = self._result(t, o.count_events)
+        finally:
+            if tally is None:
+                mcrt_tally_destroy(t)
+        r.mean = r.mean.reshape(cam.height, cam.width)
+        r.se = r.se.reshape(cam.height, cam.width)
+        r.n = r.n.reshape(cam.height, cam.width)
+        return r
+
+    def trace_flux(self, npaths, seed, tally=None, **opts):
+        o = self._opts(**opts)
+        t = mcrt_trace_flux(self.ctx.h, self.h, npaths, seed, o, tally)
+        try:
+            r = self._result(t, o.count_events)
+        finally:
+            if tally is None:
+                mcrt_tally_destroy(t)
+        r.mean = r.mean.reshape(3)
+        r.se = r.se.reshape(3)
+        r.n = r.n.reshape(3)
+        return r

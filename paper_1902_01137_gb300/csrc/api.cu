@@ -1,0 +1,697 @@
+// api.cu -- the C ABI declared in include/mcrt.h: argument checks, device
+// memory ownership, launch configuration and status reporting.  Every device
+// step of the method runs in the kernels of majorant.cu and trace.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mcrt_internal.h"
+
+using namespace mcrt;
+
+namespace {
+
+thread_local std::string g_err;   // errors of calls without a context
+
+int fail(mcrt_ctx* ctx, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(mcrt_ctx* ctx, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_err = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define LAUNCH(ctx, call)      \
+    do {                       \
+        (ctx)->launches++;     \
+        CK((ctx), (call));     \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(mcrt_ctx* ctx, T** p, size_t bytes)
+{
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes == 0 ? 16 : bytes, ctx->stream);
+}
+
+void dfree(mcrt_ctx* ctx, void* p)
+{
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+}  // namespace
+
+namespace mcrt {
+
+DevScene make_dev_scene(const mcrt_scene* sc, float k_gas)
+{
+    DevScene S{};
+    for (int a = 0; a < 3; ++a) {
+        S.n[a] = sc->n[a];
+        S.h[a] = sc->h[a];
+        S.inv_h[a] = 1.0f / sc->h[a];
+        S.nb[a] = sc->nb[a];
+    }
+    S.Lper[0] = (float)sc->n[0] * sc->h[0];
+    S.Lper[1] = (float)sc->n[1] * sc->h[1];
+    if (sc->storage == MCRT_STORAGE_BF16) S.vox16 = static_cast<const uint16_t*>(sc->d_vox);
+    else S.vox = static_cast<const float*>(sc->d_vox);
+    S.leaf = sc->d_leaf;
+    S.k_clear = sc->k_clear;
+    S.ssa_clear = sc->ssa_clear;
+    S.ssa_cloud = sc->ssa_cloud;
+    S.g = sc->g;
+    S.k_gas = k_gas;
+    S.albedo = sc->albedo;
+    for (int a = 0; a < 3; ++a) S.sun[a] = sc->sun[a];
+    return S;
+}
+
+}  // namespace mcrt
+
+extern "C" {
+
+int mcrt_version(int32_t* abi_version)
+{
+    if (abi_version) *abi_version = MCRT_ABI_VERSION;
+    return MCRT_OK;
+}
+
+const char* mcrt_status_string(int s)
+{
+    switch (s) {
+    case MCRT_OK: return "ok";
+    case MCRT_ERR_ARG: return "invalid argument";
+    case MCRT_ERR_OOM: return "out of memory";
+    case MCRT_ERR_CUDA: return "CUDA error";
+    case MCRT_ERR_TIMEOUT: return "deadline expired";
+    case MCRT_ERR_CANCELLED: return "cancelled";
+    case MCRT_ERR_STATE: return "call out of order";
+    case MCRT_ERR_BOUNDS: return "buffer too small";
+    case MCRT_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+int mcrt_create(mcrt_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(nullptr, MCRT_ERR_ARG, "mcrt_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, MCRT_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev)
+        return fail(nullptr, MCRT_ERR_ARG, "mcrt_create: device %d out of range [0, %d)", device, ndev);
+    mcrt_ctx* c = new (std::nothrow) mcrt_ctx();
+    if (!c) return fail(nullptr, MCRT_ERR_OOM, "mcrt_create: host allocation failed");
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    int l2 = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, MCRT_ERR_CUDA, "mcrt_create: %s", cudaGetErrorString(e));
+    }
+    c->l2_bytes = (size_t)l2;
+    *out = c;
+    return MCRT_OK;
+}
+
+int mcrt_destroy(mcrt_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, MCRT_ERR_ARG, "mcrt_destroy: NULL context");
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return MCRT_OK;
+}
+
+const char* mcrt_last_error(const mcrt_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+int mcrt_launch_count(const mcrt_ctx* ctx, uint64_t* count)
+{
+    if (!ctx || !count) return fail(nullptr, MCRT_ERR_ARG, "mcrt_launch_count: NULL argument");
+    *count = ctx->launches;
+    return MCRT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Scene
+// ---------------------------------------------------------------------------
+int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* d, mcrt_scene** out)
+{
+    if (!ctx || !d || !out) return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: NULL argument");
+    *out = nullptr;
+    ctx->err.clear();
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx > (1 << 20) || d->ny > (1 << 20) || d->nz > (1 << 20))
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: bad size %d x %d x %d", d->nx, d->ny, d->nz);
+    if (!finite_pos(d->dx) || !finite_pos(d->dy) || !finite_pos(d->dz))
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: voxel size must be finite and > 0");
+    if (!d->ext) return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: ext is NULL");
+    if (d->ext_mem != MCRT_MEM_HOST && d->ext_mem != MCRT_MEM_DEVICE)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: ext_mem must be MCRT_MEM_HOST or MCRT_MEM_DEVICE");
+    if (d->storage != MCRT_STORAGE_F32 && d->storage != MCRT_STORAGE_BF16)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: bad storage %d", d->storage);
+    if (!(std::isfinite(d->k_clear) && d->k_clear >= 0.0f))
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: k_clear must be finite and >= 0");
+    if (!(d->ssa_clear >= 0.0f && d->ssa_clear <= 1.0f && d->ssa_cloud >= 0.0f && d->ssa_cloud <= 1.0f))
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: albedos must be in [0, 1]");
+    if (!(std::fabs(d->hg_g) < 1.0f)) return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: |g| must be < 1");
+    CK(ctx, cudaSetDevice(ctx->device));
+    mcrt_scene* sc = new (std::nothrow) mcrt_scene();
+    if (!sc) return fail(ctx, MCRT_ERR_OOM, "mcrt_scene_create: host allocation failed");
+    sc->ctx = ctx;
+    sc->n[0] = d->nx; sc->n[1] = d->ny; sc->n[2] = d->nz;
+    sc->h[0] = d->dx; sc->h[1] = d->dy; sc->h[2] = d->dz;
+    for (int a = 0; a < 3; ++a) sc->nb[a] = ceil_div(sc->n[a], 8);
+    sc->k_clear = d->k_clear; sc->ssa_clear = d->ssa_clear; sc->ssa_cloud = d->ssa_cloud; sc->g = d->hg_g;
+    sc->storage = d->storage;
+    const size_t nbricks = (size_t)sc->nb[0] * sc->nb[1] * sc->nb[2];
+    sc->vox_bytes = nbricks * 512 * (sc->storage == MCRT_STORAGE_BF16 ? 2 : 4);
+    // pyramid capacity: up to 8 levels; level dims filled now
+    sc->lev_off.assign(10, 0);
+    sc->lev_dims.assign(30, 0);
+    size_t tot = 0;
+    for (int L = 1; L <= 8; ++L) {
+        int f = 1 << (3 * L);
+        int dd[3] = {ceil_div(sc->n[0], f), ceil_div(sc->n[1], f), ceil_div(sc->n[2], f)};
+        for (int a = 0; a < 3; ++a) sc->lev_dims[3 * L + a] = dd[a];
+        sc->lev_off[L] = tot;
+        tot += (size_t)dd[0] * dd[1] * dd[2];
+    }
+    sc->pyr_capacity = tot;
+    cudaError_t e = dalloc(ctx, &sc->d_vox, sc->vox_bytes);
+    if (e == cudaSuccess) e = dalloc(ctx, &sc->d_pyr, tot * sizeof(float));
+    if (e == cudaSuccess) e = dalloc(ctx, &sc->d_leaf, nbricks * sizeof(uint2));
+    const float* src = d->ext;
+    float* staging = nullptr;
+    const size_t nvox = (size_t)d->nx * d->ny * d->nz;
+    if (e == cudaSuccess && d->ext_mem == MCRT_MEM_HOST) {
+        e = dalloc(ctx, &staging, nvox * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(staging, d->ext, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        src = staging;
+    }
+    if (e == cudaSuccess) {
+        ctx->launches++;
+        e = launch_relayout(src, sc, ctx->stream);
+    }
+    if (staging) dfree(ctx, staging);
+    if (e != cudaSuccess) {
+        dfree(ctx, sc->d_vox); dfree(ctx, sc->d_pyr); dfree(ctx, sc->d_leaf);
+        delete sc;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, "mcrt_scene_create: %s",
+                    cudaGetErrorString(e));
+    }
+    if (d->ext_mem == MCRT_MEM_HOST) {
+        // the caller's host buffer is only borrowed for this call
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    *out = sc;
+    return MCRT_OK;
+}
+
+int mcrt_scene_destroy(mcrt_scene* sc)
+{
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_destroy: NULL scene");
+    mcrt_ctx* ctx = sc->ctx;
+    dfree(ctx, sc->d_vox);
+    dfree(ctx, sc->d_pyr);
+    dfree(ctx, sc->d_leaf);
+    cudaStreamSynchronize(ctx->stream);
+    delete sc;
+    return MCRT_OK;
+}
+
+int mcrt_scene_build_majorants(mcrt_scene* sc, int32_t levels)
+{
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_build_majorants: NULL scene");
+    mcrt_ctx* ctx = sc->ctx;
+    if (levels < 0 || levels > 8)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_build_majorants: levels %d not in [0, 8]", levels);
+    if (levels == 0) {
+        levels = 1;
+        while (levels < 8 && !(sc->lev_dims[3 * levels] == 1 && sc->lev_dims[3 * levels + 1] == 1 &&
+                               sc->lev_dims[3 * levels + 2] == 1))
+            ++levels;
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    for (int L = 2; L <= levels; ++L) {
+        LAUNCH(ctx, launch_reduce_level(sc->d_pyr + sc->lev_off[L - 1], &sc->lev_dims[3 * (L - 1)],
+                                        sc->d_pyr + sc->lev_off[L], &sc->lev_dims[3 * L], ctx->stream));
+    }
+    sc->levels = levels;
+    sc->leaf_valid = false;
+    return MCRT_OK;
+}
+
+int mcrt_scene_levels(const mcrt_scene* sc, int32_t* levels)
+{
+    if (!sc || !levels) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_levels: NULL argument");
+    *levels = sc->levels;
+    return MCRT_OK;
+}
+
+int mcrt_scene_majorant_dims(const mcrt_scene* sc, int32_t level, int32_t dims[3])
+{
+    if (!sc || !dims) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_majorant_dims: NULL argument");
+    if (level < 1 || level > 8) return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_majorant_dims: bad level %d", level);
+    for (int a = 0; a < 3; ++a) dims[a] = sc->lev_dims[3 * level + a];
+    return MCRT_OK;
+}
+
+int mcrt_scene_read_majorants(const mcrt_scene* sc, int32_t level, float* host_out, size_t n)
+{
+    if (!sc || !host_out) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_read_majorants: NULL argument");
+    mcrt_ctx* ctx = sc->ctx;
+    if (sc->levels == 0) return fail(ctx, MCRT_ERR_STATE, "mcrt_scene_read_majorants: majorants not built");
+    if (level < 1 || level > sc->levels)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_read_majorants: level %d not in [1, %d]", level, sc->levels);
+    const size_t cells = (size_t)sc->lev_dims[3 * level] * sc->lev_dims[3 * level + 1] * sc->lev_dims[3 * level + 2];
+    if (n < cells) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_scene_read_majorants: need %zu values", cells);
+    CK(ctx, cudaMemcpyAsync(host_out, sc->d_pyr + sc->lev_off[level], cells * sizeof(float), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MCRT_OK;
+}
+
+int mcrt_scene_set_ground_flat(mcrt_scene* sc, float albedo)
+{
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_set_ground_flat: NULL scene");
+    if (!(albedo >= 0.0f && albedo <= 1.0f))
+        return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_set_ground_flat: albedo must be in [0, 1]");
+    sc->albedo = albedo;
+    return MCRT_OK;
+}
+
+int mcrt_scene_set_sun(mcrt_scene* sc, float zenith_deg, float azimuth_deg)
+{
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_set_sun: NULL scene");
+    if (!(zenith_deg >= 0.0f && zenith_deg < 90.0f) || !std::isfinite(azimuth_deg))
+        return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_set_sun: zenith must be in [0, 90) degrees");
+    const double z = zenith_deg * M_PI / 180.0, a = azimuth_deg * M_PI / 180.0;
+    sc->sun_zenith = zenith_deg;
+    sc->sun_azimuth = azimuth_deg;
+    sc->sun[0] = (float)(std::sin(z) * std::cos(a));
+    sc->sun[1] = (float)(std::sin(z) * std::sin(a));
+    sc->sun[2] = (float)std::cos(z);
+    return MCRT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tracing
+// ---------------------------------------------------------------------------
+int mcrt_trace_opts_default(mcrt_trace_opts* o)
+{
+    if (!o) return fail(nullptr, MCRT_ERR_ARG, "mcrt_trace_opts_default: NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->tau_merge = 1.0f;
+    o->finest_level = 1;
+    o->sun_mode = MCRT_SUN_RATIO;
+    return MCRT_OK;
+}
+
+namespace {
+
+int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    if (sc->levels == 0) return fail(ctx, MCRT_ERR_STATE, "%s: majorants not built", who);
+    if (!(o->tau_merge >= 0.0f)) return fail(ctx, MCRT_ERR_ARG, "%s: tau_merge must be >= 0", who);
+    if (o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels)
+        return fail(ctx, MCRT_ERR_ARG, "%s: finest_level must be 0 or 1", who);
+    if (o->max_order < 0) return fail(ctx, MCRT_ERR_ARG, "%s: max_order must be >= 0", who);
+    if (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA)
+        return fail(ctx, MCRT_ERR_ARG, "%s: bad sun_mode", who);
+    if (o->block_size < 0 || o->block_size > 1024 || (o->block_size % 32) != 0)
+        return fail(ctx, MCRT_ERR_ARG, "%s: block_size must be a multiple of 32 up to 1024", who);
+    if (o->block_size > 128) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: block_size above 128", who);
+    if (o->grid_size < 0 || o->chunk < 0) return fail(ctx, MCRT_ERR_ARG, "%s: negative launch shape", who);
+    if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
+    return MCRT_OK;
+}
+
+int ensure_leaf(mcrt_scene* sc, float tau, int finest)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    if (sc->leaf_valid && sc->leaf_tau == tau && sc->leaf_finest == finest) return MCRT_OK;
+    LAUNCH(ctx, launch_leafmap(sc, tau, finest, ctx->stream));
+    sc->leaf_valid = true;
+    sc->leaf_tau = tau;
+    sc->leaf_finest = finest;
+    return MCRT_OK;
+}
+
+int get_tally(mcrt_ctx* ctx, int ncells, int nq, mcrt_tally** inout, const char* who)
+{
+    mcrt_tally* t = *inout;
+    if (t && (t->ctx != ctx || t->ncells != ncells || t->nq != nq))
+        return fail(ctx, MCRT_ERR_ARG, "%s: tally shape (%d, %d) does not match (%d, %d)", who, t ? t->ncells : 0,
+                    t ? t->nq : 0, ncells, nq);
+    if (!t) {
+        t = new (std::nothrow) mcrt_tally();
+        if (!t) return fail(ctx, MCRT_ERR_OOM, "%s: host allocation failed", who);
+        t->ctx = ctx;
+        t->ncells = ncells;
+        t->nq = nq;
+        const size_t m = (size_t)ncells * nq;
+        cudaError_t e = dalloc(ctx, &t->d_s1, m * sizeof(double));
+        if (e == cudaSuccess) e = dalloc(ctx, &t->d_s2, m * sizeof(double));
+        if (e == cudaSuccess) e = dalloc(ctx, &t->d_counters, kNumCounters * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = dalloc(ctx, &t->d_work, sizeof(WorkState));
+        if (e == cudaSuccess) e = dalloc(ctx, &t->d_out, 2 * m * sizeof(double));
+        if (e != cudaSuccess) {
+            dfree(ctx, t->d_s1); dfree(ctx, t->d_s2); dfree(ctx, t->d_counters); dfree(ctx, t->d_work);
+            dfree(ctx, t->d_out);
+            delete t;
+            return fail(ctx, MCRT_ERR_OOM, "%s: %s", who, cudaGetErrorString(e));
+        }
+        *inout = t;
+    }
+    const size_t m = (size_t)ncells * nq;
+    CK(ctx, cudaMemsetAsync(t->d_s1, 0, m * sizeof(double), ctx->stream));
+    CK(ctx, cudaMemsetAsync(t->d_s2, 0, m * sizeof(double), ctx->stream));
+    CK(ctx, cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), ctx->stream));
+    CK(ctx, cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), ctx->stream));
+    return MCRT_OK;
+}
+
+int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts* o, mcrt_tally* t, const char* who)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    const bool bf16 = sc->storage == MCRT_STORAGE_BF16;
+    const bool count = o->count_events != 0;
+    const int block = o->block_size ? o->block_size : 128;
+    int grid = o->grid_size;
+    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, block);
+    P.s1 = t->d_s1;
+    P.s2 = t->d_s2;
+    P.counters = t->d_counters;
+    P.work = static_cast<WorkState*>(t->d_work);
+    P.deadline_ns = o->deadline_ms > 0.0 ? (unsigned long long)(o->deadline_ms * 1e6) : 0ull;
+    P.cancel = reinterpret_cast<const volatile int*>(o->cancel_flag);
+    P.max_order = o->max_order;
+    P.sun_mode = o->sun_mode;
+    P.max_steps = 1u << 22;
+    cudaEvent_t e0, e1;
+    CK(ctx, cudaEventCreate(&e0));
+    CK(ctx, cudaEventCreate(&e1));
+    CK(ctx, cudaEventRecord(e0, ctx->stream));
+    ctx->launches++;
+    cudaError_t le = launch_trace(P, sensor, bf16, count, grid, block, ctx->stream);
+    CK(ctx, cudaEventRecord(e1, ctx->stream));
+    WorkState ws{};
+    cudaError_t ce = cudaMemcpyAsync(&ws, t->d_work, sizeof(ws), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(ctx, le);
+    CK(ctx, ce);
+    CK(ctx, se);
+    t->kernel_ms = ms;
+    if (ws.status == 1) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: deadline of %g ms expired", who, o->deadline_ms);
+    if (ws.status == 2) return fail(ctx, MCRT_ERR_CANCELLED, "%s: cancelled", who);
+    return MCRT_OK;
+}
+
+}  // namespace
+
+int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp, uint64_t seed,
+                      const mcrt_trace_opts* opts, mcrt_tally** tally)
+{
+    const char* who = "mcrt_trace_camera";
+    if (!sc || !cam || !tally) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    ctx->err.clear();
+    mcrt_trace_opts dflt;
+    mcrt_trace_opts_default(&dflt);
+    const mcrt_trace_opts* o = opts ? opts : &dflt;
+    int rc = check_opts(sc, o, who);
+    if (rc) return rc;
+    if (cam->width < 1 || cam->height < 1 || (long long)cam->width * cam->height > (1ll << 31) - 1)
+        return fail(ctx, MCRT_ERR_ARG, "%s: bad image size %d x %d", who, cam->width, cam->height);
+    if (spp < 1) return fail(ctx, MCRT_ERR_ARG, "%s: spp must be >= 1", who);
+    if (!(cam->fov_deg > 0.0f && cam->fov_deg < 180.0f)) return fail(ctx, MCRT_ERR_ARG, "%s: fov must be in (0, 180)", who);
+    // camera frame (host, double, then float)
+    double f[3], r[3], u[3];
+    double n = 0;
+    for (int a = 0; a < 3; ++a) { f[a] = (double)cam->target[a] - cam->pos[a]; n += f[a] * f[a]; }
+    n = std::sqrt(n);
+    if (!(n > 0)) return fail(ctx, MCRT_ERR_ARG, "%s: target equals position", who);
+    for (int a = 0; a < 3; ++a) f[a] /= n;
+    const double* up = nullptr;
+    double upd[3] = {cam->up[0], cam->up[1], cam->up[2]};
+    up = upd;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    n = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(n > 1e-12)) return fail(ctx, MCRT_ERR_ARG, "%s: up vector parallel to the view direction", who);
+    for (int a = 0; a < 3; ++a) r[a] /= n;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const int ncells = cam->width * cam->height;
+    CK(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+    if (rc) return rc;
+    rc = get_tally(ctx, ncells, 1, tally, who);
+    if (rc) return rc;
+    mcrt_tally* t = *tally;
+    t->n_per_cell = spp;
+    TraceParams P{};
+    P.S = make_dev_scene(sc, 0.0f);
+    P.total = (unsigned long long)ncells * spp;
+    uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 16u;
+    if (chunk > spp) chunk = spp;
+    while (spp % chunk) --chunk;   // a chunk never straddles two pixels
+    P.chunk = chunk;
+    P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.width = cam->width;
+    P.height = cam->height;
+    P.spp = spp;
+    for (int a = 0; a < 3; ++a) {
+        P.cam_pos[a] = cam->pos[a];
+        P.cam_f[a] = (float)f[a];
+        P.cam_r[a] = (float)r[a];
+        P.cam_u[a] = (float)u[a];
+    }
+    P.tan_half = (float)std::tan(0.5 * cam->fov_deg * M_PI / 180.0);
+    P.aspect = (float)cam->height / (float)cam->width;
+    P.Lz = (float)sc->n[2] * sc->h[2];
+    return run_trace(sc, P, kCamera, o, t, who);
+}
+
+int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_trace_opts* opts, mcrt_tally** tally)
+{
+    const char* who = "mcrt_trace_flux";
+    if (!sc || !tally) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    ctx->err.clear();
+    mcrt_trace_opts dflt;
+    mcrt_trace_opts_default(&dflt);
+    const mcrt_trace_opts* o = opts ? opts : &dflt;
+    int rc = check_opts(sc, o, who);
+    if (rc) return rc;
+    if (npaths < 1) return fail(ctx, MCRT_ERR_ARG, "%s: npaths must be >= 1", who);
+    CK(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+    if (rc) return rc;
+    rc = get_tally(ctx, 1, 3, tally, who);
+    if (rc) return rc;
+    mcrt_tally* t = *tally;
+    t->n_per_cell = npaths;
+    TraceParams P{};
+    P.S = make_dev_scene(sc, 0.0f);
+    P.total = npaths;
+    P.chunk = o->chunk ? (uint32_t)o->chunk : 16u;
+    P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.spp = 1;
+    P.Lz = (float)sc->n[2] * sc->h[2];
+    return run_trace(sc, P, kFlux, o, t, who);
+}
+
+// ---------------------------------------------------------------------------
+// Tallies
+// ---------------------------------------------------------------------------
+int mcrt_tally_shape(const mcrt_tally* t, int32_t* ncells, int32_t* nquant)
+{
+    if (!t) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_shape: NULL tally");
+    if (ncells) *ncells = t->ncells;
+    if (nquant) *nquant = t->nq;
+    return MCRT_OK;
+}
+
+int mcrt_tally_read(const mcrt_tally* t, double* mean, double* se, uint64_t* n, size_t count)
+{
+    if (!t) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_read: NULL tally");
+    mcrt_ctx* ctx = t->ctx;
+    const size_t m = (size_t)t->ncells * t->nq;
+    if (count < m) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_read: need %zu entries", m);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (mean || se) {
+        LAUNCH(ctx, launch_finalize(t->d_s1, t->d_s2, (double)t->n_per_cell, (int)m, t->d_out, ctx->stream));
+        double* h = new (std::nothrow) double[2 * m];
+        if (!h) return fail(ctx, MCRT_ERR_OOM, "mcrt_tally_read: host allocation failed");
+        cudaError_t e = cudaMemcpyAsync(h, t->d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            delete[] h;
+            return fail(ctx, MCRT_ERR_CUDA, "mcrt_tally_read: %s", cudaGetErrorString(e));
+        }
+        for (size_t i = 0; i < m; ++i) {
+            if (mean) mean[i] = h[2 * i];
+            if (se) se[i] = h[2 * i + 1];
+        }
+        delete[] h;
+    }
+    if (n)
+        for (size_t i = 0; i < m; ++i) n[i] = t->n_per_cell;
+    return MCRT_OK;
+}
+
+int mcrt_tally_read_sums(const mcrt_tally* t, double* s1, double* s2, size_t count)
+{
+    if (!t) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_read_sums: NULL tally");
+    mcrt_ctx* ctx = t->ctx;
+    const size_t m = (size_t)t->ncells * t->nq;
+    if (count < m) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_read_sums: need %zu entries", m);
+    if (s1) CK(ctx, cudaMemcpyAsync(s1, t->d_s1, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (s2) CK(ctx, cudaMemcpyAsync(s2, t->d_s2, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MCRT_OK;
+}
+
+int mcrt_tally_counters(const mcrt_tally* t, uint64_t* c, size_t n)
+{
+    if (!t || !c) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_counters: NULL argument");
+    mcrt_ctx* ctx = t->ctx;
+    if (n < 10) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_counters: need 10 entries");
+    unsigned long long h[kNumCounters];
+    CK(ctx, cudaMemcpyAsync(h, t->d_counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < n && i < (size_t)kNumCounters; ++i) c[i] = h[i];
+    return MCRT_OK;
+}
+
+int mcrt_tally_kernel_ms(const mcrt_tally* t, float* ms)
+{
+    if (!t || !ms) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_kernel_ms: NULL argument");
+    *ms = t->kernel_ms;
+    return MCRT_OK;
+}
+
+int mcrt_tally_destroy(mcrt_tally* t)
+{
+    if (!t) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_destroy: NULL tally");
+    mcrt_ctx* ctx = t->ctx;
+    dfree(ctx, t->d_s1);
+    dfree(ctx, t->d_s2);
+    dfree(ctx, t->d_counters);
+    dfree(ctx, t->d_work);
+    dfree(ctx, t->d_out);
+    cudaStreamSynchronize(ctx->stream);
+    delete t;
+    return MCRT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checks
+// ---------------------------------------------------------------------------
+int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], float tau, int32_t finest,
+                   int32_t* cells, float* tio, int32_t cap, int32_t* count, int32_t* status)
+{
+    mcrt_scene* sc = const_cast<mcrt_scene*>(sc_c);
+    if (!sc || !o || !d || !cells || !tio || !count || !status)
+        return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "mcrt_debug_dda: NULL argument");
+    mcrt_ctx* ctx = sc->ctx;
+    if (cap < 1) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_dda: cap must be >= 1");
+    mcrt_trace_opts op;
+    mcrt_trace_opts_default(&op);
+    op.tau_merge = tau;
+    op.finest_level = finest;
+    int rc = check_opts(sc, &op, "mcrt_debug_dda");
+    if (rc) return rc;
+    const float n2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(n2 > 0.0f) || !std::isfinite(n2)) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_dda: bad direction");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(o[a])) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_dda: bad origin");
+    CK(ctx, cudaSetDevice(ctx->device));
+    rc = ensure_leaf(sc, tau, finest);
+    if (rc) return rc;
+    int* dcells = nullptr;
+    float* dtio = nullptr;
+    int* dcs = nullptr;
+    CK(ctx, dalloc(ctx, &dcells, (size_t)cap * 4 * sizeof(int)));
+    CK(ctx, dalloc(ctx, &dtio, (size_t)cap * 2 * sizeof(float)));
+    CK(ctx, dalloc(ctx, &dcs, 2 * sizeof(int)));
+    ctx->launches++;
+    cudaError_t e = launch_debug_dda(make_dev_scene(sc, 0.0f), o, d, cap, dcells, dtio, dcs,
+                                     sc->storage == MCRT_STORAGE_BF16, ctx->stream);
+    int cs[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cs, dcs, sizeof(cs), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && cs[0] > 0) {
+        e = cudaMemcpyAsync(cells, dcells, (size_t)cs[0] * 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tio, dtio, (size_t)cs[0] * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    dfree(ctx, dcells);
+    dfree(ctx, dtio);
+    dfree(ctx, dcs);
+    CK(ctx, e);
+    *count = cs[0];
+    *status = cs[1];
+    return MCRT_OK;
+}
+
+int mcrt_debug_philox(mcrt_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n)
+{
+    if (!ctx || !ctr || !key || !out) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_philox: NULL argument");
+    if (n == 0) return MCRT_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    CK(ctx, dalloc(ctx, &dc, n * 16));
+    CK(ctx, dalloc(ctx, &dk, n * 8));
+    CK(ctx, dalloc(ctx, &dout, n * 16));
+    cudaError_t e = cudaMemcpyAsync(dc, ctr, n * 16, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dk, key, n * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->launches++;
+        e = launch_debug_philox(dc, dk, dout, n, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, n * 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, dc);
+    dfree(ctx, dk);
+    dfree(ctx, dout);
+    CK(ctx, e);
+    return MCRT_OK;
+}
+
+}  // extern "C"

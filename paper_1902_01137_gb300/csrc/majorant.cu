@@ -1,0 +1,184 @@
+// majorant.cu -- field ingest and the majorant pyramid (sm_103a).
+//
+// K2+K1 fused (relayout_l1): the row-major extinction field is rewritten into
+// 8x8x8 bricks (Sec. 3.1.2: voxels kept in fixed-size spatially coherent
+// blocks) and, in the same pass, the max of every brick -- the level-1 cell of
+// the pyramid -- is reduced.  One pass over HBM: 4 B read + 4 B (or 2 B) written
+// per voxel plus 4 B per 512 voxels.
+// K1 (reduce_level): level L >= 2 cells take the exact max of their (up to)
+// 8x8x8 children (Sec. 3.1.1: merged voxels store the max).  Max is exact and
+// order-free, so the result is bit-identical to any other evaluation order.
+// Leaf map: for each level-1 cell, the coarsest ancestor whose majorant times
+// its height is <= tau~ (Sec. 4.2's merge criterion), with its majorant.
+#include <cuda_bf16.h>
+
+#include "mcrt_internal.h"
+
+namespace mcrt {
+
+namespace {
+
+// One block of 256 threads = 4 consecutive bricks along x.  Thread t holds
+// row r = t >> 2 (y & 7 = r & 7, z & 7 = r >> 3) of brick q = t & 3.
+template <bool BF16>
+__global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restrict__ src, int nx, int ny, int nz,
+                                                          int nbx, int nby, void* __restrict__ dst,
+                                                          float* __restrict__ l1)
+{
+    const int t = threadIdx.x;
+    const int q = t & 3;
+    const int r = t >> 2;
+    const int bx = blockIdx.x * 4 + q;
+    const int by = blockIdx.y;
+    const int bz = blockIdx.z;
+    const int y = by * 8 + (r & 7);
+    const int z = bz * 8 + (r >> 3);
+    const int x0 = bx * 8;
+    float v[8];
+    const bool row_ok = (bx < nbx) && (y < ny) && (z < nz);
+    const size_t row = ((size_t)z * ny + y) * (size_t)nx;
+    if (row_ok && x0 + 8 <= nx && (nx & 3) == 0 &&
+        ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(src + row + x0));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(src + row + x0 + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (row_ok && x0 + i < nx) ? src[row + x0 + i] : 0.0f;
+    }
+    float m = 0.0f;
+    if (BF16) {
+        // stored voxels: nearest bf16; majorant: smallest bf16 >= the FP32 max,
+        // which bounds every nearest-rounded voxel of the brick
+        uint32_t packed[4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[i]));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[i + 1]));
+            packed[i / 2] = lo | (hi << 16);
+            m = fmaxf(m, fmaxf(v[i], v[i + 1]));
+        }
+        m = __bfloat162float(__float2bfloat16_ru(m));
+        if (bx < nbx) {
+            const size_t brick = ((size_t)bz * nby + by) * (size_t)nbx + bx;
+            uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(dst) + brick * 512 + r * 8);
+            __stcs(o, make_uint4(packed[0], packed[1], packed[2], packed[3]));
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) m = fmaxf(m, v[i]);
+        if (bx < nbx) {
+            const size_t brick = ((size_t)bz * nby + by) * (size_t)nbx + bx;
+            float4* o = reinterpret_cast<float4*>(static_cast<float*>(dst) + brick * 512 + r * 8);
+            __stcs(o, make_float4(v[0], v[1], v[2], v[3]));
+            __stcs(o + 1, make_float4(v[4], v[5], v[6], v[7]));
+        }
+    }
+    // max over the 64 rows of each brick: lanes sharing q differ in bits 2..4
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    __shared__ float part[8][4];
+    if ((t & 31) < 4) part[t >> 5][q] = m;
+    __syncthreads();
+    if (t < 4) {
+        float mm = part[0][t];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) mm = fmaxf(mm, part[w][t]);
+        const int bxx = blockIdx.x * 4 + t;
+        if (bxx < nbx) l1[((size_t)bz * nby + by) * (size_t)nbx + bxx] = mm;
+    }
+}
+
+// One warp per coarse cell; lane l takes children l, l + 32, ... of 512.
+__global__ void __launch_bounds__(256) reduce_level_kernel(const float* __restrict__ prev, int px, int py, int pz,
+                                                           float* __restrict__ out, int cx, int cy, int cz)
+{
+    const long long cell = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cell >= (long long)cx * cy * cz) return;
+    const int ix = (int)(cell % cx);
+    const int iy = (int)((cell / cx) % cy);
+    const int iz = (int)(cell / ((long long)cx * cy));
+    float m = 0.0f;
+#pragma unroll 4
+    for (int c = lane; c < 512; c += 32) {
+        const int x = ix * 8 + (c & 7), y = iy * 8 + ((c >> 3) & 7), z = iz * 8 + (c >> 6);
+        if (x < px && y < py && z < pz) m = fmaxf(m, prev[((size_t)z * py + y) * (size_t)px + x]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) out[cell] = m;
+}
+
+struct LevelTable {
+    const float* p[9];
+    int dims[9][3];
+    float hz[9];
+};
+
+// Leaf of each level-1 cell: search from the top level down to finest + 1.
+__global__ void __launch_bounds__(256) leafmap_kernel(LevelTable T, int levels, int finest, float tau,
+                                                      int n1x, int n1y, int n1z, uint2* __restrict__ leaf)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n1x * n1y * n1z) return;
+    const int cx = (int)(i % n1x), cy = (int)((i / n1x) % n1y), cz = (int)(i / ((long long)n1x * n1y));
+    for (int L = levels; L > finest; --L) {
+        const int s = 3 * (L - 1);
+        const int ax = cx >> s, ay = cy >> s, az = cz >> s;
+        const float M = T.p[L][((size_t)az * T.dims[L][1] + ay) * T.dims[L][0] + ax];
+        if (__fmul_rn(M, T.hz[L]) <= tau) {
+            leaf[i] = make_uint2(__float_as_uint(M), (unsigned)L);
+            return;
+        }
+    }
+    if (finest == 0) {
+        leaf[i] = make_uint2(0u, 0u);
+    } else {
+        const int s = 3 * (finest - 1);
+        const float M = T.p[finest][((size_t)(cz >> s) * T.dims[finest][1] + (cy >> s)) * T.dims[finest][0] + (cx >> s)];
+        leaf[i] = make_uint2(__float_as_uint(M), (unsigned)finest);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t st)
+{
+    dim3 grid((sc->nb[0] + 3) / 4, sc->nb[1], sc->nb[2]);
+    float* l1 = sc->d_pyr + sc->lev_off[1];
+    if (sc->storage == MCRT_STORAGE_BF16)
+        relayout_l1_kernel<true><<<grid, 256, 0, st>>>(src, sc->n[0], sc->n[1], sc->n[2], sc->nb[0], sc->nb[1],
+                                                       sc->d_vox, l1);
+    else
+        relayout_l1_kernel<false><<<grid, 256, 0, st>>>(src, sc->n[0], sc->n[1], sc->n[2], sc->nb[0], sc->nb[1],
+                                                        sc->d_vox, l1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_level(const float* prev, const int* pd, float* out, const int* d, cudaStream_t st)
+{
+    const long long cells = (long long)d[0] * d[1] * d[2];
+    const int warps = 8;
+    const long long blocks = (cells + warps - 1) / warps;
+    reduce_level_kernel<<<(unsigned)blocks, 32 * warps, 0, st>>>(prev, pd[0], pd[1], pd[2], out, d[0], d[1], d[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st)
+{
+    LevelTable T{};
+    for (int L = 1; L <= sc->levels && L < 9; ++L) {
+        T.p[L] = sc->d_pyr + sc->lev_off[L];
+        for (int a = 0; a < 3; ++a) T.dims[L][a] = sc->lev_dims[3 * L + a];
+        T.hz[L] = sc->h[2] * (float)(1 << (3 * L));
+    }
+    const long long n1 = (long long)sc->nb[0] * sc->nb[1] * sc->nb[2];
+    leafmap_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(T, sc->levels, finest, tau, sc->nb[0], sc->nb[1],
+                                                                   sc->nb[2], sc->d_leaf);
+    return cudaGetLastError();
+}
+
+}  // namespace mcrt

@@ -1,0 +1,302 @@
+// mcrt_device.cuh -- device-side building blocks of the tracer (sm_103a).
+//
+//  * Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
+//    per-(path, event, stream) draw sequence.
+//  * The FP32 leaf traversal over the majorant pyramid: the ray steps from
+//    leaf to leaf, a leaf being the coarsest pyramid cell whose majorant times
+//    its height is <= tau~ (Sec. 4.2), or a cell of the finest tracked level.
+//    Every operation is an explicitly rounded IEEE binary32 operation, so the
+//    leaf sequence and distances are reproducible bit for bit.
+//  * Henyey-Greenstein sampling/evaluation and direction frames (Sec. 4.1).
+//
+// No file here is shared with the CPU oracle; the oracle implements the same
+// definitions independently.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcrt {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInv4Pi = 0.0795774715459476679f;
+
+// --------------------------------------------------------------------------
+// Philox4x32-10
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Draw sequence of one (path, event, stream): counter (path lo, path hi,
+// event << 2 | stream, n >> 2), word n & 3.  Uniform ((x >> 8) + 1) 2^-24.
+struct Draws {
+    uint32_t c2;   // (event << 2) | stream
+    uint32_t n;    // next draw index
+    uint32_t b0, b1, b2, b3;
+
+    __device__ __forceinline__ void reset(uint32_t event, uint32_t stream)
+    {
+        c2 = (event << 2) | (stream & 3u);
+        n = 0;
+    }
+    __device__ __forceinline__ float u(uint32_t plo, uint32_t phi, uint2 key)
+    {
+        const uint32_t j = n & 3u;
+        if (j == 0) {
+            const uint4 r = philox4x32_10(make_uint4(plo, phi, c2, n >> 2), key);
+            b0 = r.x; b1 = r.y; b2 = r.z; b3 = r.w;
+        }
+        const uint32_t w = (j == 0) ? b0 : (j == 1) ? b1 : (j == 2) ? b2 : b3;
+        ++n;
+        return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;
+    }
+};
+
+// --------------------------------------------------------------------------
+// Scene as seen by the kernels
+// --------------------------------------------------------------------------
+struct DevScene {
+    int n[3];            // voxels per axis
+    float h[3];          // voxel size [km]
+    float inv_h[3];      // 1 / h, round to nearest
+    float Lper[2];       // n * h for the periodic axes
+    int nb[3];           // bricks (8^3 voxels) per axis == level-1 cells
+    const float* __restrict__ vox;       // brick-major FP32 field, or null
+    const uint16_t* __restrict__ vox16;  // brick-major BF16 field, or null
+    const uint2* __restrict__ leaf;      // per level-1 cell: {majorant bits, leaf level}
+    float k_clear, ssa_clear, ssa_cloud, g;
+    float k_gas;         // extra uniform pure absorber
+    float albedo;        // flat Lambertian ground
+    float sun[3];        // unit vector toward the sun
+};
+
+__device__ __forceinline__ size_t brick_index(const DevScene& S, int i, int j, int k)
+{
+    const size_t b = ((size_t)(k >> 3) * (size_t)S.nb[1] + (size_t)(j >> 3)) * (size_t)S.nb[0] + (size_t)(i >> 3);
+    const uint32_t off = ((((uint32_t)k & 7u) << 3 | ((uint32_t)j & 7u)) << 3) | ((uint32_t)i & 7u);
+    return b * 512u + off;
+}
+
+template <bool BF16>
+__device__ __forceinline__ float kfetch(const DevScene& S, int i, int j, int k)
+{
+    const size_t idx = brick_index(S, i, j, k);
+    if (BF16) return __uint_as_float((uint32_t)__ldg(S.vox16 + idx) << 16);
+    return __ldg(S.vox + idx);
+}
+
+// --------------------------------------------------------------------------
+// Leaf traversal
+// --------------------------------------------------------------------------
+struct Ray {
+    float o[3];      // segment origin
+    float d[3];      // unit direction
+    float inv_d[3];  // 1 / d (0 where d == 0)
+    int v[3];        // voxel of the current point
+    int lo[3], hi[3];// voxel range of the current leaf
+    int lev;         // leaf level
+    float M;         // leaf majorant (+ k_gas)
+    float t;         // distance of the current point from o
+    float texit;     // distance of the leaf exit from o
+    int ax;          // exit axis
+    uint32_t steps;  // leaves entered (guard)
+};
+
+// Voxel of coordinate p on one axis: floor(p / h) by the rounded reciprocal,
+// one lower when moving down onto an exact face, clamped to [lo, hi].
+__device__ __forceinline__ int locate(float p, float d, float h, float inv_h, int lo, int hi)
+{
+    int i = __float2int_rd(__fmul_rn(p, inv_h));
+    if (d < 0.0f && __fmul_rn(__int2float_rn(i), h) == p) i -= 1;
+    return min(max(i, lo), hi);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void enter_leaf(const DevScene& S, Ray& R)
+{
+    const int c1x = R.v[0] >> 3, c1y = R.v[1] >> 3, c1z = R.v[2] >> 3;
+    const uint2 e = __ldg(S.leaf + ((size_t)c1z * S.nb[1] + c1y) * S.nb[0] + c1x);
+    R.lev = (int)e.y;
+    float M = __uint_as_float(e.x);
+    if (R.lev == 0) M = kfetch<BF16>(S, R.v[0], R.v[1], R.v[2]);
+    R.M = __fadd_rn(M, S.k_gas);
+    const int s = 3 * R.lev;
+    float ta[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int c = R.v[a] >> s;
+        R.lo[a] = c << s;
+        R.hi[a] = min((c + 1) << s, S.n[a]) - 1;
+        const float d = R.d[a];
+        if (d == 0.0f) {
+            ta[a] = __int_as_float(0x7f800000);
+        } else {
+            const int B = d > 0.0f ? R.hi[a] + 1 : R.lo[a];
+            ta[a] = __fmul_rn(__fsub_rn(__fmul_rn(__int2float_rn(B), S.h[a]), R.o[a]), R.inv_d[a]);
+        }
+    }
+    int ax = 0;
+    float tm = ta[0];
+    if (ta[1] < tm) { ax = 1; tm = ta[1]; }
+    if (ta[2] < tm) { ax = 2; tm = ta[2]; }
+    R.ax = ax;
+    R.texit = fmaxf(tm, R.t);
+}
+
+// Start a ray at point p (inside the field, x/y in [0, L)) along unit d.
+template <bool BF16>
+__device__ __forceinline__ void ray_begin(const DevScene& S, Ray& R, const float p[3], const float d[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R.o[a] = p[a];
+        R.d[a] = d[a];
+        R.inv_d[a] = (d[a] != 0.0f) ? __frcp_rn(d[a]) : 0.0f;
+        R.v[a] = locate(p[a], d[a], S.h[a], S.inv_h[a], 0, S.n[a] - 1);
+    }
+    R.t = 0.0f;
+    R.steps = 0;
+    enter_leaf<BF16>(S, R);
+}
+
+enum StepResult { kInside = 0, kTop = 1, kGround = 2 };
+
+// Cross the exit face of the current leaf.  On a periodic wrap the segment
+// restarts at the exit point (o on the face exactly, t = 0); *wrapped_dt
+// receives the distance covered by the finished segment (else 0).
+template <bool BF16>
+__device__ __forceinline__ int step_leaf(const DevScene& S, Ray& R, float* wrapped_dt)
+{
+    const int ax = R.ax;
+    const float te = R.texit;
+    float p[3];
+    int nv[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        p[b] = __fmaf_rn(te, R.d[b], R.o[b]);
+        if (b == ax) nv[b] = R.d[b] > 0.0f ? R.hi[b] + 1 : R.lo[b] - 1;
+        else nv[b] = locate(p[b], R.d[b], S.h[b], S.inv_h[b], R.lo[b], R.hi[b]);
+    }
+    *wrapped_dt = 0.0f;
+    if (ax == 2) {
+        R.t = te;
+        if (nv[2] < 0) return kGround;
+        if (nv[2] >= S.n[2]) return kTop;
+    } else {
+        // periodic x / y: wrap the index; the segment restarts on the face
+        int wrapped = 0;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (b != ax) continue;
+            if (nv[b] < 0) { nv[b] = S.n[b] - 1; wrapped = 1; }
+            else if (nv[b] >= S.n[b]) { nv[b] = 0; wrapped = 2; }
+        }
+        if (wrapped) {
+            *wrapped_dt = te;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                R.o[b] = p[b];
+                if (b == ax) R.o[b] = (wrapped == 1) ? S.Lper[b < 2 ? b : 0] : 0.0f;
+            }
+            R.t = 0.0f;
+        } else {
+            R.t = te;
+        }
+    }
+    R.v[0] = nv[0]; R.v[1] = nv[1]; R.v[2] = nv[2];
+    ++R.steps;
+    enter_leaf<BF16>(S, R);
+    return kInside;
+}
+
+// Point at distance t and its voxel, clamped into the current leaf (so that
+// the extinction read there is bounded by the leaf majorant).
+__device__ __forceinline__ void point_in_leaf(const DevScene& S, const Ray& R, float p[3], int vi[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = __fmaf_rn(R.t, R.d[a], R.o[a]);
+        vi[a] = locate(p[a], R.d[a], S.h[a], S.inv_h[a], R.lo[a], R.hi[a]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Scattering
+// --------------------------------------------------------------------------
+// HG phase function normalised over 4 pi sr.
+__device__ __forceinline__ float hg_pdf(float g, float mu)
+{
+    const float den = fmaxf(1.0f + g * g - 2.0f * g * mu, 1e-12f);
+    const float r = rsqrtf(den);
+    return (1.0f - g * g) * kInv4Pi * r * r * r;
+}
+
+// Inverse-CDF HG cosine for xi in (0, 1].
+__device__ __forceinline__ float hg_sample_mu(float g, float xi)
+{
+    if (fabsf(g) < 1e-4f) return 1.0f - 2.0f * xi;
+    const float s = (1.0f - g * g) / (1.0f - g + 2.0f * g * xi);
+    const float mu = (1.0f + g * g - s * s) / (2.0f * g);
+    return fminf(fmaxf(mu, -1.0f), 1.0f);
+}
+
+// Direction with cosine mu to unit d and azimuth 2 pi xi, in the
+// orthonormal frame of Duff et al. (JCGT 2017).
+__device__ __forceinline__ void rotate_dir(const float d[3], float mu, float xi, float out[3])
+{
+    const float sign = copysignf(1.0f, d[2]);
+    const float a = -1.0f / (sign + d[2]);
+    const float b = d[0] * d[1] * a;
+    const float b1x = 1.0f + sign * d[0] * d[0] * a, b1y = sign * b, b1z = -sign * d[0];
+    const float b2x = b, b2y = sign + d[1] * d[1] * a, b2z = -d[1];
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    float sp, cp;
+    sincospif(2.0f * xi, &sp, &cp);
+    const float c = st * cp, s = st * sp;
+    float rx = c * b1x + s * b2x + mu * d[0];
+    float ry = c * b1y + s * b2y + mu * d[1];
+    float rz = c * b1z + s * b2z + mu * d[2];
+    const float inv = rsqrtf(rx * rx + ry * ry + rz * rz);
+    out[0] = rx * inv; out[1] = ry * inv; out[2] = rz * inv;
+}
+
+// Cosine-weighted direction about +z, cos(theta) = sqrt(xi1) > 0.
+__device__ __forceinline__ void cosine_up(float xi1, float xi2, float out[3])
+{
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - xi1));
+    float sp, cp;
+    sincospif(2.0f * xi2, &sp, &cp);
+    out[0] = st * cp; out[1] = st * sp; out[2] = sqrtf(xi1);
+}
+
+// Single-scattering albedo of the mixture at total extinction k_tot.
+__device__ __forceinline__ float omega_at(const DevScene& S, float k_tot)
+{
+    const float k = k_tot - S.k_gas;
+    const float kc = fmaxf(k - S.k_clear, 0.0f);
+    const float kcl = k - kc;
+    return k_tot > 0.0f ? (kc * S.ssa_cloud + kcl * S.ssa_clear) / k_tot : 0.0f;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace mcrt

@@ -1,0 +1,115 @@
+// mcrt_internal.h -- host-side objects behind the opaque C handles and the
+// launchers each .cu file provides.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mcrt.h"
+#include "mcrt_device.cuh"
+
+struct mcrt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    size_t l2_bytes = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+struct mcrt_scene {
+    mcrt_ctx* ctx = nullptr;
+    int n[3] = {0, 0, 0};
+    float h[3] = {0, 0, 0};
+    int nb[3] = {0, 0, 0};            // bricks per axis (= level-1 cells)
+    float k_clear = 0, ssa_clear = 1, ssa_cloud = 1, g = 0;
+    int storage = MCRT_STORAGE_F32;
+    void* d_vox = nullptr;            // brick-major field (float or bf16 bits)
+    size_t vox_bytes = 0;
+    // pyramid: level 1 is filled by the relayout; levels >= 2 by the build
+    int levels = 0;                   // built levels (0 = none)
+    float* d_pyr = nullptr;           // all levels, concatenated
+    size_t pyr_capacity = 0;          // floats allocated
+    std::vector<size_t> lev_off;      // offset of level L (index L), floats
+    std::vector<int> lev_dims;        // 3 ints per level (index 3L)
+    // leaf map for one (tau~, finest level)
+    uint2* d_leaf = nullptr;
+    bool leaf_valid = false;
+    float leaf_tau = 0;
+    int leaf_finest = -1;
+    float albedo = 0;
+    float sun_zenith = 0, sun_azimuth = 0;
+    float sun[3] = {0, 0, 1};
+};
+
+struct mcrt_tally {
+    mcrt_ctx* ctx = nullptr;
+    int ncells = 0, nq = 0;
+    uint64_t n_per_cell = 0;
+    double* d_s1 = nullptr;
+    double* d_s2 = nullptr;
+    unsigned long long* d_counters = nullptr;   // 16 counters
+    void* d_work = nullptr;                      // WorkState
+    double* d_out = nullptr;                     // finalize scratch (mean, se)
+    float kernel_ms = 0;
+};
+
+namespace mcrt {
+
+constexpr int kNumCounters = 16;
+
+// Work distribution and status shared by all blocks of a trace launch.
+struct WorkState {
+    unsigned long long next;   // next path id to claim
+    int status;                // 0 ok, 1 deadline, 2 cancelled
+    int pad;
+};
+
+// Launch parameters of the tracer.
+struct TraceParams {
+    DevScene S;
+    unsigned long long total;  // paths
+    uint32_t chunk;            // paths per claim
+    uint2 key;                 // Philox key (seed)
+    int max_order;
+    int sun_mode;
+    uint32_t max_steps;
+    // camera
+    int width, height;
+    uint32_t spp;
+    float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
+    float tan_half, aspect;    // tan(fov/2), height/width
+    float Lz;
+    // outputs
+    double* s1;
+    double* s2;
+    unsigned long long* counters;
+    WorkState* work;
+    // control
+    unsigned long long deadline_ns;       // 0 = none
+    const volatile int* cancel;
+};
+
+enum Sensor { kCamera = 0, kFlux = 1 };
+
+// Launchers (return cudaError of the launch).
+cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t st);
+cudaError_t launch_reduce_level(const float* prev, const int* prev_dims, float* out, const int* dims,
+                                cudaStream_t st);
+cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st);
+cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count, int grid, int block,
+                         cudaStream_t st);
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block);
+cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, double* out,
+                            cudaStream_t st);
+cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,
+                             float* tio, int* count_status, bool bf16, cudaStream_t st);
+cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                                cudaStream_t st);
+
+DevScene make_dev_scene(const mcrt_scene* sc, float k_gas);
+
+}  // namespace mcrt

@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+* Philox4x32-10, majorant pyramid (FP32 and BF16 round-up) and the leaf
+  traversal: bit-exact.
+* Monte Carlo tallies: within 4 combined standard errors of the oracle, on
+  the same seeds (the two sides draw the same random numbers, so most paths
+  coincide up to FP32 rounding; a paired check makes that explicit).
+* Closed forms met by the GPU directly (Beer, black sky, single scattering).
+* Edge cases: ragged sizes, a one-voxel field, an empty field, tau~ = 0 and
+  infinity, voxel tracking, delta tracking, order cut, bad arguments,
+  deadline and cancel flag.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1902_01137_gb300 as mod
+    from paper_1902_01137_gb300 import build
+    build.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(m):
+    c = m.Context(0)
+    yield c
+    c.close()
+
+
+def oscene(orc, sp, **kw):
+    a = dict(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear, ssa_clear=sp.ssa_clear,
+             ssa_cloud=sp.ssa_cloud, g=sp.g, ground_albedo=sp.ground_albedo, sun_zenith_deg=sp.sun_zenith_deg,
+             sun_azimuth_deg=sp.sun_azimuth_deg)
+    a.update(kw)
+    return orc.Scene(**a)
+
+
+def ocam(orc, cam):
+    return orc.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, cam.width, cam.height)
+
+
+def close_4se(a, sa, b, sb):
+    return abs(a - b) <= 4.0 * math.hypot(sa, sb) + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# bit-exact parts
+# ---------------------------------------------------------------------------
+def test_philox_bit_exact(m, ctx, orc):
+    r = np.random.default_rng(5)
+    ctr = r.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = r.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    g = m.mcrt_debug_philox(ctx.h, ctr, key)
+    o = orc.philox4x32_10(ctr, key)
+    assert np.array_equal(g, o)
+
+
+@pytest.mark.parametrize("shape,levels", [((32, 64, 64), 2), ((21, 29, 37), 2), ((1, 1, 1), 1),
+                                          ((40, 72, 72), 3), ((9, 8, 65), 3)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_majorants_bit_exact(m, ctx, orc, shape, levels, bf16):
+    r = np.random.default_rng(sum(shape))
+    k = (r.lognormal(0.0, 2.0, shape) * (r.uniform(size=shape) < 0.4)).astype(np.float32)
+    sc = m.Scene(ctx, k, 0.1, 0.1, 0.1, levels=levels, storage=m.MCRT_STORAGE_BF16 if bf16 else 0)
+    try:
+        want = orc.build_pyramid(k, levels, round_up_bf16=bf16)
+        for L in range(1, levels + 1):
+            got = sc.majorants(L)
+            assert got.shape == want[L - 1].shape
+            assert np.array_equal(got.view(np.uint32), want[L - 1].view(np.uint32)), L
+    finally:
+        sc.close()
+
+
+def _dda_field():
+    sp = scenes.random_voxels(72, 64, 40, 0.1, 3.0, seed=2, sparsity=0.5)
+    k = sp.k.copy()
+    k[:, :, 32:64] = 0.0
+    k[24:, :, :] *= 0.01
+    return sp, k
+
+
+@pytest.mark.parametrize("tau,finest", [(1.0, 1), (0.3, 0), (float("inf"), 1), (0.0, 0), (5.0, 0)])
+def test_dda_bit_exact(m, ctx, orc, tau, finest):
+    sp, k = _dda_field()
+    sc = m.Scene(ctx, k, sp.dx, sp.dy, sp.dz, levels=2)
+    osc = orc.Scene(k=k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=2, tau_merge=tau, finest_level=finest)
+    try:
+        o, d = scenes.random_rays(sp, 200, seed=17)
+        # add rays from faces and along axes
+        o = np.concatenate([o, np.array([[0.85, 0.85, 0.0], [0.85, 0.85, 4.0], [0.0, 1.05, 1.05]], np.float32)])
+        d = np.concatenate([d, np.array([[0, 0, 1], [0, 0, -1], [0.6, 0.8, 0.0]], np.float32)])
+        for i in range(len(o)):
+            cg, tg, sg = sc.dda(o[i], d[i], tau, finest, cap=2000)
+            co, to, so = orc.dda_spec(osc, o[i], d[i], cap=2000)
+            assert sg == so, i
+            assert np.array_equal(cg, co), i
+            assert np.array_equal(tg.view(np.uint32), to.view(np.uint32)), i
+    finally:
+        sc.close()
+
+
+# ---------------------------------------------------------------------------
+# statistical parity on the small config (64x64x32 blobs)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small(m, ctx):
+    sp = scenes.blobs_small(0)
+    sc = m.Scene.from_spec(ctx, sp)
+    yield sp, sc
+    sc.close()
+
+
+def test_flux_small_vs_oracle(m, orc, small):
+    sp, sc = small
+    n = 100000
+    g = sc.trace_flux(n, seed=0)
+    o, _ = orc.trace_flux(oscene(orc, sp), n, seed=0)
+    for q in range(3):
+        assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean[q], o.mean[q], g.se[q], o.se[q])
+    # same random numbers: the two estimates differ by far less than their noise
+    assert abs(g.mean[2] - o.mean[2]) < 0.25 * o.se[2]
+
+
+def _block(a, b=8):
+    h, w = a.shape
+    return a.reshape(h // b, b, w // b, b).sum(axis=(1, 3))
+
+
+def image_parity(g_mean, g_se, o_mean, o_se, spp):
+    """Block sums (8x8 pixels) and the image mean within 4 combined SE; at most
+    max(1, 3x the normal expectation) violating blocks."""
+    gm, om = _block(g_mean), _block(o_mean)
+    gs, os_ = np.sqrt(_block(g_se ** 2)), np.sqrt(_block(o_se ** 2))
+    z = np.abs(gm - om) / np.maximum(np.hypot(gs, os_), 1e-300)
+    nb = z.size
+    allowed = max(1, int(3 * nb * 6.33e-5))
+    bad = int(np.sum(z > 4.0))
+    mg, mo = g_mean.mean(), o_mean.mean()
+    sg = math.sqrt(np.sum(g_se ** 2)) / g_mean.size
+    so = math.sqrt(np.sum(o_se ** 2)) / o_mean.size
+    return bad <= allowed and close_4se(mg, sg, mo, so), (bad, allowed, mg, mo, sg, so)
+
+
+def test_camera_small_vs_oracle(m, orc, small):
+    sp, sc = small
+    cam = scenes.nadir_camera(sp, 64, 64)
+    g = sc.trace_camera(cam, 16, seed=0)
+    o, _ = orc.trace_camera(oscene(orc, sp), ocam(orc, cam), 16, seed=0)
+    ok, info = image_parity(g.mean, g.se, o.mean, o.se, 16)
+    assert ok, info
+    # paired: identical random numbers give near-identical pixels
+    rel = np.abs(g.mean - o.mean) / np.maximum(np.abs(o.mean), 1e-3)
+    assert np.median(rel) < 1e-3, np.median(rel)
+
+
+@pytest.mark.parametrize("opts", [dict(tau_merge=0.0, finest_level=0), dict(tau_merge=float("inf")),
+                                  dict(tau_merge=10.0), dict(sun_mode=1), dict(chunk=1), dict(chunk=64),
+                                  dict(block_size=64, grid_size=7)])
+def test_flux_options_vs_oracle(m, orc, small, opts):
+    sp, sc = small
+    n = 40000
+    g = sc.trace_flux(n, seed=3, **opts)
+    okw = {}
+    if "tau_merge" in opts:
+        okw["tau_merge"] = opts["tau_merge"]
+    if "finest_level" in opts:
+        okw["finest_level"] = opts["finest_level"]
+    if "sun_mode" in opts:
+        okw["sun_mode"] = opts["sun_mode"]
+    o, _ = orc.trace_flux(oscene(orc, sp, **okw), n, seed=3)
+    for q in range(3):
+        assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (opts, q, g.mean[q], o.mean[q])
+
+
+def test_launch_shape_does_not_change_results(m, small):
+    sp, sc = small
+    a = sc.trace_flux(30000, seed=9)
+    b = sc.trace_flux(30000, seed=9, block_size=32, grid_size=3, chunk=5)
+    np.testing.assert_allclose(a.mean, b.mean, rtol=1e-12)
+
+
+def test_event_counters(m, small):
+    sp, sc = small
+    r = sc.trace_flux(20000, seed=4, count_events=1)
+    c = r.counters
+    assert c["paths"] == 20000
+    assert c["tentative"] >= c["real"] > 0
+    assert c["sun_rays"] == c["paths"] + c["real"] + c["ground"]  # the direct ray plus one per vertex
+    assert c["aborted"] == 0
+    q = sc.trace_flux(20000, seed=4)
+    np.testing.assert_allclose(q.mean, r.mean, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# closed forms on the GPU directly
+# ---------------------------------------------------------------------------
+def test_beer_gpu(m, ctx):
+    k, th = 1.7, 40.0
+    sp = scenes.homogeneous(16, 16, 16, 0.1, k, levels=2, sun_zenith_deg=th)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        r = sc.trace_flux(200000, seed=5)
+        want = math.exp(-k * 1.6 / math.cos(math.radians(th)))
+        assert abs(r.mean[0] - want) < 3 * r.se[0]
+    finally:
+        sc.close()
+
+
+def test_black_sky_gpu(m, ctx):
+    rho, th = 0.3, 35.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, 0.0, levels=1, ground_albedo=rho, sun_zenith_deg=th)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        cam = scenes.nadir_camera(sp, 8, 8)
+        r = sc.trace_camera(cam, 64, seed=2)
+        want = rho * math.cos(math.radians(th)) / math.pi
+        np.testing.assert_allclose(r.mean, want, rtol=2e-6)
+    finally:
+        sc.close()
+
+
+def test_single_scattering_gpu(m, ctx):
+    k, g, om, th0, thv = 2.0, 0.7, 0.9, 30.0, 50.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, k, levels=1, g=g, ssa_cloud=om, ssa_clear=om, sun_zenith_deg=th0)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        d = np.array([math.sin(math.radians(thv)), 0.0, -math.cos(math.radians(thv))])
+        pos = np.array([0.8, 0.8, 0.8]) - 20.0 * d
+        cam = scenes.CameraSpec(tuple(pos), (0.8, 0.8, 0.8), (0.0, 0.0, 1.0), 1e-3, 1, 1)
+        r = sc.trace_camera(cam, 1 << 20, seed=4, max_order=1)
+        mu0, mu = math.cos(math.radians(th0)), math.cos(math.radians(thv))
+        s = np.array([math.sin(math.radians(th0)), 0.0, mu0])
+        cosang = float(d @ s)
+        p = (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * cosang) ** 1.5)
+        want = om * p * mu0 / (mu0 + mu) * (1 - math.exp(-k * 0.8 * (1 / mu0 + 1 / mu)))
+        assert abs(r.mean[0, 0] - want) < 3 * r.se[0, 0], (r.mean[0, 0], want, r.se[0, 0])
+    finally:
+        sc.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_ragged_field_vs_oracle(m, ctx, orc):
+    sp = scenes.random_voxels(37, 29, 21, 0.1, 6.0, seed=8, levels=2, sparsity=0.7, ground_albedo=0.4,
+                              sun_zenith_deg=20.0, g=0.6, ssa_cloud=0.95, ssa_clear=0.95)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        n = 60000
+        g = sc.trace_flux(n, seed=12)
+        o, _ = orc.trace_flux(oscene(orc, sp), n, seed=12)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean[q], o.mean[q])
+        cam = scenes.nadir_camera(sp, 24, 16)
+        gi = sc.trace_camera(cam, 32, seed=13)
+        oi, _ = orc.trace_camera(oscene(orc, sp), ocam(orc, cam), 32, seed=13)
+        ok, info = image_parity(gi.mean, gi.se, oi.mean, oi.se, 32)
+        assert ok, info
+    finally:
+        sc.close()
+
+
+def test_one_voxel_field(m, ctx, orc):
+    sp = scenes.homogeneous(1, 1, 1, 0.5, 1.3, levels=1, ground_albedo=0.5, sun_zenith_deg=10.0, g=0.3)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        g = sc.trace_flux(50000, seed=1)
+        o, _ = orc.trace_flux(oscene(orc, sp), 50000, seed=1)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q])
+    finally:
+        sc.close()
+
+
+def test_empty_field(m, ctx):
+    sp = scenes.homogeneous(16, 16, 16, 0.1, 0.0, levels=2, ground_albedo=0.0, sun_zenith_deg=0.0)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        r = sc.trace_flux(10000, seed=1)
+        np.testing.assert_allclose(r.mean, [1.0, 0.0, 1.0], atol=0)
+        cam = scenes.nadir_camera(sp, 4, 4)
+        img = sc.trace_camera(cam, 4, seed=1)
+        assert np.all(img.mean == 0.0)
+    finally:
+        sc.close()
+
+
+def test_bad_arguments(m, ctx, small):
+    sp, sc = small
+    with pytest.raises(m.McrtError) as e:
+        sc.trace_flux(0, seed=1)
+    assert e.value.status == m.MCRT_ERR_ARG
+    with pytest.raises(m.McrtError) as e:
+        m.mcrt_scene_set_sun(ctx.h, sc.h, 95.0, 0.0)
+    assert e.value.status == m.MCRT_ERR_ARG
+    with pytest.raises(m.McrtError) as e:
+        sc.trace_flux(10, seed=1, finest_level=3)
+    assert e.value.status == m.MCRT_ERR_ARG
+    with pytest.raises(m.McrtError) as e:
+        m.Scene(ctx, np.zeros((4, 4, 4), np.float32), -0.1, 0.1, 0.1)
+    assert e.value.status == m.MCRT_ERR_ARG
+    with pytest.raises(m.McrtError) as e:
+        m.mcrt_scene_read_majorants(ctx.h, sc.h, 9)
+    assert e.value.status == m.MCRT_ERR_ARG
+
+
+def test_deadline_and_cancel(m, ctx, small):
+    torch = pytest.importorskip("torch")
+    sp, sc = small
+    cam = scenes.nadir_camera(sp, 256, 256)
+    with pytest.raises(m.McrtError) as e:
+        sc.trace_camera(cam, 4096, seed=1, deadline_ms=2.0)
+    assert e.value.status == m.MCRT_ERR_TIMEOUT
+    flag = torch.ones(1, dtype=torch.int32).pin_memory()
+    with pytest.raises(m.McrtError) as e:
+        sc.trace_camera(cam, 4096, seed=1, cancel_flag=flag.data_ptr())
+    assert e.value.status == m.MCRT_ERR_CANCELLED
+    # the context is still usable afterwards
+    r = sc.trace_flux(1000, seed=2)
+    assert np.isfinite(r.mean).all()
