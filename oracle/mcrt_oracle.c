@@ -69,15 +69,25 @@ void orc_philox_batch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, i
     for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
 }
 
-/* Random stream of one (path, event, stream) triple.  Counter words:
- *   c0 = path id low 32 bits, c1 = path id high 32 bits,
- *   c2 = (event << 2) | stream, c3 = index of the 4-word block.
- * Draw n is word (n & 3) of block (n >> 2).  Key = (seed low, seed high). */
+/* Random numbers.  Every draw is addressed: stream s of event e of path p
+ * evaluates Philox at counter (p low, p high, (e << 2) | s, block) and the
+ * key (seed low, seed high), and takes a fixed word of that block:
+ *   block 0, word 0            first optical depth of a ray
+ *   block j >= 1, words 0, 1   j-th tentative collision of the ray: the
+ *                              collision test (or roulette) draw, then the
+ *                              next optical depth
+ *   block VERTEX, words 0-2    scattering/reflection direction (two draws)
+ *                              and Russian roulette at the vertex that ends
+ *                              the flight of event e (stream 0)
+ *   stream 2, block 0          path start (jitter, or ground point and
+ *                              direction)
+ * Streams: 0 free flight, 1 sun ray of the vertex, 2 path start, 3 direct
+ * sun ray of a flux path (event 0). */
+#define BLOCK_VERTEX 0xFFFFFFFFu
+
 typedef struct {
     uint32_t key[2];
     uint32_t c0, c1, c2;
-    uint32_t n;
-    uint32_t buf[4];
 } rng_t;
 
 static void rng_init(rng_t* r, uint64_t seed, uint64_t path, uint32_t event, uint32_t stream)
@@ -87,25 +97,20 @@ static void rng_init(rng_t* r, uint64_t seed, uint64_t path, uint32_t event, uin
     r->c0 = (uint32_t)path;
     r->c1 = (uint32_t)(path >> 32);
     r->c2 = (event << 2) | (stream & 3u);
-    r->n = 0;
-}
-
-static uint32_t rng_u32(rng_t* r)
-{
-    if ((r->n & 3u) == 0) {
-        uint32_t ctr[4] = {r->c0, r->c1, r->c2, r->n >> 2};
-        orc_philox4x32_10(ctr, r->key, r->buf);
-    }
-    return r->buf[r->n++ & 3u];
 }
 
 /* Uniform in (0, 1]: ((x >> 8) + 1) * 2^-24, exact in float and double. */
-static double rng_u(rng_t* r)
+static double u01(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+
+/* The four uniforms of one block. */
+static void rng_block(const rng_t* r, uint32_t block, double u[4])
 {
-    return (double)((rng_u32(r) >> 8) + 1u) * (1.0 / 16777216.0);
+    uint32_t ctr[4] = {r->c0, r->c1, r->c2, block}, out[4];
+    orc_philox4x32_10(ctr, r->key, out);
+    for (int i = 0; i < 4; ++i) u[i] = u01(out[i]);
 }
 
-double orc_u01_from_u32(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+double orc_u01_from_u32(uint32_t x) { return u01(x); }
 
 /* ===================================================================== */
 /* BF16 rounding of a finite, non-negative float (used for the optional    */
@@ -633,26 +638,29 @@ enum { EV_ESCAPE = 1, EV_GROUND = 2, EV_VOLUME = 3, EV_ABORT = 4 };
 
 typedef struct { int64_t tentative, real, leaves; } orc_counts;
 
-static int free_flight(const orc_scene* S, double p[3], const double d[3], rng_t* r,
+static int free_flight(const orc_scene* S, double p[3], const double d[3], const rng_t* r,
                        double* k_at, orc_counts* C)
 {
     trav64 T;
     trav_begin(S, &T, p, d);
-    double tau = -log(rng_u(r));
-    for (;;) {
+    double u[4];
+    rng_block(r, 0, u);
+    double tau = -log(u[0]);
+    for (uint32_t j = 1;;) {
         if (T.M > 0.0 && tau < T.M * T.seg) {
             double s = tau / T.M;
             trav_move_inside(S, &T, s);
             int vox[3];
             double k = trav_k_here(S, &T, vox);
             if (C) C->tentative++;
-            if (rng_u(r) * T.M <= k) {
+            rng_block(r, j++, u);
+            if (u[0] * T.M <= k) {
                 for (int a = 0; a < 3; ++a) p[a] = T.p[a];
                 *k_at = k;
                 if (C) C->real++;
                 return EV_VOLUME;
             }
-            tau = -log(rng_u(r));
+            tau = -log(u[1]);
         } else {
             tau -= T.M * T.seg;
             int st = trav_next_leaf(S, &T);
@@ -668,29 +676,33 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], rng_t
  * sun_mode 0: ratio tracking, t *= 1 - k/M at each tentative collision,
  * with Russian roulette below 0.1 (survive with prob t/0.1, t <- 0.1).
  * sun_mode 1: the 0/1 estimator of Sec. 2.3 (delta tracking). */
-static double transmissivity(const orc_scene* S, const double p[3], const double s[3], rng_t* r, orc_counts* C)
+static double transmissivity(const orc_scene* S, const double p[3], const double s[3], const rng_t* r,
+                             orc_counts* C)
 {
     trav64 T;
     trav_begin(S, &T, p, s);
     double t = 1.0;
-    double tau = -log(rng_u(r));
-    for (;;) {
+    double u[4];
+    rng_block(r, 0, u);
+    double tau = -log(u[0]);
+    for (uint32_t j = 1;;) {
         if (T.M > 0.0 && tau < T.M * T.seg) {
             trav_move_inside(S, &T, tau / T.M);
             int vox[3];
             double k = trav_k_here(S, &T, vox);
             if (C) C->tentative++;
+            rng_block(r, j++, u);
             if (S->sun_mode == 1) {
-                if (rng_u(r) * T.M <= k) return 0.0;
+                if (u[0] * T.M <= k) return 0.0;
             } else {
                 t *= 1.0 - k / T.M;
                 if (t <= 0.0) return 0.0;
                 if (t < 0.1) {
-                    if (rng_u(r) * 0.1 <= t) t = 0.1;
+                    if (u[0] * 0.1 <= t) t = 0.1;
                     else return 0.0;
                 }
             }
-            tau = -log(rng_u(r));
+            tau = -log(u[1]);
         } else {
             tau -= T.M * T.seg;
             int st = trav_next_leaf(S, &T);
@@ -714,21 +726,22 @@ double orc_first_collision_distance(const orc_scene* S, const double p[3], const
     rng_t r;
     rng_init(&r, seed, path, 0, 0);
     double q[3] = {p[0], p[1], p[2]};
-    double k;
-    /* unwrap: track the distance travelled along d */
     trav64 T;
     trav_begin(S, &T, q, d);
     double dist = 0.0;
-    double tau = -log(rng_u(&r));
-    for (;;) {
+    double u[4];
+    rng_block(&r, 0, u);
+    double tau = -log(u[0]);
+    for (uint32_t j = 1;;) {
         if (T.M > 0.0 && tau < T.M * T.seg) {
             double s = tau / T.M;
             trav_move_inside(S, &T, s);
             dist += s;
             int vox[3];
-            k = trav_k_here(S, &T, vox);
-            if (rng_u(&r) * T.M <= k) return dist;
-            tau = -log(rng_u(&r));
+            double k = trav_k_here(S, &T, vox);
+            rng_block(&r, j++, u);
+            if (u[0] * T.M <= k) return dist;
+            tau = -log(u[1]);
         } else {
             tau -= T.M * T.seg;
             dist += T.seg;
@@ -744,9 +757,9 @@ double orc_first_collision_distance(const orc_scene* S, const double p[3], const
 /* ground event: w * (rho / pi) * max(s_z, 0) * T_sun(x).  Then w *=      */
 /* omega (or rho), a new direction is sampled (HG about d, or cosine      */
 /* about +z), and Russian roulette applies below w = 0.01.  The path ends */
-/* at the top of atmosphere.  Draw order in stream (event e, 0): the      */
-/* flight's draws, two direction draws, then the roulette draw.  The sun  */
-/* ray of event e uses stream (e, 1).                                     */
+/* at the top of atmosphere.  The flight of event e draws from stream     */
+/* (e, 0), its vertex from block VERTEX of that stream, and the vertex's  */
+/* sun ray from stream (e, 1).                                            */
 /* ===================================================================== */
 static double omega_at(const orc_scene* S, double k_total)
 {
@@ -774,6 +787,8 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
         int score_it = (S->max_order == 0 || order <= S->max_order);
         rng_t rs;
         rng_init(&rs, seed, path, e, 1);
+        double uv[4];
+        rng_block(&r, BLOCK_VERTEX, uv);
         if (ev == EV_VOLUME) {
             double om = omega_at(S, k);
             if (score_it) {
@@ -782,8 +797,8 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
                 score += w * om * orc_hg_pdf(S->g, mu) * Ts;
             }
             w *= om;
-            double mu = orc_hg_sample_mu(S->g, rng_u(&r));
-            double phi = 2.0 * ORC_PI * rng_u(&r);
+            double mu = orc_hg_sample_mu(S->g, uv[0]);
+            double phi = 2.0 * ORC_PI * uv[1];
             double nd[3];
             rotate_dir(d, mu, phi, nd);
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
@@ -793,12 +808,11 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
                 score += w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
             }
             w *= S->ground_albedo;
-            double xi1 = rng_u(&r), xi2 = rng_u(&r);
-            cosine_up(xi1, xi2, d);
+            cosine_up(uv[0], uv[1], d);
         }
         if (S->max_order > 0 && order >= S->max_order) break;
         if (w < 0.01) {
-            if (rng_u(&r) * 0.01 <= w) w = 0.01;
+            if (uv[2] * 0.01 <= w) w = 0.01;
             else break;
         }
     }
@@ -849,7 +863,9 @@ static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp,
     int px = (int)(pix % (uint64_t)C->width), py = (int)(pix / (uint64_t)C->width);
     rng_t r;
     rng_init(&r, seed, path, 0, 2);
-    double jx = 1.0 - rng_u(&r), jy = 1.0 - rng_u(&r);
+    double uj[4];
+    rng_block(&r, 0, uj);
+    double jx = 1.0 - uj[0], jy = 1.0 - uj[1];
     double f[3], rt[3], u[3];
     cam_basis(C, f, rt, u);
     double tanh_ = tan(0.5 * C->fov_deg * ORC_PI / 180.0);
@@ -881,7 +897,9 @@ static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double o
 {
     rng_t r;
     rng_init(&r, seed, path, 0, 2);
-    double u0 = rng_u(&r), u1 = rng_u(&r), u2 = rng_u(&r), u3 = rng_u(&r);
+    double u[4];
+    rng_block(&r, 0, u);
+    double u0 = u[0], u1 = u[1], u2 = u[2], u3 = u[3];
     double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy;
     double p[3] = {(1.0 - u0) * Lx, (1.0 - u1) * Ly, 0.0};
     double d[3];
@@ -911,8 +929,10 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
     for (int i = 0; i < 6; ++i) out[i] = 0.0;
     rng_t r0;
     rng_init(&r0, seed, path, 0, 2);
+    double u0[4];
+    rng_block(&r0, 0, u0);
     double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy, Lz = (double)S->nz * S->dz;
-    double p[3] = {(1.0 - rng_u(&r0)) * Lx, (1.0 - rng_u(&r0)) * Ly, Lz};
+    double p[3] = {(1.0 - u0[0]) * Lx, (1.0 - u0[1]) * Ly, Lz};
     double d[3] = {-S->sun[0], -S->sun[1], -S->sun[2]};
     double w = 1.0;
     int scattered = 0;
@@ -923,12 +943,14 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
         int ev = free_flight(S, p, d, &r, &k, NULL);
         if (ev == EV_ESCAPE) { out[0] += w; return; }
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; out[5] += w; return; }
+        double uv[4];
+        rng_block(&r, BLOCK_VERTEX, uv);
         if (ev == EV_VOLUME) {
             double om = omega_at(S, k);
             out[3] += w * (1.0 - om);
             w *= om;
-            double mu = orc_hg_sample_mu(S->g, rng_u(&r));
-            double phi = 2.0 * ORC_PI * rng_u(&r);
+            double mu = orc_hg_sample_mu(S->g, uv[0]);
+            double phi = 2.0 * ORC_PI * uv[1];
             double nd[3];
             rotate_dir(d, mu, phi, nd);
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
@@ -937,8 +959,7 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
             if (scattered) out[2] += w; else out[1] += w;
             out[4] += w * (1.0 - S->ground_albedo);
             w *= S->ground_albedo;
-            double xi1 = rng_u(&r), xi2 = rng_u(&r);
-            cosine_up(xi1, xi2, d);
+            cosine_up(uv[0], uv[1], d);
             scattered = 1;
         }
         if (w < 1e-6) { out[5] += w; return; }
