@@ -239,8 +239,10 @@ MCRT_API int mcrt_tally_read_sums(const mcrt_tally* tally, double* s1, double* s
  * count_events was set): [0] paths, [1] tentative collisions on paths,
  * [2] real collisions, [3] ground hits, [4] leaf steps on paths,
  * [5] tentative collisions on sun rays, [6] leaf steps on sun rays,
- * [7] sun rays, [8] aborted paths (step guard), [9] free flights started.
- * n >= 10. */
+ * [7] sun rays, [8] aborted paths (step guard), [9] free flights started,
+ * and, when n >= 13: [10] most loop iterations spent on one path, [11] the
+ * longest time in ns a GPU warp ran before the work queue ran dry, [12] the
+ * longest time in ns a warp ran in total.  n >= 10. */
 MCRT_API int mcrt_tally_counters(const mcrt_tally* tally, uint64_t* counters, size_t n);
 
 /* Device time of the trace kernel that filled the tally, in ms. */

@@ -37,7 +37,7 @@ MCRT_SUN_RATIO = 0
 MCRT_SUN_DELTA = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
-                 "sun_rays", "aborted", "flights")
+                 "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total")
 
 
 class McrtError(RuntimeError):

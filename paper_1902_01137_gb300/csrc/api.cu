@@ -486,7 +486,7 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
     TraceParams P{};
     P.S = make_dev_scene(sc, 0.0f);
     P.total = (unsigned long long)ncells * spp;
-    uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 16u;
+    uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     if (chunk > spp) chunk = spp;
     while (spp % chunk) --chunk;   // a chunk never straddles two pixels
     P.chunk = chunk;
@@ -528,7 +528,7 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
     TraceParams P{};
     P.S = make_dev_scene(sc, 0.0f);
     P.total = npaths;
-    P.chunk = o->chunk ? (uint32_t)o->chunk : 16u;
+    P.chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.spp = 1;
     P.Lz = (float)sc->n[2] * sc->h[2];
@@ -590,7 +590,7 @@ int mcrt_tally_counters(const mcrt_tally* t, uint64_t* c, size_t n)
 {
     if (!t || !c) return fail(nullptr, MCRT_ERR_ARG, "mcrt_tally_counters: NULL argument");
     mcrt_ctx* ctx = t->ctx;
-    if (n < 10) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_counters: need 10 entries");
+    if (n < 10) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_counters: need at least 10 entries");
     unsigned long long h[kNumCounters];
     CK(ctx, cudaMemcpyAsync(h, t->d_counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -41,30 +41,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
-// Draw sequence of one (path, event, stream): counter (path lo, path hi,
-// event << 2 | stream, n >> 2), word n & 3.  Uniform ((x >> 8) + 1) 2^-24.
-struct Draws {
-    uint32_t c2;   // (event << 2) | stream
-    uint32_t n;    // next draw index
-    uint32_t b0, b1, b2, b3;
+// Random numbers are addressed: stream s of event e of path p evaluates
+// Philox at counter (p lo, p hi, (e << 2) | s, block) and uses fixed words of
+// the block -- block 0 word 0: first optical depth of a ray; block j >= 1:
+// the j-th tentative collision (test or roulette draw, next optical depth);
+// block kBlockVertex: the vertex ending the flight of event e (two direction
+// draws, roulette); stream 2 block 0: path start.  Streams: 0 flight, 1 sun
+// ray of a vertex, 2 path start, 3 direct sun ray of a flux path.
+constexpr uint32_t kBlockVertex = 0xFFFFFFFFu;
 
-    __device__ __forceinline__ void reset(uint32_t event, uint32_t stream)
-    {
-        c2 = (event << 2) | (stream & 3u);
-        n = 0;
-    }
-    __device__ __forceinline__ float u(uint32_t plo, uint32_t phi, uint2 key)
-    {
-        const uint32_t j = n & 3u;
-        if (j == 0) {
-            const uint4 r = philox4x32_10(make_uint4(plo, phi, c2, n >> 2), key);
-            b0 = r.x; b1 = r.y; b2 = r.z; b3 = r.w;
-        }
-        const uint32_t w = (j == 0) ? b0 : (j == 1) ? b1 : (j == 2) ? b2 : b3;
-        ++n;
-        return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;
-    }
-};
+__device__ __forceinline__ float u01(uint32_t w)
+{
+    return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;   // ((w >> 8) + 1) 2^-24
+}
+
+__device__ __forceinline__ uint4 draw_block(unsigned long long path, uint32_t c2, uint32_t block, uint2 key)
+{
+    return philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(path >> 32), c2, block), key);
+}
 
 // --------------------------------------------------------------------------
 // Scene as seen by the kernels
@@ -107,7 +101,6 @@ struct Ray {
     float d[3];      // unit direction
     float inv_d[3];  // 1 / d (0 where d == 0)
     int v[3];        // voxel of the current point
-    int lo[3], hi[3];// voxel range of the current leaf
     int lev;         // leaf level
     float M;         // leaf majorant (+ k_gas)
     float t;         // distance of the current point from o
@@ -115,6 +108,13 @@ struct Ray {
     int ax;          // exit axis
     uint32_t steps;  // leaves entered (guard)
 };
+
+// Voxel range [lo, hi] of the current leaf on axis a.
+__device__ __forceinline__ int leaf_lo(const Ray& R, int a) { return (R.v[a] >> (3 * R.lev)) << (3 * R.lev); }
+__device__ __forceinline__ int leaf_hi(const DevScene& S, const Ray& R, int a)
+{
+    return min(leaf_lo(R, a) + (1 << (3 * R.lev)), S.n[a]) - 1;
+}
 
 // Voxel of coordinate p on one axis: floor(p / h) by the rounded reciprocal,
 // one lower when moving down onto an exact face, clamped to [lo, hi].
@@ -125,11 +125,17 @@ __device__ __forceinline__ int locate(float p, float d, float h, float inv_h, in
     return min(max(i, lo), hi);
 }
 
-template <bool BF16>
-__device__ __forceinline__ void enter_leaf(const DevScene& S, Ray& R)
+// Leaf-map entry of the level-1 cell holding voxel v.
+__device__ __forceinline__ const uint2* leaf_entry(const DevScene& S, const int v[3])
 {
-    const int c1x = R.v[0] >> 3, c1y = R.v[1] >> 3, c1z = R.v[2] >> 3;
-    const uint2 e = __ldg(S.leaf + ((size_t)c1z * S.nb[1] + c1y) * S.nb[0] + c1x);
+    return S.leaf + ((size_t)(v[2] >> 3) * S.nb[1] + (v[1] >> 3)) * S.nb[0] + (v[0] >> 3);
+}
+
+// Finish entering the leaf holding R.v from its leaf-map entry: level,
+// majorant and the exit distance / axis.
+template <bool BF16>
+__device__ __forceinline__ void finish_leaf(const DevScene& S, Ray& R, uint2 e)
+{
     R.lev = (int)e.y;
     float M = __uint_as_float(e.x);
     if (R.lev == 0) M = kfetch<BF16>(S, R.v[0], R.v[1], R.v[2]);
@@ -138,14 +144,13 @@ __device__ __forceinline__ void enter_leaf(const DevScene& S, Ray& R)
     float ta[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int c = R.v[a] >> s;
-        R.lo[a] = c << s;
-        R.hi[a] = min((c + 1) << s, S.n[a]) - 1;
+        const int lo = (R.v[a] >> s) << s;
+        const int hi = min(lo + (1 << s), S.n[a]) - 1;
         const float d = R.d[a];
         if (d == 0.0f) {
             ta[a] = __int_as_float(0x7f800000);
         } else {
-            const int B = d > 0.0f ? R.hi[a] + 1 : R.lo[a];
+            const int B = d > 0.0f ? hi + 1 : lo;
             ta[a] = __fmul_rn(__fsub_rn(__fmul_rn(__int2float_rn(B), S.h[a]), R.o[a]), R.inv_d[a]);
         }
     }
@@ -170,34 +175,37 @@ __device__ __forceinline__ void ray_begin(const DevScene& S, Ray& R, const float
     }
     R.t = 0.0f;
     R.steps = 0;
-    enter_leaf<BF16>(S, R);
+    finish_leaf<BF16>(S, R, __ldg(leaf_entry(S, R.v)));
 }
 
 enum StepResult { kInside = 0, kTop = 1, kGround = 2 };
 
-// Cross the exit face of the current leaf.  On a periodic wrap the segment
-// restarts at the exit point (o on the face exactly, t = 0); *wrapped_dt
-// receives the distance covered by the finished segment (else 0).
-template <bool BF16>
-__device__ __forceinline__ int step_leaf(const DevScene& S, Ray& R, float* wrapped_dt)
+// First half of crossing the exit face of the current leaf: the voxel index
+// on the far side and, for x / y, the periodic wrap.  On a wrap the segment
+// restarts at the exit point (o on the face exactly, t = 0) and *wrapped_dt
+// receives the distance covered by the finished segment.  p receives the
+// exit point (before any wrap shift).  The caller then loads the leaf-map
+// entry of R.v and calls finish_leaf (when the result is kInside).
+__device__ __forceinline__ int step_face(const DevScene& S, Ray& R, float p[3], float* wrapped_dt)
 {
     const int ax = R.ax;
     const float te = R.texit;
-    float p[3];
+    const int s = 3 * R.lev;
     int nv[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         p[b] = __fmaf_rn(te, R.d[b], R.o[b]);
-        if (b == ax) nv[b] = R.d[b] > 0.0f ? R.hi[b] + 1 : R.lo[b] - 1;
-        else nv[b] = locate(p[b], R.d[b], S.h[b], S.inv_h[b], R.lo[b], R.hi[b]);
+        const int lo = (R.v[b] >> s) << s;
+        const int hi = min(lo + (1 << s), S.n[b]) - 1;
+        if (b == ax) nv[b] = R.d[b] > 0.0f ? hi + 1 : lo - 1;
+        else nv[b] = locate(p[b], R.d[b], S.h[b], S.inv_h[b], lo, hi);
     }
     *wrapped_dt = 0.0f;
+    R.t = te;
     if (ax == 2) {
-        R.t = te;
         if (nv[2] < 0) return kGround;
         if (nv[2] >= S.n[2]) return kTop;
     } else {
-        // periodic x / y: wrap the index; the segment restarts on the face
         int wrapped = 0;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -213,24 +221,24 @@ __device__ __forceinline__ int step_leaf(const DevScene& S, Ray& R, float* wrapp
                 if (b == ax) R.o[b] = (wrapped == 1) ? S.Lper[b < 2 ? b : 0] : 0.0f;
             }
             R.t = 0.0f;
-        } else {
-            R.t = te;
         }
     }
     R.v[0] = nv[0]; R.v[1] = nv[1]; R.v[2] = nv[2];
     ++R.steps;
-    enter_leaf<BF16>(S, R);
     return kInside;
 }
 
-// Point at distance t and its voxel, clamped into the current leaf (so that
-// the extinction read there is bounded by the leaf majorant).
+// Point at distance R.t and its voxel, clamped into the current leaf (so
+// that the extinction read there is bounded by the leaf majorant).
 __device__ __forceinline__ void point_in_leaf(const DevScene& S, const Ray& R, float p[3], int vi[3])
 {
+    const int s = 3 * R.lev;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        const int lo = (R.v[a] >> s) << s;
+        const int hi = min(lo + (1 << s), S.n[a]) - 1;
         p[a] = __fmaf_rn(R.t, R.d[a], R.o[a]);
-        vi[a] = locate(p[a], R.d[a], S.h[a], S.inv_h[a], R.lo[a], R.hi[a]);
+        vi[a] = locate(p[a], R.d[a], S.h[a], S.inv_h[a], lo, hi);
     }
 }
 

@@ -20,10 +20,20 @@
 //     (t *= 1 - k/M, Russian roulette below 0.1) or delta tracking.
 //   events: HG scattering with weight omega, Lambertian ground with weight
 //     albedo, Russian roulette below w = 0.01; escape at the top.
-// Random numbers: path id p, event e: stream (e, 0) for the flight, the new
-// direction and roulette; (e, 1) for that vertex's sun ray; (0, 2) for the
-// camera jitter / ground point; (0, 3) for the direct sun ray of a flux path.
+// Random numbers: path id p, event e: stream (e, 0) for the flight (block j
+// for its j-th tentative collision, a fixed block for the vertex ending it);
+// (e, 1) for that vertex's sun ray; (0, 2) for the camera jitter / ground
+// point; (0, 3) for the direct sun ray of a flux path.
+//
+// Loop structure (one iteration): flush finished chunks and claim new ones
+// (convergent), start paths and rays at one site each, then one traversal
+// step whose single 8-byte load fetches either the voxel of a tentative
+// collision or the leaf-map entry of the next leaf, then the rare events.
 #include "mcrt_internal.h"
+
+#ifndef MCRT_TRACE_MIN_BLOCKS
+#define MCRT_TRACE_MIN_BLOCKS 1   // resident blocks of 128 threads the register budget must allow
+#endif
 
 namespace mcrt {
 
@@ -32,6 +42,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 enum Kind { kMain = 0, kSunLocal = 1, kSunDirect = 2 };
+enum Event { EV_NONE = 0, EV_REAL, EV_GROUND, EV_ESCAPE, EV_SUN_END, EV_ABORT };
 
 // Counter slots (see mcrt_tally_counters).
 enum {
@@ -39,241 +50,91 @@ enum {
     C_SUN_TENT = 5, C_SUN_LEAF = 6, C_SUN_RAYS = 7, C_ABORT = 8, C_FLIGHTS = 9
 };
 constexpr int kCounters = 10;
+// Extra slots filled with atomicMax in counting mode: [10] most loop
+// iterations spent on one path, [11] longest time (ns) a warp ran before the
+// work queue ran dry, [12] longest time (ns) a warp ran in total.
+enum { C_MAX_ITERS = 10, C_T_DRY = 11, C_T_END = 12 };
 
 template <int SENSOR, bool BF16, bool COUNT>
-__global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ TraceParams P)
+__global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
+    constexpr int NQ = (SENSOR == kCamera) ? 1 : 3;   // quantities per path
     const DevScene& S = P.S;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // ---- per-lane path state ----------------------------------------------
-    unsigned long long pid = 0, pend = 0;
-    bool have = false;         // a path (or a chunk) is assigned
-    bool exhausted = false;    // warp-uniform: no more work to claim
+    // ---- per-lane state ------------------------------------------------------
+    unsigned long long pid = 0, pend = 0;   // current path, end of the lane's chunk
+    bool chunk = false;                     // the lane holds a chunk
+    bool inflight = false;                  // path pid is being traced
+    bool exhausted = false;                 // warp-uniform: nothing left to claim
+    unsigned cell = 0;                      // tally cell of the chunk
+    float acc[2 * NQ];                      // chunk sums of x and x^2
+#pragma unroll
+    for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
     Ray R;
     int kind = kMain;
-    float tau = 0.0f, Ts = 1.0f;
-    float w = 1.0f, score = 0.0f, cf = 0.0f, tdir = 0.0f;
-    uint32_t ev = 0;
+    bool need_begin = false;
+    uint32_t c2 = 0, blk = 1, ev = 0;
+    float tau = 0.0f, Ts = 1.0f, w = 1.0f, score = 0.0f, cf = 0.0f, tdir = 0.0f;
     bool term_after = false;
-    float vx[3] = {0, 0, 0}, nd[3] = {0, 0, 1};
-    Draws dm, ds;
-    dm.reset(0, 0);
-    ds.reset(0, 1);
-    // tallies: camera chunk sums (flushed per chunk), flux lane sums
-    double c1 = 0.0, c2 = 0.0;
-    double f[6] = {0, 0, 0, 0, 0, 0};
-    bool flush = false;
-    unsigned flush_cell = 0;
-    unsigned long long cnt[kCounters] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float vx[3] = {0.0f, 0.0f, 0.0f}, nd[3] = {0.0f, 0.0f, 1.0f};
+    unsigned long long cnt[kCounters];
+#pragma unroll
+    for (int q = 0; q < kCounters; ++q) cnt[q] = 0;
+    uint32_t path_iters = 0, max_iters = 0;
     const float mu0 = S.sun[2];
-
-    uint64_t t_start = 0;
-    if (P.deadline_ns) t_start = globaltimer_ns();
+    uint64_t t_start = 0, t_dry = 0;
+    if (P.deadline_ns || COUNT) t_start = globaltimer_ns();
     uint32_t iter = 0;
 
-    // Start the sun ray from vx toward the sun (stream (event, stream)).
-    auto begin_sun = [&](uint32_t event, uint32_t stream, int k) {
-        const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
-        ds.reset(event, stream);
-        ray_begin<BF16>(S, R, vx, S.sun);
-        kind = k;
-        Ts = 1.0f;
-        tau = -__logf(ds.u(plo, phi, P.key));
-        if (COUNT) cnt[C_SUN_RAYS]++;
-    };
-    // Start the free flight of event ev from vx along nd.
-    auto begin_flight = [&]() {
-        const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
-        dm.reset(ev, 0);
-        ray_begin<BF16>(S, R, vx, nd);
-        kind = kMain;
-        tau = -__logf(dm.u(plo, phi, P.key));
-        if (COUNT) cnt[C_FLIGHTS]++;
-    };
-    // Initialise path pid; returns false if it ends at once (camera miss).
-    auto init_path = [&]() -> bool {
-        const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
-        w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f;
-        Draws dj;
-        dj.reset(0, 2);
-        if (SENSOR == kCamera) {
-            const unsigned long long pix = pid / P.spp;
-            const int px = (int)(pix % (unsigned long long)P.width);
-            const int py = (int)(pix / (unsigned long long)P.width);
-            const float jx = 1.0f - dj.u(plo, phi, P.key);
-            const float jy = 1.0f - dj.u(plo, phi, P.key);
-            const float sx = (2.0f * ((float)px + jx) / (float)P.width - 1.0f) * P.tan_half;
-            const float sy = (2.0f * ((float)py + jy) / (float)P.height - 1.0f) * P.tan_half * P.aspect;
-            float d[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) d[a] = P.cam_f[a] + sx * P.cam_r[a] + sy * P.cam_u[a];
-            const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            d[0] *= inv; d[1] *= inv; d[2] *= inv;
-            float p[3] = {P.cam_pos[0], P.cam_pos[1], P.cam_pos[2]};
-            if (p[2] > P.Lz) {
-                if (!(d[2] < 0.0f)) return false;
-                const float t = (P.Lz - p[2]) / d[2];
-                p[0] += t * d[0];
-                p[1] += t * d[1];
-                p[2] = P.Lz;
-            } else if (p[2] < 0.0f) {
-                return false;
-            }
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                p[a] -= floorf(p[a] / S.Lper[a]) * S.Lper[a];
-                if (!(p[a] < S.Lper[a]) || p[a] < 0.0f) p[a] = 0.0f;
-            }
-            vx[0] = p[0]; vx[1] = p[1]; vx[2] = p[2];
-            nd[0] = d[0]; nd[1] = d[1]; nd[2] = d[2];
-            begin_flight();
-        } else {
-            const float u0 = dj.u(plo, phi, P.key), u1 = dj.u(plo, phi, P.key);
-            const float u2 = dj.u(plo, phi, P.key), u3 = dj.u(plo, phi, P.key);
-            vx[0] = (1.0f - u0) * S.Lper[0];
-            vx[1] = (1.0f - u1) * S.Lper[1];
-            vx[2] = 0.0f;
-            if (!(vx[0] < S.Lper[0])) vx[0] = 0.0f;
-            if (!(vx[1] < S.Lper[1])) vx[1] = 0.0f;
-            cosine_up(u2, u3, nd);
-            begin_sun(0, 3, kSunDirect);
-        }
-        return true;
-    };
-    // Score the finished path pid.
-    auto score_path = [&]() {
-        if (COUNT) cnt[C_PATHS]++;
-        if (SENSOR == kCamera) {
-            c1 += (double)score;
-            c2 += (double)score * (double)score;
-        } else {
-            const double td = (double)tdir;
-            const double tf = (double)kPi / (double)mu0 * (double)score;
-            const double tt = td + tf;
-            f[0] += td; f[1] += td * td;
-            f[2] += tf; f[3] += tf * tf;
-            f[4] += tt; f[5] += tt * tt;
-        }
-    };
-    // Move on after path pid ended: next path of the chunk, or mark idle.
-    auto next_path = [&]() {
-        for (;;) {
-            ++pid;
-            if (pid >= pend) {
-                have = false;
-                if (SENSOR == kCamera) {
-                    flush = true;
-                    flush_cell = (unsigned)((pid - 1) / P.spp);
-                }
-                return;
-            }
-            if (init_path()) return;
-            score_path();
-        }
-    };
-    // After the sun ray of a vertex (or none): add the estimate, continue.
-    auto after_vertex = [&]() {
-        score += cf * Ts;
-        if (term_after) {
-            score_path();
-            next_path();
-        } else {
-            ++ev;
-            begin_flight();
-        }
-    };
-    // Real collision (volume) or ground hit at point p of the flight.
-    auto vertex = [&](const float p[3], bool ground, float k_tot) {
-        const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
-        const int order = (int)ev + 1;
-        const bool score_it = (P.max_order == 0) || (order <= P.max_order);
-        if (!ground) {
-            const float om = omega_at(S, k_tot);
-            const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
-            cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
-            w *= om;
-            const float xi1 = dm.u(plo, phi, P.key);
-            const float xi2 = dm.u(plo, phi, P.key);
-            rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
-            if (COUNT) cnt[C_REAL]++;
-        } else {
-            cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
-            w *= S.albedo;
-            const float xi1 = dm.u(plo, phi, P.key);
-            const float xi2 = dm.u(plo, phi, P.key);
-            cosine_up(xi1, xi2, nd);
-            if (COUNT) cnt[C_GROUND]++;
-        }
-        term_after = (P.max_order > 0) && (order >= P.max_order);
-        if (!term_after && w < 0.01f) {
-            if (dm.u(plo, phi, P.key) * 0.01f <= w) w = 0.01f;
-            else term_after = true;
-        }
-        vx[0] = p[0]; vx[1] = p[1]; vx[2] = ground ? 0.0f : p[2];
-        if (score_it) {
-            begin_sun(ev, 1, kSunLocal);
-        } else {
-            Ts = 0.0f;
-            after_vertex();
-        }
-    };
-    // A sun ray ended with transmissivity Ts.
-    auto end_sun = [&]() {
-        if (kind == kSunDirect) {
-            tdir = Ts;
-            ev = 0;
-            begin_flight();
-        } else {
-            after_vertex();
-        }
-    };
-
     for (;;) {
-        // ---- convergent section: flush tallies, refill idle lanes ---------
-        if (SENSOR == kCamera) {
-            unsigned pend_mask = __ballot_sync(kFull, flush);
-            while (pend_mask) {
-                const int src = __ffs(pend_mask) - 1;
-                const unsigned cell = __shfl_sync(kFull, flush_cell, src);
-                const bool mine = flush && flush_cell == cell;
-                double a = mine ? c1 : 0.0, b = mine ? c2 : 0.0;
+        // ---- flush finished chunks: lanes sharing a cell are summed first --
+        bool pending = chunk && !inflight && pid >= pend;
+        if (pending) chunk = false;
+        unsigned fmask = __ballot_sync(kFull, pending);
+        while (fmask) {
+            const int src = __ffs(fmask) - 1;
+            const unsigned c = __shfl_sync(kFull, cell, src);
+            const bool mine = pending && cell == c;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(kFull, a, o);
-                    b += __shfl_xor_sync(kFull, b, o);
-                }
-                if (lane == src) {
-                    atomicAdd(P.s1 + cell, a);
-                    atomicAdd(P.s2 + cell, b);
-                }
-                if (mine) { flush = false; c1 = 0.0; c2 = 0.0; }
-                pend_mask = __ballot_sync(kFull, flush);
+            for (int q = 0; q < 2 * NQ; ++q) {
+                double a = mine ? (double)acc[q] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+                if (lane == src) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)c * NQ + (q >> 1), a);
             }
+            if (mine) {
+                pending = false;
+#pragma unroll
+                for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
+            }
+            fmask = __ballot_sync(kFull, pending);
         }
-        const unsigned idle = __ballot_sync(kFull, !have);
+        // ---- claim chunks for idle lanes (one atomic per warp) -------------
+        const unsigned idle = __ballot_sync(kFull, !chunk);
         if (idle && !exhausted) {
             const int nidle = __popc(idle);
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(&P.work->next, (unsigned long long)nidle * P.chunk);
             base = __shfl_sync(kFull, base, leader);
-            if (base + (unsigned long long)nidle * P.chunk >= P.total) exhausted = true;
-            if (!have) {
+            if (base + (unsigned long long)nidle * P.chunk >= P.total) {
+                exhausted = true;
+                if (COUNT) t_dry = globaltimer_ns();
+            }
+            if (!chunk) {
                 pid = base + (unsigned long long)__popc(idle & lt_mask) * P.chunk;
                 if (pid < P.total) {
                     pend = min(pid + (unsigned long long)P.chunk, P.total);
-                    have = true;
-                    if (!init_path()) {
-                        score_path();
-                        next_path();
-                    }
+                    chunk = true;
+                    inflight = false;
+                    cell = (SENSOR == kCamera) ? (unsigned)(pid / P.spp) : 0u;
                 }
             }
         }
-        if (!__any_sync(kFull, have)) break;
-        // ---- deadline / cancel, checked every 1024 iterations -------------
+        if (!__any_sync(kFull, chunk)) break;
+        // ---- deadline / cancel, every 1024 iterations ------------------------
         if ((++iter & 1023u) == 0 && (P.deadline_ns || P.cancel)) {
             int stop = 0;
             if (lane == 0) {
@@ -288,91 +149,253 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
                 break;
             }
         }
-        if (!have) continue;
+        // ---- start path pid (one site) ---------------------------------------
+        if (chunk && !inflight) {
+            const uint4 x = draw_block(pid, 2u, 0u, P.key);
+            w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
+            if (COUNT) path_iters = 0;
+            if constexpr (SENSOR == kCamera) {
+                const unsigned long long pix = pid / P.spp;
+                const int px = (int)(pix % (unsigned long long)P.width);
+                const int py = (int)(pix / (unsigned long long)P.width);
+                const float jx = 1.0f - u01(x.x), jy = 1.0f - u01(x.y);
+                const float sx = (2.0f * ((float)px + jx) / (float)P.width - 1.0f) * P.tan_half;
+                const float sy = (2.0f * ((float)py + jy) / (float)P.height - 1.0f) * P.tan_half * P.aspect;
+                float d[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) d[a] = P.cam_f[a] + sx * P.cam_r[a] + sy * P.cam_u[a];
+                const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                float q[3] = {P.cam_pos[0], P.cam_pos[1], P.cam_pos[2]};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) d[a] *= inv;
+                bool enters = true;
+                if (q[2] > P.Lz) {
+                    if (d[2] < 0.0f) {
+                        const float t = (P.Lz - q[2]) / d[2];
+                        q[0] += t * d[0];
+                        q[1] += t * d[1];
+                        q[2] = P.Lz;
+                    } else {
+                        enters = false;
+                    }
+                } else if (q[2] < 0.0f) {
+                    enters = false;
+                }
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    q[a] -= floorf(q[a] / S.Lper[a]) * S.Lper[a];
+                    if (!(q[a] < S.Lper[a]) || q[a] < 0.0f) q[a] = 0.0f;
+                }
+                if (enters) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) { vx[a] = q[a]; nd[a] = d[a]; }
+                    kind = kMain;
+                    c2 = 0u;
+                    need_begin = true;
+                    inflight = true;
+                } else {
+                    // a path that misses the field scores 0
+                    if (COUNT) cnt[C_PATHS]++;
+                    ++pid;
+                }
+            } else {
+                vx[0] = (1.0f - u01(x.x)) * S.Lper[0];
+                vx[1] = (1.0f - u01(x.y)) * S.Lper[1];
+                vx[2] = 0.0f;
+                if (!(vx[0] < S.Lper[0])) vx[0] = 0.0f;
+                if (!(vx[1] < S.Lper[1])) vx[1] = 0.0f;
+                cosine_up(u01(x.z), u01(x.w), nd);
+                kind = kSunDirect;
+                c2 = 3u;
+                Ts = 1.0f;
+                need_begin = true;
+                inflight = true;
+            }
+        }
+        if (!inflight) continue;
+        if (COUNT) ++path_iters;
 
-        // ---- one traversal step of the current ray --------------------------
-        const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
+        // ---- start a ray (one site): flight from vx along nd, or sun ray ----
+        if (need_begin) {
+            ray_begin<BF16>(S, R, vx, kind == kMain ? nd : S.sun);
+            const uint4 x = draw_block(pid, c2, 0u, P.key);
+            tau = -__logf(u01(x.x));
+            blk = 1;
+            need_begin = false;
+            if (COUNT) {
+                if (kind == kMain) cnt[C_FLIGHTS]++;
+                else cnt[C_SUN_RAYS]++;
+            }
+        }
+
+        // ---- one traversal step ----------------------------------------------
+        int evc = EV_NONE;
+        float p[3];
+        float k = 0.0f;
         const float seg = R.texit - R.t;
         const float Mseg = R.M * seg;
-        if (R.M > 0.0f && tau < Mseg) {
-            // tentative collision inside the leaf
+        const bool tent = R.M > 0.0f && tau < Mseg;
+        const uint2* ptr = nullptr;
+        uint32_t sub = 0;
+        int st = kInside;
+        if (tent) {
             R.t = fminf(R.t + __fdividef(tau, R.M), R.texit);
-            float p[3];
             int vi[3];
             point_in_leaf(S, R, p, vi);
-            const float k = __fadd_rn(kfetch<BF16>(S, vi[0], vi[1], vi[2]), S.k_gas);
+            const size_t idx = brick_index(S, vi[0], vi[1], vi[2]);
+            if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
+            else { ptr = reinterpret_cast<const uint2*>(S.vox) + (idx >> 1); sub = (uint32_t)idx & 1u; }
+        } else {
+            tau -= Mseg;
+            float wdt;
+            st = step_face(S, R, p, &wdt);
+            if (st == kInside) ptr = leaf_entry(S, R.v);
+        }
+        uint2 val = make_uint2(0u, 0u);
+        if (ptr) val = __ldg(ptr);                       // voxel or leaf entry
+        if (tent) {
+            float kv;
+            if (BF16) {
+                const uint32_t wd = (sub & 2u) ? val.y : val.x;
+                kv = __uint_as_float(((wd >> ((sub & 1u) * 16u)) & 0xFFFFu) << 16);
+            } else {
+                kv = __uint_as_float(sub ? val.y : val.x);
+            }
+            k = __fadd_rn(kv, S.k_gas);
+            const uint4 x = draw_block(pid, c2, blk, P.key);
+            ++blk;
+            const float u0 = u01(x.x);
+            const float nt = -__logf(u01(x.y));
             if (kind == kMain) {
                 if (COUNT) cnt[C_TENT]++;
-                if (dm.u(plo, phi, P.key) * R.M <= k) {
-                    vertex(p, false, k);
-                } else {
-                    tau = -__logf(dm.u(plo, phi, P.key));
-                }
+                if (u0 * R.M <= k) evc = EV_REAL;
+                else tau = nt;
             } else {
                 if (COUNT) cnt[C_SUN_TENT]++;
                 bool ended = false;
                 if (P.sun_mode == MCRT_SUN_DELTA) {
-                    if (ds.u(plo, phi, P.key) * R.M <= k) { Ts = 0.0f; ended = true; }
+                    if (u0 * R.M <= k) { Ts = 0.0f; ended = true; }
                 } else {
                     Ts *= 1.0f - __fdividef(k, R.M);
                     if (!(Ts > 0.0f)) { Ts = 0.0f; ended = true; }
                     else if (Ts < 0.1f) {
-                        if (ds.u(plo, phi, P.key) * 0.1f <= Ts) Ts = 0.1f;
+                        if (u0 * 0.1f <= Ts) Ts = 0.1f;
                         else { Ts = 0.0f; ended = true; }
                     }
                 }
-                if (ended) end_sun();
-                else tau = -__logf(ds.u(plo, phi, P.key));
+                if (ended) evc = EV_SUN_END;
+                else tau = nt;
             }
-        } else {
-            // cross to the next leaf
-            tau -= Mseg;
-            float wdt;
-            const int st = step_leaf<BF16>(S, R, &wdt);
+        } else if (st == kInside) {
             if (COUNT) {
                 if (kind == kMain) cnt[C_LEAF]++;
                 else cnt[C_SUN_LEAF]++;
             }
-            if (st == kInside && R.steps > P.max_steps) {
+            finish_leaf<BF16>(S, R, val);
+            if (R.steps > P.max_steps) evc = EV_ABORT;
+        } else if (st == kTop) {
+            evc = (kind == kMain) ? EV_ESCAPE : EV_SUN_END;
+        } else {
+            if (kind == kMain) evc = EV_GROUND;
+            else { Ts = 0.0f; evc = EV_SUN_END; }
+        }
+
+        // ---- events (rare) ----------------------------------------------------
+        if (evc != EV_NONE) {
+            bool path_done = false;
+            if (evc == EV_ABORT) {
                 if (COUNT) cnt[C_ABORT]++;
-                if (kind == kMain) { score_path(); next_path(); }
-                else { Ts = 0.0f; end_sun(); }
-            } else if (st == kTop) {
-                if (kind == kMain) { score_path(); next_path(); }
-                else end_sun();
-            } else if (st == kGround) {
-                if (kind == kMain) {
-                    float p[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) p[a] = __fmaf_rn(R.t, R.d[a], R.o[a]);
+                if (kind == kMain) path_done = true;
+                else { Ts = 0.0f; evc = EV_SUN_END; }
+            }
+            if (evc == EV_REAL || evc == EV_GROUND) {
+                // vertex: weight, estimate factor toward the sun, new direction
+                const bool ground = evc == EV_GROUND;
+                const uint4 x = draw_block(pid, ev << 2, kBlockVertex, P.key);
+                const float xi1 = u01(x.x), xi2 = u01(x.y), xr = u01(x.z);
+                const int order = (int)ev + 1;
+                const bool score_it = (P.max_order == 0) || (order <= P.max_order);
+                if (!ground) {
+                    const float om = omega_at(S, k);
+                    const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
+                    cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
+                    w *= om;
+                    rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
+                    if (COUNT) cnt[C_REAL]++;
+                } else {
+                    cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
+                    w *= S.albedo;
+                    cosine_up(xi1, xi2, nd);
+                    p[2] = 0.0f;
                     p[0] = fminf(fmaxf(p[0], 0.0f), S.Lper[0]);
                     p[1] = fminf(fmaxf(p[1], 0.0f), S.Lper[1]);
                     if (!(p[0] < S.Lper[0])) p[0] = 0.0f;
                     if (!(p[1] < S.Lper[1])) p[1] = 0.0f;
-                    vertex(p, true, 0.0f);
+                    if (COUNT) cnt[C_GROUND]++;
+                }
+                term_after = (P.max_order > 0) && (order >= P.max_order);
+                if (!term_after && w < 0.01f) {
+                    if (xr * 0.01f <= w) w = 0.01f;
+                    else term_after = true;
+                }
+                vx[0] = p[0]; vx[1] = p[1]; vx[2] = p[2];
+                if (score_it) {
+                    kind = kSunLocal;
+                    c2 = (ev << 2) | 1u;
+                    Ts = 1.0f;
+                    need_begin = true;
                 } else {
                     Ts = 0.0f;
-                    end_sun();
+                    evc = EV_SUN_END;
                 }
+            }
+            if (evc == EV_SUN_END) {
+                if (kind == kSunDirect) {
+                    tdir = Ts;
+                    ev = 0;
+                    kind = kMain;
+                    c2 = 0u;
+                    need_begin = true;
+                } else {
+                    score += cf * Ts;
+                    if (term_after) {
+                        path_done = true;
+                    } else {
+                        ++ev;
+                        kind = kMain;
+                        c2 = ev << 2;
+                        need_begin = true;
+                    }
+                }
+            }
+            if (evc == EV_ESCAPE) path_done = true;
+            if (path_done) {
+                if constexpr (SENSOR == kCamera) {
+                    acc[0] += score;
+                    acc[1] += score * score;
+                } else {
+                    const float tf = kPi / mu0 * score;
+                    const float tt = tdir + tf;
+                    acc[0] += tdir; acc[1] += tdir * tdir;
+                    acc[2] += tf; acc[3] += tf * tf;
+                    acc[4] += tt; acc[5] += tt * tt;
+                }
+                if (COUNT) {
+                    cnt[C_PATHS]++;
+                    max_iters = max(max_iters, path_iters);
+                }
+                inflight = false;
+                need_begin = false;
+                ++pid;
             }
         }
     }
 
-    // ---- end of work: flush lane sums ---------------------------------------
-    if (SENSOR == kCamera) {
-        // a deadline exit may leave chunk sums pending
-        if (flush || (have && c1 != 0.0)) {
-            const unsigned cell = flush ? flush_cell : (unsigned)(pid / P.spp);
-            atomicAdd(P.s1 + cell, c1);
-            atomicAdd(P.s2 + cell, c2);
-        }
-    } else {
+    // ---- partial sums left by a deadline / cancel exit ------------------------
+    if (chunk) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            double a = f[q];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
-            if (lane == 0 && a != 0.0) atomicAdd((q & 1) ? P.s2 + q / 2 : P.s1 + q / 2, a);
-        }
+        for (int q = 0; q < 2 * NQ; ++q)
+            if (acc[q] != 0.0f) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)cell * NQ + (q >> 1), (double)acc[q]);
     }
     if (COUNT) {
 #pragma unroll
@@ -380,6 +403,14 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
             unsigned long long a = cnt[q];
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
             if (lane == 0 && a) atomicAdd(P.counters + q, a);
+        }
+        unsigned mi = max_iters;
+        for (int o = 16; o > 0; o >>= 1) mi = max(mi, __shfl_xor_sync(kFull, mi, o));
+        if (lane == 0) {
+            const uint64_t t_end = globaltimer_ns();
+            atomicMax(P.counters + C_MAX_ITERS, (unsigned long long)mi);
+            if (t_dry) atomicMax(P.counters + C_T_DRY, (unsigned long long)(t_dry - t_start));
+            atomicMax(P.counters + C_T_END, (unsigned long long)(t_end - t_start));
         }
     }
 }
@@ -396,15 +427,16 @@ __global__ void finalize_kernel(const double* __restrict__ s1, const double* __r
     out[2 * i + 1] = n > 1.0 ? sqrt(var / (n - 1.0)) : 0.0;
 }
 
-// One thread walks one ray and records its leaves (traversal check).
+// One thread walks one ray and records its leaves (traversal check), with
+// the same device functions as the tracer.
 template <bool BF16>
 __global__ void debug_dda_kernel(DevScene S, float ox, float oy, float oz, float dx, float dy, float dz, int cap,
                                  int* cells, float* tio, int* count_status)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     Ray R;
-    const float p[3] = {ox, oy, oz}, d[3] = {dx, dy, dz};
-    ray_begin<BF16>(S, R, p, d);
+    const float p0[3] = {ox, oy, oz}, d[3] = {dx, dy, dz};
+    ray_begin<BF16>(S, R, p0, d);
     float tbase = 0.0f;
     int n = 0, status = 0;
     for (;;) {
@@ -416,11 +448,12 @@ __global__ void debug_dda_kernel(DevScene S, float ox, float oy, float oz, float
         tio[2 * n + 0] = __fadd_rn(tbase, R.t);
         tio[2 * n + 1] = __fadd_rn(tbase, R.texit);
         ++n;
-        float wdt;
-        const int st = step_leaf<BF16>(S, R, &wdt);
+        float wdt, p[3];
+        const int st = step_face(S, R, p, &wdt);
         if (wdt != 0.0f) tbase = __fadd_rn(tbase, wdt);
         if (st == kTop) { status = 1; break; }
         if (st == kGround) { status = 2; break; }
+        finish_leaf<BF16>(S, R, __ldg(leaf_entry(S, R.v)));
         if (R.steps > (1u << 22)) { status = 4; break; }
     }
     count_status[0] = n;

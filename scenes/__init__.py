@@ -156,8 +156,11 @@ def cumulus(nx: int = 512, ny: int = 512, nz: int = 160, seed: int = 0, cover: f
     top = np.where(f > thr, base + 2.0 * (f - thr) / (fmax - thr), base)   # [y][x]
     zc = (np.arange(nz) + 0.5) * dz
     incloud = (zc[:, None, None] >= base) & (zc[:, None, None] < top[None, :, :])
-    g3 = _band_limited_3d(nx, ny, nz, 24, 6, r)
-    lwc = 0.3 * np.exp(0.6 * g3.astype(np.float64))         # g m^-3
+    g3 = _band_limited_3d(nx, ny, nz, 24, 6, r).astype(np.float64)
+    # log-normal LWC with median 0.3 g m^-3 and sigma_ln 0.6 over the cloudy voxels
+    zc_ = g3[incloud]
+    g3 = (g3 - np.median(zc_)) / zc_.std()
+    lwc = 0.3 * np.exp(0.6 * g3)                            # g m^-3
     rho_w = 1.0e6                                           # g m^-3
     r_eff = 10e-6                                           # m
     k_cloud = 1.5 * lwc / (rho_w * r_eff) * 1000.0          # m^-1 -> km^-1
