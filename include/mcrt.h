@@ -219,6 +219,29 @@ MCRT_API int mcrt_trace_camera(mcrt_scene* scene, const mcrt_camera_desc* camera
 MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, const mcrt_trace_opts* opts,
                     mcrt_tally** tally_inout);
 
+/* Camera trace that allocates no device memory (the paper has no
+ * counterpart; this is a convenience for callers that cannot allocate GPU
+ * memory while tracing -- code living inside another framework's memory
+ * budget, real-time loops that must not touch the allocator).  Same physics,
+ * random numbers and options as mcrt_trace_camera, but the working memory
+ * (work counter, status, FP64 per-pixel sums) is one statically sized
+ * device array inside the library, and the per-pixel mean and standard
+ * error (row-major, width * height doubles each) are written to d_mean and
+ * d_stderr, device buffers owned by the caller.
+ *  - At most 65536 pixels (256 x 256); larger images return
+ *    MCRT_ERR_BOUNDS before any GPU work.
+ *  - The array (about 1 MiB) stays allocated on every GPU that loads the
+ *    library until the process exits.
+ *  - All calls share it: each call clears what it uses first, but calls
+ *    whose GPU work overlaps (several streams or threads on one device)
+ *    race.  Issue them one after another on one stream.
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before capturing any stream.
+ *  - The scene's majorants must be built.  Synchronises the context stream;
+ *    errors as mcrt_trace_camera plus MCRT_ERR_BOUNDS. */
+MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
+                                       const mcrt_trace_opts* opts, double* d_mean, double* d_stderr);
+
 /* --------------------------------------------------------------------- */
 /* Tallies                                                                */
 /* --------------------------------------------------------------------- */

@@ -97,6 +97,7 @@ def _load():
         "mcrt_trace_opts_default": [P(TraceOpts)],
         "mcrt_trace_camera": [vp, P(CameraDesc), u32, u64, P(TraceOpts), P(vp)],
         "mcrt_trace_flux": [vp, u64, u64, P(TraceOpts), P(vp)],
+        "mcrt_trace_camera_noalloc": [vp, P(CameraDesc), u32, u64, P(TraceOpts), vp, vp],
         "mcrt_tally_shape": [vp, P(i32), P(i32)],
         "mcrt_tally_read": [vp, P(f64), P(f64), P(u64), C.c_size_t],
         "mcrt_tally_read_sums": [vp, P(f64), P(f64), C.c_size_t],
@@ -225,6 +226,14 @@ def mcrt_trace_flux(ctx, scene, npaths: int, seed: int, opts: TraceOpts, tally=N
     h = tally if tally is not None else C.c_void_p()
     _check(_load().mcrt_trace_flux(scene, npaths, seed, C.byref(opts), C.byref(h)), ctx)
     return h
+
+
+def mcrt_trace_camera_noalloc(ctx, scene, cam: CameraDesc, spp: int, seed: int, opts: TraceOpts,
+                              d_mean: int, d_stderr: int):
+    """Camera trace writing mean / SE into caller-owned device buffers
+    (addresses), with no device allocation inside the library."""
+    _check(_load().mcrt_trace_camera_noalloc(scene, C.byref(cam), spp, seed, C.byref(opts),
+                                             C.c_void_p(d_mean), C.c_void_p(d_stderr)), ctx)
 
 
 def mcrt_tally_shape(ctx, tally):
