@@ -176,8 +176,10 @@ typedef struct {
                                /* level > finest_level is tracked whole when   */
                                /* its majorant times its height is <= tau~;    */
                                /* INFINITY = coarsest level.  Default 1.        */
-    int32_t finest_level;      /* finest level tracked: 1 (default), or 0 to    */
-                               /* track voxels where no coarser cell qualifies  */
+    int32_t finest_level;      /* finest level tracked: 0 (default: a voxel is  */
+                               /* its own leaf where no coarser cell qualifies, */
+                               /* as unmerged voxels in Sec. 4.2), or 1 (level- */
+                               /* 1 cells are always merged)                    */
     int32_t max_order;         /* 0: all scattering orders; n: score events of  */
                                /* order <= n and stop after order n             */
     int32_t sun_mode;          /* MCRT_SUN_RATIO (default) or MCRT_SUN_DELTA    */
@@ -185,6 +187,10 @@ typedef struct {
     int32_t block_size;        /* threads per block; 0 = auto                   */
     int32_t grid_size;         /* blocks; 0 = SMs x resident blocks             */
     int32_t count_events;      /* 1: also count collisions and leaf steps       */
+    int32_t rare_batch;        /* GPU lanes of a warp that must be waiting for  */
+                               /* a path start, ray start or vertex before that */
+                               /* work runs (1..32; 0 = default 8).  Launch     */
+                               /* shape only: results do not depend on it       */
     double deadline_ms;        /* > 0: stop and report MCRT_ERR_TIMEOUT after   */
                                /* this much device time                         */
     const volatile int32_t* cancel_flag; /* NULL, or a flag in host-mapped or   */
@@ -265,7 +271,10 @@ MCRT_API int mcrt_tally_read_sums(const mcrt_tally* tally, double* s1, double* s
  * [7] sun rays, [8] aborted paths (step guard), [9] free flights started,
  * and, when n >= 13: [10] most loop iterations spent on one path, [11] the
  * longest time in ns a GPU warp ran before the work queue ran dry, [12] the
- * longest time in ns a warp ran in total.  n >= 10. */
+ * longest time in ns a warp ran in total, and when n >= 22, [13..21] SM
+ * clock cycles summed over warps spent in the sections of the trace loop
+ * (loop top, random block, path start, ray start, step, vertex, load,
+ * after-load, ray/path end).  n >= 10. */
 MCRT_API int mcrt_tally_counters(const mcrt_tally* tally, uint64_t* counters, size_t n);
 
 /* Device time of the trace kernel that filled the tally, in ms. */

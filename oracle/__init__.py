@@ -196,7 +196,7 @@ class Scene:
     dz: float
     levels: int
     tau_merge: float = 1.0
-    finest_level: int = 1
+    finest_level: int = 0
     k_clear: float = 0.0
     ssa_clear: float = 1.0
     ssa_cloud: float = 1.0

@@ -37,7 +37,9 @@ MCRT_SUN_RATIO = 0
 MCRT_SUN_DELTA = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
-                 "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total")
+                 "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
+                 "clk_top", "clk_philox", "clk_start", "clk_begin", "clk_step", "clk_vertex", "clk_load",
+                 "clk_after", "clk_end")
 
 
 class McrtError(RuntimeError):
@@ -62,7 +64,8 @@ class CameraDesc(C.Structure):
 class TraceOpts(C.Structure):
     _fields_ = [("tau_merge", C.c_float), ("finest_level", C.c_int32), ("max_order", C.c_int32),
                 ("sun_mode", C.c_int32), ("chunk", C.c_int32), ("block_size", C.c_int32),
-                ("grid_size", C.c_int32), ("count_events", C.c_int32), ("deadline_ms", C.c_double),
+                ("grid_size", C.c_int32), ("count_events", C.c_int32), ("rare_batch", C.c_int32),
+                ("deadline_ms", C.c_double),
                 ("cancel_flag", C.c_void_p)]
 
 

@@ -328,7 +328,7 @@ int mcrt_trace_opts_default(mcrt_trace_opts* o)
     if (!o) return fail(nullptr, MCRT_ERR_ARG, "mcrt_trace_opts_default: NULL");
     std::memset(o, 0, sizeof(*o));
     o->tau_merge = 1.0f;
-    o->finest_level = 1;
+    o->finest_level = 0;
     o->sun_mode = MCRT_SUN_RATIO;
     return MCRT_OK;
 }
@@ -349,6 +349,7 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
         return fail(ctx, MCRT_ERR_ARG, "%s: block_size must be a multiple of 32 up to 1024", who);
     if (o->block_size > 128) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: block_size above 128", who);
     if (o->grid_size < 0 || o->chunk < 0) return fail(ctx, MCRT_ERR_ARG, "%s: negative launch shape", who);
+    if (o->rare_batch < 0 || o->rare_batch > 32) return fail(ctx, MCRT_ERR_ARG, "%s: rare_batch must be in [0, 32]", who);
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     return MCRT_OK;
 }
@@ -415,6 +416,8 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     P.max_order = o->max_order;
     P.sun_mode = o->sun_mode;
     P.max_steps = 1u << 22;
+    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
+    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
     cudaEvent_t e0, e1;
     CK(ctx, cudaEventCreate(&e0));
     CK(ctx, cudaEventCreate(&e1));
@@ -502,6 +505,8 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
     }
     P.tan_half = (float)std::tan(0.5 * cam->fov_deg * M_PI / 180.0);
     P.aspect = (float)cam->height / (float)cam->width;
+    P.inv_width = 1.0f / (float)cam->width;
+    P.inv_height = 1.0f / (float)cam->height;
     P.Lz = (float)sc->n[2] * sc->h[2];
     return run_trace(sc, P, kCamera, o, t, who);
 }

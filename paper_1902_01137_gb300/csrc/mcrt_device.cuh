@@ -180,26 +180,38 @@ __device__ __forceinline__ void ray_begin(const DevScene& S, Ray& R, const float
 
 enum StepResult { kInside = 0, kTop = 1, kGround = 2 };
 
-// First half of crossing the exit face of the current leaf: the voxel index
-// on the far side and, for x / y, the periodic wrap.  On a wrap the segment
-// restarts at the exit point (o on the face exactly, t = 0) and *wrapped_dt
-// receives the distance covered by the finished segment.  p receives the
-// exit point (before any wrap shift).  The caller then loads the leaf-map
-// entry of R.v and calls finish_leaf (when the result is kInside).
-__device__ __forceinline__ int step_face(const DevScene& S, Ray& R, float p[3], float* wrapped_dt)
+// Point at distance tn along the current segment and its voxel on each axis,
+// clamped into the current leaf (so the extinction read there is bounded by
+// the leaf majorant).  With `face`, tn is the leaf exit and the exit axis
+// index instead steps across the face (hi + 1 or lo - 1).
+__device__ __forceinline__ void advance(const DevScene& S, const Ray& R, float tn, bool face, float p[3], int nv[3])
+{
+    const int s = 3 * R.lev;
+    int lo[3], hi[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        p[b] = __fmaf_rn(tn, R.d[b], R.o[b]);
+        lo[b] = (R.v[b] >> s) << s;
+        hi[b] = min(lo[b] + (1 << s), S.n[b]) - 1;
+        nv[b] = locate(p[b], R.d[b], S.h[b], S.inv_h[b], lo[b], hi[b]);
+    }
+    // the exit axis steps across the face (its located value is discarded)
+    if (face) {
+        if (R.ax == 0) nv[0] = R.d[0] > 0.0f ? hi[0] + 1 : lo[0] - 1;
+        else if (R.ax == 1) nv[1] = R.d[1] > 0.0f ? hi[1] + 1 : lo[1] - 1;
+        else nv[2] = R.d[2] > 0.0f ? hi[2] + 1 : lo[2] - 1;
+    }
+}
+
+// Complete a face crossing prepared by advance(face = true): the ground or
+// the top, or the periodic wrap of x / y (the segment then restarts on the
+// face: o on the face exactly, t = 0, *wrapped_dt = distance of the finished
+// segment), then the new voxel.  The caller loads the leaf-map entry of R.v
+// and calls finish_leaf when the result is kInside.
+__device__ __forceinline__ int cross_face(const DevScene& S, Ray& R, const float p[3], int nv[3], float* wrapped_dt)
 {
     const int ax = R.ax;
     const float te = R.texit;
-    const int s = 3 * R.lev;
-    int nv[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        p[b] = __fmaf_rn(te, R.d[b], R.o[b]);
-        const int lo = (R.v[b] >> s) << s;
-        const int hi = min(lo + (1 << s), S.n[b]) - 1;
-        if (b == ax) nv[b] = R.d[b] > 0.0f ? hi + 1 : lo - 1;
-        else nv[b] = locate(p[b], R.d[b], S.h[b], S.inv_h[b], lo, hi);
-    }
     *wrapped_dt = 0.0f;
     R.t = te;
     if (ax == 2) {
@@ -218,7 +230,7 @@ __device__ __forceinline__ int step_face(const DevScene& S, Ray& R, float p[3], 
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
                 R.o[b] = p[b];
-                if (b == ax) R.o[b] = (wrapped == 1) ? S.Lper[b < 2 ? b : 0] : 0.0f;
+                if (b == ax) R.o[b] = (wrapped == 1) ? (b == 0 ? S.Lper[0] : S.Lper[1]) : 0.0f;
             }
             R.t = 0.0f;
         }
@@ -228,18 +240,13 @@ __device__ __forceinline__ int step_face(const DevScene& S, Ray& R, float p[3], 
     return kInside;
 }
 
-// Point at distance R.t and its voxel, clamped into the current leaf (so
-// that the extinction read there is bounded by the leaf majorant).
-__device__ __forceinline__ void point_in_leaf(const DevScene& S, const Ray& R, float p[3], int vi[3])
+// Cross the exit face of the current leaf (advance + cross_face); p receives
+// the exit point before any wrap shift.
+__device__ __forceinline__ int step_face(const DevScene& S, Ray& R, float p[3], float* wrapped_dt)
 {
-    const int s = 3 * R.lev;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int lo = (R.v[a] >> s) << s;
-        const int hi = min(lo + (1 << s), S.n[a]) - 1;
-        p[a] = __fmaf_rn(R.t, R.d[a], R.o[a]);
-        vi[a] = locate(p[a], R.d[a], S.h[a], S.inv_h[a], lo, hi);
-    }
+    int nv[3];
+    advance(S, R, R.texit, true, p, nv);
+    return cross_face(S, R, p, nv, wrapped_dt);
 }
 
 // --------------------------------------------------------------------------
@@ -257,8 +264,8 @@ __device__ __forceinline__ float hg_pdf(float g, float mu)
 __device__ __forceinline__ float hg_sample_mu(float g, float xi)
 {
     if (fabsf(g) < 1e-4f) return 1.0f - 2.0f * xi;
-    const float s = (1.0f - g * g) / (1.0f - g + 2.0f * g * xi);
-    const float mu = (1.0f + g * g - s * s) / (2.0f * g);
+    const float s = __fdividef(1.0f - g * g, 1.0f - g + 2.0f * g * xi);
+    const float mu = __fdividef(1.0f + g * g - s * s, 2.0f * g);
     return fminf(fmaxf(mu, -1.0f), 1.0f);
 }
 
@@ -267,7 +274,7 @@ __device__ __forceinline__ float hg_sample_mu(float g, float xi)
 __device__ __forceinline__ void rotate_dir(const float d[3], float mu, float xi, float out[3])
 {
     const float sign = copysignf(1.0f, d[2]);
-    const float a = -1.0f / (sign + d[2]);
+    const float a = -__frcp_rn(sign + d[2]);
     const float b = d[0] * d[1] * a;
     const float b1x = 1.0f + sign * d[0] * d[0] * a, b1y = sign * b, b1z = -sign * d[0];
     const float b2x = b, b2y = sign + d[1] * d[1] * a, b2z = -d[1];
@@ -297,7 +304,7 @@ __device__ __forceinline__ float omega_at(const DevScene& S, float k_tot)
     const float k = k_tot - S.k_gas;
     const float kc = fmaxf(k - S.k_clear, 0.0f);
     const float kcl = k - kc;
-    return k_tot > 0.0f ? (kc * S.ssa_cloud + kcl * S.ssa_clear) / k_tot : 0.0f;
+    return k_tot > 0.0f ? __fdividef(kc * S.ssa_cloud + kcl * S.ssa_clear, k_tot) : 0.0f;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns()

@@ -59,7 +59,7 @@ struct mcrt_tally {
 
 namespace mcrt {
 
-constexpr int kNumCounters = 16;
+constexpr int kNumCounters = 24;
 
 // Work distribution and status shared by all blocks of a trace launch.
 struct WorkState {
@@ -77,11 +77,14 @@ struct TraceParams {
     int max_order;
     int sun_mode;
     uint32_t max_steps;
+    int rare_batch;            // lanes waiting for a rare phase that trigger it
+    int min_steppers;          // below this many stepping lanes, run rare phases anyway
     // camera
     int width, height;
     uint32_t spp;
     float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
     float tan_half, aspect;    // tan(fov/2), height/width
+    float inv_width, inv_height;
     float Lz;
     // outputs
     double* s1;

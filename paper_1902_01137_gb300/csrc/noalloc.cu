@@ -96,7 +96,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     if (!(cam->fov_deg > 0.0f && cam->fov_deg < 180.0f)) return nfail(ctx, MCRT_ERR_ARG, "%s: fov must be in (0, 180)", who);
     if (!(o->tau_merge >= 0.0f) || o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels ||
         o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA) || o->block_size < 0 ||
-        o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0))
+        o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
+        o->rare_batch < 0 || o->rare_batch > 32)
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return nfail(ctx, MCRT_ERR_ARG, "%s: device index too large", who);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -168,6 +169,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     }
     P.tan_half = (float)std::tan(0.5 * cam->fov_deg * M_PI / 180.0);
     P.aspect = (float)cam->height / (float)cam->width;
+    P.inv_width = 1.0f / (float)cam->width;
+    P.inv_height = 1.0f / (float)cam->height;
     P.Lz = (float)sc->n[2] * sc->h[2];
     P.s1 = scratch->s1;
     P.s2 = scratch->s2;
@@ -178,6 +181,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     P.max_order = o->max_order;
     P.sun_mode = o->sun_mode;
     P.max_steps = 1u << 22;
+    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
+    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
     const bool bf16 = sc->storage == MCRT_STORAGE_BF16;
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;

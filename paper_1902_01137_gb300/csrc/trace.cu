@@ -26,13 +26,14 @@
 // point; (0, 3) for the direct sun ray of a flux path.
 //
 // Loop structure (one iteration): flush finished chunks and claim new ones
-// (convergent), start paths and rays at one site each, then one traversal
-// step whose single 8-byte load fetches either the voxel of a tentative
-// collision or the leaf-map entry of the next leaf, then the rare events.
+// (convergent); one Philox block per lane; one phase of work per lane (path
+// start, ray start, traversal step or vertex); one 8-byte load (the voxel of
+// a tentative collision or the leaf-map entry of the leaf entered); the leaf
+// set-up; the end of a ray or path.
 #include "mcrt_internal.h"
 
 #ifndef MCRT_TRACE_MIN_BLOCKS
-#define MCRT_TRACE_MIN_BLOCKS 1   // resident blocks of 128 threads the register budget must allow
+#define MCRT_TRACE_MIN_BLOCKS 8   // resident blocks of 128 threads the register budget must allow
 #endif
 
 namespace mcrt {
@@ -54,6 +55,18 @@ constexpr int kCounters = 10;
 // iterations spent on one path, [11] longest time (ns) a warp ran before the
 // work queue ran dry, [12] longest time (ns) a warp ran in total.
 enum { C_MAX_ITERS = 10, C_T_DRY = 11, C_T_END = 12 };
+// Counting mode also records, per warp, the SM clock cycles spent in each
+// section of the loop body (slots 13..21): loop top, Philox, path start,
+// ray start, step, vertex, load, after-load, ray/path end.
+constexpr int C_SEC = 13;
+constexpr int kSections = 9;
+
+// Each lane is in one phase per iteration: it starts a path, starts a ray
+// (flight or sun ray), takes one traversal step, or handles the vertex that
+// ended a flight.  Every lane evaluates exactly one Philox block per
+// iteration at one site, whose counter depends on the phase; the voxel /
+// leaf-entry load and the leaf set-up also run at one site each.
+enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX };
 
 template <int SENSOR, bool BF16, bool COUNT>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
@@ -66,31 +79,44 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     // ---- per-lane state ------------------------------------------------------
     unsigned long long pid = 0, pend = 0;   // current path, end of the lane's chunk
     bool chunk = false;                     // the lane holds a chunk
-    bool inflight = false;                  // path pid is being traced
     bool exhausted = false;                 // warp-uniform: nothing left to claim
+    int phase = PH_IDLE;
     unsigned cell = 0;                      // tally cell of the chunk
+    int px = 0, py = 0;                     // camera pixel of the chunk
     float acc[2 * NQ];                      // chunk sums of x and x^2
 #pragma unroll
     for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
     Ray R;
     int kind = kMain;
-    bool need_begin = false;
     uint32_t c2 = 0, blk = 1, ev = 0;
     float tau = 0.0f, Ts = 1.0f, w = 1.0f, score = 0.0f, cf = 0.0f, tdir = 0.0f;
-    bool term_after = false;
+    bool term_after = false, vground = false;
+    float vk = 0.0f;                        // extinction at the vertex
     float vx[3] = {0.0f, 0.0f, 0.0f}, nd[3] = {0.0f, 0.0f, 1.0f};
     unsigned long long cnt[kCounters];
 #pragma unroll
     for (int q = 0; q < kCounters; ++q) cnt[q] = 0;
     uint32_t path_iters = 0, max_iters = 0;
-    const float mu0 = S.sun[2];
+    unsigned long long sec[kSections];
+#pragma unroll
+    for (int q = 0; q < kSections; ++q) sec[q] = 0;
+    long long tclk = COUNT ? clock64() : 0;
+    auto mark = [&](int q) {
+        if (COUNT) {
+            __syncwarp();
+            const long long now = clock64();
+            sec[q] += (unsigned long long)(now - tclk);
+            tclk = now;
+        }
+    };
+    const float pi_over_mu0 = __fdividef(kPi, S.sun[2]);
     uint64_t t_start = 0, t_dry = 0;
     if (P.deadline_ns || COUNT) t_start = globaltimer_ns();
     uint32_t iter = 0;
 
     for (;;) {
         // ---- flush finished chunks: lanes sharing a cell are summed first --
-        bool pending = chunk && !inflight && pid >= pend;
+        bool pending = chunk && phase == PH_IDLE;
         if (pending) chunk = false;
         unsigned fmask = __ballot_sync(kFull, pending);
         while (fmask) {
@@ -128,8 +154,15 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (pid < P.total) {
                     pend = min(pid + (unsigned long long)P.chunk, P.total);
                     chunk = true;
-                    inflight = false;
-                    cell = (SENSOR == kCamera) ? (unsigned)(pid / P.spp) : 0u;
+                    phase = PH_START;
+                    if constexpr (SENSOR == kCamera) {
+                        const unsigned long long pix = pid / P.spp;
+                        cell = (unsigned)pix;
+                        px = (int)(pix % (unsigned long long)P.width);
+                        py = (int)(pix / (unsigned long long)P.width);
+                    } else {
+                        cell = 0u;
+                    }
                 }
             }
         }
@@ -149,18 +182,44 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 break;
             }
         }
-        // ---- start path pid (one site) ---------------------------------------
-        if (chunk && !inflight) {
-            const uint4 x = draw_block(pid, 2u, 0u, P.key);
+        if (COUNT && phase != PH_IDLE) ++path_iters;
+        if (COUNT) { __syncwarp(); tclk = clock64(); }
+
+        // ---- rare phases (path start, ray start, vertex) run in batches: a
+        //      lane waits until enough lanes of its warp need the same kind of
+        //      work, or until no lane is stepping -------------------------------
+        const bool rare = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX;
+        const unsigned rare_mask = __ballot_sync(kFull, rare);
+        const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
+        const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
+        const int ph = (phase == PH_STEP || (rare && run_rare)) ? phase : PH_IDLE;
+
+        // ---- the one Philox block of this iteration ---------------------------
+        const float seg = R.texit - R.t;
+        const float Mseg = R.M * seg;
+        const bool tent = ph == PH_STEP && R.M > 0.0f && tau < Mseg;
+        uint32_t xc2 = c2, xblk = 0u;
+        if (ph == PH_START) xc2 = 2u;
+        else if (ph == PH_STEP) xblk = blk;
+        else if (ph == PH_VERTEX) { xc2 = ev << 2; xblk = kBlockVertex; }
+        mark(0);
+        const uint4 x = draw_block(pid, xc2, xblk, P.key);
+        mark(1);
+
+        // ---- phase work before the load ---------------------------------------
+        int evc = EV_NONE;
+        float p[3];
+        const uint2* ptr = nullptr;
+        uint32_t sub = 0;
+        int st = kInside;
+        bool setup = false;          // enter a leaf after the load
+        if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
             if (COUNT) path_iters = 0;
             if constexpr (SENSOR == kCamera) {
-                const unsigned long long pix = pid / P.spp;
-                const int px = (int)(pix % (unsigned long long)P.width);
-                const int py = (int)(pix / (unsigned long long)P.width);
                 const float jx = 1.0f - u01(x.x), jy = 1.0f - u01(x.y);
-                const float sx = (2.0f * ((float)px + jx) / (float)P.width - 1.0f) * P.tan_half;
-                const float sy = (2.0f * ((float)py + jy) / (float)P.height - 1.0f) * P.tan_half * P.aspect;
+                const float sx = (2.0f * ((float)px + jx) * P.inv_width - 1.0f) * P.tan_half;
+                const float sy = (2.0f * ((float)py + jy) * P.inv_height - 1.0f) * P.tan_half * P.aspect;
                 float d[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) d[a] = P.cam_f[a] + sx * P.cam_r[a] + sy * P.cam_u[a];
@@ -171,7 +230,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 bool enters = true;
                 if (q[2] > P.Lz) {
                     if (d[2] < 0.0f) {
-                        const float t = (P.Lz - q[2]) / d[2];
+                        const float t = __fdividef(P.Lz - q[2], d[2]);
                         q[0] += t * d[0];
                         q[1] += t * d[1];
                         q[2] = P.Lz;
@@ -183,21 +242,15 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 }
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    q[a] -= floorf(q[a] / S.Lper[a]) * S.Lper[a];
+                    q[a] -= floorf(__fdividef(q[a], S.Lper[a])) * S.Lper[a];
                     if (!(q[a] < S.Lper[a]) || q[a] < 0.0f) q[a] = 0.0f;
                 }
-                if (enters) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) { vx[a] = q[a]; nd[a] = d[a]; }
-                    kind = kMain;
-                    c2 = 0u;
-                    need_begin = true;
-                    inflight = true;
-                } else {
-                    // a path that misses the field scores 0
-                    if (COUNT) cnt[C_PATHS]++;
-                    ++pid;
-                }
+                for (int a = 0; a < 3; ++a) { vx[a] = q[a]; nd[a] = d[a]; }
+                kind = kMain;
+                c2 = 0u;
+                if (enters) phase = PH_BEGIN;
+                else evc = EV_ESCAPE;          // a path that misses the field scores 0
             } else {
                 vx[0] = (1.0f - u01(x.x)) * S.Lper[0];
                 vx[1] = (1.0f - u01(x.y)) * S.Lper[1];
@@ -208,52 +261,122 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 kind = kSunDirect;
                 c2 = 3u;
                 Ts = 1.0f;
-                need_begin = true;
-                inflight = true;
+                phase = PH_BEGIN;
             }
         }
-        if (!inflight) continue;
-        if (COUNT) ++path_iters;
-
-        // ---- start a ray (one site): flight from vx along nd, or sun ray ----
-        if (need_begin) {
-            ray_begin<BF16>(S, R, vx, kind == kMain ? nd : S.sun);
-            const uint4 x = draw_block(pid, c2, 0u, P.key);
+        mark(2);
+        if (ph == PH_BEGIN) {
+            // start a ray: the flight from vx along nd, or the sun ray from vx
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float d = (kind == kMain) ? nd[a] : S.sun[a];
+                R.o[a] = vx[a];
+                R.d[a] = d;
+                R.inv_d[a] = (d != 0.0f) ? __frcp_rn(d) : 0.0f;
+                R.v[a] = locate(vx[a], d, S.h[a], S.inv_h[a], 0, S.n[a] - 1);
+            }
+            R.t = 0.0f;
+            R.steps = 0;
+            ptr = leaf_entry(S, R.v);
+            setup = true;
             tau = -__logf(u01(x.x));
             blk = 1;
-            need_begin = false;
             if (COUNT) {
                 if (kind == kMain) cnt[C_FLIGHTS]++;
                 else cnt[C_SUN_RAYS]++;
             }
         }
-
-        // ---- one traversal step ----------------------------------------------
-        int evc = EV_NONE;
-        float p[3];
-        float k = 0.0f;
-        const float seg = R.texit - R.t;
-        const float Mseg = R.M * seg;
-        const bool tent = R.M > 0.0f && tau < Mseg;
-        const uint2* ptr = nullptr;
-        uint32_t sub = 0;
-        int st = kInside;
-        if (tent) {
-            R.t = fminf(R.t + __fdividef(tau, R.M), R.texit);
-            int vi[3];
-            point_in_leaf(S, R, p, vi);
-            const size_t idx = brick_index(S, vi[0], vi[1], vi[2]);
-            if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
-            else { ptr = reinterpret_cast<const uint2*>(S.vox) + (idx >> 1); sub = (uint32_t)idx & 1u; }
-        } else {
-            tau -= Mseg;
-            float wdt;
-            st = step_face(S, R, p, &wdt);
-            if (st == kInside) ptr = leaf_entry(S, R.v);
+        mark(3);
+        if (ph == PH_STEP) {
+            // one step: to the tentative collision inside the leaf, or across
+            // the leaf's exit face; both share the point and voxel arithmetic
+            const float tn = tent ? fminf(R.t + __fdividef(tau, R.M), R.texit) : R.texit;
+            int nv[3];
+            advance(S, R, tn, !tent, p, nv);
+            if (tent) {
+                R.t = tn;
+                const size_t idx = brick_index(S, nv[0], nv[1], nv[2]);
+                if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
+                else { ptr = reinterpret_cast<const uint2*>(S.vox) + (idx >> 1); sub = (uint32_t)idx & 1u; }
+            } else {
+                tau -= Mseg;
+                float wdt;
+                st = cross_face(S, R, p, nv, &wdt);
+                if (st == kInside) {
+                    ptr = leaf_entry(S, R.v);
+                    setup = true;
+                    if (COUNT) {
+                        if (kind == kMain) cnt[C_LEAF]++;
+                        else cnt[C_SUN_LEAF]++;
+                    }
+                } else if (st == kTop) {
+                    evc = (kind == kMain) ? EV_ESCAPE : EV_SUN_END;
+                } else {
+                    if (kind == kMain) {
+                        // ground hit: the vertex is handled in a later iteration
+                        p[2] = 0.0f;
+                        p[0] = fminf(fmaxf(p[0], 0.0f), S.Lper[0]);
+                        p[1] = fminf(fmaxf(p[1], 0.0f), S.Lper[1]);
+                        if (!(p[0] < S.Lper[0])) p[0] = 0.0f;
+                        if (!(p[1] < S.Lper[1])) p[1] = 0.0f;
+                        vx[0] = p[0]; vx[1] = p[1]; vx[2] = p[2];
+                        vground = true;
+                        phase = PH_VERTEX;
+                    } else {
+                        Ts = 0.0f;
+                        evc = EV_SUN_END;
+                    }
+                }
+            }
         }
+        mark(4);
+        if (ph == PH_VERTEX) {
+            // weight, estimate factor toward the sun, new direction, roulette
+            const float xi1 = u01(x.x), xi2 = u01(x.y), xr = u01(x.z);
+            const int order = (int)ev + 1;
+            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
+            if (!vground) {
+                const float om = omega_at(S, vk);
+                const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
+                cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
+                w *= om;
+                rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
+                if (COUNT) cnt[C_REAL]++;
+            } else {
+                cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
+                w *= S.albedo;
+                cosine_up(xi1, xi2, nd);
+                if (COUNT) cnt[C_GROUND]++;
+            }
+            term_after = (P.max_order > 0) && (order >= P.max_order);
+            if (!term_after && w < 0.01f) {
+                if (xr * 0.01f <= w) w = 0.01f;
+                else term_after = true;
+            }
+            if (score_it) {
+                kind = kSunLocal;
+                c2 = (ev << 2) | 1u;
+                Ts = 1.0f;
+                phase = PH_BEGIN;
+            } else {
+                Ts = 0.0f;
+                evc = EV_SUN_END;
+            }
+        }
+
+        mark(5);
+        // ---- the one load: voxel word or leaf-map entry ---------------------
         uint2 val = make_uint2(0u, 0u);
-        if (ptr) val = __ldg(ptr);                       // voxel or leaf entry
-        if (tent) {
+        if (ptr) val = __ldg(ptr);
+        if (COUNT) asm volatile("" ::"r"(val.x), "r"(val.y));   // charge the load latency here
+        mark(6);
+
+        // ---- after the load ----------------------------------------------------
+        if (setup) {
+            finish_leaf<BF16>(S, R, val);
+            if (ph == PH_BEGIN) phase = PH_STEP;
+            else if (R.steps > P.max_steps) evc = EV_ABORT;
+        } else if (tent) {
             float kv;
             if (BF16) {
                 const uint32_t wd = (sub & 2u) ? val.y : val.x;
@@ -261,15 +384,20 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             } else {
                 kv = __uint_as_float(sub ? val.y : val.x);
             }
-            k = __fadd_rn(kv, S.k_gas);
-            const uint4 x = draw_block(pid, c2, blk, P.key);
+            const float k = __fadd_rn(kv, S.k_gas);
             ++blk;
             const float u0 = u01(x.x);
             const float nt = -__logf(u01(x.y));
             if (kind == kMain) {
                 if (COUNT) cnt[C_TENT]++;
-                if (u0 * R.M <= k) evc = EV_REAL;
-                else tau = nt;
+                if (u0 * R.M <= k) {
+                    vx[0] = p[0]; vx[1] = p[1]; vx[2] = p[2];
+                    vk = k;
+                    vground = false;
+                    phase = PH_VERTEX;
+                } else {
+                    tau = nt;
+                }
             } else {
                 if (COUNT) cnt[C_SUN_TENT]++;
                 bool ended = false;
@@ -286,21 +414,10 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (ended) evc = EV_SUN_END;
                 else tau = nt;
             }
-        } else if (st == kInside) {
-            if (COUNT) {
-                if (kind == kMain) cnt[C_LEAF]++;
-                else cnt[C_SUN_LEAF]++;
-            }
-            finish_leaf<BF16>(S, R, val);
-            if (R.steps > P.max_steps) evc = EV_ABORT;
-        } else if (st == kTop) {
-            evc = (kind == kMain) ? EV_ESCAPE : EV_SUN_END;
-        } else {
-            if (kind == kMain) evc = EV_GROUND;
-            else { Ts = 0.0f; evc = EV_SUN_END; }
         }
 
-        // ---- events (rare) ----------------------------------------------------
+        mark(7);
+        // ---- end of a ray or of the path -------------------------------------
         if (evc != EV_NONE) {
             bool path_done = false;
             if (evc == EV_ABORT) {
@@ -308,54 +425,13 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (kind == kMain) path_done = true;
                 else { Ts = 0.0f; evc = EV_SUN_END; }
             }
-            if (evc == EV_REAL || evc == EV_GROUND) {
-                // vertex: weight, estimate factor toward the sun, new direction
-                const bool ground = evc == EV_GROUND;
-                const uint4 x = draw_block(pid, ev << 2, kBlockVertex, P.key);
-                const float xi1 = u01(x.x), xi2 = u01(x.y), xr = u01(x.z);
-                const int order = (int)ev + 1;
-                const bool score_it = (P.max_order == 0) || (order <= P.max_order);
-                if (!ground) {
-                    const float om = omega_at(S, k);
-                    const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
-                    cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
-                    w *= om;
-                    rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
-                    if (COUNT) cnt[C_REAL]++;
-                } else {
-                    cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
-                    w *= S.albedo;
-                    cosine_up(xi1, xi2, nd);
-                    p[2] = 0.0f;
-                    p[0] = fminf(fmaxf(p[0], 0.0f), S.Lper[0]);
-                    p[1] = fminf(fmaxf(p[1], 0.0f), S.Lper[1]);
-                    if (!(p[0] < S.Lper[0])) p[0] = 0.0f;
-                    if (!(p[1] < S.Lper[1])) p[1] = 0.0f;
-                    if (COUNT) cnt[C_GROUND]++;
-                }
-                term_after = (P.max_order > 0) && (order >= P.max_order);
-                if (!term_after && w < 0.01f) {
-                    if (xr * 0.01f <= w) w = 0.01f;
-                    else term_after = true;
-                }
-                vx[0] = p[0]; vx[1] = p[1]; vx[2] = p[2];
-                if (score_it) {
-                    kind = kSunLocal;
-                    c2 = (ev << 2) | 1u;
-                    Ts = 1.0f;
-                    need_begin = true;
-                } else {
-                    Ts = 0.0f;
-                    evc = EV_SUN_END;
-                }
-            }
             if (evc == EV_SUN_END) {
                 if (kind == kSunDirect) {
                     tdir = Ts;
                     ev = 0;
                     kind = kMain;
                     c2 = 0u;
-                    need_begin = true;
+                    phase = PH_BEGIN;
                 } else {
                     score += cf * Ts;
                     if (term_after) {
@@ -364,7 +440,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                         ++ev;
                         kind = kMain;
                         c2 = ev << 2;
-                        need_begin = true;
+                        phase = PH_BEGIN;
                     }
                 }
             }
@@ -374,7 +450,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     acc[0] += score;
                     acc[1] += score * score;
                 } else {
-                    const float tf = kPi / mu0 * score;
+                    const float tf = pi_over_mu0 * score;
                     const float tt = tdir + tf;
                     acc[0] += tdir; acc[1] += tdir * tdir;
                     acc[2] += tf; acc[3] += tf * tf;
@@ -384,11 +460,11 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     cnt[C_PATHS]++;
                     max_iters = max(max_iters, path_iters);
                 }
-                inflight = false;
-                need_begin = false;
                 ++pid;
+                phase = (pid < pend) ? PH_START : PH_IDLE;
             }
         }
+        mark(8);
     }
 
     // ---- partial sums left by a deadline / cancel exit ------------------------
@@ -407,6 +483,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         unsigned mi = max_iters;
         for (int o = 16; o > 0; o >>= 1) mi = max(mi, __shfl_xor_sync(kFull, mi, o));
         if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < kSections; ++q) atomicAdd(P.counters + C_SEC + q, sec[q]);
             const uint64_t t_end = globaltimer_ns();
             atomicMax(P.counters + C_MAX_ITERS, (unsigned long long)mi);
             if (t_dry) atomicMax(P.counters + C_T_DRY, (unsigned long long)(t_dry - t_start));

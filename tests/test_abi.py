@@ -54,7 +54,7 @@ def test_binding_argument_checks_without_gpu(built):
     assert L.mcrt_trace_flux(None, 1, 0, None, None) == m.MCRT_ERR_ARG
     assert L.mcrt_tally_read(None, None, None, None, 0) == m.MCRT_ERR_ARG
     o = m.mcrt_trace_opts_default()
-    assert o.tau_merge == 1.0 and o.finest_level == 1 and o.sun_mode == m.MCRT_SUN_RATIO
+    assert o.tau_merge == 1.0 and o.finest_level == 0 and o.sun_mode == m.MCRT_SUN_RATIO
     v = C.c_int32()
     assert L.mcrt_version(C.byref(v)) == 0 and v.value == 1
 

@@ -168,6 +168,7 @@ def test_camera_small_vs_oracle(m, orc, small):
 
 
 @pytest.mark.parametrize("opts", [dict(tau_merge=0.0, finest_level=0), dict(tau_merge=float("inf")),
+                                  dict(tau_merge=1.0, finest_level=1), dict(tau_merge=0.5, finest_level=1),
                                   dict(tau_merge=10.0), dict(sun_mode=1), dict(chunk=1), dict(chunk=64),
                                   dict(block_size=64, grid_size=7)])
 def test_flux_options_vs_oracle(m, orc, small, opts):
