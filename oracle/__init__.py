@@ -64,6 +64,9 @@ class OrcScene(C.Structure):
         ("max_order", C.c_int32),
         ("k_gas", C.c_double),
         ("max_steps", C.c_int64),
+        ("mlp", C.POINTER(C.c_double)),
+        ("n_learned", C.c_int32),
+        ("mis_alpha", C.c_double),
     ]
 
 
@@ -209,6 +212,9 @@ class Scene:
     k_gas: float = 0.0
     max_steps: int = 1 << 22
     bf16: bool = False
+    mlp: object = None            # learned proposal parameters (11,560 float64) or None
+    n_learned: int = 8
+    mis_alpha: float = 0.5
     _keep: list = field(default_factory=list, repr=False)
 
     def sun_dir(self):
@@ -245,6 +251,12 @@ class Scene:
         s.max_order = self.max_order
         s.k_gas = self.k_gas
         s.max_steps = self.max_steps
+        if self.mlp is not None:
+            mp = np.ascontiguousarray(self.mlp, dtype=np.float64)
+            self._keep.append(mp)
+            s.mlp = _ptr(mp, C.c_double)
+        s.n_learned = self.n_learned
+        s.mis_alpha = self.mis_alpha
         return s
 
 
@@ -409,3 +421,121 @@ def trace_forward(scene: Scene, nphotons: int, seed: int, nthreads: int = 0):
 def forward_balance_residual(scene: Scene, seed: int, nphotons: int) -> float:
     st = scene.struct()
     return lib().orc_forward_balance_residual(C.byref(st), seed, 0, nphotons)
+
+
+# --------------------------------------------------------------------------
+# Learned proposal (MLP -> vMF mixture, one-sample MIS with HG)
+# --------------------------------------------------------------------------
+def _learned_sigs():
+    L = lib()
+    f64p = C.POINTER(C.c_double)
+    L.orc_mlp_nparam.restype = C.c_int
+    L.orc_mlp_forward.argtypes = [f64p, f64p, C.c_int64, f64p]
+    L.orc_mixture.argtypes = [f64p, f64p, f64p, f64p]
+    L.orc_vmf_pdf.argtypes = [f64p, C.c_double, f64p]
+    L.orc_vmf_pdf.restype = C.c_double
+    L.orc_vmf_sample.argtypes = [f64p, C.c_double, C.c_double, C.c_double, f64p]
+    L.orc_mis_sample.argtypes = [f64p, C.c_double, C.c_double, f64p, f64p, f64p, f64p, f64p]
+    L.orc_mis_sample.restype = C.c_double
+    L.orc_mixture_pdf.argtypes = [f64p, f64p]
+    L.orc_mixture_pdf.restype = C.c_double
+    L.orc_mlp_loss_grad.argtypes = [f64p, f64p, f64p, f64p, C.c_int64, f64p]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_adam_step.argtypes = [f64p, f64p, f64p, f64p, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                C.c_double]
+    return L
+
+
+MLP_SHAPES = [(64, 9), (64,), (64, 64), (64,), (64, 64), (64,), (40, 64), (40,)]
+
+
+def mlp_nparam() -> int:
+    return _learned_sigs().orc_mlp_nparam()
+
+
+def mlp_split(params):
+    """Views of the flat parameter vector in layer order (W1, b1, ..., W4, b4)."""
+    out, off = [], 0
+    for sh in MLP_SHAPES:
+        n = int(np.prod(sh))
+        out.append(np.asarray(params[off:off + n]).reshape(sh))
+        off += n
+    return out
+
+
+def mlp_forward(params, x):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 9)
+    out = np.zeros((x.shape[0], 40))
+    _learned_sigs().orc_mlp_forward(_ptr(p, C.c_double), _ptr(x, C.c_double), x.shape[0], _ptr(out, C.c_double))
+    return out
+
+
+def mixture(raw):
+    raw = np.ascontiguousarray(raw, dtype=np.float64)
+    mu = np.zeros((8, 3)); ka = np.zeros(8); pi = np.zeros(8)
+    _learned_sigs().orc_mixture(_ptr(raw, C.c_double), _ptr(mu, C.c_double), _ptr(ka, C.c_double),
+                                _ptr(pi, C.c_double))
+    return mu, ka, pi
+
+
+def vmf_pdf(mu, kappa, x):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return _learned_sigs().orc_vmf_pdf(_ptr(mu, C.c_double), float(kappa), _ptr(x, C.c_double))
+
+
+def vmf_sample(mu, kappa, xi1, xi2):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = np.zeros(3)
+    _learned_sigs().orc_vmf_sample(_ptr(mu, C.c_double), float(kappa), float(xi1), float(xi2), _ptr(out, C.c_double))
+    return out
+
+
+def mis_sample(raw, g, alpha, d, u):
+    """Returns (direction, weight factor p_HG/q, q, p_HG)."""
+    raw = np.ascontiguousarray(raw, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(3)
+    q = C.c_double(); ph = C.c_double()
+    f = _learned_sigs().orc_mis_sample(_ptr(raw, C.c_double), float(g), float(alpha), _ptr(d, C.c_double),
+                                       _ptr(u, C.c_double), _ptr(out, C.c_double), C.byref(q), C.byref(ph))
+    return out, f, q.value, ph.value
+
+
+def mixture_pdf(raw, x):
+    raw = np.ascontiguousarray(raw, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return _learned_sigs().orc_mixture_pdf(_ptr(raw, C.c_double), _ptr(x, C.c_double))
+
+
+def mlp_loss_grad(params, x, dirs, t):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 9)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+    g = np.zeros(p.size)
+    loss = _learned_sigs().orc_mlp_loss_grad(_ptr(p, C.c_double), _ptr(x, C.c_double), _ptr(dirs, C.c_double),
+                                             _ptr(t, C.c_double), x.shape[0], _ptr(g, C.c_double))
+    return loss, g
+
+
+def adam_step(params, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam update of float64 arrays params, m, v."""
+    _learned_sigs().orc_adam_step(_ptr(params, C.c_double), _ptr(m, C.c_double), _ptr(v, C.c_double),
+                                  _ptr(np.ascontiguousarray(grad, dtype=np.float64), C.c_double), params.size, t,
+                                  lr, b1, b2, eps)
+
+
+def xavier_init(seed: int):
+    """Xavier-uniform weights, zero biases (float64)."""
+    r = np.random.Generator(np.random.Philox(seed))
+    parts = []
+    for sh in MLP_SHAPES:
+        if len(sh) == 2:
+            lim = math.sqrt(6.0 / (sh[0] + sh[1]))
+            parts.append(r.uniform(-lim, lim, sh).ravel())
+        else:
+            parts.append(np.zeros(sh))
+    return np.concatenate(parts)

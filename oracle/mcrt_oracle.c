@@ -213,6 +213,9 @@ typedef struct {
     int32_t max_order;         /* 0: all orders; n: score orders <= n     */
     double k_gas;              /* extra uniform pure absorber             */
     int64_t max_steps;         /* traversal guard per ray                 */
+    const double* mlp;         /* learned proposal parameters, or NULL    */
+    int32_t n_learned;         /* volume vertices per path that use it    */
+    double mis_alpha;          /* HG share of the one-sample MIS mixture  */
 } orc_scene;
 
 static const float* level_ptr(const orc_scene* S, int level, int dims[3])
@@ -639,7 +642,7 @@ enum { EV_ESCAPE = 1, EV_GROUND = 2, EV_VOLUME = 3, EV_ABORT = 4 };
 typedef struct { int64_t tentative, real, leaves; } orc_counts;
 
 static int free_flight(const orc_scene* S, double p[3], const double d[3], const rng_t* r,
-                       double* k_at, orc_counts* C)
+                       double* k_at, int vox_at[3], orc_counts* C)
 {
     trav64 T;
     trav_begin(S, &T, p, d);
@@ -657,6 +660,7 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
             if (u[0] * T.M <= k) {
                 for (int a = 0; a < 3; ++a) p[a] = T.p[a];
                 *k_at = k;
+                if (vox_at) { vox_at[0] = vox[0]; vox_at[1] = vox[1]; vox_at[2] = vox[2]; }
                 if (C) C->real++;
                 return EV_VOLUME;
             }
@@ -761,6 +765,33 @@ double orc_first_collision_distance(const orc_scene* S, const double p[3], const
 /* (e, 0), its vertex from block VERTEX of that stream, and the vertex's  */
 /* sun ray from stream (e, 1).                                            */
 /* ===================================================================== */
+#define MLP_IN 9
+#define MLP_OUT 40
+void orc_mlp_forward(const double* params, const double* x, int64_t rows, double* out);
+double orc_mis_sample(const double* raw, double g, double alpha, const double d[3], const double u[4], double out[3],
+                      double* q_out, double* phg_out);
+
+/* Features of a volume vertex for the learned proposal: position scaled to
+ * [-1, 1] per axis, incoming direction, and ln(M + 1e-6) of the extinction
+ * at the voxel and of the level-1 and level-2 majorants of its cells (the
+ * top level when fewer levels exist). */
+static void vertex_features(const orc_scene* S, const double p[3], const double d[3], double k_tot, const int vox[3],
+                            double x[MLP_IN])
+{
+    double L[3] = {(double)S->nx * S->dx, (double)S->ny * S->dy, (double)S->nz * S->dz};
+    for (int a = 0; a < 3; ++a) x[a] = 2.0 * p[a] / L[a] - 1.0;
+    for (int a = 0; a < 3; ++a) x[3 + a] = d[a];
+    x[6] = log(k_tot + 1e-6);
+    for (int q = 1; q <= 2; ++q) {
+        int lev = q <= S->levels ? q : S->levels;
+        int dims[3];
+        const float* P = level_ptr(S, lev, dims);
+        int c[3] = {vox[0] >> (3 * lev), vox[1] >> (3 * lev), vox[2] >> (3 * lev)};
+        double M = (double)P[((int64_t)c[2] * dims[1] + c[1]) * dims[0] + c[0]] + S->k_gas;
+        x[6 + q] = log(M + 1e-6);
+    }
+}
+
 static double omega_at(const orc_scene* S, double k_total)
 {
     double k = k_total - S->k_gas;          /* cloud + clear */
@@ -775,12 +806,14 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
                              orc_counts* C, int64_t* aborted)
 {
     double w = 1.0, score = 0.0;
+    int lv = 0;                 /* volume vertices so far */
     const double* s = S->sun;
     for (uint32_t e = 0;; ++e) {
         rng_t r;
         rng_init(&r, seed, path, e, 0);
         double k;
-        int ev = free_flight(S, p, d, &r, &k, C);
+        int vox[3] = {0, 0, 0};
+        int ev = free_flight(S, p, d, &r, &k, vox, C);
         if (ev == EV_ESCAPE) break;
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; break; }
         int order = (int)e + 1;
@@ -797,10 +830,21 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
                 score += w * om * orc_hg_pdf(S->g, mu) * Ts;
             }
             w *= om;
-            double mu = orc_hg_sample_mu(S->g, uv[0]);
-            double phi = 2.0 * ORC_PI * uv[1];
             double nd[3];
-            rotate_dir(d, mu, phi, nd);
+            if (S->mlp && lv < S->n_learned) {
+                /* learned proposal: features, network, one-sample MIS */
+                double x[MLP_IN], raw[MLP_OUT], ul[4];
+                vertex_features(S, p, d, k, vox, x);
+                orc_mlp_forward(S->mlp, x, 1, raw);
+                rng_block(&r, BLOCK_VERTEX - 1u, ul);
+                double um[4] = {uv[0], uv[1], uv[3], ul[0]};
+                w *= orc_mis_sample(raw, S->g, S->mis_alpha, d, um, nd, NULL, NULL);
+            } else {
+                double mu = orc_hg_sample_mu(S->g, uv[0]);
+                double phi = 2.0 * ORC_PI * uv[1];
+                rotate_dir(d, mu, phi, nd);
+            }
+            ++lv;
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
         } else { /* ground */
             if (score_it) {
@@ -940,7 +984,7 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
         rng_t r;
         rng_init(&r, seed, path, e, 0);
         double k;
-        int ev = free_flight(S, p, d, &r, &k, NULL);
+        int ev = free_flight(S, p, d, &r, &k, NULL, NULL);
         if (ev == EV_ESCAPE) { out[0] += w; return; }
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; out[5] += w; return; }
         double uv[4];
@@ -1144,4 +1188,264 @@ double orc_forward_balance_residual(const orc_scene* S, uint64_t seed, uint64_t 
         if (res > worst) worst = res;
     }
     return worst;
+}
+
+/* ===================================================================== */
+/* Learned scattering proposal (no counterpart in the paper).             */
+/* A multilayer perceptron maps 9 vertex features to an 8-lobe von       */
+/* Mises-Fisher mixture; directions are drawn by defensive one-sample     */
+/* multiple importance sampling with the HG phase function:               */
+/*   q(w') = alpha p_HG(d.w') + (1 - alpha) sum_j pi_j f_j(w'),           */
+/* and the path weight is multiplied by p_HG(d.w') / q(w'), which keeps   */
+/* the estimator unbiased for any network.                                */
+/* Parameter vector (11,560 doubles): W1[64][9], b1[64], W2[64][64],      */
+/* b2[64], W3[64][64], b3[64], W4[40][64], b4[40] (row = output unit).    */
+/* Outputs per lobe j: mu~ (3), kappa raw, logit.  GELU: tanh form.       */
+/* ===================================================================== */
+#define MLP_H 64
+#define MLP_LOBES 8
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + 2 * (MLP_H * MLP_H + MLP_H) + MLP_OUT * MLP_H + MLP_OUT)
+
+int orc_mlp_nparam(void) { return MLP_NPARAM; }
+
+static double gelu(double x)
+{
+    const double c = 0.7978845608028654; /* sqrt(2/pi) */
+    return 0.5 * x * (1.0 + tanh(c * (x + 0.044715 * x * x * x)));
+}
+
+static double gelu_grad(double x)
+{
+    const double c = 0.7978845608028654;
+    double u = c * (x + 0.044715 * x * x * x);
+    double t = tanh(u);
+    double du = c * (1.0 + 3.0 * 0.044715 * x * x);
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * du;
+}
+
+/* One dense layer y = W x + b (W row-major [nout][nin]). */
+static void dense(const double* W, const double* b, const double* x, int nin, int nout, double* y)
+{
+    for (int o = 0; o < nout; ++o) {
+        double s = b[o];
+        for (int i = 0; i < nin; ++i) s += W[o * nin + i] * x[i];
+        y[o] = s;
+    }
+}
+
+typedef struct { const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4; } mlp_view;
+
+static mlp_view mlp_split(const double* p)
+{
+    mlp_view v;
+    v.W1 = p; p += MLP_H * MLP_IN;
+    v.b1 = p; p += MLP_H;
+    v.W2 = p; p += MLP_H * MLP_H;
+    v.b2 = p; p += MLP_H;
+    v.W3 = p; p += MLP_H * MLP_H;
+    v.b3 = p; p += MLP_H;
+    v.W4 = p; p += MLP_OUT * MLP_H;
+    v.b4 = p;
+    return v;
+}
+
+/* Forward pass of one row; z[3][64] pre-activations and h[3][64]
+ * activations are returned for the backward pass when non-NULL. */
+static void mlp_row(const mlp_view* v, const double* x, double* out, double z[3][MLP_H], double h[3][MLP_H])
+{
+    double zz[3][MLP_H], hh[3][MLP_H];
+    dense(v->W1, v->b1, x, MLP_IN, MLP_H, zz[0]);
+    for (int i = 0; i < MLP_H; ++i) hh[0][i] = gelu(zz[0][i]);
+    dense(v->W2, v->b2, hh[0], MLP_H, MLP_H, zz[1]);
+    for (int i = 0; i < MLP_H; ++i) hh[1][i] = gelu(zz[1][i]);
+    dense(v->W3, v->b3, hh[1], MLP_H, MLP_H, zz[2]);
+    for (int i = 0; i < MLP_H; ++i) hh[2][i] = gelu(zz[2][i]);
+    dense(v->W4, v->b4, hh[2], MLP_H, MLP_OUT, out);
+    if (z) memcpy(z, zz, sizeof(zz));
+    if (h) memcpy(h, hh, sizeof(hh));
+}
+
+void orc_mlp_forward(const double* params, const double* x, int64_t rows, double* out)
+{
+    mlp_view v = mlp_split(params);
+    for (int64_t r = 0; r < rows; ++r) mlp_row(&v, x + MLP_IN * r, out + MLP_OUT * r, NULL, NULL);
+}
+
+static double softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }
+
+/* Mixture parameters from the 40 raw outputs: unit axes, concentrations
+ * kappa = softplus + 1e-3, weights = softmax of the logits. */
+void orc_mixture(const double* raw, double mu[MLP_LOBES][3], double kappa[MLP_LOBES], double pi[MLP_LOBES])
+{
+    double mx = -INFINITY;
+    for (int j = 0; j < MLP_LOBES; ++j) if (raw[5 * j + 4] > mx) mx = raw[5 * j + 4];
+    double s = 0.0;
+    for (int j = 0; j < MLP_LOBES; ++j) {
+        const double* q = raw + 5 * j;
+        double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (n < 1e-12) { mu[j][0] = 0.0; mu[j][1] = 0.0; mu[j][2] = 1.0; }
+        else { mu[j][0] = q[0] / n; mu[j][1] = q[1] / n; mu[j][2] = q[2] / n; }
+        kappa[j] = softplus(q[3]) + 1e-3;
+        pi[j] = exp(q[4] - mx);
+        s += pi[j];
+    }
+    for (int j = 0; j < MLP_LOBES; ++j) pi[j] /= s;
+}
+
+/* vMF density over the sphere, kappa / (2 pi (1 - exp(-2 kappa))) exp(kappa (mu.x - 1)). */
+double orc_vmf_pdf(const double mu[3], double kappa, const double x[3])
+{
+    double c = mu[0] * x[0] + mu[1] * x[1] + mu[2] * x[2];
+    return kappa / (2.0 * ORC_PI * (-expm1(-2.0 * kappa))) * exp(kappa * (c - 1.0));
+}
+
+/* vMF sample (Wood 1994): cosine w = 1 + ln(xi + (1 - xi) exp(-2 kappa)) / kappa. */
+void orc_vmf_sample(const double mu[3], double kappa, double xi1, double xi2, double out[3])
+{
+    double w = 1.0 + log(xi1 + (1.0 - xi1) * exp(-2.0 * kappa)) / kappa;
+    if (w > 1.0) w = 1.0;
+    if (w < -1.0) w = -1.0;
+    rotate_dir(mu, w, 2.0 * ORC_PI * xi2, out);
+}
+
+static double mixture_pdf(double mu[MLP_LOBES][3], const double kappa[MLP_LOBES], const double pi[MLP_LOBES],
+                          const double x[3])
+{
+    double q = 0.0;
+    for (int j = 0; j < MLP_LOBES; ++j) q += pi[j] * orc_vmf_pdf(mu[j], kappa[j], x);
+    return q;
+}
+
+/* One-sample MIS direction at a vertex with incoming direction d.
+ * u[0]: HG cosine or vMF cosine draw, u[1]: azimuth, u[2]: HG-vs-mixture
+ * choice (HG when u[2] <= alpha), u[3]: lobe choice.  Returns the weight
+ * factor p_HG / q; *q_out and *phg_out receive q(w') and p_HG(d.w'). */
+double orc_mis_sample(const double* raw, double g, double alpha, const double d[3], const double u[4], double out[3],
+                      double* q_out, double* phg_out)
+{
+    double mu[MLP_LOBES][3], kappa[MLP_LOBES], pi[MLP_LOBES];
+    orc_mixture(raw, mu, kappa, pi);
+    if (u[2] <= alpha) {
+        rotate_dir(d, orc_hg_sample_mu(g, u[0]), 2.0 * ORC_PI * u[1], out);
+    } else {
+        int j = MLP_LOBES - 1;
+        double c = 0.0;
+        for (int i = 0; i < MLP_LOBES; ++i) {
+            c += pi[i];
+            if (u[3] <= c) { j = i; break; }
+        }
+        orc_vmf_sample(mu[j], kappa[j], u[0], u[1], out);
+    }
+    double phg = orc_hg_pdf(g, d[0] * out[0] + d[1] * out[1] + d[2] * out[2]);
+    double q = alpha * phg + (1.0 - alpha) * mixture_pdf(mu, kappa, pi, out);
+    if (q_out) *q_out = q;
+    if (phg_out) *phg_out = phg;
+    return phg / q;
+}
+
+double orc_mixture_pdf(const double* raw, const double x[3])
+{
+    double mu[MLP_LOBES][3], kappa[MLP_LOBES], pi[MLP_LOBES];
+    orc_mixture(raw, mu, kappa, pi);
+    return mixture_pdf(mu, kappa, pi, x);
+}
+
+/* Loss over `rows` training records: mean of -t_r log q_vMF(w'_r), where
+ * t_r is the record's target weight (the radiance the sampled direction
+ * brought back, weighted so that the expectation is the KL divergence
+ * between the ideal product p_HG L and the mixture, up to a constant).
+ * x: rows x 9 features, dir: rows x 3 directions, t: rows targets.
+ * grad (11,560) receives d loss / d params; returns the loss. */
+double orc_mlp_loss_grad(const double* params, const double* x, const double* dir, const double* t, int64_t rows,
+                         double* grad)
+{
+    mlp_view v = mlp_split(params);
+    memset(grad, 0, sizeof(double) * MLP_NPARAM);
+    double* gW1 = grad;
+    double* gb1 = gW1 + MLP_H * MLP_IN;
+    double* gW2 = gb1 + MLP_H;
+    double* gb2 = gW2 + MLP_H * MLP_H;
+    double* gW3 = gb2 + MLP_H;
+    double* gb3 = gW3 + MLP_H * MLP_H;
+    double* gW4 = gb3 + MLP_H;
+    double* gb4 = gW4 + MLP_OUT * MLP_H;
+    double loss = 0.0;
+    const double inv_rows = 1.0 / (double)rows;
+    for (int64_t r = 0; r < rows; ++r) {
+        const double* xr = x + MLP_IN * r;
+        const double* w = dir + 3 * r;
+        double out[MLP_OUT], z[3][MLP_H], h[3][MLP_H];
+        mlp_row(&v, xr, out, z, h);
+        double mu[MLP_LOBES][3], kappa[MLP_LOBES], pi[MLP_LOBES], f[MLP_LOBES];
+        orc_mixture(out, mu, kappa, pi);
+        double q = 0.0;
+        for (int j = 0; j < MLP_LOBES; ++j) { f[j] = orc_vmf_pdf(mu[j], kappa[j], w); q += pi[j] * f[j]; }
+        const double tr = t[r] * inv_rows;
+        loss += -tr * log(q);
+        /* d(-t log q)/d raw */
+        double dout[MLP_OUT];
+        for (int j = 0; j < MLP_LOBES; ++j) {
+            const double* raw = out + 5 * j;
+            double resp = pi[j] * f[j] / q;                     /* responsibility */
+            double n = sqrt(raw[0] * raw[0] + raw[1] * raw[1] + raw[2] * raw[2]);
+            double c = mu[j][0] * w[0] + mu[j][1] * w[1] + mu[j][2] * w[2];
+            double k = kappa[j];
+            /* d log f / d mu~ = kappa (w - (mu.w) mu) / |mu~| */
+            for (int a = 0; a < 3; ++a) {
+                double dmu = (n < 1e-12) ? 0.0 : k * (w[a] - c * mu[j][a]) / n;
+                dout[5 * j + a] = -tr * resp * dmu;
+            }
+            /* d log f / d kappa = 1/kappa - 2 e^{-2k} / (1 - e^{-2k}) + (c - 1) */
+            double e2 = exp(-2.0 * k);
+            double dk = 1.0 / k - 2.0 * e2 / (-expm1(-2.0 * k)) + (c - 1.0);
+            double sig = 1.0 / (1.0 + exp(-raw[3]));             /* softplus' */
+            dout[5 * j + 3] = -tr * resp * dk * sig;
+            dout[5 * j + 4] = -tr * (resp - pi[j]);
+        }
+        /* backward through the layers */
+        double dh[MLP_H], dz[MLP_H], dprev[MLP_H];
+        for (int o = 0; o < MLP_OUT; ++o) {
+            gb4[o] += dout[o];
+            for (int i = 0; i < MLP_H; ++i) gW4[o * MLP_H + i] += dout[o] * h[2][i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < MLP_OUT; ++o) s += v.W4[o * MLP_H + i] * dout[o];
+            dh[i] = s;
+        }
+        const double* Ws[3] = {v.W1, v.W2, v.W3};
+        double* gWs[3] = {gW1, gW2, gW3};
+        double* gbs[3] = {gb1, gb2, gb3};
+        for (int L = 2; L >= 0; --L) {
+            int nin = (L == 0) ? MLP_IN : MLP_H;
+            const double* inp = (L == 0) ? xr : h[L - 1];
+            for (int o = 0; o < MLP_H; ++o) dz[o] = dh[o] * gelu_grad(z[L][o]);
+            for (int o = 0; o < MLP_H; ++o) {
+                gbs[L][o] += dz[o];
+                for (int i = 0; i < nin; ++i) gWs[L][o * nin + i] += dz[o] * inp[i];
+            }
+            if (L > 0) {
+                for (int i = 0; i < MLP_H; ++i) {
+                    double s = 0.0;
+                    for (int o = 0; o < MLP_H; ++o) s += Ws[L][o * MLP_H + i] * dz[o];
+                    dprev[i] = s;
+                }
+                memcpy(dh, dprev, sizeof(dh));
+            }
+        }
+    }
+    return loss;
+}
+
+/* Adam (Kingma and Ba 2015) with bias correction; step t >= 1. */
+void orc_adam_step(double* params, double* m, double* v, const double* grad, int64_t n, int64_t t, double lr,
+                   double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        params[i] -= lr * mh / (sqrt(vh) + eps);
+    }
 }

@@ -340,3 +340,62 @@ def test_deadline_and_cancel(m, ctx, small):
     # the context is still usable afterwards
     r = sc.trace_flux(1000, seed=2)
     assert np.isfinite(r.mean).all()
+
+
+# ---------------------------------------------------------------------------
+# precision: BF16 voxel storage with majorants rounded up
+# ---------------------------------------------------------------------------
+def test_bf16_storage_vs_oracle_bf16(m, ctx, orc):
+    """BF16 storage traces the nearest-BF16 field exactly (majorants rounded
+    up stay bounds); the oracle traces the same rounded field in FP64."""
+    sp = scenes.blobs_small(0)
+    sc = m.Scene.from_spec(ctx, sp, storage=m.MCRT_STORAGE_BF16)
+    try:
+        n = 100000
+        g = sc.trace_flux(n, seed=5)
+        o, _ = orc.trace_flux(oscene(orc, sp, bf16=True), n, seed=5)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean[q], o.mean[q])
+        assert abs(g.mean[2] - o.mean[2]) < 0.25 * o.se[2]
+        cam = scenes.nadir_camera(sp, 64, 64)
+        gi = sc.trace_camera(cam, 16, seed=6)
+        oi, _ = orc.trace_camera(oscene(orc, sp, bf16=True), ocam(orc, cam), 16, seed=6)
+        ok, info = image_parity(gi.mean, gi.se, oi.mean, oi.se, 16)
+        assert ok, info
+        rel = np.abs(gi.mean - oi.mean) / np.maximum(np.abs(oi.mean), 1e-3)
+        assert np.median(rel) < 1e-3
+    finally:
+        sc.close()
+
+
+def test_bf16_error_against_fp64_oracle_of_fp32_field(m, ctx, orc, capsys):
+    """Error of the BF16-stored field against the FP64 oracle of the FP32
+    field.  Rounding to nearest BF16 changes each voxel by at most 2^-9
+    relative, so an optical depth tau moves by at most 2^-9 tau and a
+    transmissivity by at most a factor exp(2^-9 tau); the direct part
+    (tau_sun of the blobs <= 40) is bounded accordingly, and every tally must
+    also stay within that bound plus 4 combined SE.  The measured
+    differences are printed (the report of the precision row)."""
+    sp = scenes.blobs_small(0)
+    n = 200000
+    o, _ = orc.trace_flux(oscene(orc, sp), n, seed=8)
+    res = {}
+    for storage, name in [(m.MCRT_STORAGE_F32, "f32"), (m.MCRT_STORAGE_BF16, "bf16")]:
+        sc = m.Scene.from_spec(ctx, sp, storage=storage)
+        try:
+            res[name] = sc.trace_flux(n, seed=8)
+        finally:
+            sc.close()
+    tau_max = 40.0
+    for name, g in res.items():
+        for q in range(3):
+            d = abs(g.mean[q] - o.mean[q])
+            bound = 4.0 * math.hypot(g.se[q], o.se[q])
+            if name == "bf16":
+                bound += o.mean[q] * (math.exp(tau_max * 2.0 ** -9) - 1.0)
+            assert d <= bound, (name, q, g.mean[q], o.mean[q], bound)
+    with capsys.disabled():
+        print("\n[precision] flux T_dir/T_dif/T_tot: fp64 oracle %s | f32 %s | bf16 %s | "
+              "bf16-oracle %s (se %s)" % (np.round(o.mean, 6), np.round(res["f32"].mean, 6),
+                                           np.round(res["bf16"].mean, 6),
+                                           np.round(res["bf16"].mean - o.mean, 6), np.round(o.se, 6)))
