@@ -283,6 +283,51 @@ MCRT_API int mcrt_tally_kernel_ms(const mcrt_tally* tally, float* ms);
 MCRT_API int mcrt_tally_destroy(mcrt_tally* tally);
 
 /* --------------------------------------------------------------------- */
+/* Learned scattering proposal (a project addition; the paper has none).  */
+/* A 9-64-64-64-40 network (GELU, tanh form) maps the features of a volume */
+/* vertex -- position scaled to [-1, 1] per axis, incoming direction, and  */
+/* ln(k + 1e-6), ln(M1 + 1e-6), ln(M2 + 1e-6) of the voxel and its level-1 */
+/* and level-2 majorants -- to an 8-lobe von Mises-Fisher mixture (per     */
+/* lobe: axis, concentration softplus(.) + 1e-3, softmax weight).  The     */
+/* tracer draws the new direction by one-sample MIS from                  */
+/* q = alpha p_HG + (1 - alpha) q_vMF and multiplies the path weight by   */
+/* p_HG / q, so the estimate stays unbiased for any network.              */
+/* Parameters: 11,560 floats in the order W1[64][9], b1[64], W2[64][64],  */
+/* b2[64], W3[64][64], b3[64], W4[40][64], b4[40] (row = output unit).    */
+/* Inference runs on the tensor cores in BF16 with FP32 accumulation;    */
+/* training keeps FP32 master weights and Adam moments.                   */
+/* --------------------------------------------------------------------- */
+typedef struct mcrt_proposal mcrt_proposal;
+
+/* Number of network parameters (11,560). */
+MCRT_API int mcrt_proposal_nparams(int32_t* n);
+
+/* New network with Xavier-uniform weights drawn from Philox(seed) and zero
+ * biases; Adam state cleared. */
+MCRT_API int mcrt_proposal_create(mcrt_ctx* ctx, uint64_t seed, mcrt_proposal** out);
+MCRT_API int mcrt_proposal_destroy(mcrt_proposal* proposal);
+
+/* Copy parameters in from / out to host memory (n = 11,560).  Setting
+ * clears the Adam state. */
+MCRT_API int mcrt_proposal_set_params(mcrt_proposal* proposal, const float* host, size_t n);
+MCRT_API int mcrt_proposal_get_params(const mcrt_proposal* proposal, float* host, size_t n);
+
+/* Evaluate the network on n feature rows (host, n x 9 floats, rounded to
+ * BF16 on the device as in the tracer).  host_mix receives n x 40 mixture
+ * parameters (per lobe: unit axis (3), concentration, weight); host_raw, if
+ * not NULL, the n x 40 raw outputs. */
+MCRT_API int mcrt_proposal_eval(mcrt_proposal* proposal, const float* host_features, size_t n, float* host_mix,
+                                float* host_raw);
+
+/* One training step on n records (host): features (n x 9), sampled
+ * directions (n x 3) and target weights (n).  The loss is the mean of
+ * -t log q_vMF(direction); the gradient of that mean is written to
+ * host_grad (11,560, may be NULL) and, when lr > 0, one Adam step
+ * (beta 0.9, 0.999, eps 1e-8) is applied.  *loss_out gets the loss. */
+MCRT_API int mcrt_proposal_train_step(mcrt_proposal* proposal, const float* host_features, const float* host_dirs,
+                                      const float* host_targets, size_t n, float lr, float* loss_out, float* host_grad);
+
+/* --------------------------------------------------------------------- */
 /* Checks (used by the tests; not on the hot path)                        */
 /* --------------------------------------------------------------------- */
 

@@ -109,6 +109,13 @@ def _load():
         "mcrt_tally_destroy": [vp],
         "mcrt_debug_dda": [vp, P(f32), P(f32), f32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
+        "mcrt_proposal_nparams": [P(i32)],
+        "mcrt_proposal_create": [vp, u64, P(vp)],
+        "mcrt_proposal_destroy": [vp],
+        "mcrt_proposal_set_params": [vp, P(f32), C.c_size_t],
+        "mcrt_proposal_get_params": [vp, P(f32), C.c_size_t],
+        "mcrt_proposal_eval": [vp, P(f32), C.c_size_t, P(f32), P(f32)],
+        "mcrt_proposal_train_step": [vp, P(f32), P(f32), P(f32), C.c_size_t, f32, P(f32), P(f32)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -433,3 +440,78 @@ class Scene:
         r.se = r.se.reshape(3)
         r.n = r.n.reshape(3)
         return r
+
+
+# ---------------------------------------------------------------------------
+# Learned proposal
+# ---------------------------------------------------------------------------
+def mcrt_proposal_create(ctx, seed: int):
+    h = C.c_void_p()
+    _check(_load().mcrt_proposal_create(ctx, seed, C.byref(h)), ctx)
+    return h
+
+
+def mcrt_proposal_destroy(prop):
+    _check(_load().mcrt_proposal_destroy(prop))
+
+
+def mcrt_proposal_set_params(ctx, prop, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_load().mcrt_proposal_set_params(prop, _ptr(p, C.c_float), p.size), ctx)
+
+
+def mcrt_proposal_get_params(ctx, prop) -> np.ndarray:
+    n = C.c_int32()
+    _load().mcrt_proposal_nparams(C.byref(n))
+    p = np.zeros(n.value, dtype=np.float32)
+    _check(_load().mcrt_proposal_get_params(prop, _ptr(p, C.c_float), p.size), ctx)
+    return p
+
+
+def mcrt_proposal_eval(ctx, prop, features):
+    f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, 9)
+    mix = np.zeros((f.shape[0], 40), dtype=np.float32)
+    raw = np.zeros((f.shape[0], 40), dtype=np.float32)
+    _check(_load().mcrt_proposal_eval(prop, _ptr(f, C.c_float), f.shape[0], _ptr(mix, C.c_float),
+                                      _ptr(raw, C.c_float)), ctx)
+    return mix, raw
+
+
+def mcrt_proposal_train_step(ctx, prop, features, dirs, targets, lr=0.0):
+    f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, 9)
+    d = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(targets, dtype=np.float32).reshape(-1)
+    g = np.zeros(11560, dtype=np.float32)
+    loss = C.c_float()
+    _check(_load().mcrt_proposal_train_step(prop, _ptr(f, C.c_float), _ptr(d, C.c_float), _ptr(t, C.c_float),
+                                            f.shape[0], lr, C.byref(loss), _ptr(g, C.c_float)), ctx)
+    return loss.value, g
+
+
+class Proposal:
+    """Learned scattering proposal network on the device."""
+
+    def __init__(self, ctx: Context, seed: int = 0, params=None):
+        self.ctx = ctx
+        self.h = mcrt_proposal_create(ctx.h, seed)
+        if params is not None:
+            mcrt_proposal_set_params(ctx.h, self.h, params)
+
+    def close(self):
+        if self.h:
+            mcrt_proposal_destroy(self.h)
+            self.h = None
+
+    @property
+    def params(self):
+        return mcrt_proposal_get_params(self.ctx.h, self.h)
+
+    @params.setter
+    def params(self, p):
+        mcrt_proposal_set_params(self.ctx.h, self.h, p)
+
+    def eval(self, features):
+        return mcrt_proposal_eval(self.ctx.h, self.h, features)
+
+    def train_step(self, features, dirs, targets, lr=0.0):
+        return mcrt_proposal_train_step(self.ctx.h, self.h, features, dirs, targets, lr)

@@ -57,9 +57,22 @@ struct mcrt_tally {
     float kernel_ms = 0;
 };
 
+struct mcrt_proposal {
+    mcrt_ctx* ctx = nullptr;
+    float* d_params = nullptr;     // FP32 master parameters (11,560)
+    float* d_m = nullptr;          // Adam first moments
+    float* d_v = nullptr;          // Adam second moments
+    float* d_grad = nullptr;       // gradient accumulator
+    float* d_loss = nullptr;       // loss accumulator (1 float)
+    void* d_wbf = nullptr;         // padded BF16 inference weights
+    float* d_bias = nullptr;       // padded FP32 biases
+    int step = 0;                  // Adam steps taken
+};
+
 namespace mcrt {
 
 constexpr int kNumCounters = 24;
+constexpr int kMlpParams = 11560;
 
 // Work distribution and status shared by all blocks of a trace launch.
 struct WorkState {
@@ -114,5 +127,18 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32
                                 cudaStream_t st);
 
 DevScene make_dev_scene(const mcrt_scene* sc, float k_gas);
+
+// learned proposal network
+size_t mlp_packed_bf16_elems();
+size_t mlp_packed_bias_elems();
+cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const void* feat, int n, float* mix,
+                             float* raw, int sm_count, cudaStream_t st);
+cudaError_t launch_mlp_train(const float* params, const void* feat, const float* dirs, const float* tgt, int n,
+                             float scale, float* grad, float* loss, int sm_count, cudaStream_t st);
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
+                        int t, cudaStream_t st);
+cudaError_t launch_pack(const float* p, void* w, float* b, cudaStream_t st);
+cudaError_t launch_xavier(float* p, uint64_t seed, cudaStream_t st);
+cudaError_t launch_f32_to_bf16_rows(const float* src, int n, int cols, void* dst, int ld, cudaStream_t st);
 
 }  // namespace mcrt

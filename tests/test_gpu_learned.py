@@ -1,0 +1,118 @@
+"""GPU parity of the learned proposal's network against the FP64 oracle.
+
+* Inference (tensor cores, BF16 operands, FP32 accumulation): raw outputs
+  within a bound derived from the arithmetic -- the GPU rounds each layer's
+  activations to BF16 (relative error <= 2^-9, taken as 2^-8), the error is
+  carried through the layers by |W| and the GELU Lipschitz constant (1.13),
+  plus FP32 accumulation slack; the mixture epilogue is checked against the
+  oracle's mixture of the same raw outputs.
+* Training (FP32): the gradient of the mean KL loss against the oracle's
+  FP64 gradient on the same records, and one Adam step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1902_01137_gb300 as m
+    from paper_1902_01137_gb300 import build
+    build.build()
+    ctx = m.Context(0)
+    yield m, ctx
+    ctx.close()
+
+
+def bf16(x):
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(x)).astype(np.float64)
+
+
+def gelu(x):
+    return 0.5 * x * (1 + np.tanh(0.7978845608028654 * (x + 0.044715 * x ** 3)))
+
+
+def _params(orc, seed):
+    p = orc.xavier_init(seed)
+    r = np.random.default_rng(seed)
+    p[p.size - 40:] = r.normal(size=40) * 0.5
+    return p.astype(np.float32).astype(np.float64)
+
+
+def _features(n, seed):
+    r = np.random.default_rng(seed)
+    x = np.concatenate([r.uniform(-1, 1, (n, 3)), r.normal(size=(n, 3)), r.uniform(-8, 6, (n, 3))], axis=1)
+    x[:, 3:6] /= np.linalg.norm(x[:, 3:6], axis=1, keepdims=True)
+    return x.astype(np.float32)
+
+
+def test_mlp_inference_vs_oracle(env, orc):
+    m, ctx = env
+    p = _params(orc, 3)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        n = 1000                                   # 31 full warp tiles and a ragged tail
+        x = _features(n, 4)
+        mix, raw = prop.eval(x)
+        W1, b1, W2, b2, W3, b3, W4, b4 = orc.mlp_split(p)
+        Wb = [bf16(W) for W in (W1, W2, W3, W4)]
+        a = bf16(x.astype(np.float64))
+        ref = orc.mlp_forward(np.concatenate([Wb[0].ravel(), b1, Wb[1].ravel(), b2, Wb[2].ravel(), b3,
+                                              Wb[3].ravel(), b4]), a)
+        # error bound through the layers
+        da = np.zeros_like(a)
+        h = a
+        for W, b in ((Wb[0], b1), (Wb[1], b2), (Wb[2], b3)):
+            z = h @ W.T + b
+            dz = (np.abs(da) @ np.abs(W).T) + 64 * 2.0 ** -23 * (np.abs(h) @ np.abs(W).T + np.abs(b))
+            h = gelu(z)
+            da = 1.13 * dz + 2.0 ** -8 * np.abs(h)
+        bound = np.abs(da) @ np.abs(Wb[3]).T + 64 * 2.0 ** -23 * (np.abs(h) @ np.abs(Wb[3]).T + np.abs(b4))
+        err = np.abs(raw - ref)
+        assert np.all(err <= bound + 1e-6), (err.max(), (err - bound).max())
+        # the epilogue: mixture of the raw outputs
+        for i in range(0, n, 97):
+            mu, ka, pi = orc.mixture(raw[i].astype(np.float64))
+            got = mix[i].reshape(8, 5)
+            np.testing.assert_allclose(got[:, :3], mu, rtol=1e-5, atol=1e-6)
+            np.testing.assert_allclose(got[:, 3], ka, rtol=1e-5, atol=1e-6)
+            np.testing.assert_allclose(got[:, 4], pi, rtol=1e-4, atol=1e-7)
+    finally:
+        prop.close()
+
+
+def test_mlp_gradient_and_adam_vs_oracle(env, orc):
+    m, ctx = env
+    p = _params(orc, 5)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        n = 3000
+        x = _features(n, 6)
+        r = np.random.default_rng(7)
+        d = r.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+        t = r.exponential(size=n)
+        t[::7] = 0.0                               # records that brought nothing back
+        loss, g = prop.train_step(x, d.astype(np.float32), t.astype(np.float32), lr=0.0)
+        xb = bf16(x.astype(np.float64))            # the network sees BF16 features
+        oloss, og = orc.mlp_loss_grad(p, xb, d.astype(np.float32).astype(np.float64),
+                                      t.astype(np.float32).astype(np.float64))
+        assert loss == pytest.approx(oloss, rel=1e-4)
+        scale = np.abs(og).max()
+        assert np.abs(g - og).max() <= 2e-4 * scale, (np.abs(g - og).max(), scale)
+        # one Adam step
+        lr = 1e-3
+        loss2, g2 = prop.train_step(x, d.astype(np.float32), t.astype(np.float32), lr=lr)
+        newp = prop.params.astype(np.float64)
+        pp = p.copy(); mm = np.zeros_like(p); vv = np.zeros_like(p)
+        orc.adam_step(pp, mm, vv, g2.astype(np.float64), 1, lr=lr)
+        np.testing.assert_allclose(newp, pp, rtol=1e-5, atol=1e-7)
+    finally:
+        prop.close()
