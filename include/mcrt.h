@@ -48,6 +48,7 @@ extern "C" {
 typedef struct mcrt_ctx mcrt_ctx;
 typedef struct mcrt_scene mcrt_scene;
 typedef struct mcrt_tally mcrt_tally;
+typedef struct mcrt_proposal mcrt_proposal;
 
 typedef enum {
     MCRT_OK = 0,
@@ -191,6 +192,20 @@ typedef struct {
                                /* a path start, ray start or vertex before that */
                                /* work runs (1..32; 0 = default 8).  Launch     */
                                /* shape only: results do not depend on it       */
+    struct mcrt_proposal* proposal; /* NULL: plain HG sampling.  Else the first */
+                               /* n_learned volume vertices of every path draw  */
+                               /* their direction by one-sample MIS from        */
+                               /* alpha p_HG + (1 - alpha) q_network, weight    */
+                               /* p_HG / q (unbiased for any network)           */
+    int32_t n_learned;         /* 0 = 8                                         */
+    float mis_alpha;           /* HG share alpha in (0, 1]; 0 = 0.5             */
+    int32_t learn;             /* 1: after each batch of paths, train the       */
+                               /* network (Adam) on the vertices that batch     */
+                               /* produced; the first batch of an untrained     */
+                               /* network samples HG only                       */
+    int32_t batch_paths;       /* paths per batch in learned mode; 0 = 2^21     */
+    float learning_rate;       /* 0 = 1e-3                                      */
+    int32_t train_steps;       /* Adam steps per batch; 0 = 1                   */
     double deadline_ms;        /* > 0: stop and report MCRT_ERR_TIMEOUT after   */
                                /* this much device time                         */
     const volatile int32_t* cancel_flag; /* NULL, or a flag in host-mapped or   */
@@ -297,8 +312,6 @@ MCRT_API int mcrt_tally_destroy(mcrt_tally* tally);
 /* Inference runs on the tensor cores in BF16 with FP32 accumulation;    */
 /* training keeps FP32 master weights and Adam moments.                   */
 /* --------------------------------------------------------------------- */
-typedef struct mcrt_proposal mcrt_proposal;
-
 /* Number of network parameters (11,560). */
 MCRT_API int mcrt_proposal_nparams(int32_t* n);
 

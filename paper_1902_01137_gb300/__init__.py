@@ -65,6 +65,9 @@ class TraceOpts(C.Structure):
     _fields_ = [("tau_merge", C.c_float), ("finest_level", C.c_int32), ("max_order", C.c_int32),
                 ("sun_mode", C.c_int32), ("chunk", C.c_int32), ("block_size", C.c_int32),
                 ("grid_size", C.c_int32), ("count_events", C.c_int32), ("rare_batch", C.c_int32),
+                ("proposal", C.c_void_p), ("n_learned", C.c_int32), ("mis_alpha", C.c_float),
+                ("learn", C.c_int32), ("batch_paths", C.c_int32), ("learning_rate", C.c_float),
+                ("train_steps", C.c_int32),
                 ("deadline_ms", C.c_double),
                 ("cancel_flag", C.c_void_p)]
 
@@ -401,6 +404,8 @@ class Scene:
         for k, v in kw.items():
             if k == "cancel_flag":
                 o.cancel_flag = C.c_void_p(v)
+            elif k == "proposal":
+                o.proposal = v.h if hasattr(v, "h") else v
             else:
                 setattr(o, k, v)
         return o

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 
 #include "mcrt_internal.h"
 
@@ -350,6 +351,14 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
     if (o->block_size > 128) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: block_size above 128", who);
     if (o->grid_size < 0 || o->chunk < 0) return fail(ctx, MCRT_ERR_ARG, "%s: negative launch shape", who);
     if (o->rare_batch < 0 || o->rare_batch > 32) return fail(ctx, MCRT_ERR_ARG, "%s: rare_batch must be in [0, 32]", who);
+    if (o->proposal) {
+        if (o->proposal->ctx != ctx) return fail(ctx, MCRT_ERR_ARG, "%s: proposal belongs to another context", who);
+        if (o->n_learned < 0 || o->n_learned > 64) return fail(ctx, MCRT_ERR_ARG, "%s: n_learned must be in [0, 64]", who);
+        if (!(o->mis_alpha >= 0.0f && o->mis_alpha <= 1.0f)) return fail(ctx, MCRT_ERR_ARG, "%s: mis_alpha must be in [0, 1]", who);
+        if (o->batch_paths < 0 || o->train_steps < 0 || !(o->learning_rate >= 0.0f))
+            return fail(ctx, MCRT_ERR_ARG, "%s: bad learned-mode options", who);
+        if (o->count_events) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: counting with a proposal", who);
+    }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     return MCRT_OK;
 }
@@ -441,6 +450,140 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     return MCRT_OK;
 }
 
+// Learned proposal: paths are traced in batches; within a batch, round 0
+// runs fresh paths up to their first volume vertex, the network evaluates the
+// stopped paths' features, and each later round resumes them (one-sample MIS
+// direction) up to the next learned vertex; after n_learned rounds the paths
+// finish with HG sampling.  With learning on, every batch ends with Adam
+// steps on the vertices its resumed paths recorded.
+int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_trace_opts* o, mcrt_tally* t,
+                unsigned long long spp, const char* who)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    mcrt_proposal* prop = o->proposal;
+    const bool bf16 = sc->storage == MCRT_STORAGE_BF16;
+    const int NL = o->n_learned ? o->n_learned : 8;
+    const float alpha = o->mis_alpha > 0.0f ? o->mis_alpha : 0.5f;
+    const float lr = o->learning_rate > 0.0f ? o->learning_rate : 1e-3f;
+    const int steps = o->train_steps ? o->train_steps : 1;
+    unsigned long long B = o->batch_paths ? (unsigned long long)o->batch_paths : (1ull << 21);
+    if (B < spp) B = spp;
+    B = (B / spp) * spp;                                 // batches hold whole pixels
+    const unsigned long long total = P0.total;
+    if (B > total) B = total;
+    const unsigned rec_cap = o->learn ? (1u << 20) : 0u;
+    const int block = o->block_size ? o->block_size : 128;
+    const int grid = o->grid_size ? o->grid_size : ctx->sm_count * trace_learned_blocks_per_sm(sensor, bf16, block);
+    // work buffers
+    uint4 *qa = nullptr, *qb = nullptr, *fa = nullptr, *fb = nullptr, *rfeat = nullptr;
+    float *mix = nullptr, *fin = nullptr, *rdir = nullptr, *rval = nullptr, *tgt = nullptr;
+    unsigned* cnt = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(p), bytes ? bytes : 16, ctx->stream);
+    };
+    A(&qa, B * 64); A(&qb, B * 64); A(&fa, B * 32); A(&fb, B * 32); A(&mix, B * 160); A(&fin, B * 4);
+    A(&cnt, 16);
+    if (rec_cap) { A(&rfeat, (size_t)rec_cap * 32); A(&rdir, (size_t)rec_cap * 12); A(&rval, (size_t)rec_cap * 16); A(&tgt, (size_t)rec_cap * 4); }
+    auto release = [&]() {
+        for (void* p : {(void*)qa, (void*)qb, (void*)fa, (void*)fb, (void*)mix, (void*)fin, (void*)cnt, (void*)rfeat,
+                        (void*)rdir, (void*)rval, (void*)tgt})
+            if (p) cudaFreeAsync(p, ctx->stream);
+    };
+    if (e != cudaSuccess) { release(); return fail(ctx, MCRT_ERR_OOM, "%s: %s", who, cudaGetErrorString(e)); }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, ctx->stream);
+    int status = 0;
+    const int lev2 = sc->levels >= 2 ? 2 : sc->levels;
+    for (unsigned long long b0 = 0; b0 < total && e == cudaSuccess && status == 0; b0 += B) {
+        const unsigned long long nb = (total - b0 < B) ? total - b0 : B;
+        const bool warm = o->learn && prop->step == 0;   // untrained network: HG only, records collected
+        TraceParams P = P0;
+        P.learned = 1;
+        P.n_learned = NL;
+        P.mis_alpha = warm ? 1.0f : alpha;
+        P.path_base = b0;
+        P.final_score = fin;
+        P.pyr1 = sc->d_pyr + sc->lev_off[1];
+        P.pyr2 = sc->d_pyr + sc->lev_off[lev2];
+        for (int a = 0; a < 3; ++a) { P.d1[a] = sc->lev_dims[3 + a]; P.d2[a] = sc->lev_dims[3 * lev2 + a]; }
+        P.lev2 = lev2;
+        P.rec_cap = rec_cap;
+        P.rec_slots = rec_cap ? rec_cap / (unsigned)NL : 0u;
+        P.rec_feat = rfeat; P.rec_dir = rdir; P.rec_val = rval;
+        P.rec_count = rec_cap ? cnt + 1 : nullptr;
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 16, ctx->stream);
+        uint4 *qin = qa, *qout = qb, *fin_feat = fa, *fout = fb;
+        unsigned n_in = 0;
+        for (int r = 0; r <= NL && e == cudaSuccess; ++r) {
+            P.resume = r > 0;
+            P.total = r == 0 ? nb : n_in;
+            P.chunk = r == 0 ? P0.chunk : 1u;
+            P.qin = qin; P.qin_feat = fin_feat; P.qin_mix = mix;
+            P.qout = qout; P.qout_feat = fout; P.qout_count = cnt; P.qout_cap = (unsigned)nb;
+            if (P.total == 0) break;
+            if (r > 0) {
+                ctx->launches++;
+                e = launch_mlp_infer(prop->d_wbf, prop->d_bias, fin_feat, (int)n_in, mix, nullptr, ctx->sm_count, ctx->stream);
+            }
+            if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), ctx->stream);
+            if (e == cudaSuccess) { ctx->launches++; e = launch_trace_learned(P, sensor, bf16, grid, block, ctx->stream); }
+            WorkState ws{};
+            unsigned n_out = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&n_out, cnt, 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&ws, t->d_work, sizeof(ws), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (ws.status) { status = ws.status; break; }
+            n_in = n_out;
+            // the outgoing buffers of this round are the incoming ones of the next
+            qin = (r % 2 == 0) ? qb : qa;
+            qout = (r % 2 == 0) ? qa : qb;
+            fin_feat = (r % 2 == 0) ? fb : fa;
+            fout = (r % 2 == 0) ? fa : fb;
+        }
+        if (e == cudaSuccess && status == 0 && rec_cap) {
+            unsigned nrec = 0;
+            e = cudaMemcpyAsync(&nrec, cnt + 1, 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (nrec > rec_cap) nrec = rec_cap;
+            if (e == cudaSuccess && nrec > 0) {
+                ctx->launches++;
+                e = launch_targets(rval, fin, nrec, tgt, ctx->stream);
+                for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+                    e = cudaMemsetAsync(prop->d_grad, 0, kMlpParams * sizeof(float), ctx->stream);
+                    if (e == cudaSuccess) {
+                        ctx->launches += 3;
+                        e = launch_mlp_train(prop->d_params, rfeat, rdir, tgt, (int)nrec, 1.0f / (float)nrec, prop->d_grad,
+                                             prop->d_loss, ctx->sm_count, ctx->stream);
+                    }
+                    if (e == cudaSuccess) {
+                        prop->step++;
+                        e = launch_adam(prop->d_params, prop->d_m, prop->d_v, prop->d_grad, kMlpParams, lr, 0.9f, 0.999f,
+                                        1e-8f, prop->step, ctx->stream);
+                    }
+                    if (e == cudaSuccess) e = launch_pack(prop->d_params, prop->d_wbf, prop->d_bias, ctx->stream);
+                }
+            }
+        }
+    }
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    CK(ctx, e);
+    CK(ctx, se);
+    t->kernel_ms = ms;
+    if (status == 1) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: deadline of %g ms expired", who, o->deadline_ms);
+    if (status == 2) return fail(ctx, MCRT_ERR_CANCELLED, "%s: cancelled", who);
+    return MCRT_OK;
+}
+
 }  // namespace
 
 int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp, uint64_t seed,
@@ -508,6 +651,17 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
     P.inv_width = 1.0f / (float)cam->width;
     P.inv_height = 1.0f / (float)cam->height;
     P.Lz = (float)sc->n[2] * sc->h[2];
+    if (o->proposal) {
+        P.deadline_ns = o->deadline_ms > 0.0 ? (unsigned long long)(o->deadline_ms * 1e6) : 0ull;
+        P.cancel = reinterpret_cast<const volatile int*>(o->cancel_flag);
+        P.max_order = o->max_order;
+        P.sun_mode = o->sun_mode;
+        P.max_steps = 1u << 22;
+        P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
+        P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+        P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
+        return run_learned(sc, P, kCamera, o, t, spp, who);
+    }
     return run_trace(sc, P, kCamera, o, t, who);
 }
 
@@ -537,6 +691,17 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.spp = 1;
     P.Lz = (float)sc->n[2] * sc->h[2];
+    if (o->proposal) {
+        P.deadline_ns = o->deadline_ms > 0.0 ? (unsigned long long)(o->deadline_ms * 1e6) : 0ull;
+        P.cancel = reinterpret_cast<const volatile int*>(o->cancel_flag);
+        P.max_order = o->max_order;
+        P.sun_mode = o->sun_mode;
+        P.max_steps = 1u << 22;
+        P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
+        P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+        P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
+        return run_learned(sc, P, kFlux, o, t, 1ull, who);
+    }
     return run_trace(sc, P, kFlux, o, t, who);
 }
 

@@ -99,6 +99,33 @@ struct TraceParams {
     float tan_half, aspect;    // tan(fov/2), height/width
     float inv_width, inv_height;
     float Lz;
+    // learned proposal (wavefront rounds): paths stop at their first
+    // n_learned volume vertices, the network evaluates the queue, and the next
+    // launch resumes them
+    int learned;               // 0 plain HG; 1 learned rounds
+    int resume;                // 0: fresh paths [0, total); 1: queue slots [0, total)
+    int n_learned;             // volume vertices per path drawn with the network
+    float mis_alpha;           // HG share of the one-sample MIS mixture
+    unsigned long long path_base;  // first path id of the batch (record / final-score index origin)
+    const uint4* qin;          // resumed states, 4 x uint4 per slot
+    const uint4* qin_feat;     // their feature rows (16 bf16 = 2 uint4)
+    const float* qin_mix;      // their mixture parameters (40 floats)
+    uint4* qout;               // suspended states
+    uint4* qout_feat;          // suspended feature rows
+    unsigned* qout_count;
+    unsigned qout_cap;
+    // training records (written when a resumed vertex samples its direction)
+    uint4* rec_feat;           // feature rows
+    float* rec_dir;            // 3 floats
+    float* rec_val;            // 4 floats: score before the vertex, w*omega, own estimate, path index
+    unsigned* rec_count;
+    unsigned rec_cap;
+    unsigned rec_slots;        // only queue slots below this are recorded
+    float* final_score;        // per path of the batch
+    const float* pyr1;         // level-1 majorants (features)
+    const float* pyr2;         // level-2 (or top) majorants
+    int d1[3], d2[3];
+    int lev2;                  // level of pyr2
     // outputs
     double* s1;
     double* s2;
@@ -119,6 +146,9 @@ cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStre
 cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count, int grid, int block,
                          cudaStream_t st);
 int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block);
+cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
+int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
+cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);
 cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, double* out,
                             cudaStream_t st);
 cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,

@@ -30,6 +30,8 @@
 // start, ray start, traversal step or vertex); one 8-byte load (the voxel of
 // a tentative collision or the leaf-map entry of the leaf entered); the leaf
 // set-up; the end of a ray or path.
+#include <cuda_bf16.h>
+
 #include "mcrt_internal.h"
 
 #ifndef MCRT_TRACE_MIN_BLOCKS
@@ -66,9 +68,9 @@ constexpr int kSections = 9;
 // ended a flight.  Every lane evaluates exactly one Philox block per
 // iteration at one site, whose counter depends on the phase; the voxel /
 // leaf-entry load and the leaf set-up also run at one site each.
-enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX };
+enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME };
 
-template <int SENSOR, bool BF16, bool COUNT>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
     constexpr int NQ = (SENSOR == kCamera) ? 1 : 3;   // quantities per path
@@ -92,6 +94,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     float tau = 0.0f, Ts = 1.0f, w = 1.0f, score = 0.0f, cf = 0.0f, tdir = 0.0f;
     bool term_after = false, vground = false;
     float vk = 0.0f;                        // extinction at the vertex
+    uint32_t lv = 0;                        // volume vertices so far (learned mode)
+    uint32_t cur_rec = 0xFFFFFFFFu;         // training record awaiting its own estimate
+    bool suspend = false;                   // stop this path until the network has run
     float vx[3] = {0.0f, 0.0f, 0.0f}, nd[3] = {0.0f, 0.0f, 1.0f};
     unsigned long long cnt[kCounters];
 #pragma unroll
@@ -154,7 +159,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (pid < P.total) {
                     pend = min(pid + (unsigned long long)P.chunk, P.total);
                     chunk = true;
-                    phase = PH_START;
+                    phase = (LEARNED && P.resume) ? PH_RESUME : PH_START;
+                    if (LEARNED && !P.resume) { pid += P.path_base; pend += P.path_base; }
                     if constexpr (SENSOR == kCamera) {
                         const unsigned long long pix = pid / P.spp;
                         cell = (unsigned)pix;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         // ---- rare phases (path start, ray start, vertex) run in batches: a
         //      lane waits until enough lanes of its warp need the same kind of
         //      work, or until no lane is stepping -------------------------------
-        const bool rare = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX;
+        const bool rare = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX || phase == PH_RESUME;
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         // ---- phase work before the load ---------------------------------------
         int evc = EV_NONE;
         float p[3];
+        int nv[3] = {0, 0, 0};
         const uint2* ptr = nullptr;
         uint32_t sub = 0;
         int st = kInside;
@@ -291,7 +298,6 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             // one step: to the tentative collision inside the leaf, or across
             // the leaf's exit face; both share the point and voxel arithmetic
             const float tn = tent ? fminf(R.t + __fdividef(tau, R.M), R.texit) : R.texit;
-            int nv[3];
             advance(S, R, tn, !tent, p, nv);
             if (tent) {
                 R.t = tn;
@@ -364,6 +370,94 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
 
+        if (LEARNED && ph == PH_RESUME) {
+            // resume a path stopped at a learned vertex: state, network output,
+            // one-sample MIS direction, weight p_HG / q
+            const uint32_t slot = (uint32_t)pid;
+            const uint4 q0 = P.qin[4 * (size_t)slot], q1 = P.qin[4 * (size_t)slot + 1];
+            const uint4 q2 = P.qin[4 * (size_t)slot + 2], q3 = P.qin[4 * (size_t)slot + 3];
+            pid = (unsigned long long)q0.x | ((unsigned long long)q0.y << 32);
+            pend = pid + 1;
+            ev = q0.z;
+            lv = q0.w;
+            vx[0] = __uint_as_float(q1.x); vx[1] = __uint_as_float(q1.y); vx[2] = __uint_as_float(q1.z);
+            vk = __uint_as_float(q1.w);
+            R.d[0] = __uint_as_float(q2.x); R.d[1] = __uint_as_float(q2.y); R.d[2] = __uint_as_float(q2.z);
+            w = __uint_as_float(q2.w);
+            score = __uint_as_float(q3.x);
+            tdir = __uint_as_float(q3.y);
+            term_after = false;
+            if constexpr (SENSOR == kCamera) cell = (unsigned)(pid / P.spp);
+            kind = kMain;
+            c2 = ev << 2;
+            const uint4 xv = draw_block(pid, ev << 2, kBlockVertex, P.key);
+            const uint4 xl = draw_block(pid, ev << 2, kBlockVertex - 1u, P.key);
+            const float xi1 = u01(xv.x), xi2 = u01(xv.y), xr = u01(xv.z), xc = u01(xv.w), xlobe = u01(xl.x);
+            const int order = (int)ev + 1;
+            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
+            const float om = omega_at(S, vk);
+            const float mu_s = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
+            cf = score_it ? w * om * hg_pdf(S.g, mu_s) : 0.0f;
+            const float* mix = P.qin_mix + 40 * (size_t)slot;
+            if (xc <= P.mis_alpha) {
+                rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
+            } else {
+                int j = 7;
+                float cum = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    cum += __ldg(mix + 5 * i + 4);
+                    if (j == 7 && i < 7 && xlobe <= cum) j = i;
+                }
+                const float mu_l[3] = {__ldg(mix + 5 * j), __ldg(mix + 5 * j + 1), __ldg(mix + 5 * j + 2)};
+                const float kap = __ldg(mix + 5 * j + 3);
+                float cw = 1.0f + __logf(xi1 + (1.0f - xi1) * __expf(-2.0f * kap)) / kap;
+                cw = fminf(fmaxf(cw, -1.0f), 1.0f);
+                rotate_dir(mu_l, cw, xi2, nd);
+            }
+            const float phg = hg_pdf(S.g, R.d[0] * nd[0] + R.d[1] * nd[1] + R.d[2] * nd[2]);
+            float qv = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float kap = __ldg(mix + 5 * i + 3);
+                const float c = __ldg(mix + 5 * i) * nd[0] + __ldg(mix + 5 * i + 1) * nd[1] + __ldg(mix + 5 * i + 2) * nd[2];
+                qv += __ldg(mix + 5 * i + 4) * kap / (2.0f * kPi * (-expm1f(-2.0f * kap))) * __expf(kap * (c - 1.0f));
+            }
+            const float qmix = P.mis_alpha * phg + (1.0f - P.mis_alpha) * qv;
+            // training record: features, direction, score so far, w * omega
+            if (P.rec_count && slot < P.rec_slots) {
+                const unsigned idx = atomicAdd(P.rec_count, 1u);
+                if (idx < P.rec_cap) {
+                    P.rec_feat[2 * (size_t)idx] = P.qin_feat[2 * (size_t)slot];
+                    P.rec_feat[2 * (size_t)idx + 1] = P.qin_feat[2 * (size_t)slot + 1];
+                    P.rec_dir[3 * (size_t)idx] = nd[0];
+                    P.rec_dir[3 * (size_t)idx + 1] = nd[1];
+                    P.rec_dir[3 * (size_t)idx + 2] = nd[2];
+                    P.rec_val[4 * (size_t)idx] = score;
+                    P.rec_val[4 * (size_t)idx + 1] = w * om;
+                    P.rec_val[4 * (size_t)idx + 2] = 0.0f;
+                    P.rec_val[4 * (size_t)idx + 3] = __uint_as_float((uint32_t)(pid - P.path_base));
+                    cur_rec = idx;
+                }
+            }
+            w *= om * __fdividef(phg, fmaxf(qmix, 1e-30f));
+            ++lv;
+            if (COUNT) cnt[C_REAL]++;
+            term_after = (P.max_order > 0) && (order >= P.max_order);
+            if (!term_after && w < 0.01f) {
+                if (xr * 0.01f <= w) w = 0.01f;
+                else term_after = true;
+            }
+            if (score_it) {
+                kind = kSunLocal;
+                c2 = (ev << 2) | 1u;
+                Ts = 1.0f;
+                phase = PH_BEGIN;
+            } else {
+                Ts = 0.0f;
+                evc = EV_SUN_END;
+            }
+        }
         mark(5);
         // ---- the one load: voxel word or leaf-map entry ---------------------
         uint2 val = make_uint2(0u, 0u);
@@ -395,6 +489,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     vk = k;
                     vground = false;
                     phase = PH_VERTEX;
+                    if (LEARNED && lv < (uint32_t)P.n_learned) suspend = true;
                 } else {
                     tau = nt;
                 }
@@ -434,6 +529,10 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     phase = PH_BEGIN;
                 } else {
                     score += cf * Ts;
+                    if (LEARNED && cur_rec != 0xFFFFFFFFu) {
+                        P.rec_val[4 * (size_t)cur_rec + 2] = cf * Ts;
+                        cur_rec = 0xFFFFFFFFu;
+                    }
                     if (term_after) {
                         path_done = true;
                     } else {
@@ -460,8 +559,58 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     cnt[C_PATHS]++;
                     max_iters = max(max_iters, path_iters);
                 }
+                if (LEARNED && P.final_score) P.final_score[pid - P.path_base] = score;
                 ++pid;
                 phase = (pid < pend) ? PH_START : PH_IDLE;
+            }
+        }
+        // ---- stop paths at a learned vertex: state and features to the queue
+        if (LEARNED) {
+            const unsigned smask = __ballot_sync(kFull, suspend);
+            if (smask) {
+                const int leader = __ffs(smask) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(P.qout_count, (unsigned)__popc(smask));
+                base = __shfl_sync(kFull, base, leader);
+                if (suspend) {
+                    const unsigned slot = base + (unsigned)__popc(smask & lt_mask);
+                    if (slot < P.qout_cap) {
+                        // features: position in [-1, 1], incoming direction, ln(k), ln(M1), ln(M2)
+                        const float Lz = (float)S.n[2] * S.h[2];
+                        float f[9];
+                        f[0] = 2.0f * vx[0] / S.Lper[0] - 1.0f;
+                        f[1] = 2.0f * vx[1] / S.Lper[1] - 1.0f;
+                        f[2] = 2.0f * vx[2] / Lz - 1.0f;
+                        f[3] = R.d[0]; f[4] = R.d[1]; f[5] = R.d[2];
+                        f[6] = logf(vk + 1e-6f);
+                        const float M1 = __ldg(P.pyr1 + ((size_t)(nv[2] >> 3) * P.d1[1] + (nv[1] >> 3)) * P.d1[0] +
+                                               (nv[0] >> 3));
+                        const int s2 = 3 * P.lev2;
+                        const float M2 = __ldg(P.pyr2 + ((size_t)(nv[2] >> s2) * P.d2[1] + (nv[1] >> s2)) * P.d2[0] +
+                                               (nv[0] >> s2));
+                        f[7] = logf(M1 + S.k_gas + 1e-6f);
+                        f[8] = logf(M2 + S.k_gas + 1e-6f);
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const __nv_bfloat162 v = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                            pk[i] = *reinterpret_cast<const uint32_t*>(&v);
+                        }
+                        pk[4] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f[8]));
+                        pk[5] = pk[6] = pk[7] = 0u;
+                        P.qout_feat[2 * (size_t)slot] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        P.qout_feat[2 * (size_t)slot + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        P.qout[4 * (size_t)slot] = make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), ev, lv);
+                        P.qout[4 * (size_t)slot + 1] = make_uint4(__float_as_uint(vx[0]), __float_as_uint(vx[1]),
+                                                                  __float_as_uint(vx[2]), __float_as_uint(vk));
+                        P.qout[4 * (size_t)slot + 2] = make_uint4(__float_as_uint(R.d[0]), __float_as_uint(R.d[1]),
+                                                                  __float_as_uint(R.d[2]), __float_as_uint(w));
+                        P.qout[4 * (size_t)slot + 3] = make_uint4(__float_as_uint(score), __float_as_uint(tdir), 0u, 0u);
+                    }
+                    suspend = false;
+                    ++pid;
+                    phase = (pid < pend) ? PH_START : PH_IDLE;
+                }
             }
         }
         mark(8);
@@ -548,20 +697,40 @@ __global__ void debug_philox_kernel(const uint32_t* __restrict__ ctr, const uint
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
 }
 
-template <int SENSOR, bool BF16, bool COUNT>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED>
 const void* kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT>);
+    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED>);
 }
 
 const void* pick(int sensor, bool bf16, bool count)
 {
     if (sensor == kCamera) {
-        if (bf16) return count ? kernel_ptr<kCamera, true, true>() : kernel_ptr<kCamera, true, false>();
-        return count ? kernel_ptr<kCamera, false, true>() : kernel_ptr<kCamera, false, false>();
+        if (bf16) return count ? kernel_ptr<kCamera, true, true, false>() : kernel_ptr<kCamera, true, false, false>();
+        return count ? kernel_ptr<kCamera, false, true, false>() : kernel_ptr<kCamera, false, false, false>();
     }
-    if (bf16) return count ? kernel_ptr<kFlux, true, true>() : kernel_ptr<kFlux, true, false>();
-    return count ? kernel_ptr<kFlux, false, true>() : kernel_ptr<kFlux, false, false>();
+    if (bf16) return count ? kernel_ptr<kFlux, true, true, false>() : kernel_ptr<kFlux, true, false, false>();
+    return count ? kernel_ptr<kFlux, false, true, false>() : kernel_ptr<kFlux, false, false, false>();
+}
+
+const void* pick_learned(int sensor, bool bf16)
+{
+    if (sensor == kCamera) return bf16 ? kernel_ptr<kCamera, true, false, true>() : kernel_ptr<kCamera, false, false, true>();
+    return bf16 ? kernel_ptr<kFlux, true, false, true>() : kernel_ptr<kFlux, false, false, true>();
+}
+
+// Target weight of each training record: the radiance its sampled direction
+// brought back, (final score - score before the vertex - the vertex's own
+// local estimate) / (w * omega).
+__global__ void targets_kernel(const float* __restrict__ rec_val, const float* __restrict__ final_score, unsigned n,
+                               float* __restrict__ tgt)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = reinterpret_cast<const float4*>(rec_val)[i];
+    const float fin = final_score[__float_as_uint(v.w)];
+    const float t = v.y > 0.0f ? (fin - v.x - v.z) / v.y : 0.0f;
+    tgt[i] = fmaxf(t, 0.0f);
 }
 
 }  // namespace
@@ -571,6 +740,26 @@ cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
     return cudaLaunchKernel(pick(sensor, bf16, count), dim3(grid), dim3(block), args, 0, st);
+}
+
+cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st)
+{
+    void* args[] = {const_cast<TraceParams*>(&P)};
+    return cudaLaunchKernel(pick_learned(sensor, bf16), dim3(grid), dim3(block), args, 0, st);
+}
+
+int trace_learned_blocks_per_sm(int sensor, bool bf16, int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_learned(sensor, bf16), block, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    targets_kernel<<<(n + 255) / 256, 256, 0, st>>>(rec_val, final_score, n, tgt);
+    return cudaGetLastError();
 }
 
 int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block)

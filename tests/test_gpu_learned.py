@@ -116,3 +116,73 @@ def test_mlp_gradient_and_adam_vs_oracle(env, orc):
         np.testing.assert_allclose(newp, pp, rtol=1e-5, atol=1e-7)
     finally:
         prop.close()
+
+
+# ---------------------------------------------------------------------------
+# the learned proposal inside the tracer
+# ---------------------------------------------------------------------------
+def _oscene(orc, sp, **kw):
+    a = dict(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear, ssa_clear=sp.ssa_clear,
+             ssa_cloud=sp.ssa_cloud, g=sp.g, ground_albedo=sp.ground_albedo, sun_zenith_deg=sp.sun_zenith_deg)
+    a.update(kw)
+    return orc.Scene(**a)
+
+
+def _close(a, sa, b, sb):
+    return abs(a - b) <= 4.0 * math.hypot(sa, sb)
+
+
+def test_learned_tracer_unbiased_and_matches_oracle(env, orc):
+    """A fixed network (no training): the MIS-weighted estimate equals the
+    plain one (GPU and oracle) and the oracle's learned estimate with the same
+    parameters, within 4 combined SE, for flux and image tallies."""
+    import scenes
+    m, ctx = env
+    sp = scenes.blobs_small(0)
+    p = _params(orc, 21)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        n = 100000
+        plain = sc.trace_flux(n, seed=41)
+        learned = sc.trace_flux(n, seed=42, proposal=prop, batch_paths=30000)
+        ol, _ = orc.trace_flux(_oscene(orc, sp, mlp=p), n, seed=42)
+        op, _ = orc.trace_flux(_oscene(orc, sp), n, seed=41)
+        for q in range(3):
+            assert _close(learned.mean[q], learned.se[q], plain.mean[q], plain.se[q]), (q, learned.mean, plain.mean)
+            assert _close(learned.mean[q], learned.se[q], ol.mean[q], ol.se[q]), (q, learned.mean, ol.mean)
+            assert _close(plain.mean[q], plain.se[q], op.mean[q], op.se[q])
+        cam = scenes.nadir_camera(sp, 32, 32)
+        a = sc.trace_camera(cam, 64, seed=43)
+        b = sc.trace_camera(cam, 64, seed=44, proposal=prop, batch_paths=16384)
+        ma, mb = a.mean.mean(), b.mean.mean()
+        sa = math.sqrt((a.se ** 2).sum()) / a.se.size
+        sb = math.sqrt((b.se ** 2).sum()) / b.se.size
+        assert _close(ma, sa, mb, sb), (ma, mb, sa, sb)
+        blocks = lambda x: x.reshape(4, 8, 4, 8).sum(axis=(1, 3))
+        z = np.abs(blocks(a.mean) - blocks(b.mean)) / np.hypot(np.sqrt(blocks(a.se ** 2)), np.sqrt(blocks(b.se ** 2)))
+        assert int((z > 4).sum()) <= 1
+    finally:
+        prop.close()
+        sc.close()
+
+
+def test_online_training_changes_network_and_stays_unbiased(env, orc):
+    import scenes
+    m, ctx = env
+    sp = scenes.blobs_small(0)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, seed=5)
+    try:
+        p0 = prop.params.copy()
+        n = 200000
+        learned = sc.trace_flux(n, seed=51, proposal=prop, learn=1, batch_paths=25000, train_steps=4)
+        p1 = prop.params
+        assert np.abs(p1 - p0).max() > 1e-4            # Adam moved the weights
+        assert np.all(np.isfinite(p1))
+        plain = sc.trace_flux(n, seed=52)
+        for q in range(3):
+            assert _close(learned.mean[q], learned.se[q], plain.mean[q], plain.se[q]), (q, learned.mean, plain.mean)
+    finally:
+        prop.close()
+        sc.close()
