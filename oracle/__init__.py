@@ -397,15 +397,15 @@ def trace_camera(scene: Scene, cam: Camera, spp: int, seed: int, pix_range=None,
 
 
 def trace_flux(scene: Scene, npaths: int, seed: int, begin: int = 0, nthreads: int = 0):
-    """Domain-mean ground transmittance tallies (T_dir, T_dif, T_tot)."""
+    """Domain-mean ground transmittance tallies (T_dir, T_dif, T_tot, dT/dg)."""
     st = scene.struct()
-    sums = np.zeros(6, dtype=np.float64)
+    sums = np.zeros(8, dtype=np.float64)
     stats = np.zeros(4, dtype=np.int64)
     rc = lib().orc_trace_flux(C.byref(st), seed, begin, begin + npaths, _ptr(sums, C.c_double),
                               nthreads or default_threads(), _ptr(stats, C.c_int64))
     if rc != 0:
         raise ValueError("bad flux request")
-    return Tally(sums[0::2].copy(), sums[1::2].copy(), np.full(3, float(npaths))), stats
+    return Tally(sums[0::2].copy(), sums[1::2].copy(), np.full(4, float(npaths))), stats
 
 
 def trace_forward(scene: Scene, nphotons: int, seed: int, nthreads: int = 0):

@@ -802,9 +802,30 @@ static double omega_at(const orc_scene* S, double k_total)
     return (kc * S->ssa_cloud + kcl * S->ssa_clear) / k_total;
 }
 
+/* d/dg of ln p_HG(mu) = -2g / (1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu). */
+double orc_hg_dlog_dg(double g, double mu)
+{
+    return -2.0 * g / (1.0 - g * g) - 3.0 * (g - mu) / (1.0 + g * g - 2.0 * g * mu);
+}
+
+/* Backward path; *dscore (may be NULL) receives the derivative of the
+ * score with respect to the HG asymmetry g, by the score-function method:
+ * each local estimate c_j also contributes c_j (sum of d ln p_HG / dg of
+ * the directions sampled before vertex j + d ln p_HG / dg of its own phase
+ * value toward the sun); ground terms only carry the earlier sum. */
+static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
+                               orc_counts* C, int64_t* aborted, double* dscore);
+
 static double trace_backward(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                              orc_counts* C, int64_t* aborted)
 {
+    return trace_backward_d(S, p, d, seed, path, C, aborted, NULL);
+}
+
+static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
+                               orc_counts* C, int64_t* aborted, double* dscore)
+{
+    double sg = 0.0, ds = 0.0;
     double w = 1.0, score = 0.0;
     int lv = 0;                 /* volume vertices so far */
     const double* s = S->sun;
@@ -827,7 +848,9 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
             if (score_it) {
                 double Ts = transmissivity(S, p, s, &rs, C);
                 double mu = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
-                score += w * om * orc_hg_pdf(S->g, mu) * Ts;
+                double c = w * om * orc_hg_pdf(S->g, mu) * Ts;
+                score += c;
+                ds += c * (sg + orc_hg_dlog_dg(S->g, mu));
             }
             w *= om;
             double nd[3];
@@ -843,13 +866,16 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
                 double mu = orc_hg_sample_mu(S->g, uv[0]);
                 double phi = 2.0 * ORC_PI * uv[1];
                 rotate_dir(d, mu, phi, nd);
+                sg += orc_hg_dlog_dg(S->g, mu);
             }
             ++lv;
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
         } else { /* ground */
             if (score_it) {
                 double Ts = transmissivity(S, p, s, &rs, C);
-                score += w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
+                double c = w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
+                score += c;
+                ds += c * sg;
             }
             w *= S->ground_albedo;
             cosine_up(uv[0], uv[1], d);
@@ -860,6 +886,7 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
             else break;
         }
     }
+    if (dscore) *dscore = ds;
     return score;
 }
 
@@ -936,7 +963,7 @@ static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp,
 /* One ground-flux path: uniform ground point, cosine-weighted upward
  * direction (stream (0, 2): four draws); direct part from stream (0, 3).
  * out[0] = T_dir, out[1] = T_dif = pi / mu0 * sum of local estimates. */
-static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[2],
+static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[3],
                       orc_counts* cnt, int64_t* aborted)
 {
     rng_t r;
@@ -952,10 +979,12 @@ static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double o
     rng_init(&rd, seed, path, 0, 3);
     double q[3] = {p[0], p[1], p[2]};
     double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
-    double score = trace_backward(S, p, d, seed, path, cnt, aborted);
+    double dsc = 0.0;
+    double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc);
     double mu0 = S->sun[2];
     out[0] = Tdir;
     out[1] = ORC_PI / mu0 * score;
+    out[2] = ORC_PI / mu0 * dsc;
 }
 
 /* ===================================================================== */
@@ -1047,16 +1076,17 @@ static void run_block(job_t* J, int64_t b)
             J->out[2 * pix + 1] += sc * sc;
         }
     } else if (J->kind == 1) {
-        double acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (uint64_t path = p0; path < p1; ++path) {
-            double o[2];
+            double o[3];
             flux_path(J->S, J->seed, path, o, &cnt, &ab);
             double tot = o[0] + o[1];
             acc[0] += o[0]; acc[1] += o[0] * o[0];
             acc[2] += o[1]; acc[3] += o[1] * o[1];
             acc[4] += tot;  acc[5] += tot * tot;
+            acc[6] += o[2]; acc[7] += o[2] * o[2];
         }
-        for (int i = 0; i < 6; ++i) J->out[6 * b + i] = acc[i];
+        for (int i = 0; i < 8; ++i) J->out[8 * b + i] = acc[i];
     } else {
         double acc[12];
         for (int i = 0; i < 12; ++i) acc[i] = 0.0;
@@ -1122,7 +1152,8 @@ int orc_trace_camera(const orc_scene* S, const orc_camera* C, uint32_t spp, uint
     return 0;
 }
 
-/* Flux: paths [begin, end); sums[6] = (sum, sum^2) of T_dir, T_dif, T_tot. */
+/* Flux: paths [begin, end); sums[8] = (sum, sum^2) of T_dir, T_dif, T_tot,
+ * dT/dg (score-function derivative with respect to the HG asymmetry). */
 int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end, double* sums,
                    int nthreads, int64_t* stats)
 {
@@ -1132,14 +1163,14 @@ int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t e
     J.S = S; J.kind = 1; J.seed = seed; J.begin = begin; J.end = end;
     J.block = 1024;
     J.nblocks = (int64_t)((end - begin + J.block - 1) / J.block);
-    J.out = (double*)calloc((size_t)(6 * J.nblocks + 6), sizeof(double));
+    J.out = (double*)calloc((size_t)(8 * J.nblocks + 8), sizeof(double));
     J.aborted = (int64_t*)calloc((size_t)(J.nblocks + 1), sizeof(int64_t));
     J.counts = (orc_counts*)calloc((size_t)(J.nblocks + 1), sizeof(orc_counts));
     run_job(&J, nthreads);
-    for (int i = 0; i < 6; ++i) sums[i] = 0.0;
+    for (int i = 0; i < 8; ++i) sums[i] = 0.0;
     int64_t ab = 0; orc_counts tot = {0, 0, 0};
     for (int64_t b = 0; b < J.nblocks; ++b) {
-        for (int i = 0; i < 6; ++i) sums[i] += J.out[6 * b + i];
+        for (int i = 0; i < 8; ++i) sums[i] += J.out[8 * b + i];
         ab += J.aborted[b];
         tot.tentative += J.counts[b].tentative; tot.real += J.counts[b].real; tot.leaves += J.counts[b].leaves;
     }

@@ -239,3 +239,54 @@ def test_free_path_exponential(orc):
     se = dist.std() / math.sqrt(dist.size)
     assert abs(dist.mean() - 1.0 / k) < 3 * se
     assert stats.kstest(dist, "expon", args=(0, 1.0 / k)).pvalue > 1e-3
+
+
+def test_dT_dg_score_estimator_matches_finite_differences(orc):
+    """d T_dif / d g by the score-function estimator against central
+    differences of T_dif at g +- 0.01 with common random numbers."""
+    sp = scenes.blobs_small(0)
+    n = 150000
+    g0, h = 0.85, 0.01
+    T0, _ = orc.trace_flux(_oscene(orc, sp, g=g0), n, seed=61)
+    Tp, _ = orc.trace_flux(_oscene(orc, sp, g=g0 + h), n, seed=61)
+    Tm, _ = orc.trace_flux(_oscene(orc, sp, g=g0 - h), n, seed=61)
+    fd = (Tp.mean[1] - Tm.mean[1]) / (2 * h)
+    est, se = T0.mean[3], T0.se[3]
+    # the central difference of means of correlated estimates: its own noise
+    # is bounded by that of the two runs (taken independent, conservative)
+    fd_se = math.hypot(Tp.se[1], Tm.se[1]) / (2 * h)
+    assert abs(est - fd) < 4 * math.hypot(se, fd_se), (est, fd, se, fd_se)
+    # the direct part does not depend on g
+    assert Tp.mean[0] == T0.mean[0] == Tm.mean[0]
+
+
+def test_dT_dg_single_scattering_closed_form(orc):
+    """Order-1 ground flux under a homogeneous slab over a black ground:
+    T_dif,1 = (pi/mu0) int_{up} L1(mu) mu dOmega with the transmitted single-
+    scattering radiance; its g-derivative is the same integral of d p_HG/dg."""
+    from scipy import integrate
+    kk, H, g, th0 = 0.7, 0.8, 0.6, 30.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, kk, levels=1, g=g, ssa_cloud=1.0, ssa_clear=1.0, sun_zenith_deg=th0)
+    T, _ = orc.trace_flux(_oscene(orc, sp, max_order=1), 200000, seed=62)
+    mu0 = math.cos(math.radians(th0))
+    tau = kk * H
+
+    def L1(mu, phi, dphase):
+        s = (math.sin(math.radians(th0)), 0.0, mu0)
+        d = (math.sqrt(1 - mu * mu) * math.cos(phi), math.sqrt(1 - mu * mu) * math.sin(phi), mu)   # looking up
+        c = d[0] * s[0] + d[1] * s[1] + d[2] * s[2]
+        pf = dphase(c)
+        if abs(mu - mu0) < 1e-9:
+            return pf * tau / mu0 * math.exp(-tau / mu0)
+        return pf * mu0 / (mu0 - mu) * (math.exp(-tau / mu0) - math.exp(-tau / mu))
+
+    pHG = lambda c: (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * c) ** 1.5)
+    # d p_HG / d g written out from the closed form of p_HG
+    dpHG = lambda c: pHG(c) * (-2 * g / (1 - g * g) - 1.5 * (2 * g - 2 * c) / (1 + g * g - 2 * g * c))
+    # T = (1 / mu0) int_{upper hemisphere} L(mu) mu dOmega  (F0 = 1)
+    flux = lambda dp: integrate.dblquad(lambda phi, mu: L1(mu, phi, dp) * mu, 0, 1, 0, 2 * math.pi,
+                                        epsabs=1e-9)[0] / mu0
+    want_T = flux(pHG)
+    want_d = flux(dpHG)
+    assert abs(T.mean[1] - want_T) < 3 * T.se[1], (T.mean[1], want_T)
+    assert abs(T.mean[3] - want_d) < 3 * T.se[3], (T.mean[3], want_d)
