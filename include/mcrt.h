@@ -263,6 +263,37 @@ MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, 
 MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
                                        const mcrt_trace_opts* opts, double* d_mean, double* d_stderr);
 
+/* Many flux problems in one persistent launch (paths of all items share one
+ * work queue; the paper builds one grid per spectral quadrature point and
+ * traces them separately, Sec. 3.1.1 and Sec. 6).  Item i traces npaths
+ * ground-flux paths through its scene with an extra uniform pure absorber
+ * k_gas (a spectral band's gas: majorants become M + k_gas, so one pyramid
+ * serves every band) under its own sun; path j of an item draws exactly the
+ * random numbers path j of mcrt_trace_flux with the item's seed draws.  The
+ * tally has n cells x 4 quantities: T_dir, T_dif, T_tot and dT_tot/dg, the
+ * derivative with respect to the HG asymmetry estimated along the same paths
+ * by the score-function method.  Scenes must have majorants; items must
+ * share FP32 or BF16 storage.  The learned proposal is not used here. */
+typedef struct {
+    const mcrt_scene* scene;
+    float k_gas;               /* gas absorption of the band [km^-1], >= 0     */
+    float sun_zenith_deg;      /* [0, 90)                                       */
+    float sun_azimuth_deg;
+    uint64_t npaths;           /* >= 1                                          */
+    uint64_t seed;
+} mcrt_batch_item;
+
+MCRT_API int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const mcrt_trace_opts* opts,
+                              mcrt_tally** tally_inout);
+
+/* Launch-shape autotuner for a batch: times mcrt_trace_batch on a fraction
+ * of every item's paths for each candidate (paths per claim 1, 2, 4, 8;
+ * rare-phase wait 4, 8, 12 lanes; 64 or 128 threads per block) and writes
+ * the fastest into *opts_inout (*best_ms: its time).  Results of a trace do
+ * not depend on these choices, only its speed. */
+MCRT_API int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, double path_fraction,
+                                 mcrt_trace_opts* opts_inout, float* best_ms);
+
 /* --------------------------------------------------------------------- */
 /* Tallies                                                                */
 /* --------------------------------------------------------------------- */

@@ -61,6 +61,11 @@ class CameraDesc(C.Structure):
                 ("fov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("k_gas", C.c_float), ("sun_zenith_deg", C.c_float),
+                ("sun_azimuth_deg", C.c_float), ("npaths", C.c_uint64), ("seed", C.c_uint64)]
+
+
 class TraceOpts(C.Structure):
     _fields_ = [("tau_merge", C.c_float), ("finest_level", C.c_int32), ("max_order", C.c_int32),
                 ("sun_mode", C.c_int32), ("chunk", C.c_int32), ("block_size", C.c_int32),
@@ -112,6 +117,8 @@ def _load():
         "mcrt_tally_destroy": [vp],
         "mcrt_debug_dda": [vp, P(f32), P(f32), f32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
+        "mcrt_trace_batch": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
+        "mcrt_autotune_batch": [vp, P(BatchItem), i32, C.c_double, P(TraceOpts), P(f32)],
         "mcrt_proposal_nparams": [P(i32)],
         "mcrt_proposal_create": [vp, u64, P(vp)],
         "mcrt_proposal_destroy": [vp],
@@ -520,3 +527,46 @@ class Proposal:
 
     def train_step(self, features, dirs, targets, lr=0.0):
         return mcrt_proposal_train_step(self.ctx.h, self.h, features, dirs, targets, lr)
+
+
+# ---------------------------------------------------------------------------
+# Batches
+# ---------------------------------------------------------------------------
+def make_batch_items(items):
+    """items: sequence of (scene handle, k_gas, sun zenith, sun azimuth, npaths, seed)."""
+    arr = (BatchItem * len(items))()
+    for i, (sc, kg, z, a, n, seed) in enumerate(items):
+        arr[i].scene = sc.h if hasattr(sc, "h") else sc
+        if arr[i].scene is None:
+            arr[i].scene = 0
+        arr[i].k_gas, arr[i].sun_zenith_deg, arr[i].sun_azimuth_deg = kg, z, a
+        arr[i].npaths, arr[i].seed = n, seed
+    return arr
+
+
+def mcrt_trace_batch(ctx, items, opts: TraceOpts, tally=None):
+    arr = items if isinstance(items, C.Array) else make_batch_items(items)
+    h = tally if tally is not None else C.c_void_p()
+    _check(_load().mcrt_trace_batch(ctx, arr, len(arr), C.byref(opts), C.byref(h)), ctx)
+    return h
+
+
+def mcrt_autotune_batch(ctx, items, fraction: float, opts: TraceOpts):
+    arr = items if isinstance(items, C.Array) else make_batch_items(items)
+    best = C.c_float()
+    _check(_load().mcrt_autotune_batch(ctx, arr, len(arr), fraction, C.byref(opts), C.byref(best)), ctx)
+    return opts, best.value
+
+
+def trace_batch(ctx: Context, items, tally=None, **kw):
+    """Returns Result with mean / se of shape (n_items, 4):
+    T_dir, T_dif, T_tot, dT_tot/dg."""
+    o = Scene._opts(**kw)
+    t = mcrt_trace_batch(ctx.h, items, o, tally)
+    try:
+        mean, se, n = mcrt_tally_read(ctx.h, t)
+        ms = mcrt_tally_kernel_ms(ctx.h, t)
+    finally:
+        if tally is None:
+            mcrt_tally_destroy(t)
+    return Result(mean.reshape(-1, 4), se.reshape(-1, 4), n.reshape(-1, 4), ms, {})

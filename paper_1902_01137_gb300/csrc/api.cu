@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 #include <utility>
 
 #include "mcrt_internal.h"
@@ -401,6 +402,7 @@ int get_tally(mcrt_ctx* ctx, int ncells, int nq, mcrt_tally** inout, const char*
         *inout = t;
     }
     const size_t m = (size_t)ncells * nq;
+    t->cell_n.clear();
     CK(ctx, cudaMemsetAsync(t->d_s1, 0, m * sizeof(double), ctx->stream));
     CK(ctx, cudaMemsetAsync(t->d_s2, 0, m * sizeof(double), ctx->stream));
     CK(ctx, cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), ctx->stream));
@@ -706,6 +708,145 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
 }
 
 // ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const mcrt_trace_opts* opts,
+                     mcrt_tally** tally)
+{
+    const char* who = "mcrt_trace_batch";
+    if (!ctx || !items || !tally) return fail(ctx, MCRT_ERR_ARG, "%s: NULL argument", who);
+    ctx->err.clear();
+    if (n < 1 || n > (1 << 20)) return fail(ctx, MCRT_ERR_ARG, "%s: item count %d not in [1, 2^20]", who, n);
+    mcrt_trace_opts dflt;
+    mcrt_trace_opts_default(&dflt);
+    const mcrt_trace_opts* o = opts ? opts : &dflt;
+    if (o->proposal) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: learned proposal in batches", who);
+    if (o->count_events) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: counting in batches", who);
+    const uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
+    std::vector<BatchItem> h((size_t)n);
+    unsigned long long begin = 0;
+    bool bf16 = false;
+    for (int i = 0; i < n; ++i) {
+        const mcrt_batch_item& it = items[i];
+        if (!it.scene || it.scene->ctx != ctx) return fail(ctx, MCRT_ERR_ARG, "%s: item %d: bad scene", who, i);
+        mcrt_scene* sc = const_cast<mcrt_scene*>(it.scene);
+        int rc = check_opts(sc, o, who);
+        if (rc) return rc;
+        if (it.npaths < 1) return fail(ctx, MCRT_ERR_ARG, "%s: item %d: npaths must be >= 1", who, i);
+        if (!(it.k_gas >= 0.0f) || !std::isfinite(it.k_gas))
+            return fail(ctx, MCRT_ERR_ARG, "%s: item %d: k_gas must be finite and >= 0", who, i);
+        if (!(it.sun_zenith_deg >= 0.0f && it.sun_zenith_deg < 90.0f) || !std::isfinite(it.sun_azimuth_deg))
+            return fail(ctx, MCRT_ERR_ARG, "%s: item %d: sun zenith must be in [0, 90)", who, i);
+        if (i > 0 && (sc->storage == MCRT_STORAGE_BF16) != bf16)
+            return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: items mix FP32 and BF16 storage", who);
+        bf16 = sc->storage == MCRT_STORAGE_BF16;
+        CK(ctx, cudaSetDevice(ctx->device));
+        rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+        if (rc) return rc;
+        h[i].S = make_dev_scene(sc, it.k_gas);
+        const double z = it.sun_zenith_deg * M_PI / 180.0, a = it.sun_azimuth_deg * M_PI / 180.0;
+        h[i].S.sun[0] = (float)(std::sin(z) * std::cos(a));
+        h[i].S.sun[1] = (float)(std::sin(z) * std::sin(a));
+        h[i].S.sun[2] = (float)std::cos(z);
+        h[i].begin = begin;
+        h[i].npaths = it.npaths;
+        h[i].key = make_uint2((uint32_t)it.seed, (uint32_t)(it.seed >> 32));
+        begin += (it.npaths + chunk - 1) / chunk * chunk;
+    }
+    int rc = get_tally(ctx, n, 4, tally, who);
+    if (rc) return rc;
+    mcrt_tally* t = *tally;
+    t->n_per_cell = 0;
+    t->cell_n.assign((size_t)n, 0);
+    for (int i = 0; i < n; ++i) t->cell_n[i] = items[i].npaths;
+    if (t->d_cell_n) dfree(ctx, t->d_cell_n);
+    t->d_cell_n = nullptr;
+    CK(ctx, cudaMallocAsync(reinterpret_cast<void**>(&t->d_cell_n), sizeof(unsigned long long) * (size_t)n,
+                            ctx->stream));
+    CK(ctx, cudaMemcpyAsync(t->d_cell_n, t->cell_n.data(), sizeof(unsigned long long) * (size_t)n,
+                            cudaMemcpyHostToDevice, ctx->stream));
+    BatchItem* d_items = nullptr;
+    CK(ctx, cudaMallocAsync(reinterpret_cast<void**>(&d_items), sizeof(BatchItem) * (size_t)n, ctx->stream));
+    cudaError_t e = cudaMemcpyAsync(d_items, h.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    TraceParams P{};
+    P.S = h[0].S;
+    P.items = d_items;
+    P.n_items = n;
+    P.total = begin;
+    P.chunk = chunk;
+    P.key = h[0].key;
+    P.spp = 1;
+    P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
+    P.deadline_ns = o->deadline_ms > 0.0 ? (unsigned long long)(o->deadline_ms * 1e6) : 0ull;
+    P.cancel = reinterpret_cast<const volatile int*>(o->cancel_flag);
+    P.max_order = o->max_order;
+    P.sun_mode = o->sun_mode;
+    P.max_steps = 1u << 22;
+    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
+    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+    const int block = o->block_size ? o->block_size : 128;
+    const int grid = o->grid_size ? o->grid_size : ctx->sm_count * trace_batch_blocks_per_sm(bf16, block);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess) { ctx->launches++; e = launch_trace_batch(P, bf16, grid, block, ctx->stream); }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    WorkState ws{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ws, t->d_work, sizeof(ws), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(d_items, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(ctx, e);
+    CK(ctx, se);
+    t->kernel_ms = ms;
+    if (ws.status == 1) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: deadline of %g ms expired", who, o->deadline_ms);
+    if (ws.status == 2) return fail(ctx, MCRT_ERR_CANCELLED, "%s: cancelled", who);
+    return MCRT_OK;
+}
+
+int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, double path_fraction,
+                        mcrt_trace_opts* opts_inout, float* best_ms)
+{
+    const char* who = "mcrt_autotune_batch";
+    if (!ctx || !items || !opts_inout) return fail(ctx, MCRT_ERR_ARG, "%s: NULL argument", who);
+    if (!(path_fraction > 0.0 && path_fraction <= 1.0)) return fail(ctx, MCRT_ERR_ARG, "%s: path_fraction in (0, 1]", who);
+    if (n < 1) return fail(ctx, MCRT_ERR_ARG, "%s: no items", who);
+    std::vector<mcrt_batch_item> sub(items, items + n);
+    for (auto& it : sub) {
+        it.npaths = (uint64_t)std::ceil((double)it.npaths * path_fraction);
+        if (it.npaths < 1) it.npaths = 1;
+    }
+    // candidate launch shapes: paths per claim x lanes a rare phase waits for x block size
+    const int chunks[] = {1, 2, 4, 8};
+    const int rares[] = {4, 8, 12};
+    const int blocks[] = {64, 128};
+    mcrt_tally* t = nullptr;
+    float best = 3.0e38f;
+    mcrt_trace_opts bo = *opts_inout;
+    for (int b : blocks)
+        for (int c : chunks)
+            for (int r : rares) {
+                mcrt_trace_opts o = *opts_inout;
+                o.chunk = c;
+                o.rare_batch = r;
+                o.block_size = b;
+                o.grid_size = 0;
+                int rc = mcrt_trace_batch(ctx, sub.data(), n, &o, &t);
+                if (rc) { if (t) mcrt_tally_destroy(t); return rc; }
+                if (t->kernel_ms < best) { best = t->kernel_ms; bo = o; }
+            }
+    if (t) mcrt_tally_destroy(t);
+    *opts_inout = bo;
+    if (best_ms) *best_ms = best;
+    return MCRT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Tallies
 // ---------------------------------------------------------------------------
 int mcrt_tally_shape(const mcrt_tally* t, int32_t* ncells, int32_t* nquant)
@@ -724,7 +865,8 @@ int mcrt_tally_read(const mcrt_tally* t, double* mean, double* se, uint64_t* n, 
     if (count < m) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_tally_read: need %zu entries", m);
     CK(ctx, cudaSetDevice(ctx->device));
     if (mean || se) {
-        LAUNCH(ctx, launch_finalize(t->d_s1, t->d_s2, (double)t->n_per_cell, (int)m, t->d_out, ctx->stream));
+        LAUNCH(ctx, launch_finalize(t->d_s1, t->d_s2, (double)t->n_per_cell, (int)m,
+                                    t->cell_n.empty() ? nullptr : t->d_cell_n, t->nq, t->d_out, ctx->stream));
         double* h = new (std::nothrow) double[2 * m];
         if (!h) return fail(ctx, MCRT_ERR_OOM, "mcrt_tally_read: host allocation failed");
         cudaError_t e = cudaMemcpyAsync(h, t->d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
@@ -740,7 +882,7 @@ int mcrt_tally_read(const mcrt_tally* t, double* mean, double* se, uint64_t* n, 
         delete[] h;
     }
     if (n)
-        for (size_t i = 0; i < m; ++i) n[i] = t->n_per_cell;
+        for (size_t i = 0; i < m; ++i) n[i] = t->cell_n.empty() ? t->n_per_cell : t->cell_n[i / t->nq];
     return MCRT_OK;
 }
 
@@ -784,6 +926,7 @@ int mcrt_tally_destroy(mcrt_tally* t)
     dfree(ctx, t->d_counters);
     dfree(ctx, t->d_work);
     dfree(ctx, t->d_out);
+    dfree(ctx, t->d_cell_n);
     cudaStreamSynchronize(ctx->stream);
     delete t;
     return MCRT_OK;

@@ -289,6 +289,12 @@ __device__ __forceinline__ void rotate_dir(const float d[3], float mu, float xi,
     out[0] = rx * inv; out[1] = ry * inv; out[2] = rz * inv;
 }
 
+// d/dg of ln p_HG(mu) = -2g / (1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu).
+__device__ __forceinline__ float hg_dlog_dg(float g, float mu)
+{
+    return __fdividef(-2.0f * g, 1.0f - g * g) - __fdividef(3.0f * (g - mu), fmaxf(1.0f + g * g - 2.0f * g * mu, 1e-12f));
+}
+
 // Cosine-weighted direction about +z, cos(theta) = sqrt(xi1) > 0.
 __device__ __forceinline__ void cosine_up(float xi1, float xi2, float out[3])
 {

@@ -55,6 +55,8 @@ struct mcrt_tally {
     void* d_work = nullptr;                      // WorkState
     double* d_out = nullptr;                     // finalize scratch (mean, se)
     float kernel_ms = 0;
+    std::vector<uint64_t> cell_n;                // per-cell path counts (batches) ...
+    unsigned long long* d_cell_n = nullptr;      // ... and their device copy
 };
 
 struct mcrt_proposal {
@@ -79,6 +81,16 @@ struct WorkState {
     unsigned long long next;   // next path id to claim
     int status;                // 0 ok, 1 deadline, 2 cancelled
     int pad;
+};
+
+// One item of a batch: a scene (with its band's gas absorption and sun), a
+// chunk-aligned range of work ids, and its own Philox key; path i of the
+// item draws the numbers path i of a single trace with that seed would.
+struct BatchItem {
+    DevScene S;
+    unsigned long long begin;   // first work id (chunk aligned)
+    unsigned long long npaths;
+    uint2 key;
 };
 
 // Launch parameters of the tracer.
@@ -126,6 +138,9 @@ struct TraceParams {
     const float* pyr2;         // level-2 (or top) majorants
     int d1[3], d2[3];
     int lev2;                  // level of pyr2
+    // batches (flux sensor): items sorted by begin
+    const BatchItem* items;
+    int n_items;
     // outputs
     double* s1;
     double* s2;
@@ -149,8 +164,10 @@ int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block);
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
 int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);
-cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, double* out,
-                            cudaStream_t st);
+cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, int grid, int block, cudaStream_t st);
+int trace_batch_blocks_per_sm(bool bf16, int block);
+cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
+                            int nq, double* out, cudaStream_t st);
 cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,
                              float* tio, int* count_status, bool bf16, cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,

@@ -70,11 +70,11 @@ constexpr int kSections = 9;
 // leaf-entry load and the leaf set-up also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME };
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
-    constexpr int NQ = (SENSOR == kCamera) ? 1 : 3;   // quantities per path
-    const DevScene& S = P.S;
+    // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg in batches)
+    constexpr int NQ = (SENSOR == kCamera) ? 1 : (BATCH ? 4 : 3);
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             tclk = now;
         }
     };
-    const float pi_over_mu0 = __fdividef(kPi, S.sun[2]);
+    int item = 0;                           // batch item of the lane's chunk
+    uint2 rkey = P.key;                     // Philox key of that item
+    float sg = 0.0f, sv_pending = 0.0f, cfs = 0.0f, dscore = 0.0f;   // d/dg (batches)
     uint64_t t_start = 0, t_dry = 0;
     if (P.deadline_ns || COUNT) t_start = globaltimer_ns();
     uint32_t iter = 0;
@@ -161,13 +163,28 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     chunk = true;
                     phase = (LEARNED && P.resume) ? PH_RESUME : PH_START;
                     if (LEARNED && !P.resume) { pid += P.path_base; pend += P.path_base; }
+                    if constexpr (BATCH) {
+                        // items own chunk-aligned id ranges: find the item, use its local ids
+                        int lo = 0, hi = P.n_items - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (P.items[mid].begin <= pid) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        item = lo;
+                        const unsigned long long b = P.items[lo].begin, np = P.items[lo].npaths;
+                        pid -= b;
+                        pend = min(pend - b, np);
+                        rkey = P.items[lo].key;
+                        if (pid >= np) { chunk = false; phase = PH_IDLE; }
+                    }
                     if constexpr (SENSOR == kCamera) {
                         const unsigned long long pix = pid / P.spp;
                         cell = (unsigned)pix;
                         px = (int)(pix % (unsigned long long)P.width);
                         py = (int)(pix / (unsigned long long)P.width);
                     } else {
-                        cell = 0u;
+                        cell = BATCH ? (unsigned)item : 0u;
                     }
                 }
             }
@@ -200,6 +217,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
         const int ph = (phase == PH_STEP || (rare && run_rare)) ? phase : PH_IDLE;
 
+        // ---- the scene of the lane's chunk (one per batch item) ---------------
+        const DevScene& S = BATCH ? P.items[item].S : P.S;
+
         // ---- the one Philox block of this iteration ---------------------------
         const float seg = R.texit - R.t;
         const float Mseg = R.M * seg;
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         else if (ph == PH_STEP) xblk = blk;
         else if (ph == PH_VERTEX) { xc2 = ev << 2; xblk = kBlockVertex; }
         mark(0);
-        const uint4 x = draw_block(pid, xc2, xblk, P.key);
+        const uint4 x = draw_block(pid, xc2, xblk, rkey);
         mark(1);
 
         // ---- phase work before the load ---------------------------------------
@@ -222,6 +242,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         bool setup = false;          // enter a leaf after the load
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
+            if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; }
             if (COUNT) path_iters = 0;
             if constexpr (SENSOR == kCamera) {
                 const float jx = 1.0f - u01(x.x), jy = 1.0f - u01(x.y);
@@ -346,12 +367,15 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
                 cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
                 w *= om;
-                rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
+                const float mu_new = hg_sample_mu(S.g, xi1);
+                rotate_dir(R.d, mu_new, xi2, nd);
+                if (BATCH) { cfs = hg_dlog_dg(S.g, mu); sv_pending = hg_dlog_dg(S.g, mu_new); }
                 if (COUNT) cnt[C_REAL]++;
             } else {
                 cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
                 w *= S.albedo;
                 cosine_up(xi1, xi2, nd);
+                if (BATCH) { cfs = 0.0f; sv_pending = 0.0f; }
                 if (COUNT) cnt[C_GROUND]++;
             }
             term_after = (P.max_order > 0) && (order >= P.max_order);
@@ -529,6 +553,10 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     phase = PH_BEGIN;
                 } else {
                     score += cf * Ts;
+                    if (BATCH) {
+                        dscore += cf * Ts * (sg + cfs);
+                        sg += sv_pending;
+                    }
                     if (LEARNED && cur_rec != 0xFFFFFFFFu) {
                         P.rec_val[4 * (size_t)cur_rec + 2] = cf * Ts;
                         cur_rec = 0xFFFFFFFFu;
@@ -549,11 +577,16 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     acc[0] += score;
                     acc[1] += score * score;
                 } else {
+                    const float pi_over_mu0 = __fdividef(kPi, S.sun[2]);
                     const float tf = pi_over_mu0 * score;
                     const float tt = tdir + tf;
                     acc[0] += tdir; acc[1] += tdir * tdir;
                     acc[2] += tf; acc[3] += tf * tf;
                     acc[4] += tt; acc[5] += tt * tt;
+                    if constexpr (BATCH) {
+                        const float dt = pi_over_mu0 * dscore;
+                        acc[6] += dt; acc[7] += dt * dt;
+                    }
                 }
                 if (COUNT) {
                     cnt[C_PATHS]++;
@@ -642,11 +675,14 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     }
 }
 
-__global__ void finalize_kernel(const double* __restrict__ s1, const double* __restrict__ s2, double n, int count,
-                                double* __restrict__ out)
+// Mean and standard error of each tally entry from its FP64 sums; a batch
+// passes each cell's own path count (cell_n, nq entries per cell).
+__global__ void finalize_kernel(const double* __restrict__ s1, const double* __restrict__ s2, double n_all, int count,
+                                const unsigned long long* __restrict__ cell_n, int nq, double* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
+    const double n = cell_n ? (double)cell_n[i / nq] : n_all;
     const double m = s1[i] / n;
     double var = s2[i] / n - m * m;
     if (var < 0.0) var = 0.0;
@@ -713,6 +749,12 @@ const void* pick(int sensor, bool bf16, bool count)
     return count ? kernel_ptr<kFlux, false, true, false>() : kernel_ptr<kFlux, false, false, false>();
 }
 
+const void* pick_batch(bool bf16)
+{
+    return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, false, false, true>)
+                : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, false, false, true>);
+}
+
 const void* pick_learned(int sensor, bool bf16)
 {
     if (sensor == kCamera) return bf16 ? kernel_ptr<kCamera, true, false, true>() : kernel_ptr<kCamera, false, false, true>();
@@ -755,6 +797,19 @@ int trace_learned_blocks_per_sm(int sensor, bool bf16, int block)
     return nb > 0 ? nb : 1;
 }
 
+cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, int grid, int block, cudaStream_t st)
+{
+    void* args[] = {const_cast<TraceParams*>(&P)};
+    return cudaLaunchKernel(pick_batch(bf16), dim3(grid), dim3(block), args, 0, st);
+}
+
+int trace_batch_blocks_per_sm(bool bf16, int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_batch(bf16), block, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
@@ -770,9 +825,10 @@ int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block)
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, double* out, cudaStream_t st)
+cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
+                            int nq, double* out, cudaStream_t st)
 {
-    finalize_kernel<<<(count + 255) / 256, 256, 0, st>>>(s1, s2, n, count, out);
+    finalize_kernel<<<(count + 255) / 256, 256, 0, st>>>(s1, s2, n, count, cell_n, nq, out);
     return cudaGetLastError();
 }
 

@@ -142,9 +142,35 @@ def _band_limited_3d(nx: int, ny: int, nz: int, kxy: int, kz: int, r: np.random.
     return f.astype(np.float32)
 
 
+def _band_limited_3d_coeffs(nx: int, ny: int, nz: int, kxy: int, kz: int, r: np.random.Generator):
+    kxs = np.arange(-kxy, kxy + 1)
+    kzs = np.arange(-kz, kz + 1)
+    KZ, KY, KX = np.meshgrid(kzs, kxs, kxs, indexing="ij")
+    kk = np.sqrt(KX.astype(np.float64) ** 2 + KY ** 2 + (KZ * 3.2) ** 2)
+    amp = np.where(kk > 0, np.power(np.maximum(kk, 1e-12), -11.0 / 6.0), 0.0)
+    c = (r.standard_normal(KX.shape) + 1j * r.standard_normal(KX.shape)) * amp
+    return KZ % nz, KY % ny, KX % nx, c.astype(np.complex64)
+
+
+def _band_limited_3d(nx: int, ny: int, nz: int, kxy: int, kz: int, r: np.random.Generator) -> np.ndarray:
+    """Unit-variance periodic 3D Gaussian field with a k^-11/3 spectrum,
+    band-limited to |kx|,|ky| <= kxy and |kz| <= kz (cycles per domain)."""
+    iz, iy, ix, c = _band_limited_3d_coeffs(nx, ny, nz, kxy, kz, r)
+    F = np.zeros((nz, ny, nx), dtype=np.complex64)
+    F[iz, iy, ix] = c
+    f = np.fft.ifftn(F).real.astype(np.float64)
+    f = (f - f.mean()) / f.std()
+    return f.astype(np.float32)
+
+
 def cumulus(nx: int = 512, ny: int = 512, nz: int = 160, seed: int = 0, cover: float = 0.20,
-            k_clear: float = 0.01) -> SceneSpec:
-    """Shallow-cumulus-like field over a 12.8 x 12.8 x 4 km domain."""
+            k_clear: float = 0.01, device=None) -> SceneSpec:
+    """Shallow-cumulus-like field over a 12.8 x 12.8 x 4 km domain.
+
+    With ``device`` (a torch CUDA device) the 3D part is transformed and the
+    field assembled on that device and ``k`` is a device tensor: the same
+    random draws, but FFT rounding differs from numpy's, so such a field is
+    for timing only (parity cases use the host form)."""
     Lx, Lz = 12.8, 4.0
     dx = Lx / nx
     dz = Lz / nz
@@ -155,19 +181,83 @@ def cumulus(nx: int = 512, ny: int = 512, nz: int = 160, seed: int = 0, cover: f
     base = 0.8
     top = np.where(f > thr, base + 2.0 * (f - thr) / (fmax - thr), base)   # [y][x]
     zc = (np.arange(nz) + 0.5) * dz
-    incloud = (zc[:, None, None] >= base) & (zc[:, None, None] < top[None, :, :])
-    g3 = _band_limited_3d(nx, ny, nz, 24, 6, r).astype(np.float64)
-    # log-normal LWC with median 0.3 g m^-3 and sigma_ln 0.6 over the cloudy voxels
-    zc_ = g3[incloud]
-    g3 = (g3 - np.median(zc_)) / zc_.std()
-    lwc = 0.3 * np.exp(0.6 * g3)                            # g m^-3
     rho_w = 1.0e6                                           # g m^-3
     r_eff = 10e-6                                           # m
-    k_cloud = 1.5 * lwc / (rho_w * r_eff) * 1000.0          # m^-1 -> km^-1
-    k = np.where(incloud, k_cloud, 0.0) + k_clear
-    return SceneSpec(name="cumulus-%dx%dx%d" % (nx, ny, nz), k=k.astype(np.float32), dx=dx, dy=dx, dz=dz,
+    kfac = 1.5 / (rho_w * r_eff) * 1000.0                   # LWC [g m^-3] -> extinction [km^-1]
+    if device is None:
+        incloud = (zc[:, None, None] >= base) & (zc[:, None, None] < top[None, :, :])
+        g3 = _band_limited_3d(nx, ny, nz, 24, 6, r).astype(np.float64)
+        # log-normal LWC with median 0.3 g m^-3 and sigma_ln 0.6 over the cloudy voxels
+        zc_ = g3[incloud]
+        g3 = (g3 - np.median(zc_)) / zc_.std()
+        lwc = 0.3 * np.exp(0.6 * g3)                        # g m^-3
+        k = (np.where(incloud, kfac * lwc, 0.0) + k_clear).astype(np.float32)
+    else:
+        import torch
+        iz, iy, ix, c = _band_limited_3d_coeffs(nx, ny, nz, 24, 6, r)
+        F = torch.zeros((nz, ny, nx), dtype=torch.complex64, device=device)
+        F[torch.from_numpy(iz).to(device), torch.from_numpy(iy).to(device), torch.from_numpy(ix).to(device)] = \
+            torch.from_numpy(c).to(device)
+        g3 = torch.fft.ifftn(F).real
+        del F
+        g3 = (g3 - g3.mean()) / g3.std()
+        zt = torch.from_numpy(zc).to(device=device, dtype=torch.float32)
+        tt = torch.from_numpy(top).to(device=device, dtype=torch.float32)
+        incloud = (zt[:, None, None] >= base) & (zt[:, None, None] < tt[None, :, :])
+        zc_ = g3[incloud]
+        g3 = (g3 - zc_.median()) / zc_.std()
+        k = torch.where(incloud, kfac * 0.3 * torch.exp(0.6 * g3), torch.zeros((), device=device)) + k_clear
+        k = k.to(torch.float32).contiguous()
+    return SceneSpec(name="cumulus-%dx%dx%d" % (nx, ny, nz), k=k, dx=dx, dy=dx, dz=dz,
                      levels=3, k_clear=k_clear, ssa_clear=0.9, ssa_cloud=0.999, g=0.86, ground_albedo=0.1,
                      sun_zenith_deg=60.0)
+
+
+@dataclass
+class BatchInstance:
+    """One field of a batch with its sun and spectral bands."""
+    nx: int
+    nz: int
+    field_seed: int
+    sun_zenith_deg: float
+    sun_azimuth_deg: float
+    k_gas: list              # one gas absorption [km^-1] per band
+    npaths: int              # paths of the instance, split over its bands
+
+
+BATCH_SIZES = ((64, 32), (128, 40), (256, 80), (512, 160), (1024, 160))
+
+
+def batch_instances(seed: int = 0, n: int = 96, max_nx: int = 1024, paths_lo: float = 1e5,
+                    paths_hi: float = 1e7) -> list:
+    """Many flux problems of uneven sizes: field sizes drawn uniformly from
+    64^2x32 ... 1024^2x160 (cumulus statistics over the same 12.8 km domain),
+    1-16 spectral bands per field with log-normal gas absorption (median
+    1e-3 km^-1, sigma_ln 2), sun zenith uniform in [0, 75] deg, azimuth
+    uniform, and a log-uniform path count in [paths_lo, paths_hi] per field."""
+    r = _rng(seed)
+    sizes = [s for s in BATCH_SIZES if s[0] <= max_nx]
+    out = []
+    for i in range(n):
+        nx, nz = sizes[int(r.integers(0, len(sizes)))]
+        nb = int(r.integers(1, 17))
+        kg = list(np.exp(np.log(1e-3) + 2.0 * r.standard_normal(nb)))
+        out.append(BatchInstance(nx=nx, nz=nz, field_seed=1000 + i, sun_zenith_deg=float(r.uniform(0.0, 75.0)),
+                                 sun_azimuth_deg=float(r.uniform(0.0, 360.0)), k_gas=[float(v) for v in kg],
+                                 npaths=int(round(math.exp(r.uniform(math.log(paths_lo), math.log(paths_hi)))))))
+    return out
+
+
+def batch_items(instances, scene_of) -> list:
+    """Flattens instances into (scene, k_gas, zenith, azimuth, npaths, seed)
+    items, one per band; ``scene_of(i)`` gives instance i's scene."""
+    items = []
+    for i, b in enumerate(instances):
+        nb = len(b.k_gas)
+        per = max(1, b.npaths // nb)
+        for j, kg in enumerate(b.k_gas):
+            items.append((scene_of(i), kg, b.sun_zenith_deg, b.sun_azimuth_deg, per, (i << 8) | j))
+    return items
 
 
 def homogeneous(nx: int, ny: int, nz: int, d: float, k: float, **kw) -> SceneSpec:
