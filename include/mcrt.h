@@ -288,11 +288,33 @@ MCRT_API int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32
 
 /* Launch-shape autotuner for a batch: times mcrt_trace_batch on a fraction
  * of every item's paths for each candidate (paths per claim 1, 2, 4, 8;
- * rare-phase wait 4, 8, 12 lanes; 64 or 128 threads per block) and writes
- * the fastest into *opts_inout (*best_ms: its time).  Results of a trace do
+ * rare-phase wait 4, 8, 12 lanes; 64 or 128 threads per block; the better
+ * of two runs each) and writes the fastest into *opts_inout (*best_ms: its
+ * time).  Too small a fraction lets the last, straggling paths dominate;
+ * a quarter of the paths or more tunes for the full batch.  Results of a trace do
  * not depend on these choices, only its speed. */
 MCRT_API int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, double path_fraction,
                                  mcrt_trace_opts* opts_inout, float* best_ms);
+
+/* A batch prepared once and replayed: the items are laid out on the device
+ * and the whole batch (tally reset, the persistent trace kernel, finalize,
+ * copies of the results and the status to pinned host memory) is captured
+ * into one CUDA graph, so a run costs one graph launch.  The scenes must
+ * outlive the plan and keep their majorants; a run traces the same paths
+ * again unless mcrt_batch_plan_set_seeds changes the seeds.  Deadline and
+ * cancel flag are not available in plans (MCRT_ERR_UNSUPPORTED).
+ * mcrt_batch_plan_run: mean and se (either may be NULL) receive n x 4
+ * entries in the order of mcrt_trace_batch; *kernel_ms the graph's device
+ * time (the trace kernel plus microseconds of reset, finalize and copies).  mcrt_batch_plan_tally lends the plan's tally (owned by the plan;
+ * do not destroy it) for mcrt_tally_read and friends. */
+typedef struct mcrt_batch_plan mcrt_batch_plan;
+
+MCRT_API int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n,
+                                    const mcrt_trace_opts* opts, mcrt_batch_plan** out);
+MCRT_API int mcrt_batch_plan_set_seeds(mcrt_batch_plan* plan, const uint64_t* seeds, int32_t n);
+MCRT_API int mcrt_batch_plan_run(mcrt_batch_plan* plan, double* mean, double* se, size_t count, float* kernel_ms);
+MCRT_API int mcrt_batch_plan_tally(const mcrt_batch_plan* plan, const mcrt_tally** tally);
+MCRT_API int mcrt_batch_plan_destroy(mcrt_batch_plan* plan);
 
 /* --------------------------------------------------------------------- */
 /* Tallies                                                                */

@@ -119,6 +119,11 @@ def _load():
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
         "mcrt_trace_batch": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
         "mcrt_autotune_batch": [vp, P(BatchItem), i32, C.c_double, P(TraceOpts), P(f32)],
+        "mcrt_batch_plan_create": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
+        "mcrt_batch_plan_set_seeds": [vp, P(C.c_uint64), i32],
+        "mcrt_batch_plan_run": [vp, P(C.c_double), P(C.c_double), C.c_size_t, P(f32)],
+        "mcrt_batch_plan_tally": [vp, P(vp)],
+        "mcrt_batch_plan_destroy": [vp],
         "mcrt_proposal_nparams": [P(i32)],
         "mcrt_proposal_create": [vp, u64, P(vp)],
         "mcrt_proposal_destroy": [vp],
@@ -570,3 +575,49 @@ def trace_batch(ctx: Context, items, tally=None, **kw):
         if tally is None:
             mcrt_tally_destroy(t)
     return Result(mean.reshape(-1, 4), se.reshape(-1, 4), n.reshape(-1, 4), ms, {})
+
+
+def mcrt_batch_plan_create(ctx, items, opts: TraceOpts):
+    arr = items if isinstance(items, C.Array) else make_batch_items(items)
+    h = C.c_void_p()
+    _check(_load().mcrt_batch_plan_create(ctx, arr, len(arr), C.byref(opts), C.byref(h)), ctx)
+    return h
+
+
+def mcrt_batch_plan_set_seeds(ctx, plan, seeds):
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check(_load().mcrt_batch_plan_set_seeds(plan, _ptr(s, C.c_uint64), s.size), ctx)
+
+
+def mcrt_batch_plan_run(ctx, plan, n_items: int):
+    mean = np.zeros(n_items * 4)
+    se = np.zeros(n_items * 4)
+    ms = C.c_float()
+    _check(_load().mcrt_batch_plan_run(plan, _ptr(mean, C.c_double), _ptr(se, C.c_double), mean.size,
+                                       C.byref(ms)), ctx)
+    return mean.reshape(n_items, 4), se.reshape(n_items, 4), ms.value
+
+
+def mcrt_batch_plan_destroy(plan):
+    _check(_load().mcrt_batch_plan_destroy(plan))
+
+
+class BatchPlan:
+    """A batch captured into a CUDA graph; ``run()`` replays it."""
+
+    def __init__(self, ctx: Context, items, **kw):
+        self.ctx = ctx
+        self.n = len(items)
+        self.h = mcrt_batch_plan_create(ctx.h, items, Scene._opts(**kw))
+
+    def set_seeds(self, seeds):
+        mcrt_batch_plan_set_seeds(self.ctx.h, self.h, seeds)
+
+    def run(self):
+        mean, se, ms = mcrt_batch_plan_run(self.ctx.h, self.h, self.n)
+        return Result(mean, se, None, ms, {})
+
+    def close(self):
+        if self.h:
+            mcrt_batch_plan_destroy(self.h)
+            self.h = None
