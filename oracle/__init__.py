@@ -67,6 +67,9 @@ class OrcScene(C.Structure):
         ("mlp", C.POINTER(C.c_double)),
         ("n_learned", C.c_int32),
         ("mis_alpha", C.c_double),
+        ("hf", C.POINTER(C.c_float)),
+        ("hnx", C.c_int32), ("hny", C.c_int32),
+        ("hmax", C.c_double),
     ]
 
 
@@ -117,6 +120,10 @@ def lib():
             L.orc_trace_flux.argtypes = [sp, C.c_uint64, C.c_uint64, C.c_uint64, f64p, C.c_int, i64p]
             L.orc_trace_forward.argtypes = [sp, C.c_uint64, C.c_uint64, C.c_uint64, f64p, C.c_int, i64p]
             L.orc_forward_balance_residual.argtypes = [sp, C.c_uint64, C.c_uint64, C.c_uint64]
+            L.orc_terrain_height.argtypes = [sp, C.c_double, C.c_double, f64p]
+            L.orc_terrain_height.restype = C.c_double
+            L.orc_terrain_hit.argtypes = [sp, f64p, f64p, f64p, i64p, C.POINTER(C.c_int)]
+            L.orc_terrain_hit.restype = C.c_int
             L.orc_forward_balance_residual.restype = C.c_double
             _lib = L
     return _lib
@@ -215,6 +222,7 @@ class Scene:
     mlp: object = None            # learned proposal parameters (11,560 float64) or None
     n_learned: int = 8
     mis_alpha: float = 0.5
+    heights: object = None        # heightfield ground [hny][hnx] float32 km (periodic), or None: flat
     _keep: list = field(default_factory=list, repr=False)
 
     def sun_dir(self):
@@ -257,6 +265,12 @@ class Scene:
             s.mlp = _ptr(mp, C.c_double)
         s.n_learned = self.n_learned
         s.mis_alpha = self.mis_alpha
+        if self.heights is not None:
+            hf = np.ascontiguousarray(self.heights, dtype=np.float32)
+            self._keep.append(hf)
+            s.hf = _ptr(hf, C.c_float)
+            s.hny, s.hnx = hf.shape
+            s.hmax = float(hf.max())
         return s
 
 
@@ -406,6 +420,29 @@ def trace_flux(scene: Scene, npaths: int, seed: int, begin: int = 0, nthreads: i
     if rc != 0:
         raise ValueError("bad flux request")
     return Tally(sums[0::2].copy(), sums[1::2].copy(), np.full(4, float(npaths))), stats
+
+
+def terrain_height(scene: Scene, x: float, y: float):
+    """Surface height of the heightfield ground at (x, y) and its normal."""
+    st = scene.struct()
+    n = np.zeros(3)
+    z = lib().orc_terrain_height(C.byref(st), x, y, _ptr(n, C.c_double))
+    return z, n
+
+
+def terrain_hit(scene: Scene, o, d):
+    """First hit of the ray o + t d with the heightfield: (t, (i, j), tri)
+    with the unwrapped cell and triangle (0: u >= v, 1: u < v), or None."""
+    st = scene.struct()
+    oo = np.ascontiguousarray(o, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    t = np.zeros(1)
+    cell = np.zeros(2, dtype=np.int64)
+    tri = C.c_int()
+    if not lib().orc_terrain_hit(C.byref(st), _ptr(oo, C.c_double), _ptr(dd, C.c_double), _ptr(t, C.c_double),
+                                 _ptr(cell, C.c_int64), C.byref(tri)):
+        return None
+    return float(t[0]), (int(cell[0]), int(cell[1])), int(tri.value)
 
 
 def trace_forward(scene: Scene, nphotons: int, seed: int, nthreads: int = 0):

@@ -216,6 +216,9 @@ typedef struct {
     const double* mlp;         /* learned proposal parameters, or NULL    */
     int32_t n_learned;         /* volume vertices per path that use it    */
     double mis_alpha;          /* HG share of the one-sample MIS mixture  */
+    const float* hf;           /* heightfield ground [km] (x fastest), or NULL: flat z = 0 */
+    int32_t hnx, hny;          /* heightfield samples per axis (periodic)  */
+    double hmax;               /* largest height                          */
 } orc_scene;
 
 static const float* level_ptr(const orc_scene* S, int level, int dims[3])
@@ -631,6 +634,154 @@ void orc_hg_sample_dirs(double g, const double* d_in, const double* xi, int64_t 
 }
 
 /* ===================================================================== */
+/* Heightfield ground (an extension of the paper's flat Lambertian        */
+/* ground; the paper finds the ground's shape matters little for the      */
+/* cloud estimates, Sec. 1).  Heights h[j][i] sit at the corners of a     */
+/* periodic hnx x hny grid of cells of size Lx/hnx x Ly/hny.  Cell (i, j) */
+/* is cut along its diagonal from corner (i, j) to corner (i+1, j+1):     */
+/* with u, v the position in the cell scaled to [0, 1], triangle A        */
+/* (u >= v) has corners 00, 10, 11 and triangle B (u < v) corners 00, 11, */
+/* 01.  On a triangle the surface is the plane z = c + a u + b v.         */
+/* ===================================================================== */
+#define ORC_TERRAIN_OFFSET 1e-5      /* km: a path leaves the surface this far along its normal */
+#define ORC_TERRAIN_MAX_CELLS 1000000
+
+static int64_t wrap_index(int64_t i, int64_t n)
+{
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+static double hf_at(const orc_scene* S, int64_t i, int64_t j)
+{
+    return (double)S->hf[wrap_index(j, S->hny) * S->hnx + wrap_index(i, S->hnx)];
+}
+
+static void tri_plane(const orc_scene* S, int64_t i, int64_t j, int tri, double* a, double* b, double* c)
+{
+    double h00 = hf_at(S, i, j), h10 = hf_at(S, i + 1, j), h01 = hf_at(S, i, j + 1), h11 = hf_at(S, i + 1, j + 1);
+    *c = h00;
+    if (tri == 0) { *a = h10 - h00; *b = h11 - h10; }
+    else          { *a = h11 - h01; *b = h01 - h00; }
+}
+
+/* Unit upward normal of the plane z = c + a u + b v, u = x / hx - i. */
+static void tri_normal(const orc_scene* S, int64_t i, int64_t j, int tri, double n[3])
+{
+    double a, b, c;
+    tri_plane(S, i, j, tri, &a, &b, &c);
+    double hx = (double)S->nx * S->dx / S->hnx, hy = (double)S->ny * S->dy / S->hny;
+    double gx = a / hx, gy = b / hy;
+    double inv = 1.0 / sqrt(gx * gx + gy * gy + 1.0);
+    n[0] = -gx * inv; n[1] = -gy * inv; n[2] = inv;
+}
+
+/* Surface height and normal at (x, y). */
+double orc_terrain_height(const orc_scene* S, double x, double y, double n[3])
+{
+    double hx = (double)S->nx * S->dx / S->hnx, hy = (double)S->ny * S->dy / S->hny;
+    int64_t i = (int64_t)floor(x / hx), j = (int64_t)floor(y / hy);
+    double u = x / hx - (double)i, v = y / hy - (double)j;
+    int tri = u >= v ? 0 : 1;
+    double a, b, c;
+    tri_plane(S, i, j, tri, &a, &b, &c);
+    if (n) tri_normal(S, i, j, tri, n);
+    return c + a * u + b * v;
+}
+
+/* First point where the ray p + t d (t >= 0) meets the surface.  The
+ * ray's horizontal projection is walked cell by cell (2D DDA over
+ * unwrapped cell indices) over the part of the ray with z <= hmax (it
+ * reaches z = 0, at or below every height, last); in each cell the ray
+ * crosses at most two triangle pieces, split where u = v; on a piece the
+ * ray's height above the plane, f(t), is linear, and the hit is the first
+ * t where f reaches 0 (at the piece start if f is already <= 0 there).
+ * Returns 1 with the distance, the (unwrapped) cell and the triangle;
+ * 0 if the ray leaves the relief layer first. */
+int orc_terrain_hit(const orc_scene* S, const double p[3], const double d[3], double* t_hit, int64_t cell[2],
+                    int* tri_out)
+{
+    if (!S->hf) return 0;
+    double hx = (double)S->nx * S->dx / S->hnx, hy = (double)S->ny * S->dy / S->hny;
+    double t0 = 0.0, t1;
+    if (p[2] > S->hmax) {
+        if (d[2] >= 0.0) return 0;
+        t0 = (S->hmax - p[2]) / d[2];
+    }
+    if (d[2] < 0.0) t1 = -p[2] / d[2];
+    else if (d[2] > 0.0) t1 = (S->hmax - p[2]) / d[2];
+    else t1 = INFINITY;
+    if (t1 < t0) return 0;
+    double x0 = p[0] + t0 * d[0], y0 = p[1] + t0 * d[1];
+    int64_t i = (int64_t)floor(x0 / hx), j = (int64_t)floor(y0 / hy);
+    if (d[0] < 0.0 && (double)i * hx == x0) i -= 1;
+    if (d[1] < 0.0 && (double)j * hy == y0) j -= 1;
+    double t = t0;
+    for (int64_t step = 0; step < ORC_TERRAIN_MAX_CELLS; ++step) {
+        double tx = d[0] > 0.0 ? ((double)(i + 1) * hx - p[0]) / d[0]
+                  : d[0] < 0.0 ? ((double)i * hx - p[0]) / d[0] : INFINITY;
+        double ty = d[1] > 0.0 ? ((double)(j + 1) * hy - p[1]) / d[1]
+                  : d[1] < 0.0 ? ((double)j * hy - p[1]) / d[1] : INFINITY;
+        double te = fmin(fmin(tx, ty), t1);
+        if (te < t) te = t;
+        /* pieces of [t, te] on either side of the diagonal u = v */
+        double g0 = (p[0] / hx - (double)i) - (p[1] / hy - (double)j), g1 = d[0] / hx - d[1] / hy;
+        double cut[3] = {t, te, te};
+        int np = 1;
+        if (g1 != 0.0) {
+            double tm = -g0 / g1;
+            if (tm > t && tm < te) { cut[1] = tm; cut[2] = te; np = 2; }
+        }
+        for (int q = 0; q < np; ++q) {
+            double a0 = cut[q], b0 = cut[q + 1];
+            double mid = 0.5 * (a0 + b0);
+            int tri = (g0 + g1 * mid) >= 0.0 ? 0 : 1;
+            double A, B, Cc;
+            tri_plane(S, i, j, tri, &A, &B, &Cc);
+            double fa = (p[2] + a0 * d[2]) - (Cc + A * ((p[0] + a0 * d[0]) / hx - (double)i) +
+                                             B * ((p[1] + a0 * d[1]) / hy - (double)j));
+            double fb = (p[2] + b0 * d[2]) - (Cc + A * ((p[0] + b0 * d[0]) / hx - (double)i) +
+                                             B * ((p[1] + b0 * d[1]) / hy - (double)j));
+            double th;
+            if (fa <= 0.0) th = a0;
+            else if (fb <= 0.0) th = a0 + fa * (b0 - a0) / (fa - fb);
+            else continue;
+            *t_hit = th;
+            if (cell) { cell[0] = i; cell[1] = j; }
+            if (tri_out) *tri_out = tri;
+            return 1;
+        }
+        if (te >= t1) return 0;
+        if (tx <= ty) i += d[0] > 0.0 ? 1 : -1;
+        else j += d[1] > 0.0 ? 1 : -1;
+        t = te;
+    }
+    return 0;
+}
+
+/* The ray's terrain hit with its normal, or 0. */
+static int terrain_hit_normal(const orc_scene* S, const double p[3], const double d[3], double* t, double n[3])
+{
+    int64_t cell[2];
+    int tri;
+    if (!orc_terrain_hit(S, p, d, t, cell, &tri)) return 0;
+    tri_normal(S, cell[0], cell[1], tri, n);
+    return 1;
+}
+
+/* Cosine-weighted direction about the unit normal n (the flat ground's
+ * cosine_up when n = +z). */
+static void cosine_about(const double n[3], double xi1, double xi2, double out[3])
+{
+    double b1[3], b2[3];
+    onb(n, b1, b2);
+    double st = sqrt(fmax(0.0, 1.0 - xi1)), ct = sqrt(xi1);
+    double phi = 2.0 * ORC_PI * xi2;
+    double c = st * cos(phi), s = st * sin(phi);
+    for (int a = 0; a < 3; ++a) out[a] = c * b1[a] + s * b2[a] + ct * n[a];
+}
+
+/* ===================================================================== */
 /* Free flight with null collisions (Sec. 2.3, steps 4a-4g; Eq. 2): the   */
 /* optical depth -ln(u) is spent across leaves of uniform majorant M;     */
 /* at a tentative collision the true extinction k is read and the         */
@@ -641,18 +792,33 @@ enum { EV_ESCAPE = 1, EV_GROUND = 2, EV_VOLUME = 3, EV_ABORT = 4 };
 
 typedef struct { int64_t tentative, real, leaves; } orc_counts;
 
+static void wrap_xy(const orc_scene* S, double p[3]);
+
+/* With a heightfield the flight also ends where the ray meets the surface
+ * (distance tg, found before the flight): the leaf holding that point is
+ * cut there, and a flight that spends none of its optical depth before it
+ * is a ground event with the triangle's normal in n_ground. */
 static int free_flight(const orc_scene* S, double p[3], const double d[3], const rng_t* r,
-                       double* k_at, int vox_at[3], orc_counts* C)
+                       double* k_at, int vox_at[3], orc_counts* C, double n_ground[3])
 {
+    const double p0[3] = {p[0], p[1], p[2]};
+    double tg = INFINITY, ng[3] = {0.0, 0.0, 1.0};
+    const int has_tg = S->hf ? terrain_hit_normal(S, p0, d, &tg, ng) : 0;
+    double dist = 0.0;
+    if (n_ground) { n_ground[0] = 0.0; n_ground[1] = 0.0; n_ground[2] = 1.0; }
     trav64 T;
     trav_begin(S, &T, p, d);
     double u[4];
     rng_block(r, 0, u);
     double tau = -log(u[0]);
     for (uint32_t j = 1;;) {
-        if (T.M > 0.0 && tau < T.M * T.seg) {
+        double seg = T.seg;
+        const int ground_here = has_tg && dist + seg >= tg;
+        if (ground_here) seg = fmax(tg - dist, 0.0);
+        if (T.M > 0.0 && tau < T.M * seg) {
             double s = tau / T.M;
             trav_move_inside(S, &T, s);
+            dist += s;
             int vox[3];
             double k = trav_k_here(S, &T, vox);
             if (C) C->tentative++;
@@ -665,12 +831,22 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
                 return EV_VOLUME;
             }
             tau = -log(u[1]);
+        } else if (ground_here) {
+            for (int a = 0; a < 3; ++a) p[a] = p0[a] + tg * d[a];
+            wrap_xy(S, p);
+            if (n_ground) { n_ground[0] = ng[0]; n_ground[1] = ng[1]; n_ground[2] = ng[2]; }
+            return EV_GROUND;
         } else {
             tau -= T.M * T.seg;
+            dist += T.seg;
             int st = trav_next_leaf(S, &T);
             if (C) C->leaves++;
             if (st == 1) { for (int a = 0; a < 3; ++a) p[a] = T.p[a]; return EV_ESCAPE; }
-            if (st == 2) { for (int a = 0; a < 3; ++a) p[a] = T.p[a]; return EV_GROUND; }
+            if (st == 2) {
+                for (int a = 0; a < 3; ++a) p[a] = T.p[a];
+                if (S->hf && n_ground) orc_terrain_height(S, p[0], p[1], n_ground);
+                return EV_GROUND;
+            }
             if (st == 4) return EV_ABORT;
         }
     }
@@ -683,6 +859,10 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
 static double transmissivity(const orc_scene* S, const double p[3], const double s[3], const rng_t* r,
                              orc_counts* C)
 {
+    if (S->hf) {                        /* shadow of the terrain */
+        double tg;
+        if (orc_terrain_hit(S, p, s, &tg, NULL, NULL)) return 0.0;
+    }
     trav64 T;
     trav_begin(S, &T, p, s);
     double t = 1.0;
@@ -834,7 +1014,8 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
         rng_init(&r, seed, path, e, 0);
         double k;
         int vox[3] = {0, 0, 0};
-        int ev = free_flight(S, p, d, &r, &k, vox, C);
+        double ng[3];
+        int ev = free_flight(S, p, d, &r, &k, vox, C, ng);
         if (ev == EV_ESCAPE) break;
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; break; }
         int order = (int)e + 1;
@@ -870,7 +1051,7 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
             }
             ++lv;
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
-        } else { /* ground */
+        } else if (!S->hf) { /* flat ground */
             if (score_it) {
                 double Ts = transmissivity(S, p, s, &rs, C);
                 double c = w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
@@ -879,6 +1060,18 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
             }
             w *= S->ground_albedo;
             cosine_up(uv[0], uv[1], d);
+        } else { /* heightfield: leave the surface along its normal, cosine about it */
+            for (int a = 0; a < 3; ++a) p[a] += ORC_TERRAIN_OFFSET * ng[a];
+            wrap_xy(S, p);
+            if (score_it) {
+                double ns = ng[0] * s[0] + ng[1] * s[1] + ng[2] * s[2];
+                double Ts = ns > 0.0 ? transmissivity(S, p, s, &rs, C) : 0.0;
+                double c = w * (S->ground_albedo / ORC_PI) * fmax(ns, 0.0) * Ts;
+                score += c;
+                ds += c * sg;
+            }
+            w *= S->ground_albedo;
+            cosine_about(ng, uv[0], uv[1], d);
         }
         if (S->max_order > 0 && order >= S->max_order) break;
         if (w < 0.01) {
@@ -974,14 +1167,34 @@ static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double o
     double Lx = (double)S->nx * S->dx, Ly = (double)S->ny * S->dy;
     double p[3] = {(1.0 - u0) * Lx, (1.0 - u1) * Ly, 0.0};
     double d[3];
-    cosine_up(u2, u3, d);
     rng_t rd;
     rng_init(&rd, seed, path, 0, 3);
+    double mu0 = S->sun[2];
+    if (S->hf) {
+        /* heightfield: the point on the surface above (x, y), directions
+         * cosine-weighted about its normal n; irradiance of the tilted
+         * element per unit horizontal area: direct max(n.s, 0) / (n_z mu0)
+         * T_sun, diffuse pi / (n_z mu0) times the local estimates */
+        double n[3];
+        p[2] = orc_terrain_height(S, p[0], p[1], n);
+        for (int a = 0; a < 3; ++a) p[a] += ORC_TERRAIN_OFFSET * n[a];
+        wrap_xy(S, p);
+        cosine_about(n, u2, u3, d);
+        double ns = n[0] * S->sun[0] + n[1] * S->sun[1] + n[2] * S->sun[2];
+        double q[3] = {p[0], p[1], p[2]};
+        double Tdir = ns > 0.0 ? transmissivity(S, q, S->sun, &rd, cnt) : 0.0;
+        double dsc = 0.0;
+        double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc);
+        out[0] = fmax(ns, 0.0) / (n[2] * mu0) * Tdir;
+        out[1] = ORC_PI / (n[2] * mu0) * score;
+        out[2] = ORC_PI / (n[2] * mu0) * dsc;
+        return;
+    }
+    cosine_up(u2, u3, d);
     double q[3] = {p[0], p[1], p[2]};
     double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
     double dsc = 0.0;
     double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc);
-    double mu0 = S->sun[2];
     out[0] = Tdir;
     out[1] = ORC_PI / mu0 * score;
     out[2] = ORC_PI / mu0 * dsc;
@@ -1013,7 +1226,7 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
         rng_t r;
         rng_init(&r, seed, path, e, 0);
         double k;
-        int ev = free_flight(S, p, d, &r, &k, NULL, NULL);
+        int ev = free_flight(S, p, d, &r, &k, NULL, NULL, NULL);
         if (ev == EV_ESCAPE) { out[0] += w; return; }
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; out[5] += w; return; }
         double uv[4];
@@ -1184,7 +1397,7 @@ int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t e
 int orc_trace_forward(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end, double* sums,
                       int nthreads, int64_t* stats)
 {
-    if (end < begin) return -1;
+    if (end < begin || S->hf) return -1;      /* the forward photon knows the flat ground only */
     job_t J;
     memset(&J, 0, sizeof(J));
     J.S = S; J.kind = 2; J.seed = seed; J.begin = begin; J.end = end;
