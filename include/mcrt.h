@@ -147,6 +147,23 @@ MCRT_API int mcrt_scene_read_majorants(const mcrt_scene* scene, int32_t level, f
 /* Flat Lambertian ground of albedo in [0, 1] (Sec. 4.1). */
 MCRT_API int mcrt_scene_set_ground_flat(mcrt_scene* scene, float albedo);
 
+/* Heightfield ground instead of the flat one (an extension of the paper's
+ * flat Lambertian ground, Sec. 1 and Sec. 4.1).  heights: hny rows of hnx
+ * FP32 heights [km] (x fastest) at the corners of a periodic grid of
+ * hnx x hny cells spanning the field's x-y extent; each cell is cut along
+ * the diagonal from corner (i, j) to (i+1, j+1) into two planar triangles.
+ * mem: MCRT_MEM_HOST or MCRT_MEM_DEVICE (borrowed for the call, copied).
+ * Heights must be finite and in [0, nz * dz] (MCRT_ERR_ARG otherwise).
+ * Paths end their flights on the surface, sun rays that meet it are
+ * shadowed, ground vertices use the facet normal (Lambertian about it,
+ * local estimate rho/pi * max(n.s, 0) * T_sun), and the flux sensor sits
+ * on the surface: per unit horizontal area, T_dir = max(n.s, 0) / (n_z mu0)
+ * * T_sun and T_dif = pi / (n_z mu0) * sum of estimates.  A max pyramid of
+ * 4 x 4 blocks (while both sizes divide) lets rays skip terrain below them.
+ * Not available with a learned proposal or in batches. */
+MCRT_API int mcrt_scene_set_ground_heightfield(mcrt_scene* scene, const float* heights, int32_t hnx, int32_t hny,
+                                               int32_t mem, float albedo);
+
 /* Collimated sun; zenith in [0, 90) degrees, azimuth measured from +x
  * toward +y (App. C scene table convention).  Direction toward the sun:
  * (sin z cos a, sin z sin a, cos z). */
@@ -405,6 +422,13 @@ MCRT_API int mcrt_proposal_train_step(mcrt_proposal* proposal, const float* host
 MCRT_API int mcrt_debug_dda(const mcrt_scene* scene, const float o[3], const float d[3], float tau_merge,
                    int32_t finest_level, int32_t* cells, float* t_in_out, int32_t cap, int32_t* count,
                    int32_t* status);
+
+/* Heightfield checks (MCRT_ERR_STATE on a flat ground): t_out[i] = the
+ * distance t along ray i, o + t d (host arrays of n x 3 floats), to its
+ * first surface hit, or +inf; and the surface height and unit normal at
+ * n points (xy: n x 2; zn_out: n x 4 = z, nx, ny, nz). */
+MCRT_API int mcrt_debug_terrain(const mcrt_scene* scene, int32_t n, const float* o, const float* d, float* t_out);
+MCRT_API int mcrt_debug_terrain_height(const mcrt_scene* scene, int32_t n, const float* xy, float* zn_out);
 
 /* Philox4x32-10 evaluated on the device for n (counter[4], key[2]) pairs
  * (host arrays); out receives 4 words per pair. */

@@ -104,6 +104,9 @@ def _load():
         "mcrt_scene_majorant_dims": [vp, i32, P(i32)],
         "mcrt_scene_read_majorants": [vp, i32, P(f32), C.c_size_t],
         "mcrt_scene_set_ground_flat": [vp, f32],
+        "mcrt_scene_set_ground_heightfield": [vp, vp, i32, i32, i32, f32],
+        "mcrt_debug_terrain": [vp, i32, P(f32), P(f32), P(f32)],
+        "mcrt_debug_terrain_height": [vp, i32, P(f32), P(f32)],
         "mcrt_scene_set_sun": [vp, f32, f32],
         "mcrt_trace_opts_default": [P(TraceOpts)],
         "mcrt_trace_camera": [vp, P(CameraDesc), u32, u64, P(TraceOpts), P(vp)],
@@ -229,6 +232,35 @@ def mcrt_scene_read_majorants(ctx, scene, level: int) -> np.ndarray:
 
 def mcrt_scene_set_ground_flat(ctx, scene, albedo: float):
     _check(_load().mcrt_scene_set_ground_flat(scene, albedo), ctx)
+
+
+def mcrt_scene_set_ground_heightfield(ctx, scene, heights, albedo: float):
+    """heights: [hny][hnx] km, numpy array or CUDA tensor."""
+    if hasattr(heights, "is_cuda") and heights.is_cuda:
+        import torch
+        hh = heights.contiguous().to(torch.float32)
+        ptr, mem = C.c_void_p(hh.data_ptr()), MCRT_MEM_DEVICE
+    else:
+        hh = np.ascontiguousarray(heights, dtype=np.float32)
+        ptr, mem = C.c_void_p(hh.ctypes.data), MCRT_MEM_HOST
+    hny, hnx = hh.shape
+    _check(_load().mcrt_scene_set_ground_heightfield(scene, ptr, hnx, hny, mem, albedo), ctx)
+
+
+def mcrt_debug_terrain(ctx, scene, o, d):
+    oo = np.ascontiguousarray(o, dtype=np.float32).reshape(-1, 3)
+    dd = np.ascontiguousarray(d, dtype=np.float32).reshape(-1, 3)
+    t = np.zeros(oo.shape[0], dtype=np.float32)
+    _check(_load().mcrt_debug_terrain(scene, oo.shape[0], _ptr(oo, C.c_float), _ptr(dd, C.c_float),
+                                      _ptr(t, C.c_float)), ctx)
+    return t
+
+
+def mcrt_debug_terrain_height(ctx, scene, xy):
+    p = np.ascontiguousarray(xy, dtype=np.float32).reshape(-1, 2)
+    out = np.zeros((p.shape[0], 4), dtype=np.float32)
+    _check(_load().mcrt_debug_terrain_height(scene, p.shape[0], _ptr(p, C.c_float), _ptr(out, C.c_float)), ctx)
+    return out[:, 0], out[:, 1:]
 
 
 def mcrt_scene_set_sun(ctx, scene, zenith_deg: float, azimuth_deg: float):
@@ -406,6 +438,15 @@ class Scene:
 
     def majorants(self, level):
         return mcrt_scene_read_majorants(self.ctx.h, self.h, level)
+
+    def set_heightfield(self, heights, albedo):
+        mcrt_scene_set_ground_heightfield(self.ctx.h, self.h, heights, albedo)
+
+    def terrain_hit(self, o, d):
+        return mcrt_debug_terrain(self.ctx.h, self.h, o, d)
+
+    def terrain_height(self, xy):
+        return mcrt_debug_terrain_height(self.ctx.h, self.h, xy)
 
     def dda(self, o, d, tau_merge=1.0, finest_level=1, cap=4096):
         return mcrt_debug_dda(self.ctx.h, self.h, o, d, tau_merge, finest_level, cap)

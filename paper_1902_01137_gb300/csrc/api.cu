@@ -84,6 +84,18 @@ DevScene make_dev_scene(const mcrt_scene* sc, float k_gas)
     S.k_gas = k_gas;
     S.albedo = sc->albedo;
     for (int a = 0; a < 3; ++a) S.sun[a] = sc->sun[a];
+    if (sc->d_hf) {
+        S.hf = sc->d_hf;
+        S.hpyr = sc->d_hpyr;
+        for (int a = 0; a < 2; ++a) {
+            S.hn[a] = sc->hn[a];
+            S.hc[a] = (float)((double)sc->n[a] * sc->h[a] / sc->hn[a]);
+            S.inv_hc[a] = 1.0f / S.hc[a];
+        }
+        S.hmax = sc->hmax;
+        S.hlev = sc->hlev;
+        for (int L = 0; L < kMaxHfLevels; ++L) S.hoff[L] = sc->hoff[L];
+    }
     return S;
 }
 
@@ -242,6 +254,8 @@ int mcrt_scene_destroy(mcrt_scene* sc)
     dfree(ctx, sc->d_vox);
     dfree(ctx, sc->d_pyr);
     dfree(ctx, sc->d_leaf);
+    dfree(ctx, sc->d_hf);
+    dfree(ctx, sc->d_hpyr);
     cudaStreamSynchronize(ctx->stream);
     delete sc;
     return MCRT_OK;
@@ -305,6 +319,73 @@ int mcrt_scene_set_ground_flat(mcrt_scene* sc, float albedo)
     if (!(albedo >= 0.0f && albedo <= 1.0f))
         return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_set_ground_flat: albedo must be in [0, 1]");
     sc->albedo = albedo;
+    dfree(sc->ctx, sc->d_hf);
+    dfree(sc->ctx, sc->d_hpyr);
+    sc->d_hf = sc->d_hpyr = nullptr;
+    sc->hlev = 0;
+    return MCRT_OK;
+}
+
+int mcrt_scene_set_ground_heightfield(mcrt_scene* sc, const float* heights, int32_t hnx, int32_t hny, int32_t mem,
+                                      float albedo)
+{
+    const char* who = "mcrt_scene_set_ground_heightfield";
+    if (!sc || !heights) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (!(albedo >= 0.0f && albedo <= 1.0f)) return fail(ctx, MCRT_ERR_ARG, "%s: albedo must be in [0, 1]", who);
+    if (hnx < 1 || hny < 1 || hnx > (1 << 16) || hny > (1 << 16))
+        return fail(ctx, MCRT_ERR_ARG, "%s: bad size %d x %d", who, hnx, hny);
+    if (mem != MCRT_MEM_HOST && mem != MCRT_MEM_DEVICE)
+        return fail(ctx, MCRT_ERR_ARG, "%s: mem must be MCRT_MEM_HOST or MCRT_MEM_DEVICE", who);
+    CK(ctx, cudaSetDevice(ctx->device));
+    // levels: 4 x 4 blocks while both sizes divide
+    int lev = 1;
+    while (lev < kMaxHfLevels && hnx % (1 << (2 * lev)) == 0 && hny % (1 << (2 * lev)) == 0) ++lev;
+    int off[kMaxHfLevels] = {};
+    size_t total = 0;
+    for (int L = 0; L < lev; ++L) {
+        off[L] = (int)total;
+        total += (size_t)(hnx >> (2 * L)) * (size_t)(hny >> (2 * L));
+    }
+    const size_t n = (size_t)hnx * hny;
+    float *dh = nullptr, *dp = nullptr;
+    int* bad = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dh), n * sizeof(float), ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&dp), total * sizeof(float), ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dh, heights, n * sizeof(float),
+                            mem == MCRT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream);
+    const float top = (float)sc->n[2] * sc->h[2];
+    if (e == cudaSuccess) { ctx->launches++; e = launch_hf_check(dh, (long long)n, top, bad, ctx->stream); }
+    if (e == cudaSuccess) { ctx->launches += lev; e = launch_hf_pyramid(dh, hnx, hny, dp, off, lev, ctx->stream); }
+    const size_t ntop = (size_t)(hnx >> (2 * (lev - 1))) * (size_t)(hny >> (2 * (lev - 1)));
+    std::vector<float> tops(ntop);
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tops.data(), dp + off[lev - 1], ntop * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (bad) cudaFreeAsync(bad, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess || hbad) {
+        dfree(ctx, dh);
+        dfree(ctx, dp);
+        if (e != cudaSuccess) return fail(ctx, MCRT_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
+        return fail(ctx, MCRT_ERR_ARG, "%s: heights must be finite and in [0, %g] km", who, (double)top);
+    }
+    dfree(ctx, sc->d_hf);
+    dfree(ctx, sc->d_hpyr);
+    sc->d_hf = dh;
+    sc->d_hpyr = dp;
+    sc->hn[0] = hnx;
+    sc->hn[1] = hny;
+    sc->hlev = lev;
+    for (int L = 0; L < kMaxHfLevels; ++L) sc->hoff[L] = off[L];
+    float hm = 0.0f;
+    for (float v : tops) hm = std::fmax(hm, v);
+    sc->hmax = hm;
+    sc->albedo = albedo;
     return MCRT_OK;
 }
 
@@ -359,6 +440,7 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
         if (o->batch_paths < 0 || o->train_steps < 0 || !(o->learning_rate >= 0.0f))
             return fail(ctx, MCRT_ERR_ARG, "%s: bad learned-mode options", who);
         if (o->count_events) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: counting with a proposal", who);
+        if (sc->d_hf) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a proposal over a heightfield ground", who);
     }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     return MCRT_OK;
@@ -417,7 +499,7 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;
     int grid = o->grid_size;
-    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, block);
+    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, block);
     P.s1 = t->d_s1;
     P.s2 = t->d_s2;
     P.counters = t->d_counters;
@@ -739,6 +821,7 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
             return fail(ctx, MCRT_ERR_ARG, "%s: item %d: k_gas must be finite and >= 0", who, i);
         if (!(it.sun_zenith_deg >= 0.0f && it.sun_zenith_deg < 90.0f) || !std::isfinite(it.sun_azimuth_deg))
             return fail(ctx, MCRT_ERR_ARG, "%s: item %d: sun zenith must be in [0, 90)", who, i);
+        if (sc->d_hf) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: item %d: heightfield ground in batches", who, i);
         if (i > 0 && (sc->storage == MCRT_STORAGE_BF16) != bf16)
             return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: items mix FP32 and BF16 storage", who);
         bf16 = sc->storage == MCRT_STORAGE_BF16;
@@ -1180,6 +1263,56 @@ int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], f
     CK(ctx, e);
     *count = cs[0];
     *status = cs[1];
+    return MCRT_OK;
+}
+
+int mcrt_debug_terrain(const mcrt_scene* sc, int32_t n, const float* o, const float* d, float* t_out)
+{
+    const char* who = "mcrt_debug_terrain";
+    if (!sc || (n > 0 && (!o || !d || !t_out))) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (!sc->d_hf) return fail(ctx, MCRT_ERR_STATE, "%s: the scene has a flat ground", who);
+    if (n < 0 || n > (1 << 24)) return fail(ctx, MCRT_ERR_ARG, "%s: bad ray count %d", who, n);
+    if (n == 0) return MCRT_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    float* buf = nullptr;
+    CK(ctx, cudaMallocAsync(reinterpret_cast<void**>(&buf), (size_t)n * 7 * sizeof(float), ctx->stream));
+    cudaError_t e = cudaMemcpyAsync(buf, o, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf + 3 * (size_t)n, d, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->launches++;
+        e = launch_debug_terrain(make_dev_scene(sc, 0.0f), buf, buf + 3 * (size_t)n, n, buf + 6 * (size_t)n, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t_out, buf + 6 * (size_t)n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(buf, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    CK(ctx, e);
+    return MCRT_OK;
+}
+
+int mcrt_debug_terrain_height(const mcrt_scene* sc, int32_t n, const float* xy, float* zn_out)
+{
+    const char* who = "mcrt_debug_terrain_height";
+    if (!sc || (n > 0 && (!xy || !zn_out))) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (!sc->d_hf) return fail(ctx, MCRT_ERR_STATE, "%s: the scene has a flat ground", who);
+    if (n < 0 || n > (1 << 24)) return fail(ctx, MCRT_ERR_ARG, "%s: bad point count %d", who, n);
+    if (n == 0) return MCRT_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    float* buf = nullptr;
+    CK(ctx, cudaMallocAsync(reinterpret_cast<void**>(&buf), (size_t)n * 6 * sizeof(float), ctx->stream));
+    cudaError_t e = cudaMemcpyAsync(buf, xy, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->launches++;
+        e = launch_debug_terrain_height(make_dev_scene(sc, 0.0f), buf, n, buf + 2 * (size_t)n, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(zn_out, buf + 2 * (size_t)n, (size_t)n * 4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(buf, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    CK(ctx, e);
     return MCRT_OK;
 }
 

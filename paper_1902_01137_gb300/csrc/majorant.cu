@@ -181,4 +181,63 @@ cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStre
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Heightfield ground: max pyramid.  Level 0 holds each cell's maximum over
+// its 4 corner heights (periodic); level L the maximum over 4 x 4 cells of
+// level L - 1.  Also a scan for invalid heights (not finite, < 0 or above
+// the top of the field).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void hf_cellmax_kernel(const float* __restrict__ h, int nx, int ny, float* __restrict__ out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nx * ny) return;
+    const int i = (int)(idx % nx), j = (int)(idx / nx);
+    const int i1 = i + 1 == nx ? 0 : i + 1, j1 = j + 1 == ny ? 0 : j + 1;
+    out[idx] = fmaxf(fmaxf(h[(size_t)j * nx + i], h[(size_t)j * nx + i1]),
+                     fmaxf(h[(size_t)j1 * nx + i], h[(size_t)j1 * nx + i1]));
+}
+
+__global__ void hf_reduce4_kernel(const float* __restrict__ in, int nx, int ny, float* __restrict__ out)
+{
+    // out is (nx / 4) x (ny / 4)
+    const int ox = nx >> 2, oy = ny >> 2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)ox * oy) return;
+    const int i = (int)(idx % ox), j = (int)(idx / ox);
+    float m = in[(size_t)(4 * j) * nx + 4 * i];
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) m = fmaxf(m, in[(size_t)(4 * j + b) * nx + 4 * i + a]);
+    out[idx] = m;
+}
+
+__global__ void hf_check_kernel(const float* __restrict__ h, long long n, float top, int* __restrict__ bad)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const float v = h[idx];
+    if (!(v >= 0.0f && v <= top)) atomicOr(bad, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_hf_pyramid(const float* h, int nx, int ny, float* pyr, const int* off, int levels, cudaStream_t st)
+{
+    const long long n0 = (long long)nx * ny;
+    hf_cellmax_kernel<<<(unsigned)((n0 + 255) / 256), 256, 0, st>>>(h, nx, ny, pyr + off[0]);
+    for (int L = 1; L < levels; ++L) {
+        const int px = nx >> (2 * (L - 1)), py = ny >> (2 * (L - 1));
+        const long long n = (long long)(px >> 2) * (py >> 2);
+        hf_reduce4_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pyr + off[L - 1], px, py, pyr + off[L]);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hf_check(const float* h, long long n, float top, int* bad, cudaStream_t st)
+{
+    hf_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h, n, top, bad);
+    return cudaGetLastError();
+}
+
 }  // namespace mcrt

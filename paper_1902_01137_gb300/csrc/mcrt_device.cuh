@@ -63,6 +63,8 @@ __device__ __forceinline__ uint4 draw_block(unsigned long long path, uint32_t c2
 // --------------------------------------------------------------------------
 // Scene as seen by the kernels
 // --------------------------------------------------------------------------
+constexpr int kMaxHfLevels = 12;
+
 struct DevScene {
     int n[3];            // voxels per axis
     float h[3];          // voxel size [km]
@@ -74,8 +76,20 @@ struct DevScene {
     const uint2* __restrict__ leaf;      // per level-1 cell: {majorant bits, leaf level}
     float k_clear, ssa_clear, ssa_cloud, g;
     float k_gas;         // extra uniform pure absorber
-    float albedo;        // flat Lambertian ground
+    float albedo;        // Lambertian ground
     float sun[3];        // unit vector toward the sun
+    // heightfield ground (hf null: flat ground at z = 0).  Heights sit at
+    // the corners of a periodic grid of hn[0] x hn[1] cells; hpyr holds the
+    // cell maxima (level 0: max of a cell's 4 corners) and hlev - 1 coarser
+    // levels of 4 x 4 blocks, concatenated at hoff[level].
+    const float* __restrict__ hf;
+    const float* __restrict__ hpyr;
+    int hn[2];
+    float hc[2];         // cell size [km]
+    float inv_hc[2];
+    float hmax;          // largest height
+    int hlev;
+    int hoff[kMaxHfLevels];
 };
 
 __device__ __forceinline__ size_t brick_index(const DevScene& S, int i, int j, int k)
@@ -302,6 +316,161 @@ __device__ __forceinline__ void cosine_up(float xi1, float xi2, float out[3])
     float sp, cp;
     sincospif(2.0f * xi2, &sp, &cp);
     out[0] = st * cp; out[1] = st * sp; out[2] = sqrtf(xi1);
+}
+
+// Cosine-weighted direction about the unit normal n (Duff et al. frame);
+// the same draws as cosine_up, tilted.
+__device__ __forceinline__ void cosine_about(const float n[3], float xi1, float xi2, float out[3])
+{
+    const float sign = copysignf(1.0f, n[2]);
+    const float a = -__frcp_rn(sign + n[2]);
+    const float b = n[0] * n[1] * a;
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - xi1)), ct = sqrtf(xi1);
+    float sp, cp;
+    sincospif(2.0f * xi2, &sp, &cp);
+    const float c = st * cp, s = st * sp;
+    out[0] = c * (1.0f + sign * n[0] * n[0] * a) + s * b + ct * n[0];
+    out[1] = c * (sign * b) + s * (sign + n[1] * n[1] * a) + ct * n[1];
+    out[2] = c * (-sign * n[0]) + s * (-n[1]) + ct * n[2];
+}
+
+// --------------------------------------------------------------------------
+// Heightfield ground.  Cell (i, j) is cut along its diagonal from corner
+// (i, j) to (i+1, j+1): with u, v the position in the cell scaled to [0, 1],
+// triangle A (u >= v) has corners 00, 10, 11 and triangle B (u < v) corners
+// 00, 11, 01; on a triangle the surface is z = c + a u + b v.
+// --------------------------------------------------------------------------
+constexpr float kTerrainOffset = 1e-5f;   // km: a path leaves the surface this far along its normal
+
+__device__ __forceinline__ int wrap_mod(int i, int n)
+{
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float hf_at(const DevScene& S, int i, int j)
+{
+    return __ldg(S.hf + (size_t)wrap_mod(j, S.hn[1]) * S.hn[0] + wrap_mod(i, S.hn[0]));
+}
+
+__device__ __forceinline__ void hf_plane(const DevScene& S, int i, int j, bool triA, float* a, float* b, float* c)
+{
+    const float h00 = hf_at(S, i, j), h10 = hf_at(S, i + 1, j), h01 = hf_at(S, i, j + 1), h11 = hf_at(S, i + 1, j + 1);
+    *c = h00;
+    if (triA) { *a = h10 - h00; *b = h11 - h10; }
+    else      { *a = h11 - h01; *b = h01 - h00; }
+}
+
+// Surface height at (x, y) and the unit upward normal of its triangle.
+__device__ __forceinline__ float hf_height(const DevScene& S, float x, float y, float n[3])
+{
+    const float fx = x * S.inv_hc[0], fy = y * S.inv_hc[1];
+    const int i = __float2int_rd(fx), j = __float2int_rd(fy);
+    const float u = fx - (float)i, v = fy - (float)j;
+    float a, b, c;
+    hf_plane(S, i, j, u >= v, &a, &b, &c);
+    const float gx = a * S.inv_hc[0], gy = b * S.inv_hc[1];
+    const float inv = rsqrtf(gx * gx + gy * gy + 1.0f);
+    n[0] = -gx * inv; n[1] = -gy * inv; n[2] = inv;
+    return c + a * u + b * v;
+}
+
+// First distance t >= 0 at which the ray o + t d meets the surface, or
+// +inf.  Only the part of the ray with z <= hmax can hit (it reaches z = 0,
+// at or below every height, last).  The ray's horizontal projection walks
+// the max pyramid over unwrapped cell indices: a cell whose maximum lies
+// below the ray's lowest point over the cell is skipped whole, otherwise
+// the walk descends into its 4 x 4 children; after a step that leaves the
+// parent block it climbs one level.  In a level-0 cell the ray crosses at
+// most two triangle pieces (split where u = v); on a piece the ray's height
+// above the plane, f(t), is linear and the hit is where f first reaches 0
+// (the piece start if f <= 0 there).
+static __device__ __forceinline__ float terrain_hit(const DevScene& S, const float o[3], const float d[3])
+{
+    const float kInf = __int_as_float(0x7f800000);
+    float t0 = 0.0f, t1;
+    if (o[2] > S.hmax) {
+        if (!(d[2] < 0.0f)) return kInf;
+        t0 = __fdiv_rn(S.hmax - o[2], d[2]);
+    }
+    if (d[2] < 0.0f) t1 = __fdiv_rn(-o[2], d[2]);
+    else if (d[2] > 0.0f) t1 = __fdiv_rn(S.hmax - o[2], d[2]);
+    else t1 = kInf;
+    if (t1 < t0) return kInf;
+    const float inv_dx = d[0] != 0.0f ? __frcp_rn(d[0]) : 0.0f;
+    const float inv_dy = d[1] != 0.0f ? __frcp_rn(d[1]) : 0.0f;
+    int L = S.hlev - 1;
+    float t = t0;
+    int i, j;
+    {
+        const float cx = S.hc[0] * (float)(1 << (2 * L)), cy = S.hc[1] * (float)(1 << (2 * L));
+        const float x = __fmaf_rn(t, d[0], o[0]), y = __fmaf_rn(t, d[1], o[1]);
+        i = __float2int_rd(__fdiv_rn(x, cx));
+        j = __float2int_rd(__fdiv_rn(y, cy));
+        if (d[0] < 0.0f && (float)i * cx == x) i -= 1;
+        if (d[1] < 0.0f && (float)j * cy == y) j -= 1;
+    }
+    for (int it = 0; it < (1 << 16); ++it) {
+        const int sh = 2 * L;
+        const float cx = S.hc[0] * (float)(1 << sh), cy = S.hc[1] * (float)(1 << sh);
+        const float tx = d[0] > 0.0f ? ((float)(i + 1) * cx - o[0]) * inv_dx
+                       : d[0] < 0.0f ? ((float)i * cx - o[0]) * inv_dx : kInf;
+        const float ty = d[1] > 0.0f ? ((float)(j + 1) * cy - o[1]) * inv_dy
+                       : d[1] < 0.0f ? ((float)j * cy - o[1]) * inv_dy : kInf;
+        const float te = fmaxf(fminf(fminf(tx, ty), t1), t);
+        const int nx = S.hn[0] >> sh, ny = S.hn[1] >> sh;
+        const float cmax = __ldg(S.hpyr + S.hoff[L] + (size_t)wrap_mod(j, ny) * nx + wrap_mod(i, nx));
+        const float zlo = __fmaf_rn(d[2] < 0.0f ? te : t, d[2], o[2]);
+        if (zlo <= cmax) {
+            if (L > 0) {
+                // descend into the child holding the point at t
+                const float hx = cx * 0.25f, hy = cy * 0.25f;
+                const float x = __fmaf_rn(t, d[0], o[0]), y = __fmaf_rn(t, d[1], o[1]);
+                int ci = __float2int_rd(__fdiv_rn(x, hx)), cj = __float2int_rd(__fdiv_rn(y, hy));
+                if (d[0] < 0.0f && (float)ci * hx == x) ci -= 1;
+                if (d[1] < 0.0f && (float)cj * hy == y) cj -= 1;
+                i = min(max(ci, 4 * i), 4 * i + 3);
+                j = min(max(cj, 4 * j), 4 * j + 3);
+                --L;
+                continue;
+            }
+            // level 0: the triangle pieces of [t, te]
+            const float g0 = (o[0] * S.inv_hc[0] - (float)i) - (o[1] * S.inv_hc[1] - (float)j);
+            const float g1 = d[0] * S.inv_hc[0] - d[1] * S.inv_hc[1];
+            float cut1 = te;
+            int np = 1;
+            if (g1 != 0.0f) {
+                const float tm = __fdiv_rn(-g0, g1);
+                if (tm > t && tm < te) { cut1 = tm; np = 2; }
+            }
+            for (int q = 0; q < np; ++q) {
+                const float a0 = q == 0 ? t : cut1, b0 = q == 0 ? cut1 : te;
+                const bool triA = __fmaf_rn(g1, 0.5f * (a0 + b0), g0) >= 0.0f;
+                float A, B, Cc;
+                hf_plane(S, i, j, triA, &A, &B, &Cc);
+                const float ua = __fmaf_rn(a0, d[0], o[0]) * S.inv_hc[0] - (float)i;
+                const float va = __fmaf_rn(a0, d[1], o[1]) * S.inv_hc[1] - (float)j;
+                const float ub = __fmaf_rn(b0, d[0], o[0]) * S.inv_hc[0] - (float)i;
+                const float vb = __fmaf_rn(b0, d[1], o[1]) * S.inv_hc[1] - (float)j;
+                const float fa = __fmaf_rn(a0, d[2], o[2]) - (Cc + A * ua + B * va);
+                const float fb = __fmaf_rn(b0, d[2], o[2]) - (Cc + A * ub + B * vb);
+                if (fa <= 0.0f) return a0;
+                if (fb <= 0.0f) return a0 + fa * __fdiv_rn(b0 - a0, fa - fb);
+            }
+        }
+        // step to the next cell of this level; climb when leaving the parent block
+        if (te >= t1) return kInf;
+        const int pi = i >> 2, pj = j >> 2;
+        if (tx <= ty) i += d[0] > 0.0f ? 1 : -1;
+        else j += d[1] > 0.0f ? 1 : -1;
+        t = te;
+        if (L < S.hlev - 1 && ((i >> 2) != pi || (j >> 2) != pj)) {
+            i >>= 2;
+            j >>= 2;
+            ++L;
+        }
+    }
+    return kInf;
 }
 
 // Single-scattering albedo of the mixture at total extinction k_tot.

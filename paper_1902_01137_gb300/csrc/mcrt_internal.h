@@ -43,6 +43,13 @@ struct mcrt_scene {
     float albedo = 0;
     float sun_zenith = 0, sun_azimuth = 0;
     float sun[3] = {0, 0, 1};
+    // heightfield ground (null: flat)
+    float* d_hf = nullptr;
+    float* d_hpyr = nullptr;
+    int hn[2] = {0, 0};
+    float hmax = 0;
+    int hlev = 0;
+    int hoff[mcrt::kMaxHfLevels] = {};
 };
 
 struct mcrt_tally {
@@ -158,9 +165,13 @@ cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t
 cudaError_t launch_reduce_level(const float* prev, const int* prev_dims, float* out, const int* dims,
                                 cudaStream_t st);
 cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st);
+cudaError_t launch_hf_pyramid(const float* h, int nx, int ny, float* pyr, const int* off, int levels, cudaStream_t st);
+cudaError_t launch_hf_check(const float* h, long long n, float top, int* bad, cudaStream_t st);
+cudaError_t launch_debug_terrain(const DevScene& S, const float* o, const float* d, int n, float* t, cudaStream_t st);
+cudaError_t launch_debug_terrain_height(const DevScene& S, const float* xy, int n, float* zn, cudaStream_t st);
 cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count, int grid, int block,
                          cudaStream_t st);
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block);
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, int block);
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
 int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);

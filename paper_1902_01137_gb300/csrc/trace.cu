@@ -70,7 +70,7 @@ constexpr int kSections = 9;
 // leaf-entry load and the leaf set-up also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME };
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
     // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg in batches)
@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     uint32_t lv = 0;                        // volume vertices so far (learned mode)
     uint32_t cur_rec = 0xFFFFFFFFu;         // training record awaiting its own estimate
     bool suspend = false;                   // stop this path until the network has run
+    float tg = __int_as_float(0x7f800000);  // heightfield: distance of the flight's ground hit from R.o
+    float fz = 1.0f;                        // heightfield flux: n_z of the surface at the path start
     float vx[3] = {0.0f, 0.0f, 0.0f}, nd[3] = {0.0f, 0.0f, 1.0f};
     unsigned long long cnt[kCounters];
 #pragma unroll
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const DevScene& S = BATCH ? P.items[item].S : P.S;
 
         // ---- the one Philox block of this iteration ---------------------------
-        const float seg = R.texit - R.t;
+        const float seg = (TERRAIN ? fminf(R.texit, tg) : R.texit) - R.t;
         const float Mseg = R.M * seg;
         const bool tent = ph == PH_STEP && R.M > 0.0f && tau < Mseg;
         uint32_t xc2 = c2, xblk = 0u;
@@ -285,11 +287,33 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 vx[2] = 0.0f;
                 if (!(vx[0] < S.Lper[0])) vx[0] = 0.0f;
                 if (!(vx[1] < S.Lper[1])) vx[1] = 0.0f;
-                cosine_up(u01(x.z), u01(x.w), nd);
                 kind = kSunDirect;
                 c2 = 3u;
                 Ts = 1.0f;
                 phase = PH_BEGIN;
+                if constexpr (TERRAIN) {
+                    // the surface point above (x, y), lifted along its normal;
+                    // directions cosine-weighted about the normal; the direct
+                    // irradiance of the tilted element per horizontal area is
+                    // max(n.s, 0) / (n_z mu0) T_sun, kept in tdir until T_sun
+                    float n[3];
+                    vx[2] = hf_height(S, vx[0], vx[1], n);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) vx[a] += kTerrainOffset * n[a];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        if (vx[a] < 0.0f) vx[a] += S.Lper[a];
+                        if (!(vx[a] < S.Lper[a])) vx[a] -= S.Lper[a];
+                        if (!(vx[a] >= 0.0f && vx[a] < S.Lper[a])) vx[a] = 0.0f;
+                    }
+                    cosine_about(n, u01(x.z), u01(x.w), nd);
+                    fz = n[2];
+                    const float ns = n[0] * S.sun[0] + n[1] * S.sun[1] + n[2] * S.sun[2];
+                    tdir = __fdividef(fmaxf(ns, 0.0f), n[2] * S.sun[2]);
+                    if (!(ns > 0.0f)) { kind = kMain; c2 = 0u; }     // self-shadowed: no direct sun ray
+                } else {
+                    cosine_up(u01(x.z), u01(x.w), nd);
+                }
             }
         }
         mark(2);
@@ -309,6 +333,17 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             setup = true;
             tau = -__logf(u01(x.x));
             blk = 1;
+            if constexpr (TERRAIN) {
+                // the flight ends at the surface; a sun ray that meets it is shadowed
+                tg = terrain_hit(S, R.o, R.d);
+                if (kind != kMain && tg < __int_as_float(0x7f800000)) {
+                    Ts = 0.0f;
+                    evc = EV_SUN_END;
+                    ptr = nullptr;
+                    setup = false;
+                }
+                if (kind != kMain) tg = __int_as_float(0x7f800000);
+            }
             if (COUNT) {
                 if (kind == kMain) cnt[C_FLIGHTS]++;
                 else cnt[C_SUN_RAYS]++;
@@ -318,9 +353,22 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         if (ph == PH_STEP) {
             // one step: to the tentative collision inside the leaf, or across
             // the leaf's exit face; both share the point and voxel arithmetic
-            const float tn = tent ? fminf(R.t + __fdividef(tau, R.M), R.texit) : R.texit;
-            advance(S, R, tn, !tent, p, nv);
-            if (tent) {
+            const bool at_ground = TERRAIN && !tent && tg <= R.texit;   // the surface cuts this leaf
+            const float tn = tent ? fminf(R.t + __fdividef(tau, R.M), TERRAIN ? fminf(R.texit, tg) : R.texit)
+                                  : (at_ground ? tg : R.texit);
+            advance(S, R, tn, !tent && !at_ground, p, nv);
+            if (at_ground) {
+                // ground vertex at the surface hit (x, y wrapped into the domain)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    if (p[a] < 0.0f) p[a] += S.Lper[a];
+                    if (!(p[a] < S.Lper[a])) p[a] -= S.Lper[a];
+                    if (!(p[a] >= 0.0f && p[a] < S.Lper[a])) p[a] = 0.0f;
+                }
+                vx[0] = p[0]; vx[1] = p[1]; vx[2] = fmaxf(p[2], 0.0f);
+                vground = true;
+                phase = PH_VERTEX;
+            } else if (tent) {
                 R.t = tn;
                 const size_t idx = brick_index(S, nv[0], nv[1], nv[2]);
                 if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
@@ -329,6 +377,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 tau -= Mseg;
                 float wdt;
                 st = cross_face(S, R, p, nv, &wdt);
+                if (TERRAIN) tg -= wdt;                  // a periodic wrap restarts the segment
                 if (st == kInside) {
                     ptr = leaf_entry(S, R.v);
                     setup = true;
@@ -371,6 +420,24 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 rotate_dir(R.d, mu_new, xi2, nd);
                 if (BATCH) { cfs = hg_dlog_dg(S.g, mu); sv_pending = hg_dlog_dg(S.g, mu_new); }
                 if (COUNT) cnt[C_REAL]++;
+            } else if constexpr (TERRAIN) {
+                // tilted ground: leave the surface along its normal, estimate
+                // with n.s, scatter cosine-weighted about n
+                float n[3];
+                hf_height(S, vx[0], vx[1], n);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vx[a] += kTerrainOffset * n[a];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    if (vx[a] < 0.0f) vx[a] += S.Lper[a];
+                    if (!(vx[a] < S.Lper[a])) vx[a] -= S.Lper[a];
+                    if (!(vx[a] >= 0.0f && vx[a] < S.Lper[a])) vx[a] = 0.0f;
+                }
+                const float ns = n[0] * S.sun[0] + n[1] * S.sun[1] + n[2] * S.sun[2];
+                cf = (score_it && ns > 0.0f) ? w * (S.albedo * (1.0f / kPi)) * ns : 0.0f;
+                w *= S.albedo;
+                cosine_about(n, xi1, xi2, nd);
+                if (COUNT) cnt[C_GROUND]++;
             } else {
                 cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
                 w *= S.albedo;
@@ -383,7 +450,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (xr * 0.01f <= w) w = 0.01f;
                 else term_after = true;
             }
-            if (score_it) {
+            // (a ground facet turned away from the sun sends no sun ray)
+            if (score_it && (!TERRAIN || !vground || cf > 0.0f)) {
                 kind = kSunLocal;
                 c2 = (ev << 2) | 1u;
                 Ts = 1.0f;
@@ -546,7 +614,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
             if (evc == EV_SUN_END) {
                 if (kind == kSunDirect) {
-                    tdir = Ts;
+                    tdir = TERRAIN ? tdir * Ts : Ts;
                     ev = 0;
                     kind = kMain;
                     c2 = 0u;
@@ -577,7 +645,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     acc[0] += score;
                     acc[1] += score * score;
                 } else {
-                    const float pi_over_mu0 = __fdividef(kPi, S.sun[2]);
+                    const float pi_over_mu0 = __fdividef(kPi, TERRAIN ? fz * S.sun[2] : S.sun[2]);
                     const float tf = pi_over_mu0 * score;
                     const float tt = tdir + tf;
                     acc[0] += tdir; acc[1] += tdir * tdir;
@@ -723,6 +791,27 @@ __global__ void debug_dda_kernel(DevScene S, float ox, float oy, float oz, float
     count_status[1] = status;
 }
 
+// One thread per ray: the heightfield hit distance (terrain check).
+__global__ void debug_terrain_kernel(DevScene S, const float* __restrict__ o, const float* __restrict__ d, int n,
+                                     float* __restrict__ t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float oo[3] = {o[3 * i], o[3 * i + 1], o[3 * i + 2]};
+    const float dd[3] = {d[3 * i], d[3 * i + 1], d[3 * i + 2]};
+    t[i] = terrain_hit(S, oo, dd);
+}
+
+// One thread per point: surface height and normal (z, nx, ny, nz).
+__global__ void debug_terrain_height_kernel(DevScene S, const float* __restrict__ xy, int n, float* __restrict__ zn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float nn[3];
+    zn[4 * i] = hf_height(S, xy[2 * i], xy[2 * i + 1], nn);
+    zn[4 * i + 1] = nn[0]; zn[4 * i + 2] = nn[1]; zn[4 * i + 3] = nn[2];
+}
+
 __global__ void debug_philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
                                     uint32_t* __restrict__ out, size_t n)
 {
@@ -733,20 +822,26 @@ __global__ void debug_philox_kernel(const uint32_t* __restrict__ ctr, const uint
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
 }
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool TERRAIN = false>
 const void* kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED>);
+    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED, false, TERRAIN>);
 }
 
-const void* pick(int sensor, bool bf16, bool count)
+template <bool TERRAIN>
+const void* pick_t(int sensor, bool bf16, bool count)
 {
     if (sensor == kCamera) {
-        if (bf16) return count ? kernel_ptr<kCamera, true, true, false>() : kernel_ptr<kCamera, true, false, false>();
-        return count ? kernel_ptr<kCamera, false, true, false>() : kernel_ptr<kCamera, false, false, false>();
+        if (bf16) return count ? kernel_ptr<kCamera, true, true, false, TERRAIN>() : kernel_ptr<kCamera, true, false, false, TERRAIN>();
+        return count ? kernel_ptr<kCamera, false, true, false, TERRAIN>() : kernel_ptr<kCamera, false, false, false, TERRAIN>();
     }
-    if (bf16) return count ? kernel_ptr<kFlux, true, true, false>() : kernel_ptr<kFlux, true, false, false>();
-    return count ? kernel_ptr<kFlux, false, true, false>() : kernel_ptr<kFlux, false, false, false>();
+    if (bf16) return count ? kernel_ptr<kFlux, true, true, false, TERRAIN>() : kernel_ptr<kFlux, true, false, false, TERRAIN>();
+    return count ? kernel_ptr<kFlux, false, true, false, TERRAIN>() : kernel_ptr<kFlux, false, false, false, TERRAIN>();
+}
+
+const void* pick(int sensor, bool bf16, bool count, bool terrain)
+{
+    return terrain ? pick_t<true>(sensor, bf16, count) : pick_t<false>(sensor, bf16, count);
 }
 
 const void* pick_batch(bool bf16)
@@ -781,7 +876,7 @@ cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count
                          cudaStream_t st)
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
-    return cudaLaunchKernel(pick(sensor, bf16, count), dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(pick(sensor, bf16, count, P.S.hf != nullptr), dim3(grid), dim3(block), args, 0, st);
 }
 
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st)
@@ -817,10 +912,10 @@ cudaError_t launch_targets(const float* rec_val, const float* final_score, unsig
     return cudaGetLastError();
 }
 
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, int block)
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count), block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count, terrain), block, 0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
@@ -841,6 +936,20 @@ cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, 
     else
         debug_dda_kernel<false><<<1, 32, 0, st>>>(S, o[0], o[1], o[2], d[0], d[1], d[2], cap, cells, tio,
                                                    count_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_terrain(const DevScene& S, const float* o, const float* d, int n, float* t, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    debug_terrain_kernel<<<(n + 127) / 128, 128, 0, st>>>(S, o, d, n, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_terrain_height(const DevScene& S, const float* xy, int n, float* zn, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    debug_terrain_height_kernel<<<(n + 127) / 128, 128, 0, st>>>(S, xy, n, zn);
     return cudaGetLastError();
 }
 

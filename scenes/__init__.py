@@ -260,6 +260,19 @@ def batch_items(instances, scene_of) -> list:
     return items
 
 
+def heightfield(n: int = 4096, relief: float = 0.3, seed: int = 0, psd_slope: float = -3.2) -> np.ndarray:
+    """Periodic fractal terrain: n x n heights [km] from a Gaussian field
+    with a 2D power spectrum ~ k^psd_slope, rescaled to [0, relief]."""
+    r = _rng(seed)
+    kx = np.fft.fftfreq(n) * n
+    kk = np.sqrt(kx[None, :] ** 2 + kx[:, None] ** 2)
+    amp = np.where(kk > 0, np.power(np.maximum(kk, 1e-12), psd_slope / 2.0), 0.0)
+    c = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) * amp
+    f = np.fft.ifft2(c).real
+    f = (f - f.min()) / (f.max() - f.min()) * relief
+    return f.astype(np.float32)
+
+
 def homogeneous(nx: int, ny: int, nz: int, d: float, k: float, **kw) -> SceneSpec:
     """Uniform field (pins: Beer's law, single scattering)."""
     levels = kw.pop("levels", 1)
