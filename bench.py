@@ -16,6 +16,17 @@ per pixel (67,108,864 paths), mean/SE finalize.
              counting run with the same seed) / kernel time, over measured HBM
   cpu_baseline  the CPU oracle on a bounded pixel sample of the same image
 
+  fom        1/(relative variance x time) of the learned proposal against
+             plain HG sampling on the small blob field at sun zenith 60 deg:
+             domain-mean ground flux T_tot and a 512 x 512 image, with the
+             network's online training time counted and, separately, frozen
+
+``--workload batch``: 96 flux problems (fields 64^2x32 ... 1024^2x160 with
+1-16 gas bands each, sun zenith 0-75 deg) in one persistent launch, launch
+shape chosen by the autotuner.  ``--workload sweep``: the refinement sweep
+(128^2x40 ... 2048^2x640 over a 4096^2 heightfield, 1e8 flux paths per
+point, FP32 and BF16 storage, FP64 oracle difference at the two smallest).
+
 ``--impl reference`` times the CPU oracle alone on the same workload.
 Multi-GPU (torchrun): every rank renders an independent replica of the image
 with its own seed (paths are independent: weak scaling, no collective on the
@@ -290,6 +301,9 @@ def run_gpu(args):
         v, cores, desc, paths, dt = oracle_sample(spec, cam, target_s=args.ref_seconds)
         cpu = {"value": v, "unit": "paths/s", "cores": cores, "kind": "oracle", "sample": desc}
 
+    fom = None
+    if rank == 0 and not args.no_fom:
+        fom = learned_fom(m, ctx)
     events = cnt["tentative"] + cnt["sun_tentative"]
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -300,12 +314,297 @@ def run_gpu(args):
             "e2e": {"value": e2e_val, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk,
             "collision_events_per_s": events / (kavg / 1e3),
+            "fom": fom,
             "counters": cnt}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def _fom(rel, ms):
+    return 1.0 / (rel * rel * ms / 1e3)
+
+
+def learned_fom(m, ctx):
+    """Learned proposal vs plain HG sampling (1/(rel. variance x time)) on
+    the 64x64x32 blob field, sun zenith 60 deg.  The flux figure uses T_tot
+    over 2^24 paths; the image figure the mean pixel relative variance of a
+    512 x 512 image at 16 spp.  'online' counts the network's training
+    (2^26 paths in batches of 2^20, 2 Adam steps each) in the time of the
+    estimate those paths give; 'frozen' reuses the trained network."""
+    import scenes
+    spec = scenes.blobs_small(0)
+    spec.sun_zenith_deg = 60.0
+    sc = m.Scene.from_spec(ctx, spec)
+    out = {"field": "blobs 64x64x32 @100m, sun 60 deg", "quantity": "T_tot flux; 512x512 image @16 spp"}
+    try:
+        N = 1 << 24
+        sc.trace_flux(1 << 20, seed=1)
+        plain = sc.trace_flux(N, seed=3)
+        rel_p = plain.se[2] / plain.mean[2]
+        out["plain"] = {"fom": _fom(rel_p, plain.kernel_ms), "rel_se": rel_p, "ms": plain.kernel_ms, "paths": N}
+        cam = scenes.nadir_camera(spec, 512, 512)
+
+        def img_rel(r):
+            ok = r.mean > 1e-3 * r.mean.max()
+            return float(np.sqrt(np.mean((r.se[ok] / r.mean[ok]) ** 2)))
+        ip = sc.trace_camera(cam, 16, seed=3)
+        out["plain_image"] = {"fom": _fom(img_rel(ip), ip.kernel_ms), "rel_se": img_rel(ip), "ms": ip.kernel_ms}
+        for tag, nl, alpha in (("alpha0.5_nl8", 8, 0.5), ("alpha0.75_nl1", 1, 0.75)):
+            prop = m.Proposal(ctx, seed=7)
+            try:
+                tr = sc.trace_flux(1 << 26, seed=4, proposal=prop, learn=1, batch_paths=1 << 20, n_learned=nl,
+                                   mis_alpha=alpha, train_steps=2)
+                rel_t = tr.se[2] / tr.mean[2]
+                fr = sc.trace_flux(N, seed=5, proposal=prop, learn=0, batch_paths=1 << 24, n_learned=nl,
+                                   mis_alpha=alpha)
+                rel_f = fr.se[2] / fr.mean[2]
+                fi = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=nl,
+                                     mis_alpha=alpha)
+                out[tag] = {
+                    "online": {"fom": _fom(rel_t, tr.kernel_ms), "rel_se": rel_t, "ms": tr.kernel_ms,
+                               "paths": 1 << 26, "adam_steps": 128},
+                    "frozen": {"fom": _fom(rel_f, fr.kernel_ms), "rel_se": rel_f, "ms": fr.kernel_ms},
+                    "frozen_image": {"fom": _fom(img_rel(fi), fi.kernel_ms), "rel_se": img_rel(fi),
+                                     "ms": fi.kernel_ms},
+                    "ratio_frozen_vs_plain": _fom(rel_f, fr.kernel_ms) / _fom(rel_p, plain.kernel_ms),
+                    "ratio_image_vs_plain": _fom(img_rel(fi), fi.kernel_ms) / _fom(img_rel(ip), ip.kernel_ms),
+                }
+            finally:
+                prop.close()
+    finally:
+        sc.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Batching workload
+# ---------------------------------------------------------------------------
+BATCH_METRIC_NOTE = "96 flux problems (1-16 gas bands each) in one persistent launch"
+
+
+def run_batch(args):
+    import torch
+    import scenes
+    import paper_1902_01137_gb300 as m
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = m.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    inst = scenes.batch_instances(0)
+    specs = [scenes.cumulus(b.nx, b.nx, b.nz, seed=b.field_seed, device=dev) for b in inst]
+    field_bytes = sum(int(s.k.numel()) * 4 for s in specs)
+
+    def make_scenes(fields):
+        return [m.Scene(ctx, f, sp.dx, sp.dy, sp.dz, k_clear=sp.k_clear, ssa_clear=sp.ssa_clear,
+                        ssa_cloud=sp.ssa_cloud, g=sp.g, levels=sp.levels, albedo=sp.ground_albedo)
+                for f, sp in zip(fields, specs)]
+
+    dev_fields = [sp.k for sp in specs]
+    sc = make_scenes(dev_fields)
+    items = scenes.batch_items(inst, lambda i: sc[i])
+    seeds0 = [it[5] for it in items]
+    paths = sum(it[4] for it in items)
+    opts, best = m.mcrt_autotune_batch(ctx.h, m.make_batch_items(items), 0.25, m.mcrt_trace_opts_default())
+    shape = dict(chunk=opts.chunk, rare_batch=opts.rare_batch, block_size=opts.block_size)
+    cr = m.trace_batch(ctx, items, count_events=1, **shape)
+    cnt = cr.counters
+    for s_ in sc:
+        s_.close()
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(fields, seed_off):
+        scs = make_scenes(fields)
+        try:
+            its = [(scs[i], kg, z, a, n, seed + seed_off)
+                   for i, (_, kg, z, a, n, seed) in zip(_item_instance(inst), items)]
+            r = m.trace_batch(ctx, its, **shape)
+        finally:
+            for s_ in scs:
+                s_.close()
+        return r
+
+    for i in range(args.warmup):
+        step(dev_fields, 1000 * (rank + 1) + i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = ctx.launches
+    step_ms, kern_ms = [], []
+    for i in range(args.steps):
+        flush_buf.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step(dev_fields, 1000 * (rank + 1) + 100 + i)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(r.kernel_ms)
+    torch.cuda.synchronize()
+    launches = ctx.launches - l0
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clk = clocks.stop()
+    value = world * paths * args.steps / (total_ms / 1e3)
+    # e2e: fields from pinned host memory, tallies back to the host
+    e2e = None
+    if not args.no_e2e:
+        host_fields = [f.cpu().pin_memory() for f in dev_fields]
+        ems = []
+        for i in range(max(1, min(args.steps, 2))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = step(host_fields, 5000 + i)
+            _ = r.mean.sum()
+            ems.append((time.perf_counter() - t0) * 1e3)
+        del host_fields
+        e2e = world * paths * len(ems) / (sum(ems) / 1e3)
+    pk = peaks()
+    leaf_entries = cnt["leaf_steps"] + cnt["sun_leaf_steps"] + cnt["sun_rays"] + cnt.get("flights", 0)
+    vox_reads = cnt["tentative"] + cnt["sun_tentative"]
+    alg = 4 * vox_reads + 8 * leaf_entries
+    kavg = statistics.mean(kern_ms)
+    ach = alg / (kavg / 1e3) / 1e9
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = batch_oracle_sample(inst, target_s=args.ref_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch: " + BATCH_METRIC_NOTE, "items": len(items), "instances": len(inst),
+                       "paths_per_step": paths, "field_bytes": field_bytes, "launch_shape": shape,
+                       "autotune_best_ms_on_quarter": best, "l2": "flushed between steps",
+                       "step": "96 scenes (relayout, pyramid, leaf maps) + one batch trace"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_source": "measured" if pk else "fallback",
+                         "kernel": "trace_kernel<flux,f32,batch>", "kernel_ms": kavg, "alg_bytes_per_launch": alg},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "paths/s", "h2d_bytes_per_step": field_bytes,
+                    "d2h_bytes_per_step": len(items) * 4 * 16},
+            "gpu_launches": launches, "clocks": clk, "counters": cnt}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _item_instance(inst):
+    """Instance index of each flattened item (one per band)."""
+    out = []
+    for i, b in enumerate(inst):
+        out += [i] * len(b.k_gas)
+    return out
+
+
+def batch_oracle_sample(inst, target_s=12.0):
+    """The oracle on the batch's smallest fields (64^2x32 and 128^2x40
+    instances, all bands), paths/s over about target_s seconds."""
+    import oracle
+    import scenes
+    oracle.build()
+    cores = oracle.default_threads()
+    small = [(i, b) for i, b in enumerate(inst) if b.nx <= 128][:4]
+    jobs = []
+    for i, b in small:
+        sp = scenes.cumulus(b.nx, b.nx, b.nz, seed=b.field_seed)
+        for kg in b.k_gas:
+            osc = oracle.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear,
+                               ssa_clear=sp.ssa_clear, ssa_cloud=sp.ssa_cloud, g=sp.g,
+                               ground_albedo=sp.ground_albedo, sun_zenith_deg=b.sun_zenith_deg,
+                               sun_azimuth_deg=b.sun_azimuth_deg, k_gas=kg)
+            jobs.append(osc)
+    n = 2000
+    t0 = time.perf_counter()
+    oracle.trace_flux(jobs[0], n, seed=1, nthreads=cores)
+    dt = time.perf_counter() - t0
+    per = max(1000, int(n * target_s / max(dt, 1e-3) / len(jobs)))
+    t0 = time.perf_counter()
+    for j, osc in enumerate(jobs):
+        oracle.trace_flux(osc, per, seed=j, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": per * len(jobs) / dt, "unit": "paths/s", "cores": cores, "kind": "oracle",
+            "sample": "%d paths on each of %d items (all bands of the first %d instances with 64^2x32 or 128^2x40 "
+                      "fields)" % (per, len(jobs), len(small))}
+
+
+# ---------------------------------------------------------------------------
+# Refinement sweep with a heightfield ground
+# ---------------------------------------------------------------------------
+SWEEP = ((128, 40), (256, 80), (512, 160), (1024, 320), (2048, 640))
+
+
+def run_sweep(args):
+    import torch
+    import scenes
+    import paper_1902_01137_gb300 as m
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = m.Context(local)
+    hf = scenes.heightfield(4096, 0.3, seed=0)
+    npaths = args.sweep_paths
+    points = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for nx, nz in SWEEP:
+        spec = scenes.cumulus(nx, nx, nz, seed=0, device=dev)
+        spec.sun_zenith_deg = 60.0
+        row = {"field": "%dx%dx%d" % (nx, nx, nz), "dx_m": 12800.0 / nx, "voxels": nx * nx * nz, "paths": npaths}
+        for name, storage in (("f32", m.MCRT_STORAGE_F32), ("bf16", m.MCRT_STORAGE_BF16)):
+            sc = m.Scene.from_spec(ctx, spec, storage=storage)
+            try:
+                sc.set_heightfield(hf, spec.ground_albedo)
+                sc.trace_flux(1 << 20, seed=1)
+                r = sc.trace_flux(npaths, seed=7)
+                row[name] = {"ms": r.kernel_ms, "paths_per_s": npaths / (r.kernel_ms / 1e3),
+                             "ns_per_path": r.kernel_ms * 1e6 / npaths, "mean": list(map(float, r.mean)),
+                             "se": list(map(float, r.se))}
+            finally:
+                sc.close()
+        f, b = row["f32"], row["bf16"]
+        row["bf16_minus_f32_in_se"] = [(b["mean"][q] - f["mean"][q]) / math.hypot(b["se"][q], f["se"][q])
+                                       for q in range(3)]
+        if nx <= 256 and not args.no_cpu_baseline:
+            import oracle
+            hspec = scenes.cumulus(nx, nx, nz, seed=0)
+            osc = oracle.Scene(k=hspec.k, dx=hspec.dx, dy=hspec.dy, dz=hspec.dz, levels=hspec.levels,
+                               k_clear=hspec.k_clear, ssa_clear=hspec.ssa_clear, ssa_cloud=hspec.ssa_cloud,
+                               g=hspec.g, ground_albedo=hspec.ground_albedo, sun_zenith_deg=60.0, heights=hf)
+            no = 1 << 20
+            t0 = time.perf_counter()
+            o, _ = oracle.trace_flux(osc, no, seed=7)
+            row["oracle_fp64"] = {"paths": no, "s": time.perf_counter() - t0, "mean": list(map(float, o.mean[:3])),
+                                  "se": list(map(float, o.se[:3])),
+                                  "f32_minus_oracle_in_se": [(f["mean"][q] - o.mean[q]) / math.hypot(f["se"][q], o.se[q])
+                                                             for q in range(3)],
+                                  "note": "host field from numpy FFT (the device field differs by FFT rounding)"}
+        points.append(row)
+        del spec
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    line = {"metric": METRIC, "workload": "refinement sweep, 4096^2 heightfield (0-300 m), sun 60 deg, flux",
+            "unit": "paths/s", "points": points, "clocks": clk, "data": "synthetic"}
+    print(json.dumps(line))
+    ctx.close()
     return 0
 
 
@@ -318,6 +617,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep"])
+    ap.add_argument("--sweep-paths", type=int, default=100_000_000)
+    ap.add_argument("--no-fom", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per trace launch, if captured for this kernel version")
     args = ap.parse_args()
@@ -325,6 +627,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

@@ -612,10 +612,11 @@ def trace_batch(ctx: Context, items, tally=None, **kw):
     try:
         mean, se, n = mcrt_tally_read(ctx.h, t)
         ms = mcrt_tally_kernel_ms(ctx.h, t)
+        cnt = mcrt_tally_counters(ctx.h, t) if o.count_events else {}
     finally:
         if tally is None:
             mcrt_tally_destroy(t)
-    return Result(mean.reshape(-1, 4), se.reshape(-1, 4), n.reshape(-1, 4), ms, {})
+    return Result(mean.reshape(-1, 4), se.reshape(-1, 4), n.reshape(-1, 4), ms, cnt)
 
 
 def mcrt_batch_plan_create(ctx, items, opts: TraceOpts):

@@ -804,7 +804,6 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
 {
     if (n < 1 || n > (1 << 20)) return fail(ctx, MCRT_ERR_ARG, "%s: item count %d not in [1, 2^20]", who, n);
     if (o->proposal) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: learned proposal in batches", who);
-    if (o->count_events) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: counting in batches", who);
     const uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     h.assign((size_t)n, BatchItem{});
     unsigned long long begin = 0;
@@ -885,7 +884,7 @@ int batch_tally(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, mcrt_tal
 int batch_grid(mcrt_ctx* ctx, const mcrt_trace_opts* o, bool bf16, int* block)
 {
     *block = o->block_size ? o->block_size : 128;
-    return o->grid_size ? o->grid_size : ctx->sm_count * trace_batch_blocks_per_sm(bf16, *block);
+    return o->grid_size ? o->grid_size : ctx->sm_count * trace_batch_blocks_per_sm(bf16, o->count_events != 0, *block);
 }
 
 }  // namespace
@@ -920,7 +919,7 @@ int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, con
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-    if (e == cudaSuccess) { ctx->launches++; e = launch_trace_batch(P, bf16, grid, block, ctx->stream); }
+    if (e == cudaSuccess) { ctx->launches++; e = launch_trace_batch(P, bf16, o->count_events != 0, grid, block, ctx->stream); }
     if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
     WorkState ws{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ws, t->d_work, sizeof(ws), cudaMemcpyDeviceToHost, ctx->stream);
@@ -1060,7 +1059,7 @@ int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t 
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_s2, 0, m * sizeof(double), p->st);
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), p->st);
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), p->st);
-        if (c == cudaSuccess) c = launch_trace_batch(P, bf16, grid, block, p->st);
+        if (c == cudaSuccess) c = launch_trace_batch(P, bf16, o->count_events != 0, grid, block, p->st);
         if (c == cudaSuccess) c = launch_finalize(t->d_s1, t->d_s2, 0.0, (int)m, t->d_cell_n, 4, t->d_out, p->st);
         if (c == cudaSuccess)
             c = cudaMemcpyAsync(p->h_out, t->d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, p->st);

@@ -844,8 +844,11 @@ const void* pick(int sensor, bool bf16, bool count, bool terrain)
     return terrain ? pick_t<true>(sensor, bf16, count) : pick_t<false>(sensor, bf16, count);
 }
 
-const void* pick_batch(bool bf16)
+const void* pick_batch(bool bf16, bool count)
 {
+    if (count)
+        return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, true, false, true>)
+                    : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, true, false, true>);
     return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, false, false, true>)
                 : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, false, false, true>);
 }
@@ -892,16 +895,16 @@ int trace_learned_blocks_per_sm(int sensor, bool bf16, int block)
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, int grid, int block, cudaStream_t st)
+cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, int grid, int block, cudaStream_t st)
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
-    return cudaLaunchKernel(pick_batch(bf16), dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(pick_batch(bf16, count), dim3(grid), dim3(block), args, 0, st);
 }
 
-int trace_batch_blocks_per_sm(bool bf16, int block)
+int trace_batch_blocks_per_sm(bool bf16, bool count, int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_batch(bf16), block, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_batch(bf16, count), block, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
