@@ -608,6 +608,25 @@ def run_sweep(args):
     return 0
 
 
+def run_profile_case():
+    """A small case of the bench kernel for ncu: the same 512x512x160 field
+    (160 MiB, larger than L2), a 512 x 512 image at 16 spp (4,194,304
+    paths), two launches."""
+    import torch
+    import paper_1902_01137_gb300 as m
+    spec, _ = make_workload()
+    import scenes
+    cam = scenes.nadir_camera(spec, 512, 512)
+    ctx = m.Context(0)
+    sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    for i in range(2):
+        r = sc.trace_camera(cam, 16, seed=7 + i)
+        print("launch", i, "kernel_ms", r.kernel_ms, "mean", float(r.mean.mean()), flush=True)
+    sc.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -620,6 +639,8 @@ def main():
     ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep"])
     ap.add_argument("--sweep-paths", type=int, default=100_000_000)
     ap.add_argument("--no-fom", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per trace launch, if captured for this kernel version")
     args = ap.parse_args()
@@ -627,6 +648,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case()
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "sweep":

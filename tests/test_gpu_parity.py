@@ -396,6 +396,6 @@ def test_bf16_error_against_fp64_oracle_of_fp32_field(m, ctx, orc, capsys):
             assert d <= bound, (name, q, g.mean[q], o.mean[q], bound)
     with capsys.disabled():
         print("\n[precision] flux T_dir/T_dif/T_tot: fp64 oracle %s | f32 %s | bf16 %s | "
-              "bf16-oracle %s (se %s)" % (np.round(o.mean, 6), np.round(res["f32"].mean, 6),
+              "bf16-oracle %s (se %s)" % (np.round(o.mean[:3], 6), np.round(res["f32"].mean, 6),
                                            np.round(res["bf16"].mean, 6),
-                                           np.round(res["bf16"].mean - o.mean, 6), np.round(o.se, 6)))
+                                           np.round(res["bf16"].mean - o.mean[:3], 6), np.round(o.se[:3], 6)))
