@@ -381,7 +381,8 @@ __device__ __forceinline__ float hf_height(const DevScene& S, float x, float y, 
 // the max pyramid over unwrapped cell indices: a cell whose maximum lies
 // below the ray's lowest point over the cell is skipped whole, otherwise
 // the walk descends into its 4 x 4 children; after a step that leaves the
-// parent block it climbs one level.  In a level-0 cell the ray crosses at
+// parent block it climbs one level.  A ray starting inside the relief layer
+// starts the walk at level 0.  In a level-0 cell the ray crosses at
 // most two triangle pieces (split where u = v); on a piece the ray's height
 // above the plane, f(t), is linear and the hit is where f first reaches 0
 // (the piece start if f <= 0 there).
@@ -399,7 +400,9 @@ static __device__ __forceinline__ float terrain_hit(const DevScene& S, const flo
     if (t1 < t0) return kInf;
     const float inv_dx = d[0] != 0.0f ? __frcp_rn(d[0]) : 0.0f;
     const float inv_dy = d[1] != 0.0f ? __frcp_rn(d[1]) : 0.0f;
-    int L = S.hlev - 1;
+    // a ray starting inside the relief layer is near the surface: begin at
+    // level 0 and climb; one entering from above begins at the top level
+    int L = t0 > 0.0f ? S.hlev - 1 : 0;
     float t = t0;
     int i, j;
     {

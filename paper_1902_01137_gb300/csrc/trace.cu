@@ -68,7 +68,7 @@ constexpr int kSections = 9;
 // ended a flight.  Every lane evaluates exactly one Philox block per
 // iteration at one site, whose counter depends on the phase; the voxel /
 // leaf-entry load and the leaf set-up also run at one site each.
-enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME };
+enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
 template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     uint32_t cur_rec = 0xFFFFFFFFu;         // training record awaiting its own estimate
     bool suspend = false;                   // stop this path until the network has run
     float tg = __int_as_float(0x7f800000);  // heightfield: distance of the flight's ground hit from R.o
+    float tpend = __int_as_float(0x7f800000);   // heightfield: where the flight enters the relief layer (walk pending)
     float fz = 1.0f;                        // heightfield flux: n_z of the surface at the path start
     float vx[3] = {0.0f, 0.0f, 0.0f}, nd[3] = {0.0f, 0.0f, 1.0f};
     unsigned long long cnt[kCounters];
@@ -213,7 +214,11 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         // ---- rare phases (path start, ray start, vertex) run in batches: a
         //      lane waits until enough lanes of its warp need the same kind of
         //      work, or until no lane is stepping -------------------------------
-        const bool rare = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX || phase == PH_RESUME;
+        // (heightfield: a flight whose current leaf reaches down into the relief
+        //  layer first finds its ground hit, a rare phase of its own)
+        if (TERRAIN && phase == PH_STEP && R.texit >= tpend) phase = PH_TERRAIN;
+        const bool rare = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX || phase == PH_RESUME ||
+                          (TERRAIN && phase == PH_TERRAIN);
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
@@ -242,6 +247,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         uint32_t sub = 0;
         int st = kInside;
         bool setup = false;          // enter a leaf after the load
+        bool walk = false;           // heightfield: find this ray's ground hit now
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
             if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; }
@@ -334,19 +340,37 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             tau = -__logf(u01(x.x));
             blk = 1;
             if constexpr (TERRAIN) {
-                // the flight ends at the surface; a sun ray that meets it is shadowed
-                tg = terrain_hit(S, R.o, R.d);
-                if (kind != kMain && tg < __int_as_float(0x7f800000)) {
-                    Ts = 0.0f;
-                    evc = EV_SUN_END;
-                    ptr = nullptr;
-                    setup = false;
+                // a sun ray that meets the surface is shadowed (found now: sun rays
+                // only start inside the relief layer at the ground or below hmax);
+                // a flight ends at the surface, found now when it starts inside the
+                // relief layer, else once its traversal reaches z = hmax
+                tg = __int_as_float(0x7f800000);
+                tpend = __int_as_float(0x7f800000);
+                if (kind == kMain && R.o[2] > S.hmax) {
+                    if (R.d[2] < 0.0f) tpend = __fdiv_rn(S.hmax - R.o[2], R.d[2]);
+                } else {
+                    walk = true;
                 }
-                if (kind != kMain) tg = __int_as_float(0x7f800000);
             }
             if (COUNT) {
                 if (kind == kMain) cnt[C_FLIGHTS]++;
                 else cnt[C_SUN_RAYS]++;
+            }
+        }
+        if (TERRAIN && ph == PH_TERRAIN) {
+            walk = true;
+            tpend = __int_as_float(0x7f800000);
+            phase = PH_STEP;
+        }
+        if (TERRAIN && walk) {
+            const float th = terrain_hit(S, R.o, R.d);
+            if (kind == kMain) {
+                tg = th;
+            } else if (th < __int_as_float(0x7f800000)) {
+                Ts = 0.0f;
+                evc = EV_SUN_END;
+                ptr = nullptr;
+                setup = false;
             }
         }
         mark(3);
@@ -377,7 +401,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 tau -= Mseg;
                 float wdt;
                 st = cross_face(S, R, p, nv, &wdt);
-                if (TERRAIN) tg -= wdt;                  // a periodic wrap restarts the segment
+                if (TERRAIN) { tg -= wdt; tpend -= wdt; }   // a periodic wrap restarts the segment
                 if (st == kInside) {
                     ptr = leaf_entry(S, R.v);
                     setup = true;
