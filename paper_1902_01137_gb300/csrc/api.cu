@@ -89,6 +89,7 @@ DevScene make_dev_scene(const mcrt_scene* sc, float k_gas)
         S.hpyr = sc->d_hpyr;
         for (int a = 0; a < 2; ++a) {
             S.hn[a] = sc->hn[a];
+            S.hmask[a] = (sc->hn[a] & (sc->hn[a] - 1)) == 0 ? sc->hn[a] - 1 : -1;
             S.hc[a] = (float)((double)sc->n[a] * sc->h[a] / sc->hn[a]);
             S.inv_hc[a] = 1.0f / S.hc[a];
         }

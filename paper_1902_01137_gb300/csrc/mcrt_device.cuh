@@ -88,6 +88,7 @@ struct DevScene {
     float hc[2];         // cell size [km]
     float inv_hc[2];
     float hmax;          // largest height
+    int hmask[2];        // hn - 1 when hn is a power of two (index wrap by mask), else -1
     int hlev;
     int hoff[kMaxHfLevels];
 };
@@ -348,17 +349,29 @@ __device__ __forceinline__ int wrap_mod(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ float hf_at(const DevScene& S, int i, int j)
+// Periodic index on axis a at pyramid level L (n = hn >> 2L cells).
+__device__ __forceinline__ int hf_wrap(const DevScene& S, int a, int i, int L)
 {
-    return __ldg(S.hf + (size_t)wrap_mod(j, S.hn[1]) * S.hn[0] + wrap_mod(i, S.hn[0]));
+    return S.hmask[a] >= 0 ? (i & (S.hmask[a] >> (2 * L))) : wrap_mod(i, S.hn[a] >> (2 * L));
 }
 
-__device__ __forceinline__ void hf_plane(const DevScene& S, int i, int j, bool triA, float* a, float* b, float* c)
+// The 4 corner heights of cell (i, j): h[0] = (i, j), h[1] = (i+1, j),
+// h[2] = (i, j+1), h[3] = (i+1, j+1).
+__device__ __forceinline__ void hf_corners(const DevScene& S, int i, int j, float h[4])
 {
-    const float h00 = hf_at(S, i, j), h10 = hf_at(S, i + 1, j), h01 = hf_at(S, i, j + 1), h11 = hf_at(S, i + 1, j + 1);
-    *c = h00;
-    if (triA) { *a = h10 - h00; *b = h11 - h10; }
-    else      { *a = h11 - h01; *b = h01 - h00; }
+    const int i0 = hf_wrap(S, 0, i, 0), i1 = hf_wrap(S, 0, i + 1, 0);
+    const size_t r0 = (size_t)hf_wrap(S, 1, j, 0) * S.hn[0], r1 = (size_t)hf_wrap(S, 1, j + 1, 0) * S.hn[0];
+    h[0] = __ldg(S.hf + r0 + i0);
+    h[1] = __ldg(S.hf + r0 + i1);
+    h[2] = __ldg(S.hf + r1 + i0);
+    h[3] = __ldg(S.hf + r1 + i1);
+}
+
+__device__ __forceinline__ void hf_plane(const float h[4], bool triA, float* a, float* b, float* c)
+{
+    *c = h[0];
+    if (triA) { *a = h[1] - h[0]; *b = h[3] - h[1]; }
+    else      { *a = h[3] - h[2]; *b = h[2] - h[0]; }
 }
 
 // Surface height at (x, y) and the unit upward normal of its triangle.
@@ -367,8 +380,10 @@ __device__ __forceinline__ float hf_height(const DevScene& S, float x, float y, 
     const float fx = x * S.inv_hc[0], fy = y * S.inv_hc[1];
     const int i = __float2int_rd(fx), j = __float2int_rd(fy);
     const float u = fx - (float)i, v = fy - (float)j;
+    float hc4[4];
+    hf_corners(S, i, j, hc4);
     float a, b, c;
-    hf_plane(S, i, j, u >= v, &a, &b, &c);
+    hf_plane(hc4, u >= v, &a, &b, &c);
     const float gx = a * S.inv_hc[0], gy = b * S.inv_hc[1];
     const float inv = rsqrtf(gx * gx + gy * gy + 1.0f);
     n[0] = -gx * inv; n[1] = -gy * inv; n[2] = inv;
@@ -421,8 +436,8 @@ static __device__ __forceinline__ float terrain_hit(const DevScene& S, const flo
         const float ty = d[1] > 0.0f ? ((float)(j + 1) * cy - o[1]) * inv_dy
                        : d[1] < 0.0f ? ((float)j * cy - o[1]) * inv_dy : kInf;
         const float te = fmaxf(fminf(fminf(tx, ty), t1), t);
-        const int nx = S.hn[0] >> sh, ny = S.hn[1] >> sh;
-        const float cmax = __ldg(S.hpyr + S.hoff[L] + (size_t)wrap_mod(j, ny) * nx + wrap_mod(i, nx));
+        const int nx = S.hn[0] >> sh;
+        const float cmax = __ldg(S.hpyr + S.hoff[L] + (size_t)hf_wrap(S, 1, j, L) * nx + hf_wrap(S, 0, i, L));
         const float zlo = __fmaf_rn(d[2] < 0.0f ? te : t, d[2], o[2]);
         if (zlo <= cmax) {
             if (L > 0) {
@@ -446,11 +461,13 @@ static __device__ __forceinline__ float terrain_hit(const DevScene& S, const flo
                 const float tm = __fdiv_rn(-g0, g1);
                 if (tm > t && tm < te) { cut1 = tm; np = 2; }
             }
+            float hc4[4];
+            hf_corners(S, i, j, hc4);
             for (int q = 0; q < np; ++q) {
                 const float a0 = q == 0 ? t : cut1, b0 = q == 0 ? cut1 : te;
                 const bool triA = __fmaf_rn(g1, 0.5f * (a0 + b0), g0) >= 0.0f;
                 float A, B, Cc;
-                hf_plane(S, i, j, triA, &A, &B, &Cc);
+                hf_plane(hc4, triA, &A, &B, &Cc);
                 const float ua = __fmaf_rn(a0, d[0], o[0]) * S.inv_hc[0] - (float)i;
                 const float va = __fmaf_rn(a0, d[1], o[1]) * S.inv_hc[1] - (float)j;
                 const float ub = __fmaf_rn(b0, d[0], o[0]) * S.inv_hc[0] - (float)i;
