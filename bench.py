@@ -269,9 +269,8 @@ def run_gpu(args):
     launches = ctx.launches - launches0
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1902_01137_gb300 import shard
+        total_ms = shard.max_over_ranks(total_ms)
         torch.distributed.barrier()
     clk = clocks.stop()
     paths_per_step = W * H * SPP
@@ -469,9 +468,8 @@ def run_batch(args):
     launches = ctx.launches - l0
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1902_01137_gb300 import shard
+        total_ms = shard.max_over_ranks(total_ms)
     clk = clocks.stop()
     value = world * paths * args.steps / (total_ms / 1e3)
     # e2e: fields from pinned host memory, tallies back to the host

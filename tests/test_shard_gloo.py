@@ -1,0 +1,85 @@
+"""Multi-process path sharding on CPU (world size 2, gloo).
+
+Each rank traces a contiguous path-id range (the CPU oracle stands in for
+a rank's GPU on this machine) and the per-rank FP64 sums are reduced in
+rank order.  The reduced sums equal one process's sums to FP64 rounding,
+are bit-identical on both ranks and from run to run, and independent
+replicas (distinct seeds) combine to an estimate consistent with a single
+run.  The max-over-ranks step time is the largest rank's.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _scene():
+    import oracle
+    import scenes
+    sp = scenes.blobs_small(0)
+    return oracle.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear,
+                        ssa_clear=sp.ssa_clear, ssa_cloud=sp.ssa_cloud, g=sp.g, ground_albedo=sp.ground_albedo,
+                        sun_zenith_deg=sp.sun_zenith_deg)
+
+
+def _worker(rank, world, port, total, out_dir):
+    import torch.distributed as dist
+    import oracle
+    from paper_1902_01137_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        S = _scene()
+        b, e = shard.shard_range(total, rank, world, align=1024)
+        t, _ = oracle.trace_flux(S, e - b, seed=5, begin=b, nthreads=2)
+        r1 = shard.reduce_sums([t.s1, t.s2, t.n[:1]])
+        r2 = shard.reduce_sums([t.s1, t.s2, t.n[:1]])
+        # independent replicas: own seed, own paths
+        rt, _ = oracle.trace_flux(S, 4096, seed=shard.replica_seed(77, rank), nthreads=2)
+        rep = shard.reduce_sums([rt.s1, rt.s2, rt.n[:1]])
+        mx = shard.max_over_ranks(10.0 + rank)
+        np.savez(os.path.join(out_dir, "r%d.npz" % rank), s1=r1[0], s2=r1[1], n=r1[2], s1b=r2[0], s2b=r2[1],
+                 rs1=rep[0], rs2=rep[1], rn=rep[2], mx=mx, b=b, e=e)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_ranges_cover_and_align():
+    from paper_1902_01137_gb300 import shard
+    for total in (0, 1, 1023, 1024, 5000, 10 ** 6 + 7):
+        for world in (1, 2, 3, 8):
+            rs = [shard.shard_range(total, r, world, align=64) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == total
+            for (b0, e0), (b1, e1) in zip(rs, rs[1:]):
+                assert e0 == b1 and b0 <= e0 and e0 % 64 == 0
+    assert len({shard.replica_seed(1, r) for r in range(64)}) == 64
+    with pytest.raises(ValueError):
+        shard.shard_range(10, 2, 2)
+
+
+def test_two_ranks_gloo_match_one_process(tmp_path):
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_1902_01137_gb300 import shard
+    total = 6000
+    port = 29500 + (os.getpid() % 1000)
+    mp.start_processes(_worker, args=(2, port, total, str(tmp_path)), nprocs=2, start_method="spawn")
+    a = np.load(tmp_path / "r0.npz")
+    b = np.load(tmp_path / "r1.npz")
+    for k in ("s1", "s2", "n", "rs1", "rs2", "rn", "mx"):
+        assert np.array_equal(a[k], b[k]), k                   # identical result on both ranks
+    assert np.array_equal(a["s1"], a["s1b"]) and np.array_equal(a["s2"], a["s2b"])   # deterministic
+    one, _ = oracle.trace_flux(_scene(), total, seed=5, nthreads=2)
+    np.testing.assert_allclose(a["s1"], one.s1, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a["s2"], one.s2, rtol=1e-12, atol=1e-12)
+    assert float(a["n"][0]) == total
+    assert float(a["mx"]) == 11.0                               # max over ranks
+    assert (int(a["b"]), int(a["e"]), int(b["b"]), int(b["e"])) == (0, 3072, 3072, total)
+    # replicas combine to a consistent estimate
+    m, se = shard.mean_se(a["rs1"], a["rs2"], a["rn"][0])
+    for q in range(3):
+        assert abs(m[q] - one.mean[q]) <= 4 * math.hypot(se[q], one.se[q])
