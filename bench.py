@@ -12,7 +12,7 @@ per pixel (67,108,864 paths), mean/SE finalize.
              copy of the field and device->host read of the image (mean, SE)
              inside the timed region
   roofline   trace kernel: algorithmic bytes (4 B per voxel read at a
-             tentative collision + 8 B per leaf entered, counted by a separate
+             tentative collision + 4 B of majorant per leaf entered, counted by a separate
              counting run with the same seed) / kernel time, over measured HBM
   cpu_baseline  the CPU oracle on a bounded pixel sample of the same image
 
@@ -299,7 +299,7 @@ def run_gpu(args):
     pk = peaks()
     leaf_entries = cnt["leaf_steps"] + cnt["sun_leaf_steps"] + cnt["sun_rays"] + cnt.get("flights", 0)
     vox_reads = cnt["tentative"] + cnt["sun_tentative"]
-    alg_bytes = 4 * vox_reads + 8 * leaf_entries
+    alg_bytes = 4 * vox_reads + 4 * leaf_entries
     kavg = statistics.mean(kern_ms)
     achieved = alg_bytes / (kavg / 1e3) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
@@ -488,7 +488,7 @@ def run_batch(args):
     pk = peaks()
     leaf_entries = cnt["leaf_steps"] + cnt["sun_leaf_steps"] + cnt["sun_rays"] + cnt.get("flights", 0)
     vox_reads = cnt["tentative"] + cnt["sun_tentative"]
-    alg = 4 * vox_reads + 8 * leaf_entries
+    alg = 4 * vox_reads + 4 * leaf_entries
     kavg = statistics.mean(kern_ms)
     ach = alg / (kavg / 1e3) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
