@@ -64,7 +64,12 @@ typedef enum {
 
 enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };
 enum { MCRT_STORAGE_F32 = 0, MCRT_STORAGE_BF16 = 1 };
-enum { MCRT_SUN_RATIO = 0, MCRT_SUN_DELTA = 1 };
+/* Sun transmissivity estimators: ratio tracking (Sec. 2.3's null-collision
+ * algorithm scoring 1 - k/M per tentative collision), delta tracking (its
+ * 0/1 form), decomposition tracking (each leaf's minorant m is a control
+ * whose exp(-m s) is applied exactly; ratio tracking on k - m with majorant
+ * M - m; a voxel leaf is crossed without random draws). */
+enum { MCRT_SUN_RATIO = 0, MCRT_SUN_DELTA = 1, MCRT_SUN_DECOMP = 2 };
 
 /* Library version and the ABI version it was built with. */
 MCRT_API int mcrt_version(int32_t* abi_version);
@@ -144,6 +149,13 @@ MCRT_API int mcrt_scene_majorant_dims(const mcrt_scene* scene, int32_t level, in
  * MCRT_ERR_STATE before mcrt_scene_build_majorants. */
 MCRT_API int mcrt_scene_read_majorants(const mcrt_scene* scene, int32_t level, float* host_out, size_t n);
 
+/* The minorant pyramid built with the majorants (exact min over each
+ * cell's existing children; for BF16 storage, the min of the stored
+ * values), read like mcrt_scene_read_majorants.  It is the control of
+ * decomposition tracking (MCRT_SUN_DECOMP); the paper's octree keeps the
+ * min beside the max (Sec. 3.1.1). */
+MCRT_API int mcrt_scene_read_minorants(const mcrt_scene* scene, int32_t level, float* host_out, size_t n);
+
 /* Flat Lambertian ground of albedo in [0, 1] (Sec. 4.1). */
 MCRT_API int mcrt_scene_set_ground_flat(mcrt_scene* scene, float albedo);
 
@@ -200,7 +212,7 @@ typedef struct {
                                /* 1 cells are always merged)                    */
     int32_t max_order;         /* 0: all scattering orders; n: score events of  */
                                /* order <= n and stop after order n             */
-    int32_t sun_mode;          /* MCRT_SUN_RATIO (default) or MCRT_SUN_DELTA    */
+    int32_t sun_mode;          /* MCRT_SUN_RATIO (default), _DELTA or _DECOMP   */
     int32_t chunk;             /* paths a GPU thread claims at once; 0 = auto   */
     int32_t block_size;        /* threads per block; 0 = auto                   */
     int32_t grid_size;         /* blocks; 0 = SMs x resident blocks             */

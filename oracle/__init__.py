@@ -70,6 +70,7 @@ class OrcScene(C.Structure):
         ("hf", C.POINTER(C.c_float)),
         ("hnx", C.c_int32), ("hny", C.c_int32),
         ("hmax", C.c_double),
+        ("pyr_min", C.POINTER(C.c_float)),
     ]
 
 
@@ -104,6 +105,9 @@ def lib():
             L.orc_pyramid_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
             L.orc_pyramid_size.restype = C.c_int64
             L.orc_build_pyramid.argtypes = [f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f32p]
+            L.orc_build_pyramid_min.argtypes = [f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f32p]
+            L.orc_bf16_round_down.argtypes = [C.c_float]
+            L.orc_bf16_round_down.restype = C.c_float
             L.orc_dda_spec.argtypes = [sp, f32p, f32p, C.c_int, i32p, f32p, i32p]
             L.orc_dda_bruteforce.argtypes = [sp, f64p, f64p, C.c_double, C.c_int, i32p, f64p, i32p]
             L.orc_hg_pdf.argtypes = [C.c_double, C.c_double]
@@ -186,6 +190,30 @@ def build_pyramid(k_zyx: np.ndarray, levels: int, round_up_bf16: bool = False):
     return res
 
 
+def build_pyramid_min(k_zyx: np.ndarray, levels: int, round_nearest_bf16: bool = False):
+    """Minorant pyramid (exact FP32 min per cell over its existing children;
+    with round_nearest_bf16, the min of the BF16-rounded voxels)."""
+    k = np.ascontiguousarray(k_zyx, dtype=np.float32)
+    nz, ny, nx = k.shape
+    tot = lib().orc_pyramid_size(nx, ny, nz, levels)
+    out = np.zeros(tot, dtype=np.float32)
+    rc = lib().orc_build_pyramid_min(_ptr(k, C.c_float), nx, ny, nz, levels, int(round_nearest_bf16),
+                                     _ptr(out, C.c_float))
+    if rc != 0:
+        raise ValueError("bad pyramid request")
+    res, off = [], 0
+    for l in range(1, levels + 1):
+        dx, dy, dz = level_dims((nx, ny, nz), l)
+        n = dx * dy * dz
+        res.append(out[off:off + n].reshape(dz, dy, dx))
+        off += n
+    return res
+
+
+def bf16_round_down(x: float) -> float:
+    return lib().orc_bf16_round_down(float(x))
+
+
 def bf16_round_nearest(x: float) -> float:
     return lib().orc_bf16_round_nearest(float(x))
 
@@ -238,13 +266,17 @@ class Scene:
         pyr = build_pyramid(k, self.levels, round_up_bf16=False) if not self.bf16 else \
             build_pyramid(np.ascontiguousarray(self.k, dtype=np.float32), self.levels, round_up_bf16=True)
         flat = np.ascontiguousarray(np.concatenate([p.ravel() for p in pyr]).astype(np.float32))
-        self._keep = [k, flat]
+        pmin = build_pyramid_min(np.ascontiguousarray(self.k, dtype=np.float32), self.levels,
+                                 round_nearest_bf16=bool(self.bf16))
+        flat_min = np.ascontiguousarray(np.concatenate([p.ravel() for p in pmin]).astype(np.float32))
+        self._keep = [k, flat, flat_min]
         s = OrcScene()
         s.nx, s.ny, s.nz = nx, ny, nz
         s.dx, s.dy, s.dz = self.dx, self.dy, self.dz
         s.k = _ptr(k, C.c_float)
         s.levels = self.levels
         s.pyr = _ptr(flat, C.c_float)
+        s.pyr_min = _ptr(flat_min, C.c_float)
         s.tau_merge = self.tau_merge
         s.finest_level = self.finest_level
         s.k_clear = self.k_clear

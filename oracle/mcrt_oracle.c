@@ -138,6 +138,13 @@ float orc_bf16_round_up(float x)
     return u2f(u);
 }
 
+/* Largest bfloat16 value <= x, for x >= 0 (minorants must stay bounds). */
+float orc_bf16_round_down(float x)
+{
+    if (isnan(x) || isinf(x) || x <= 0.0f) return x <= 0.0f ? 0.0f : x;
+    return u2f(f2u(x) & 0xFFFF0000u);
+}
+
 /* ===================================================================== */
 /* Majorant pyramid (Sec. 3.1.1, "Construction"; Sec. 2.4: the majorant   */
 /* is piecewise uniform over the cells of a coarser grid).  Level 0 is   */
@@ -193,6 +200,38 @@ int orc_build_pyramid(const float* k, int nx, int ny, int nz, int levels, int ro
     return 0;
 }
 
+/* Minorant pyramid (the paper's octree keeps the min beside the max,
+ * Sec. 3.1.1): a level-L cell stores the exact min over its existing
+ * children.  round_nearest_bf16 != 0 takes the min over RN_bf16 of the
+ * voxels (the values a BF16-stored field holds). */
+int orc_build_pyramid_min(const float* k, int nx, int ny, int nz, int levels, int round_nearest_bf16, float* out)
+{
+    if (levels < 1) return -1;
+    const float* prev = k;
+    int pd[3] = {nx, ny, nz};
+    float* cur = out;
+    for (int l = 1; l <= levels; ++l) {
+        int d[3]; orc_level_dims(nx, ny, nz, l, d);
+        for (int cz = 0; cz < d[2]; ++cz)
+            for (int cy = 0; cy < d[1]; ++cy)
+                for (int cx = 0; cx < d[0]; ++cx) {
+                    float m = INFINITY;
+                    for (int z = 8 * cz; z < 8 * cz + 8 && z < pd[2]; ++z)
+                        for (int y = 8 * cy; y < 8 * cy + 8 && y < pd[1]; ++y)
+                            for (int x = 8 * cx; x < 8 * cx + 8 && x < pd[0]; ++x) {
+                                float v = prev[((int64_t)z * pd[1] + y) * pd[0] + x];
+                                if (l == 1 && round_nearest_bf16) v = orc_bf16_round_nearest(v);
+                                if (v < m) m = v;
+                            }
+                    cur[((int64_t)cz * d[1] + cy) * d[0] + cx] = m;
+                }
+        prev = cur;
+        pd[0] = d[0]; pd[1] = d[1]; pd[2] = d[2];
+        cur += (int64_t)d[0] * d[1] * d[2];
+    }
+    return 0;
+}
+
 /* ===================================================================== */
 /* Scene description shared by the traversal and the estimators.          */
 /* ===================================================================== */
@@ -219,6 +258,7 @@ typedef struct {
     const float* hf;           /* heightfield ground [km] (x fastest), or NULL: flat z = 0 */
     int32_t hnx, hny;          /* heightfield samples per axis (periodic)  */
     double hmax;               /* largest height                          */
+    const float* pyr_min;      /* minorant levels 1..levels (layout of pyr), or NULL: 0 */
 } orc_scene;
 
 static const float* level_ptr(const orc_scene* S, int level, int dims[3])
@@ -241,25 +281,41 @@ static float kvox(const orc_scene* S, const int v[3])
  * whose bound on the vertical optical depth, M * h_z (FP32 product), is
  * <= tau~; otherwise the cell of level finest_level.  (Sec. 4.2: cells are
  * merged while the merged vertical optical depth stays below tau~; the
- * merged cell stores the max, Sec. 3.1.1.) */
-static void leaf_of(const orc_scene* S, const int v[3], int* lev_out, float* M_out)
+ * merged cell stores the max, Sec. 3.1.1.)  *m_out (may be NULL) receives
+ * the leaf's minorant: the voxel itself for a voxel leaf, else the cell's
+ * min rounded down to bfloat16 (the leaf map holds it in 16 bits). */
+static void leaf_of_m(const orc_scene* S, const int v[3], int* lev_out, float* M_out, float* m_out)
 {
     for (int L = S->levels; L > S->finest_level; --L) {
         int d[3];
         const float* P = level_ptr(S, L, d);
-        int c[3] = {v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L)};
-        float M = P[((int64_t)c[2] * d[1] + c[1]) * d[0] + c[0]];
+        int64_t ci = ((int64_t)(v[2] >> (3 * L)) * d[1] + (v[1] >> (3 * L))) * d[0] + (v[0] >> (3 * L));
+        float M = P[ci];
         float hz = S->dz * (float)(1 << (3 * L));
         float tz = M * hz;
-        if (tz <= S->tau_merge) { *lev_out = L; *M_out = M; return; }
+        if (tz <= S->tau_merge) {
+            *lev_out = L; *M_out = M;
+            if (m_out) *m_out = S->pyr_min ? orc_bf16_round_down(S->pyr_min[P - S->pyr + ci]) : 0.0f;
+            return;
+        }
     }
     int L = S->finest_level;
-    if (L == 0) { *lev_out = 0; *M_out = kvox(S, v); return; }
+    if (L == 0) {
+        *lev_out = 0; *M_out = kvox(S, v);
+        if (m_out) *m_out = *M_out;
+        return;
+    }
     int d[3];
     const float* P = level_ptr(S, L, d);
-    int c[3] = {v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L)};
+    int64_t ci = ((int64_t)(v[2] >> (3 * L)) * d[1] + (v[1] >> (3 * L))) * d[0] + (v[0] >> (3 * L));
     *lev_out = L;
-    *M_out = P[((int64_t)c[2] * d[1] + c[1]) * d[0] + c[0]];
+    *M_out = P[ci];
+    if (m_out) *m_out = S->pyr_min ? orc_bf16_round_down(S->pyr_min[P - S->pyr + ci]) : 0.0f;
+}
+
+static void leaf_of(const orc_scene* S, const int v[3], int* lev_out, float* M_out)
+{
+    leaf_of_m(S, v, lev_out, M_out, NULL);
 }
 
 /* Voxel range [lo, hi] covered by the level-L cell containing voxel v. */
@@ -480,6 +536,7 @@ typedef struct {
     int v[3];        /* voxel of p for the current leaf */
     int lev;         /* leaf level */
     double M;        /* leaf majorant (+ k_gas) */
+    double m;        /* leaf minorant (+ k_gas) */
     int lo[3], hi[3];
     double seg;      /* distance from p to the leaf exit */
     int exit_axis;
@@ -500,9 +557,10 @@ static int locate64(const orc_scene* S, double p, double d, int a)
 static void trav_setup_leaf(const orc_scene* S, trav64* T)
 {
     const double h[3] = {S->dx, S->dy, S->dz};
-    float Mf;
-    leaf_of(S, T->v, &T->lev, &Mf);
+    float Mf, mf;
+    leaf_of_m(S, T->v, &T->lev, &Mf, &mf);
     T->M = (double)Mf + S->k_gas;
+    T->m = (double)mf + S->k_gas;
     cell_range(S, T->lev, T->v, T->lo, T->hi);
     double best = INFINITY;
     int ax = 0;
@@ -855,7 +913,14 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
 /* Transmissivity from p toward direction s up to the top of atmosphere.
  * sun_mode 0: ratio tracking, t *= 1 - k/M at each tentative collision,
  * with Russian roulette below 0.1 (survive with prob t/0.1, t <- 0.1).
- * sun_mode 1: the 0/1 estimator of Sec. 2.3 (delta tracking). */
+ * sun_mode 1: the 0/1 estimator of Sec. 2.3 (delta tracking).
+ * sun_mode 2: decomposition (residual ratio) tracking: each leaf's
+ * minorant m is a control extinction whose transmissivity exp(-m s) is
+ * applied exactly over every distance s travelled, and ratio tracking runs
+ * on the residual k - m with majorant M - m (t *= 1 - (k - m)/(M - m)).
+ * A voxel leaf has m = M = k: it is crossed with no random draw at all.
+ * Roulette below 0.1 as in ratio tracking; at a leaf crossing it draws
+ * word 3 of the next block (the block is then used up). */
 static double transmissivity(const orc_scene* S, const double p[3], const double s[3], const rng_t* r,
                              orc_counts* C)
 {
@@ -869,9 +934,12 @@ static double transmissivity(const orc_scene* S, const double p[3], const double
     double u[4];
     rng_block(r, 0, u);
     double tau = -log(u[0]);
+    const int decomp = S->sun_mode == 2;
     for (uint32_t j = 1;;) {
-        if (T.M > 0.0 && tau < T.M * T.seg) {
-            trav_move_inside(S, &T, tau / T.M);
+        double Mt = decomp ? T.M - T.m : T.M;      /* tracking majorant */
+        if (Mt > 0.0 && tau < Mt * T.seg) {
+            double ds = tau / Mt;
+            trav_move_inside(S, &T, ds);
             int vox[3];
             double k = trav_k_here(S, &T, vox);
             if (C) C->tentative++;
@@ -879,7 +947,8 @@ static double transmissivity(const orc_scene* S, const double p[3], const double
             if (S->sun_mode == 1) {
                 if (u[0] * T.M <= k) return 0.0;
             } else {
-                t *= 1.0 - k / T.M;
+                if (decomp) t *= exp(-T.m * ds) * (1.0 - (k - T.m) / Mt);
+                else t *= 1.0 - k / T.M;
                 if (t <= 0.0) return 0.0;
                 if (t < 0.1) {
                     if (u[0] * 0.1 <= t) t = 0.1;
@@ -888,11 +957,17 @@ static double transmissivity(const orc_scene* S, const double p[3], const double
             }
             tau = -log(u[1]);
         } else {
-            tau -= T.M * T.seg;
+            tau -= Mt * T.seg;
+            if (decomp) t *= exp(-T.m * T.seg);
             int st = trav_next_leaf(S, &T);
             if (C) C->leaves++;
             if (st == 1) return t;
             if (st == 2 || st == 4) return 0.0;
+            if (decomp && t < 0.1) {
+                rng_block(r, j++, u);
+                if (u[3] * 0.1 <= t) t = 0.1;
+                else return 0.0;
+            }
         }
     }
 }

@@ -35,6 +35,7 @@ MCRT_STORAGE_F32 = 0
 MCRT_STORAGE_BF16 = 1
 MCRT_SUN_RATIO = 0
 MCRT_SUN_DELTA = 1
+MCRT_SUN_DECOMP = 2
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -103,6 +104,7 @@ def _load():
         "mcrt_scene_levels": [vp, P(i32)],
         "mcrt_scene_majorant_dims": [vp, i32, P(i32)],
         "mcrt_scene_read_majorants": [vp, i32, P(f32), C.c_size_t],
+        "mcrt_scene_read_minorants": [vp, i32, P(f32), C.c_size_t],
         "mcrt_scene_set_ground_flat": [vp, f32],
         "mcrt_scene_set_ground_heightfield": [vp, vp, i32, i32, i32, f32],
         "mcrt_debug_terrain": [vp, i32, P(f32), P(f32), P(f32)],
@@ -227,6 +229,13 @@ def mcrt_scene_read_majorants(ctx, scene, level: int) -> np.ndarray:
     dx, dy, dz = mcrt_scene_majorant_dims(ctx, scene, level)
     out = np.zeros(dx * dy * dz, dtype=np.float32)
     _check(_load().mcrt_scene_read_majorants(scene, level, _ptr(out, C.c_float), out.size), ctx)
+    return out.reshape(dz, dy, dx)
+
+
+def mcrt_scene_read_minorants(ctx, scene, level: int) -> np.ndarray:
+    dx, dy, dz = mcrt_scene_majorant_dims(ctx, scene, level)
+    out = np.zeros(dx * dy * dz, dtype=np.float32)
+    _check(_load().mcrt_scene_read_minorants(scene, level, _ptr(out, C.c_float), out.size), ctx)
     return out.reshape(dz, dy, dx)
 
 
@@ -438,6 +447,9 @@ class Scene:
 
     def majorants(self, level):
         return mcrt_scene_read_majorants(self.ctx.h, self.h, level)
+
+    def minorants(self, level):
+        return mcrt_scene_read_minorants(self.ctx.h, self.h, level)
 
     def set_heightfield(self, heights, albedo):
         mcrt_scene_set_ground_heightfield(self.ctx.h, self.h, heights, albedo)

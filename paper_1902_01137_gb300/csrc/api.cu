@@ -218,7 +218,7 @@ int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* d, mcrt_scene** out)
     }
     sc->pyr_capacity = tot;
     cudaError_t e = dalloc(ctx, &sc->d_vox, sc->vox_bytes);
-    if (e == cudaSuccess) e = dalloc(ctx, &sc->d_pyr, tot * sizeof(float));
+    if (e == cudaSuccess) e = dalloc(ctx, &sc->d_pyr, 2 * tot * sizeof(float));   // max levels, then min levels
     if (e == cudaSuccess) e = dalloc(ctx, &sc->d_leaf, nbricks * sizeof(uint2));
     const float* src = d->ext;
     float* staging = nullptr;
@@ -277,7 +277,10 @@ int mcrt_scene_build_majorants(mcrt_scene* sc, int32_t levels)
     CK(ctx, cudaSetDevice(ctx->device));
     for (int L = 2; L <= levels; ++L) {
         LAUNCH(ctx, launch_reduce_level(sc->d_pyr + sc->lev_off[L - 1], &sc->lev_dims[3 * (L - 1)],
-                                        sc->d_pyr + sc->lev_off[L], &sc->lev_dims[3 * L], ctx->stream));
+                                        sc->d_pyr + sc->lev_off[L], &sc->lev_dims[3 * L], false, ctx->stream));
+        float* mn = sc->d_pyr + sc->pyr_capacity;
+        LAUNCH(ctx, launch_reduce_level(mn + sc->lev_off[L - 1], &sc->lev_dims[3 * (L - 1)], mn + sc->lev_off[L],
+                                        &sc->lev_dims[3 * L], true, ctx->stream));
     }
     sc->levels = levels;
     sc->leaf_valid = false;
@@ -310,6 +313,21 @@ int mcrt_scene_read_majorants(const mcrt_scene* sc, int32_t level, float* host_o
     if (n < cells) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_scene_read_majorants: need %zu values", cells);
     CK(ctx, cudaMemcpyAsync(host_out, sc->d_pyr + sc->lev_off[level], cells * sizeof(float), cudaMemcpyDeviceToHost,
                             ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MCRT_OK;
+}
+
+int mcrt_scene_read_minorants(const mcrt_scene* sc, int32_t level, float* host_out, size_t n)
+{
+    if (!sc || !host_out) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_read_minorants: NULL argument");
+    mcrt_ctx* ctx = sc->ctx;
+    if (sc->levels == 0) return fail(ctx, MCRT_ERR_STATE, "mcrt_scene_read_minorants: majorants not built");
+    if (level < 1 || level > sc->levels)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_read_minorants: level %d not in [1, %d]", level, sc->levels);
+    const size_t cells = (size_t)sc->lev_dims[3 * level] * sc->lev_dims[3 * level + 1] * sc->lev_dims[3 * level + 2];
+    if (n < cells) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_scene_read_minorants: need %zu values", cells);
+    CK(ctx, cudaMemcpyAsync(host_out, sc->d_pyr + sc->pyr_capacity + sc->lev_off[level], cells * sizeof(float),
+                            cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MCRT_OK;
 }
@@ -427,7 +445,7 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
     if (o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels)
         return fail(ctx, MCRT_ERR_ARG, "%s: finest_level must be 0 or 1", who);
     if (o->max_order < 0) return fail(ctx, MCRT_ERR_ARG, "%s: max_order must be >= 0", who);
-    if (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA)
+    if (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA && o->sun_mode != MCRT_SUN_DECOMP)
         return fail(ctx, MCRT_ERR_ARG, "%s: bad sun_mode", who);
     if (o->block_size < 0 || o->block_size > 1024 || (o->block_size % 32) != 0)
         return fail(ctx, MCRT_ERR_ARG, "%s: block_size must be a multiple of 32 up to 1024", who);

@@ -9,7 +9,9 @@
 // 8x8x8 children (Sec. 3.1.1: merged voxels store the max).  Max is exact and
 // order-free, so the result is bit-identical to any other evaluation order.
 // Leaf map: for each level-1 cell, the coarsest ancestor whose majorant times
-// its height is <= tau~ (Sec. 4.2's merge criterion), with its majorant.
+// its height is <= tau~ (Sec. 4.2's merge criterion), with its majorant and
+// its minorant (the min pyramid, built alongside the max: the paper's octree
+// keeps both, Sec. 3.1.1).
 #include <cuda_bf16.h>
 
 #include "mcrt_internal.h"
@@ -23,7 +25,7 @@ namespace {
 template <bool BF16>
 __global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restrict__ src, int nx, int ny, int nz,
                                                           int nbx, int nby, void* __restrict__ dst,
-                                                          float* __restrict__ l1)
+                                                          float* __restrict__ l1, float* __restrict__ l1min)
 {
     const int t = threadIdx.x;
     const int q = t & 3;
@@ -48,6 +50,7 @@ __global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restric
         for (int i = 0; i < 8; ++i) v[i] = (row_ok && x0 + i < nx) ? src[row + x0 + i] : 0.0f;
     }
     float m = 0.0f;
+    float mn = __int_as_float(0x7f800000);   // min over the existing voxels (as stored)
     if (BF16) {
         // stored voxels: nearest bf16; majorant: smallest bf16 >= the FP32 max,
         // which bounds every nearest-rounded voxel of the brick
@@ -58,6 +61,8 @@ __global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restric
             const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[i + 1]));
             packed[i / 2] = lo | (hi << 16);
             m = fmaxf(m, fmaxf(v[i], v[i + 1]));
+            if (row_ok && x0 + i < nx) mn = fminf(mn, __uint_as_float(lo << 16));
+            if (row_ok && x0 + i + 1 < nx) mn = fminf(mn, __uint_as_float(hi << 16));
         }
         m = __bfloat162float(__float2bfloat16_ru(m));
         if (bx < nbx) {
@@ -67,7 +72,10 @@ __global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restric
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) m = fmaxf(m, v[i]);
+        for (int i = 0; i < 8; ++i) {
+            m = fmaxf(m, v[i]);
+            if (row_ok && x0 + i < nx) mn = fminf(mn, v[i]);
+        }
         if (bx < nbx) {
             const size_t brick = ((size_t)bz * nby + by) * (size_t)nbx + bx;
             float4* o = reinterpret_cast<float4*>(static_cast<float*>(dst) + brick * 512 + r * 8);
@@ -79,19 +87,27 @@ __global__ void __launch_bounds__(256) relayout_l1_kernel(const float* __restric
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-    __shared__ float part[8][4];
-    if ((t & 31) < 4) part[t >> 5][q] = m;
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 4));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 16));
+    __shared__ float part[8][4], partmin[8][4];
+    if ((t & 31) < 4) { part[t >> 5][q] = m; partmin[t >> 5][q] = mn; }
     __syncthreads();
     if (t < 4) {
-        float mm = part[0][t];
+        float mm = part[0][t], mmn = partmin[0][t];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) mm = fmaxf(mm, part[w][t]);
+        for (int w = 1; w < 8; ++w) { mm = fmaxf(mm, part[w][t]); mmn = fminf(mmn, partmin[w][t]); }
         const int bxx = blockIdx.x * 4 + t;
-        if (bxx < nbx) l1[((size_t)bz * nby + by) * (size_t)nbx + bxx] = mm;
+        if (bxx < nbx) {
+            l1[((size_t)bz * nby + by) * (size_t)nbx + bxx] = mm;
+            l1min[((size_t)bz * nby + by) * (size_t)nbx + bxx] = mmn;
+        }
     }
 }
 
 // One warp per coarse cell; lane l takes children l, l + 32, ... of 512.
+// MIN: the minorant level (min over the existing children) instead.
+template <bool MIN>
 __global__ void __launch_bounds__(256) reduce_level_kernel(const float* __restrict__ prev, int px, int py, int pz,
                                                            float* __restrict__ out, int cx, int cy, int cz)
 {
@@ -101,19 +117,26 @@ __global__ void __launch_bounds__(256) reduce_level_kernel(const float* __restri
     const int ix = (int)(cell % cx);
     const int iy = (int)((cell / cx) % cy);
     const int iz = (int)(cell / ((long long)cx * cy));
-    float m = 0.0f;
+    float m = MIN ? __int_as_float(0x7f800000) : 0.0f;
 #pragma unroll 4
     for (int c = lane; c < 512; c += 32) {
         const int x = ix * 8 + (c & 7), y = iy * 8 + ((c >> 3) & 7), z = iz * 8 + (c >> 6);
-        if (x < px && y < py && z < pz) m = fmaxf(m, prev[((size_t)z * py + y) * (size_t)px + x]);
+        if (x < px && y < py && z < pz) {
+            const float v = prev[((size_t)z * py + y) * (size_t)px + x];
+            m = MIN ? fminf(m, v) : fmaxf(m, v);
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, m, o);
+        m = MIN ? fminf(m, w) : fmaxf(m, w);
+    }
     if (lane == 0) out[cell] = m;
 }
 
 struct LevelTable {
     const float* p[9];
+    const float* pmin[9];
     int dims[9][3];
     float hz[9];
 };
@@ -128,9 +151,11 @@ __global__ void __launch_bounds__(256) leafmap_kernel(LevelTable T, int levels, 
     for (int L = levels; L > finest; --L) {
         const int s = 3 * (L - 1);
         const int ax = cx >> s, ay = cy >> s, az = cz >> s;
-        const float M = T.p[L][((size_t)az * T.dims[L][1] + ay) * T.dims[L][0] + ax];
+        const size_t c = ((size_t)az * T.dims[L][1] + ay) * T.dims[L][0] + ax;
+        const float M = T.p[L][c];
         if (__fmul_rn(M, T.hz[L]) <= tau) {
-            leaf[i] = make_uint2(__float_as_uint(M), (unsigned)L);
+            // .y: the minorant rounded down to bfloat16 (high half) | the level
+            leaf[i] = make_uint2(__float_as_uint(M), (__float_as_uint(T.pmin[L][c]) & 0xFFFF0000u) | (unsigned)L);
             return;
         }
     }
@@ -138,8 +163,9 @@ __global__ void __launch_bounds__(256) leafmap_kernel(LevelTable T, int levels, 
         leaf[i] = make_uint2(0u, 0u);
     } else {
         const int s = 3 * (finest - 1);
-        const float M = T.p[finest][((size_t)(cz >> s) * T.dims[finest][1] + (cy >> s)) * T.dims[finest][0] + (cx >> s)];
-        leaf[i] = make_uint2(__float_as_uint(M), (unsigned)finest);
+        const size_t c = ((size_t)(cz >> s) * T.dims[finest][1] + (cy >> s)) * T.dims[finest][0] + (cx >> s);
+        const float M = T.p[finest][c];
+        leaf[i] = make_uint2(__float_as_uint(M), (__float_as_uint(T.pmin[finest][c]) & 0xFFFF0000u) | (unsigned)finest);
     }
 }
 
@@ -149,21 +175,28 @@ cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t
 {
     dim3 grid((sc->nb[0] + 3) / 4, sc->nb[1], sc->nb[2]);
     float* l1 = sc->d_pyr + sc->lev_off[1];
+    float* l1min = sc->d_pyr + sc->pyr_capacity + sc->lev_off[1];
     if (sc->storage == MCRT_STORAGE_BF16)
         relayout_l1_kernel<true><<<grid, 256, 0, st>>>(src, sc->n[0], sc->n[1], sc->n[2], sc->nb[0], sc->nb[1],
-                                                       sc->d_vox, l1);
+                                                       sc->d_vox, l1, l1min);
     else
         relayout_l1_kernel<false><<<grid, 256, 0, st>>>(src, sc->n[0], sc->n[1], sc->n[2], sc->nb[0], sc->nb[1],
-                                                        sc->d_vox, l1);
+                                                        sc->d_vox, l1, l1min);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_level(const float* prev, const int* pd, float* out, const int* d, cudaStream_t st)
+cudaError_t launch_reduce_level(const float* prev, const int* pd, float* out, const int* d, bool min_level,
+                                cudaStream_t st)
 {
     const long long cells = (long long)d[0] * d[1] * d[2];
     const int warps = 8;
     const long long blocks = (cells + warps - 1) / warps;
-    reduce_level_kernel<<<(unsigned)blocks, 32 * warps, 0, st>>>(prev, pd[0], pd[1], pd[2], out, d[0], d[1], d[2]);
+    if (min_level)
+        reduce_level_kernel<true><<<(unsigned)blocks, 32 * warps, 0, st>>>(prev, pd[0], pd[1], pd[2], out, d[0], d[1],
+                                                                            d[2]);
+    else
+        reduce_level_kernel<false><<<(unsigned)blocks, 32 * warps, 0, st>>>(prev, pd[0], pd[1], pd[2], out, d[0], d[1],
+                                                                             d[2]);
     return cudaGetLastError();
 }
 
@@ -172,6 +205,7 @@ cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStre
     LevelTable T{};
     for (int L = 1; L <= sc->levels && L < 9; ++L) {
         T.p[L] = sc->d_pyr + sc->lev_off[L];
+        T.pmin[L] = sc->d_pyr + sc->pyr_capacity + sc->lev_off[L];
         for (int a = 0; a < 3; ++a) T.dims[L][a] = sc->lev_dims[3 * L + a];
         T.hz[L] = sc->h[2] * (float)(1 << (3 * L));
     }

@@ -118,6 +118,7 @@ struct Ray {
     int v[3];        // voxel of the current point
     int lev;         // leaf level
     float M;         // leaf majorant (+ k_gas)
+    float mn;        // leaf minorant (+ k_gas)
     float t;         // distance of the current point from o
     float texit;     // distance of the leaf exit from o
     int ax;          // exit axis
@@ -151,10 +152,12 @@ __device__ __forceinline__ const uint2* leaf_entry(const DevScene& S, const int 
 template <bool BF16>
 __device__ __forceinline__ void finish_leaf(const DevScene& S, Ray& R, uint2 e)
 {
-    R.lev = (int)e.y;
-    float M = __uint_as_float(e.x);
-    if (R.lev == 0) M = kfetch<BF16>(S, R.v[0], R.v[1], R.v[2]);
+    // entry: .x majorant bits, .y = minorant rounded down to bfloat16 | level
+    R.lev = (int)(e.y & 0xFFFFu);
+    float M = __uint_as_float(e.x), mn = __uint_as_float(e.y & 0xFFFF0000u);
+    if (R.lev == 0) M = mn = kfetch<BF16>(S, R.v[0], R.v[1], R.v[2]);
     R.M = __fadd_rn(M, S.k_gas);
+    R.mn = __fadd_rn(mn, S.k_gas);
     const int s = 3 * R.lev;
     float ta[3];
 #pragma unroll

@@ -31,7 +31,7 @@ struct mcrt_scene {
     size_t vox_bytes = 0;
     // pyramid: level 1 is filled by the relayout; levels >= 2 by the build
     int levels = 0;                   // built levels (0 = none)
-    float* d_pyr = nullptr;           // all levels, concatenated
+    float* d_pyr = nullptr;           // all levels, concatenated; the minorant levels follow at + pyr_capacity
     size_t pyr_capacity = 0;          // floats allocated
     std::vector<size_t> lev_off;      // offset of level L (index L), floats
     std::vector<int> lev_dims;        // 3 ints per level (index 3L)
@@ -162,7 +162,7 @@ enum Sensor { kCamera = 0, kFlux = 1 };
 
 // Launchers (return cudaError of the launch).
 cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t st);
-cudaError_t launch_reduce_level(const float* prev, const int* prev_dims, float* out, const int* dims,
+cudaError_t launch_reduce_level(const float* prev, const int* prev_dims, float* out, const int* dims, bool min_level,
                                 cudaStream_t st);
 cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st);
 cudaError_t launch_hf_pyramid(const float* h, int nx, int ny, float* pyr, const int* off, int levels, cudaStream_t st);

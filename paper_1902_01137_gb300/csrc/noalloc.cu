@@ -95,7 +95,7 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     if (spp < 1) return nfail(ctx, MCRT_ERR_ARG, "%s: spp must be >= 1", who);
     if (!(cam->fov_deg > 0.0f && cam->fov_deg < 180.0f)) return nfail(ctx, MCRT_ERR_ARG, "%s: fov must be in (0, 180)", who);
     if (!(o->tau_merge >= 0.0f) || o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels ||
-        o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA) || o->block_size < 0 ||
+        o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA && o->sun_mode != MCRT_SUN_DECOMP) || o->block_size < 0 ||
         o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
         o->rare_batch < 0 || o->rare_batch > 32)
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);

@@ -229,8 +229,12 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
 
         // ---- the one Philox block of this iteration ---------------------------
         const float seg = (TERRAIN ? fminf(R.texit, tg) : R.texit) - R.t;
-        const float Mseg = R.M * seg;
-        const bool tent = ph == PH_STEP && R.M > 0.0f && tau < Mseg;
+        // tracking majorant: the leaf's M, or M - m for a sun ray in
+        // decomposition tracking (the minorant m is applied exactly)
+        const bool decomp = kind != kMain && P.sun_mode == MCRT_SUN_DECOMP;
+        const float Mt = decomp ? R.M - R.mn : R.M;
+        const float Mseg = Mt * seg;
+        const bool tent = ph == PH_STEP && Mt > 0.0f && tau < Mseg;
         uint32_t xc2 = c2, xblk = 0u;
         if (ph == PH_START) xc2 = 2u;
         else if (ph == PH_STEP) xblk = blk;
@@ -378,8 +382,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             // one step: to the tentative collision inside the leaf, or across
             // the leaf's exit face; both share the point and voxel arithmetic
             const bool at_ground = TERRAIN && !tent && tg <= R.texit;   // the surface cuts this leaf
-            const float tn = tent ? fminf(R.t + __fdividef(tau, R.M), TERRAIN ? fminf(R.texit, tg) : R.texit)
+            const float tn = tent ? fminf(R.t + __fdividef(tau, Mt), TERRAIN ? fminf(R.texit, tg) : R.texit)
                                   : (at_ground ? tg : R.texit);
+            if (decomp) Ts *= __expf(-R.mn * (tn - R.t));   // the control over this piece of the leaf
             advance(S, R, tn, !tent && !at_ground, p, nv);
             if (at_ground) {
                 // ground vertex at the surface hit (x, y wrapped into the domain)
@@ -402,7 +407,13 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 float wdt;
                 st = cross_face(S, R, p, nv, &wdt);
                 if (TERRAIN) { tg -= wdt; tpend -= wdt; }   // a periodic wrap restarts the segment
-                if (st == kInside) {
+                if (st == kInside && decomp && Ts < 0.1f) {
+                    // roulette at a leaf crossing: word 3 of the next block, which it uses up
+                    if (u01(x.w) * 0.1f <= Ts) Ts = 0.1f;
+                    else { Ts = 0.0f; evc = EV_SUN_END; }
+                    ++blk;
+                }
+                if (st == kInside && evc == EV_NONE) {
                     ptr = leaf_entry(S, R.v);
                     setup = true;
                     if (COUNT) {
@@ -615,7 +626,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (P.sun_mode == MCRT_SUN_DELTA) {
                     if (u0 * R.M <= k) { Ts = 0.0f; ended = true; }
                 } else {
-                    Ts *= 1.0f - __fdividef(k, R.M);
+                    if (P.sun_mode == MCRT_SUN_DECOMP) Ts *= 1.0f - __fdividef(k - R.mn, R.M - R.mn);
+                    else Ts *= 1.0f - __fdividef(k, R.M);
                     if (!(Ts > 0.0f)) { Ts = 0.0f; ended = true; }
                     else if (Ts < 0.1f) {
                         if (u0 * 0.1f <= Ts) Ts = 0.1f;

@@ -77,10 +77,13 @@ def test_majorants_bit_exact(m, ctx, orc, shape, levels, bf16):
     sc = m.Scene(ctx, k, 0.1, 0.1, 0.1, levels=levels, storage=m.MCRT_STORAGE_BF16 if bf16 else 0)
     try:
         want = orc.build_pyramid(k, levels, round_up_bf16=bf16)
+        want_min = orc.build_pyramid_min(k, levels, round_nearest_bf16=bf16)
         for L in range(1, levels + 1):
             got = sc.majorants(L)
             assert got.shape == want[L - 1].shape
             assert np.array_equal(got.view(np.uint32), want[L - 1].view(np.uint32)), L
+            gmin = sc.minorants(L)
+            assert np.array_equal(gmin.view(np.uint32), want_min[L - 1].view(np.uint32)), ("min", L)
     finally:
         sc.close()
 
@@ -169,7 +172,8 @@ def test_camera_small_vs_oracle(m, orc, small):
 
 @pytest.mark.parametrize("opts", [dict(tau_merge=0.0, finest_level=0), dict(tau_merge=float("inf")),
                                   dict(tau_merge=1.0, finest_level=1), dict(tau_merge=0.5, finest_level=1),
-                                  dict(tau_merge=10.0), dict(sun_mode=1), dict(chunk=1), dict(chunk=64),
+                                  dict(tau_merge=10.0), dict(sun_mode=1), dict(sun_mode=2),
+                                  dict(sun_mode=2, tau_merge=1.0, finest_level=1), dict(chunk=1), dict(chunk=64),
                                   dict(block_size=64, grid_size=7)])
 def test_flux_options_vs_oracle(m, orc, small, opts):
     sp, sc = small
@@ -185,6 +189,33 @@ def test_flux_options_vs_oracle(m, orc, small, opts):
     o, _ = orc.trace_flux(oscene(orc, sp, **okw), n, seed=3)
     for q in range(3):
         assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (opts, q, g.mean[q], o.mean[q])
+
+
+def test_decomposition_tracking_closed_form_and_variance(m, ctx, orc, small):
+    """Decomposition tracking on the GPU: exp(-tau) with zero variance through
+    a uniform slab whose extinction is a bfloat16 value (the leaves'
+    minorant equals it) and tau < ln 10; on the blob field the same
+    expectation as ratio tracking with a smaller diffuse variance, paired
+    with the oracle's decomposition tracking."""
+    k, th = 0.75, 40.0
+    sp = scenes.homogeneous(16, 16, 16, 0.1, k, levels=2, sun_zenith_deg=th)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        r = sc.trace_flux(20000, seed=2, sun_mode=2)
+        want = math.exp(-k * 16 * float(np.float32(0.1)) / math.cos(math.radians(th)))
+        assert r.mean[0] == pytest.approx(want, rel=2e-6) and r.se[0] < 1e-6 * want
+    finally:
+        sc.close()
+    sp, sc = small
+    n = 200000
+    a = sc.trace_flux(n, seed=31, sun_mode=0)
+    b = sc.trace_flux(n, seed=31, sun_mode=2)
+    o, _ = orc.trace_flux(oscene(orc, sp, sun_mode=2), n, seed=31)
+    for q in range(3):
+        assert close_4se(a.mean[q], a.se[q], b.mean[q], b.se[q])
+        assert close_4se(b.mean[q], b.se[q], o.mean[q], o.se[q])
+    assert abs(b.mean[2] - o.mean[2]) < 0.25 * o.se[2]
+    assert b.se[1] < a.se[1]
 
 
 def test_launch_shape_does_not_change_results(m, small):

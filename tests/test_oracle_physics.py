@@ -30,14 +30,20 @@ def _oscene(orc, sp, **kw):
     return orc.Scene(**args)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_beer_homogeneous_slab(orc, mode):
-    k, H, th = 1.7, 1.6, 40.0
+    # (decomposition: k = 0.75 is a bfloat16 value, so the leaves' minorant
+    #  is k itself, and tau < ln 10 keeps the roulette out)
+    k, H, th = (1.7 if mode < 2 else 0.75), 16 * float(np.float32(0.1)), 40.0   # 16 voxels of FP32 0.1 km
     sp = scenes.homogeneous(16, 16, 16, 0.1, k, levels=2, sun_zenith_deg=th)
     sc = _oscene(orc, sp, sun_mode=mode)
     T, _ = orc.trace_flux(sc, 40000, seed=5)
     want = math.exp(-k * H / math.cos(math.radians(th)))
-    assert abs(T.mean[0] - want) < 3.0 * T.se[0], (T.mean[0], want, T.se[0])
+    assert abs(T.mean[0] - want) < 3.0 * T.se[0] + 1e-12, (T.mean[0], want, T.se[0])
+    if mode == 2:
+        # decomposition tracking: the uniform field is its own minorant, so
+        # every path gets exp(-tau) exactly (no random draw on the sun ray)
+        assert T.mean[0] == pytest.approx(want, rel=1e-12) and T.se[0] < 1e-12
 
 
 def test_beer_layered_slabs(orc):
@@ -52,12 +58,17 @@ def test_beer_layered_slabs(orc):
     k = np.broadcast_to(kz[:, None, None], (nz, 16, 16)).astype(np.float32).copy()
     th = 25.0
     sp = scenes.SceneSpec("layers", k, 0.05, 0.05, 0.05, 2, 0.0, 1.0, 1.0, 0.85, 0.0, th)
-    for tau, fin in [(1.0, 1), (0.0, 0), (float("inf"), 1)]:
-        sc = _oscene(orc, sp, tau_merge=tau, finest_level=fin)
+    for tau, fin, mode in [(1.0, 1, 0), (0.0, 0, 0), (float("inf"), 1, 0), (1.0, 1, 2), (0.0, 0, 2),
+                           (float("inf"), 1, 2)]:
+        sc = _oscene(orc, sp, tau_merge=tau, finest_level=fin, sun_mode=mode)
         T, _ = orc.trace_flux(sc, 30000, seed=9)
-        tau_v = float(np.sum(kz.astype(np.float64) * 0.05))
+        tau_v = float(np.sum(kz.astype(np.float64) * float(np.float32(0.05))))   # FP32 voxel height
         want = math.exp(-tau_v / math.cos(math.radians(th)))
-        assert abs(T.mean[0] - want) < 3.0 * T.se[0], (tau, T.mean[0], want, T.se[0])
+        assert abs(T.mean[0] - want) < 3.0 * T.se[0] + 1e-12, (tau, mode, T.mean[0], want, T.se[0])
+        if mode == 2 and fin == 0:
+            # voxel leaves: the control is the voxel, exp(-tau) exactly (roulette aside:
+            # tau here is below ln 10, so no path is rouletted)
+            assert T.mean[0] == pytest.approx(want, rel=1e-9) and T.se[0] < 1e-12
 
 
 def _exact_optical_depth(orc, sp, o, d):
@@ -75,7 +86,7 @@ def _exact_optical_depth(orc, sp, o, d):
     return tau
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_heterogeneous_ray_transmissivity(orc, mode):
     sp = scenes.random_voxels(32, 32, 24, 0.1, 4.0, seed=21, levels=2, sparsity=0.6)
     r = np.random.default_rng(7)
@@ -89,6 +100,11 @@ def test_heterogeneous_ray_transmissivity(orc, mode):
         want = math.exp(-tau)
         se = t.std(ddof=1) / math.sqrt(t.size)
         assert abs(t.mean() - want) < 3.0 * se + 1e-12, (j, t.mean(), want, se, tau)
+        if mode == 2:
+            # the control removes most of the variance ratio tracking has
+            r0 = orc.transmissivity_many(orc.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=2, tau_merge=1.0,
+                                                   sun_mode=0), o, v, seed=1000 + j, n=100000)
+            assert t.var() < r0.var()
 
 
 def test_majorant_invariance(orc):
@@ -105,6 +121,18 @@ def test_majorant_invariance(orc):
                 d = abs(res[i].mean[q] - res[j].mean[q])
                 s = math.hypot(res[i].se[q], res[j].se[q])
                 assert d < 4.0 * s, (i, j, q, d, s)
+
+
+def test_decomposition_tracking_tallies_match_ratio_tracking(orc):
+    """Sun transmissivity by decomposition tracking (minorant control, ratio
+    tracking on the residual) gives the same flux expectations as ratio
+    tracking, with a smaller variance of the diffuse part."""
+    sp = scenes.blobs_small(0)
+    a, _ = orc.trace_flux(_oscene(orc, sp, sun_mode=0), 60000, seed=41)
+    b, _ = orc.trace_flux(_oscene(orc, sp, sun_mode=2), 60000, seed=42)
+    for q in range(3):
+        assert abs(a.mean[q] - b.mean[q]) < 4.0 * math.hypot(a.se[q], b.se[q]), (q, a.mean[q], b.mean[q])
+    assert b.se[1] < a.se[1]
 
 
 def test_black_sky_lambertian_ground(orc):

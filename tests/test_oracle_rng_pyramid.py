@@ -117,3 +117,27 @@ def test_pyramid_bf16_round_up_bounds_rn_field(orc):
     plain = orc.build_pyramid(k, 2)
     want = np.array([orc.bf16_round_up(v) for v in plain[0].ravel()], dtype=np.float32).reshape(plain[0].shape)
     assert np.array_equal(pyr[0], want)
+
+
+@pytest.mark.parametrize("shape", [(32, 64, 64), (13, 9, 17)])
+def test_minorant_pyramid_equals_block_min(orc, shape):
+    r = np.random.default_rng(5)
+    k = (r.lognormal(0.0, 2.0, shape) * (r.uniform(size=shape) < 0.7)).astype(np.float32)
+    got = orc.build_pyramid_min(k, 2)
+    # block min over existing children: pad with +inf to whole blocks
+    pz, py, px = (-(-s // 8) * 8 for s in shape)
+    pad = np.full((pz, py, px), np.inf, dtype=np.float32)
+    pad[:shape[0], :shape[1], :shape[2]] = k
+    l1 = pad.reshape(pz // 8, 8, py // 8, 8, px // 8, 8).min(axis=(1, 3, 5))
+    assert np.array_equal(got[0], l1)
+    assert got[1].min() == k.min() and np.all(got[1] <= got[0].min())
+    rn = orc.bf16_round_nearest_array(k)
+    gb = orc.build_pyramid_min(k, 1, round_nearest_bf16=True)[0]
+    padb = np.full((pz, py, px), np.inf, dtype=np.float32)
+    padb[:shape[0], :shape[1], :shape[2]] = rn
+    assert np.array_equal(gb, padb.reshape(pz // 8, 8, py // 8, 8, px // 8, 8).min(axis=(1, 3, 5)))
+    # rounding down to bfloat16 keeps a minorant
+    for v in (0.0, 1e-3, 0.3, 45.1, 431.7):
+        d = orc.bf16_round_down(v)
+        assert d <= v and (np.float32(d).view(np.uint32) & 0xFFFF) == 0
+        assert d == 0.0 or orc.bf16_round_up(v) == d or v - d < v * 2.0 ** -7
