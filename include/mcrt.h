@@ -299,9 +299,12 @@ MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc
  * k_gas (a spectral band's gas: majorants become M + k_gas, so one pyramid
  * serves every band) under its own sun; path j of an item draws exactly the
  * random numbers path j of mcrt_trace_flux with the item's seed draws.  The
- * tally has n cells x 4 quantities: T_dir, T_dif, T_tot and dT_tot/dg, the
- * derivative with respect to the HG asymmetry estimated along the same paths
- * by the score-function method.  Scenes must have majorants; items must
+ * tally has n cells x 5 quantities: T_dir, T_dif, T_tot, dT_tot/dg (the
+ * derivative with respect to the HG asymmetry, by the score-function
+ * method) and dT_tot/dalpha (with respect to the cloud droplets'
+ * absorptivity alpha = 1 - omega_cloud at fixed extinction, the sensitivity
+ * of Sec. 6.1: each estimate times the sum of d ln omega / d alpha over the
+ * path's volume vertices so far), both along the same paths.  Scenes must have majorants; items must
  * share FP32 or BF16 storage.  The learned proposal is not used here. */
 typedef struct {
     const mcrt_scene* scene;
@@ -332,7 +335,7 @@ MCRT_API int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, in
  * outlive the plan and keep their majorants; a run traces the same paths
  * again unless mcrt_batch_plan_set_seeds changes the seeds.  Deadline and
  * cancel flag are not available in plans (MCRT_ERR_UNSUPPORTED).
- * mcrt_batch_plan_run: mean and se (either may be NULL) receive n x 4
+ * mcrt_batch_plan_run: mean and se (either may be NULL) receive n x 5
  * entries in the order of mcrt_trace_batch; *kernel_ms the graph's device
  * time (the trace kernel plus microseconds of reset, finalize and copies).  mcrt_batch_plan_tally lends the plan's tally (owned by the plan;
  * do not destroy it) for mcrt_tally_read and friends. */

@@ -443,15 +443,16 @@ def trace_camera(scene: Scene, cam: Camera, spp: int, seed: int, pix_range=None,
 
 
 def trace_flux(scene: Scene, npaths: int, seed: int, begin: int = 0, nthreads: int = 0):
-    """Domain-mean ground transmittance tallies (T_dir, T_dif, T_tot, dT/dg)."""
+    """Domain-mean ground transmittance tallies (T_dir, T_dif, T_tot, dT/dg,
+    dT/dalpha)."""
     st = scene.struct()
-    sums = np.zeros(8, dtype=np.float64)
+    sums = np.zeros(10, dtype=np.float64)
     stats = np.zeros(4, dtype=np.int64)
     rc = lib().orc_trace_flux(C.byref(st), seed, begin, begin + npaths, _ptr(sums, C.c_double),
                               nthreads or default_threads(), _ptr(stats, C.c_int64))
     if rc != 0:
         raise ValueError("bad flux request")
-    return Tally(sums[0::2].copy(), sums[1::2].copy(), np.full(4, float(npaths))), stats
+    return Tally(sums[0::2].copy(), sums[1::2].copy(), np.full(5, float(npaths))), stats
 
 
 def terrain_height(scene: Scene, x: float, y: float):

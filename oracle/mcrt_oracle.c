@@ -1067,20 +1067,29 @@ double orc_hg_dlog_dg(double g, double mu)
  * score with respect to the HG asymmetry g, by the score-function method:
  * each local estimate c_j also contributes c_j (sum of d ln p_HG / dg of
  * the directions sampled before vertex j + d ln p_HG / dg of its own phase
- * value toward the sun); ground terms only carry the earlier sum. */
+ * value toward the sun); ground terms only carry the earlier sum.
+ * *dalpha (may be NULL) receives the derivative with respect to the cloud
+ * droplets' absorptivity alpha = 1 - omega_cloud at fixed extinction (the
+ * sensitivity of Sec. 6.1): only the weights depend on it, through
+ * omega = (k_c (1 - alpha) + k_clear omega_clear) / k, so each estimate c_j
+ * contributes c_j times the sum over volume vertices up to and including j
+ * of d ln omega / d alpha = -k_c / (k omega).  (Roulette keeps this form:
+ * a survival's probability w / 0.01 carries the same logarithmic
+ * derivative as the weight it replaces.) */
 static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
-                               orc_counts* C, int64_t* aborted, double* dscore);
+                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha);
 
 static double trace_backward(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                              orc_counts* C, int64_t* aborted)
 {
-    return trace_backward_d(S, p, d, seed, path, C, aborted, NULL);
+    return trace_backward_d(S, p, d, seed, path, C, aborted, NULL, NULL);
 }
 
 static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
-                               orc_counts* C, int64_t* aborted, double* dscore)
+                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha)
 {
     double sg = 0.0, ds = 0.0;
+    double sa = 0.0, da = 0.0;
     double w = 1.0, score = 0.0;
     int lv = 0;                 /* volume vertices so far */
     const double* s = S->sun;
@@ -1101,12 +1110,18 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
         rng_block(&r, BLOCK_VERTEX, uv);
         if (ev == EV_VOLUME) {
             double om = omega_at(S, k);
+            if (om > 0.0) {
+                double kc = k - S->k_gas - S->k_clear;
+                if (kc < 0.0) kc = 0.0;
+                sa += -kc / (k * om);
+            }
             if (score_it) {
                 double Ts = transmissivity(S, p, s, &rs, C);
                 double mu = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
                 double c = w * om * orc_hg_pdf(S->g, mu) * Ts;
                 score += c;
                 ds += c * (sg + orc_hg_dlog_dg(S->g, mu));
+                da += c * sa;
             }
             w *= om;
             double nd[3];
@@ -1132,6 +1147,7 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 double c = w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
                 score += c;
                 ds += c * sg;
+                da += c * sa;
             }
             w *= S->ground_albedo;
             cosine_up(uv[0], uv[1], d);
@@ -1144,6 +1160,7 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 double c = w * (S->ground_albedo / ORC_PI) * fmax(ns, 0.0) * Ts;
                 score += c;
                 ds += c * sg;
+                da += c * sa;
             }
             w *= S->ground_albedo;
             cosine_about(ng, uv[0], uv[1], d);
@@ -1155,6 +1172,7 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
         }
     }
     if (dscore) *dscore = ds;
+    if (dalpha) *dalpha = da;
     return score;
 }
 
@@ -1231,7 +1249,7 @@ static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp,
 /* One ground-flux path: uniform ground point, cosine-weighted upward
  * direction (stream (0, 2): four draws); direct part from stream (0, 3).
  * out[0] = T_dir, out[1] = T_dif = pi / mu0 * sum of local estimates. */
-static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[3],
+static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[4],
                       orc_counts* cnt, int64_t* aborted)
 {
     rng_t r;
@@ -1258,21 +1276,23 @@ static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double o
         double ns = n[0] * S->sun[0] + n[1] * S->sun[1] + n[2] * S->sun[2];
         double q[3] = {p[0], p[1], p[2]};
         double Tdir = ns > 0.0 ? transmissivity(S, q, S->sun, &rd, cnt) : 0.0;
-        double dsc = 0.0;
-        double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc);
+        double dsc = 0.0, dal = 0.0;
+        double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc, &dal);
         out[0] = fmax(ns, 0.0) / (n[2] * mu0) * Tdir;
         out[1] = ORC_PI / (n[2] * mu0) * score;
         out[2] = ORC_PI / (n[2] * mu0) * dsc;
+        out[3] = ORC_PI / (n[2] * mu0) * dal;
         return;
     }
     cosine_up(u2, u3, d);
     double q[3] = {p[0], p[1], p[2]};
     double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
-    double dsc = 0.0;
-    double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc);
+    double dsc = 0.0, dal = 0.0;
+    double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc, &dal);
     out[0] = Tdir;
     out[1] = ORC_PI / mu0 * score;
     out[2] = ORC_PI / mu0 * dsc;
+    out[3] = ORC_PI / mu0 * dal;
 }
 
 /* ===================================================================== */
@@ -1364,17 +1384,18 @@ static void run_block(job_t* J, int64_t b)
             J->out[2 * pix + 1] += sc * sc;
         }
     } else if (J->kind == 1) {
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (uint64_t path = p0; path < p1; ++path) {
-            double o[3];
+            double o[4];
             flux_path(J->S, J->seed, path, o, &cnt, &ab);
             double tot = o[0] + o[1];
             acc[0] += o[0]; acc[1] += o[0] * o[0];
             acc[2] += o[1]; acc[3] += o[1] * o[1];
             acc[4] += tot;  acc[5] += tot * tot;
             acc[6] += o[2]; acc[7] += o[2] * o[2];
+            acc[8] += o[3]; acc[9] += o[3] * o[3];
         }
-        for (int i = 0; i < 8; ++i) J->out[8 * b + i] = acc[i];
+        for (int i = 0; i < 10; ++i) J->out[10 * b + i] = acc[i];
     } else {
         double acc[12];
         for (int i = 0; i < 12; ++i) acc[i] = 0.0;
@@ -1440,8 +1461,9 @@ int orc_trace_camera(const orc_scene* S, const orc_camera* C, uint32_t spp, uint
     return 0;
 }
 
-/* Flux: paths [begin, end); sums[8] = (sum, sum^2) of T_dir, T_dif, T_tot,
- * dT/dg (score-function derivative with respect to the HG asymmetry). */
+/* Flux: paths [begin, end); sums[10] = (sum, sum^2) of T_dir, T_dif, T_tot,
+ * dT/dg (score-function derivative with respect to the HG asymmetry), dT/dalpha
+ * (derivative with respect to the cloud droplets' absorptivity). */
 int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t end, double* sums,
                    int nthreads, int64_t* stats)
 {
@@ -1451,14 +1473,14 @@ int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t e
     J.S = S; J.kind = 1; J.seed = seed; J.begin = begin; J.end = end;
     J.block = 1024;
     J.nblocks = (int64_t)((end - begin + J.block - 1) / J.block);
-    J.out = (double*)calloc((size_t)(8 * J.nblocks + 8), sizeof(double));
+    J.out = (double*)calloc((size_t)(10 * J.nblocks + 10), sizeof(double));
     J.aborted = (int64_t*)calloc((size_t)(J.nblocks + 1), sizeof(int64_t));
     J.counts = (orc_counts*)calloc((size_t)(J.nblocks + 1), sizeof(orc_counts));
     run_job(&J, nthreads);
-    for (int i = 0; i < 8; ++i) sums[i] = 0.0;
+    for (int i = 0; i < 10; ++i) sums[i] = 0.0;
     int64_t ab = 0; orc_counts tot = {0, 0, 0};
     for (int64_t b = 0; b < J.nblocks; ++b) {
-        for (int i = 0; i < 8; ++i) sums[i] += J.out[8 * b + i];
+        for (int i = 0; i < 10; ++i) sums[i] += J.out[10 * b + i];
         ab += J.aborted[b];
         tot.tentative += J.counts[b].tentative; tot.real += J.counts[b].real; tot.leaves += J.counts[b].leaves;
     }

@@ -617,8 +617,8 @@ def mcrt_autotune_batch(ctx, items, fraction: float, opts: TraceOpts):
 
 
 def trace_batch(ctx: Context, items, tally=None, **kw):
-    """Returns Result with mean / se of shape (n_items, 4):
-    T_dir, T_dif, T_tot, dT_tot/dg."""
+    """Returns Result with mean / se of shape (n_items, 5):
+    T_dir, T_dif, T_tot, dT_tot/dg, dT_tot/dalpha."""
     o = Scene._opts(**kw)
     t = mcrt_trace_batch(ctx.h, items, o, tally)
     try:
@@ -628,7 +628,7 @@ def trace_batch(ctx: Context, items, tally=None, **kw):
     finally:
         if tally is None:
             mcrt_tally_destroy(t)
-    return Result(mean.reshape(-1, 4), se.reshape(-1, 4), n.reshape(-1, 4), ms, cnt)
+    return Result(mean.reshape(-1, 5), se.reshape(-1, 5), n.reshape(-1, 5), ms, cnt)
 
 
 def mcrt_batch_plan_create(ctx, items, opts: TraceOpts):
@@ -644,12 +644,12 @@ def mcrt_batch_plan_set_seeds(ctx, plan, seeds):
 
 
 def mcrt_batch_plan_run(ctx, plan, n_items: int):
-    mean = np.zeros(n_items * 4)
-    se = np.zeros(n_items * 4)
+    mean = np.zeros(n_items * 5)
+    se = np.zeros(n_items * 5)
     ms = C.c_float()
     _check(_load().mcrt_batch_plan_run(plan, _ptr(mean, C.c_double), _ptr(se, C.c_double), mean.size,
                                        C.byref(ms)), ctx)
-    return mean.reshape(n_items, 4), se.reshape(n_items, 4), ms.value
+    return mean.reshape(n_items, 5), se.reshape(n_items, 5), ms.value
 
 
 def mcrt_batch_plan_destroy(plan):

@@ -882,10 +882,10 @@ TraceParams batch_params(const std::vector<BatchItem>& h, const BatchItem* d_ite
     return P;
 }
 
-// A batch tally: n cells x 4 quantities with each cell's own path count.
+// A batch tally: n cells x 5 quantities with each cell's own path count.
 int batch_tally(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, mcrt_tally** tally, const char* who)
 {
-    int rc = get_tally(ctx, n, 4, tally, who);
+    int rc = get_tally(ctx, n, 5, tally, who);
     if (rc) return rc;
     mcrt_tally* t = *tally;
     t->n_per_cell = 0;
@@ -1053,7 +1053,7 @@ int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t 
     int rc = prepare_batch(ctx, items, n, o, who, p->h, total, bf16);
     if (rc == MCRT_OK) rc = batch_tally(ctx, items, n, &p->t, who);
     if (rc) { plan_free(p); return rc; }
-    const size_t m = (size_t)n * 4;
+    const size_t m = (size_t)n * 5;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_items), sizeof(BatchItem) * (size_t)n);
@@ -1079,7 +1079,7 @@ int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t 
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), p->st);
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), p->st);
         if (c == cudaSuccess) c = launch_trace_batch(P, bf16, o->count_events != 0, grid, block, p->st);
-        if (c == cudaSuccess) c = launch_finalize(t->d_s1, t->d_s2, 0.0, (int)m, t->d_cell_n, 4, t->d_out, p->st);
+        if (c == cudaSuccess) c = launch_finalize(t->d_s1, t->d_s2, 0.0, (int)m, t->d_cell_n, 5, t->d_out, p->st);
         if (c == cudaSuccess)
             c = cudaMemcpyAsync(p->h_out, t->d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, p->st);
         if (c == cudaSuccess) c = cudaMemcpyAsync(p->h_ws, t->d_work, sizeof(WorkState), cudaMemcpyDeviceToHost, p->st);
@@ -1111,7 +1111,7 @@ int mcrt_batch_plan_run(mcrt_batch_plan* p, double* mean, double* se, size_t cou
 {
     if (!p) return fail(nullptr, MCRT_ERR_ARG, "mcrt_batch_plan_run: NULL plan");
     mcrt_ctx* ctx = p->ctx;
-    const size_t m = p->h.size() * 4;
+    const size_t m = p->h.size() * 5;
     if ((mean || se) && count < m) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_batch_plan_run: need %zu entries", m);
     CK(ctx, cudaSetDevice(ctx->device));
     CK(ctx, cudaStreamSynchronize(ctx->stream));      // work queued before the call (e.g. field uploads)

@@ -73,8 +73,8 @@ enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_
 template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
-    // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg in batches)
-    constexpr int NQ = (SENSOR == kCamera) ? 1 : (BATCH ? 4 : 3);
+    // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg, dT/dalpha in batches)
+    constexpr int NQ = (SENSOR == kCamera) ? 1 : (BATCH ? 5 : 3);
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     int item = 0;                           // batch item of the lane's chunk
     uint2 rkey = P.key;                     // Philox key of that item
     float sg = 0.0f, sv_pending = 0.0f, cfs = 0.0f, dscore = 0.0f;   // d/dg (batches)
+    float sa = 0.0f, dal = 0.0f;            // d/dalpha, the droplets' absorptivity (batches)
     uint64_t t_start = 0, t_dry = 0;
     if (P.deadline_ns || COUNT) t_start = globaltimer_ns();
     uint32_t iter = 0;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         bool walk = false;           // heightfield: find this ray's ground hit now
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
-            if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; }
+            if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; sa = 0.0f; dal = 0.0f; }
             if (COUNT) path_iters = 0;
             if constexpr (SENSOR == kCamera) {
                 const float jx = 1.0f - u01(x.x), jy = 1.0f - u01(x.y);
@@ -453,7 +454,12 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 w *= om;
                 const float mu_new = hg_sample_mu(S.g, xi1);
                 rotate_dir(R.d, mu_new, xi2, nd);
-                if (BATCH) { cfs = hg_dlog_dg(S.g, mu); sv_pending = hg_dlog_dg(S.g, mu_new); }
+                if (BATCH) {
+                    cfs = hg_dlog_dg(S.g, mu);
+                    sv_pending = hg_dlog_dg(S.g, mu_new);
+                    // d ln omega / d alpha = -k_cloud / (k omega) at this vertex
+                    if (om > 0.0f) sa -= __fdividef(fmaxf(vk - S.k_gas - S.k_clear, 0.0f), vk * om);
+                }
                 if (COUNT) cnt[C_REAL]++;
             } else if constexpr (TERRAIN) {
                 // tilted ground: leave the surface along its normal, estimate
@@ -659,6 +665,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     score += cf * Ts;
                     if (BATCH) {
                         dscore += cf * Ts * (sg + cfs);
+                        dal += cf * Ts * sa;
                         sg += sv_pending;
                     }
                     if (LEARNED && cur_rec != 0xFFFFFFFFu) {
@@ -690,6 +697,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     if constexpr (BATCH) {
                         const float dt = pi_over_mu0 * dscore;
                         acc[6] += dt; acc[7] += dt * dt;
+                        const float da = pi_over_mu0 * dal;
+                        acc[8] += da; acc[9] += da * da;
                     }
                 }
                 if (COUNT) {

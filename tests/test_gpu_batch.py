@@ -1,8 +1,8 @@
 """Batches (many flux problems in one persistent launch) against the oracle.
 
 * Each item against the oracle's flux tracer with that item's gas
-  absorption, sun and phase function: T_dir, T_dif, T_tot and dT_tot/dg
-  within 4 combined standard errors.
+  absorption, sun and phase function: T_dir, T_dif, T_tot, dT_tot/dg and
+  dT_tot/dalpha within 4 combined standard errors.
 * Each item against a single-problem GPU trace with the same seed: path j of
   the item draws what path j of the single trace draws, so the two differ
   only in how FP32 chunk sums are grouped (relative <= 64 * 2^-24 ~ 4e-6).
@@ -69,11 +69,11 @@ def test_batch_items_vs_oracle(m, ctx, orc, two_scenes):
     items = [(sa, 0.0, 30.0, 0.0, n, 11), (sb, 0.05, 60.0, 40.0, n, 12), (sa, 0.6, 75.0, 200.0, n, 13),
              (sb, 0.0, 0.0, 0.0, n, 14)]
     r = m.trace_batch(ctx, items)
-    assert r.mean.shape == (4, 4)
+    assert r.mean.shape == (4, 5)
     for i, (s, kg, z, az, npaths, seed) in enumerate(items):
         sp = a if s is sa else b
         o, _ = orc.trace_flux(oscene(orc, sp, k_gas=kg, sun_zenith_deg=z, sun_azimuth_deg=az), npaths, seed=seed)
-        for q in range(4):
+        for q in range(5):
             assert close_4se(r.mean[i, q], r.se[i, q], o.mean[q], o.se[q]), (i, q, r.mean[i], o.mean)
         assert np.all(r.n[i] == npaths)
         # same random numbers on both sides: far closer than the noise
@@ -130,7 +130,25 @@ def test_batch_gas_closed_form(m, ctx):
             mu0 = math.cos(math.radians(z))
             want = math.exp(-kg * H / mu0)
             assert abs(r.mean[i, 0] - want) <= 3 * r.se[i, 0] + 1e-12, (i, r.mean[i, 0], want)
-            assert r.mean[i, 1] == 0.0 and r.mean[i, 3] == 0.0
+            assert r.mean[i, 1] == 0.0 and r.mean[i, 3] == 0.0 and r.mean[i, 4] == 0.0
+    finally:
+        sc.close()
+
+
+def test_batch_dalpha_scales_each_order(m, ctx):
+    """Pure cloud over a black ground: the order-n estimate carries omega^n,
+    so -omega dT/dalpha = T for orders capped at 1 and 2 T(<=2) - T(<=1)
+    for the cap 2, on the same paths (FP32 sums: rel 2e-5)."""
+    om = 0.9
+    sp = scenes.homogeneous(16, 16, 8, 0.1, 1.3, levels=1, g=0.7, ssa_cloud=om, ssa_clear=1.0, sun_zenith_deg=25.0)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        it = [(sc, 0.0, 25.0, 0.0, 50000, 71)]
+        one = m.trace_batch(ctx, it, max_order=1)
+        two = m.trace_batch(ctx, it, max_order=2)
+        assert one.mean[0, 1] > 0.01
+        assert -om * one.mean[0, 4] == pytest.approx(one.mean[0, 1], rel=2e-5)
+        assert -om * two.mean[0, 4] == pytest.approx(2 * two.mean[0, 1] - one.mean[0, 1], rel=2e-5)
     finally:
         sc.close()
 
@@ -183,7 +201,7 @@ def test_graph_plan_replays_the_batch(m, ctx, two_scenes):
         plan.set_seeds([101, 102, 103])
         r3 = plan.run()
         assert not np.allclose(r3.mean[0, :3], r1.mean[0, :3], rtol=1e-9, atol=0)
-        for q in range(4):
+        for q in range(5):
             assert close_4se(r3.mean[0, q], r3.se[0, q], r1.mean[0, q], r1.se[0, q])
         other = m.trace_batch(ctx, [(s, kg, z, az, n, 101 + i) for i, (s, kg, z, az, n, _) in enumerate(items)])
         np.testing.assert_allclose(r3.mean, other.mean, rtol=4e-6, atol=1e-12)
@@ -192,8 +210,8 @@ def test_graph_plan_replays_the_batch(m, ctx, two_scenes):
         h = C.c_void_p()
         assert m.lib().mcrt_batch_plan_tally(plan.h, C.byref(h)) == 0
         mean, se, n = m.mcrt_tally_read(ctx.h, h)
-        np.testing.assert_allclose(mean.reshape(3, 4), r3.mean, rtol=1e-12)
-        assert list(n.reshape(3, 4)[:, 0]) == [20000, 9, 15000]
+        np.testing.assert_allclose(mean.reshape(3, 5), r3.mean, rtol=1e-12)
+        assert list(n.reshape(3, 5)[:, 0]) == [20000, 9, 15000]
     finally:
         plan.close()
     with pytest.raises(m.McrtError) as e:

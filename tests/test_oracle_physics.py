@@ -318,3 +318,33 @@ def test_dT_dg_single_scattering_closed_form(orc):
     want_d = flux(dpHG)
     assert abs(T.mean[1] - want_T) < 3 * T.se[1], (T.mean[1], want_T)
     assert abs(T.mean[3] - want_d) < 3 * T.se[3], (T.mean[3], want_d)
+
+
+def test_dT_dalpha_scales_each_order_exactly(orc):
+    """In a pure cloud (no clear-sky part) over a black ground, the order-n
+    estimate carries omega^n, so its derivative with respect to the
+    absorptivity alpha = 1 - omega is -n/omega times it.  With orders capped
+    at 1 and at 2 on the same seed (the same paths), the sensitivity estimate
+    must satisfy -omega dT/dalpha = T(<=1) exactly for the cap 1 and
+    2 T(<=2) - T(<=1) for the cap 2 (path by path, so up to FP64 rounding)."""
+    om = 0.9
+    sp = scenes.homogeneous(16, 16, 8, 0.1, 1.3, levels=1, g=0.7, ssa_cloud=om, ssa_clear=1.0, sun_zenith_deg=25.0)
+    one, _ = orc.trace_flux(_oscene(orc, sp, max_order=1), 20000, seed=71)
+    two, _ = orc.trace_flux(_oscene(orc, sp, max_order=2), 20000, seed=71)
+    assert one.mean[1] > 0.01
+    assert -om * one.mean[4] == pytest.approx(one.mean[1], rel=1e-12)
+    assert -om * two.mean[4] == pytest.approx(2 * two.mean[1] - one.mean[1], rel=1e-12)
+
+
+def test_dT_dalpha_matches_finite_differences(orc):
+    """Central differences over omega_cloud = 1 - alpha -/+ delta on common
+    random numbers (the free paths do not depend on alpha)."""
+    sp = scenes.blobs_small(0)
+    om, delta, n = 0.95, 0.01, 60000
+    mid, _ = orc.trace_flux(_oscene(orc, sp, ssa_cloud=om), n, seed=81)
+    lo, _ = orc.trace_flux(_oscene(orc, sp, ssa_cloud=om + delta), n, seed=81)    # alpha - delta
+    hi, _ = orc.trace_flux(_oscene(orc, sp, ssa_cloud=om - delta), n, seed=81)    # alpha + delta
+    fd = (hi.mean[2] - lo.mean[2]) / (2 * delta)
+    sfd = (hi.se[2] + lo.se[2]) / (2 * delta)
+    assert fd < 0.0                                       # more absorption, less light
+    assert abs(mid.mean[4] - fd) <= 4 * math.hypot(mid.se[4], sfd), (mid.mean[4], mid.se[4], fd, sfd)
