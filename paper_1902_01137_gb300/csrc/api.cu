@@ -460,6 +460,8 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
             return fail(ctx, MCRT_ERR_ARG, "%s: bad learned-mode options", who);
         if (o->count_events) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: counting with a proposal", who);
         if (sc->d_hf) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a proposal over a heightfield ground", who);
+        if (o->sun_mode == MCRT_SUN_DECOMP)
+            return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: decomposition tracking with a proposal", who);
     }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     return MCRT_OK;
@@ -518,7 +520,7 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;
     int grid = o->grid_size;
-    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, block);
+    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP, block);
     P.s1 = t->d_s1;
     P.s2 = t->d_s2;
     P.counters = t->d_counters;
@@ -823,6 +825,7 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
 {
     if (n < 1 || n > (1 << 20)) return fail(ctx, MCRT_ERR_ARG, "%s: item count %d not in [1, 2^20]", who, n);
     if (o->proposal) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: learned proposal in batches", who);
+    if (o->sun_mode == MCRT_SUN_DECOMP) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: decomposition tracking in batches", who);
     const uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     h.assign((size_t)n, BatchItem{});
     unsigned long long begin = 0;

@@ -171,7 +171,7 @@ cudaError_t launch_debug_terrain(const DevScene& S, const float* o, const float*
 cudaError_t launch_debug_terrain_height(const DevScene& S, const float* xy, int n, float* zn, cudaStream_t st);
 cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count, int grid, int block,
                          cudaStream_t st);
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, int block);
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool decomp, int block);
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
 int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);

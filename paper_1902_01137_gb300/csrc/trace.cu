@@ -70,7 +70,8 @@ constexpr int kSections = 9;
 // leaf-entry load and the leaf set-up also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false,
+          bool DECOMP = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
     // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg, dT/dalpha in batches)
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const float seg = (TERRAIN ? fminf(R.texit, tg) : R.texit) - R.t;
         // tracking majorant: the leaf's M, or M - m for a sun ray in
         // decomposition tracking (the minorant m is applied exactly)
-        const bool decomp = kind != kMain && P.sun_mode == MCRT_SUN_DECOMP;
+        const bool decomp = DECOMP && kind != kMain;
         const float Mt = decomp ? R.M - R.mn : R.M;
         const float Mseg = Mt * seg;
         const bool tent = ph == PH_STEP && Mt > 0.0f && tau < Mseg;
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (P.sun_mode == MCRT_SUN_DELTA) {
                     if (u0 * R.M <= k) { Ts = 0.0f; ended = true; }
                 } else {
-                    if (P.sun_mode == MCRT_SUN_DECOMP) Ts *= 1.0f - __fdividef(k - R.mn, R.M - R.mn);
+                    if (DECOMP) Ts *= 1.0f - __fdividef(k - R.mn, R.M - R.mn);
                     else Ts *= 1.0f - __fdividef(k, R.M);
                     if (!(Ts > 0.0f)) { Ts = 0.0f; ended = true; }
                     else if (Ts < 0.1f) {
@@ -867,26 +868,34 @@ __global__ void debug_philox_kernel(const uint32_t* __restrict__ ctr, const uint
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
 }
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool TERRAIN = false>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool TERRAIN = false, bool DECOMP = false>
 const void* kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED, false, TERRAIN>);
+    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED, false, TERRAIN, DECOMP>);
 }
 
-template <bool TERRAIN>
+template <bool TERRAIN, bool DECOMP>
 const void* pick_t(int sensor, bool bf16, bool count)
 {
     if (sensor == kCamera) {
-        if (bf16) return count ? kernel_ptr<kCamera, true, true, false, TERRAIN>() : kernel_ptr<kCamera, true, false, false, TERRAIN>();
-        return count ? kernel_ptr<kCamera, false, true, false, TERRAIN>() : kernel_ptr<kCamera, false, false, false, TERRAIN>();
+        if (bf16) return count ? kernel_ptr<kCamera, true, true, false, TERRAIN, DECOMP>()
+                               : kernel_ptr<kCamera, true, false, false, TERRAIN, DECOMP>();
+        return count ? kernel_ptr<kCamera, false, true, false, TERRAIN, DECOMP>()
+                     : kernel_ptr<kCamera, false, false, false, TERRAIN, DECOMP>();
     }
-    if (bf16) return count ? kernel_ptr<kFlux, true, true, false, TERRAIN>() : kernel_ptr<kFlux, true, false, false, TERRAIN>();
-    return count ? kernel_ptr<kFlux, false, true, false, TERRAIN>() : kernel_ptr<kFlux, false, false, false, TERRAIN>();
+    if (bf16) return count ? kernel_ptr<kFlux, true, true, false, TERRAIN, DECOMP>()
+                           : kernel_ptr<kFlux, true, false, false, TERRAIN, DECOMP>();
+    return count ? kernel_ptr<kFlux, false, true, false, TERRAIN, DECOMP>()
+                 : kernel_ptr<kFlux, false, false, false, TERRAIN, DECOMP>();
 }
 
-const void* pick(int sensor, bool bf16, bool count, bool terrain)
+// Kernel of a plain trace: sensor, storage, counting, heightfield ground and
+// the sun-ray estimator (decomposition tracking has variants of its own, so
+// the others keep their registers).
+const void* pick(int sensor, bool bf16, bool count, bool terrain, bool decomp)
 {
-    return terrain ? pick_t<true>(sensor, bf16, count) : pick_t<false>(sensor, bf16, count);
+    if (decomp) return terrain ? pick_t<true, true>(sensor, bf16, count) : pick_t<false, true>(sensor, bf16, count);
+    return terrain ? pick_t<true, false>(sensor, bf16, count) : pick_t<false, false>(sensor, bf16, count);
 }
 
 const void* pick_batch(bool bf16, bool count)
@@ -924,7 +933,8 @@ cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count
                          cudaStream_t st)
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
-    return cudaLaunchKernel(pick(sensor, bf16, count, P.S.hf != nullptr), dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(pick(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP), dim3(grid),
+                            dim3(block), args, 0, st);
 }
 
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st)
@@ -960,10 +970,11 @@ cudaError_t launch_targets(const float* rec_val, const float* final_score, unsig
     return cudaGetLastError();
 }
 
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, int block)
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool decomp, int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count, terrain), block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count, terrain, decomp), block, 0) !=
+        cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
