@@ -620,6 +620,46 @@ def run_sweep(args):
     return 0
 
 
+def run_tau(args):
+    """The merge threshold sweep (Sec. 4.2, Sec. 5): the bench image traced
+    with leaves chosen at several tau~ (finest level 0 and 1); per point the
+    trace time and, from a counting run, the traversal work (leaf steps of
+    flights and sun rays) and the collision work (tentative collisions, null
+    ones among them) -- the paper's partition of the time between the
+    acceleration structure and null collisions."""
+    import torch
+    import paper_1902_01137_gb300 as m
+    spec, cam = make_workload()
+    ctx = m.Context(0)
+    sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    points = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    try:
+        sc.trace_camera(cam, 4, seed=1)
+        for fin in (0, 1):
+            for tau in (0.0, 0.1, 0.3, 1.0, 3.0, 10.0, 100.0, float("inf")):
+                if fin == 1 and tau == 0.0:
+                    continue
+                ms = [sc.trace_camera(cam, SPP, seed=10 + i, tau_merge=tau, finest_level=fin).kernel_ms
+                      for i in range(2)]
+                c = sc.trace_camera(cam, SPP, seed=10, tau_merge=tau, finest_level=fin, count_events=1).counters
+                P = c["paths"]
+                points.append({"tau_merge": tau if math.isfinite(tau) else "inf", "finest_level": fin,
+                               "ms": min(ms), "paths_per_s": W * H * SPP / (min(ms) / 1e3),
+                               "leaf_steps_per_path": (c["leaf_steps"] + c["sun_leaf_steps"]) / P,
+                               "tentative_per_path": (c["tentative"] + c["sun_tentative"]) / P,
+                               "null_per_path": (c["tentative"] - c["real"]) / P,
+                               "sun_tentative_per_path": c["sun_tentative"] / P})
+    finally:
+        sc.close()
+        ctx.close()
+    clk = clocks.stop()
+    print(json.dumps({"metric": METRIC, "workload": "tau~ sweep: " + WORKLOAD, "unit": "paths/s",
+                      "points": points, "clocks": clk, "data": "synthetic"}))
+    return 0
+
+
 def run_profile_case():
     """A small case of the bench kernel for ncu: the same 512x512x160 field
     (160 MiB, larger than L2), a 512 x 512 image at 16 spp (4,194,304
@@ -648,7 +688,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep"])
+    ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep", "tau"])
     ap.add_argument("--sweep-paths", type=int, default=100_000_000)
     ap.add_argument("--no-fom", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
@@ -666,6 +706,8 @@ def main():
         return run_batch(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "tau":
+        return run_tau(args)
     return run_gpu(args)
 
 
