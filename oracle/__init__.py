@@ -71,6 +71,7 @@ class OrcScene(C.Structure):
         ("hnx", C.c_int32), ("hny", C.c_int32),
         ("hmax", C.c_double),
         ("pyr_min", C.POINTER(C.c_float)),
+        ("clear_phase", C.c_int32),
     ]
 
 
@@ -114,6 +115,10 @@ def lib():
             L.orc_hg_pdf.restype = C.c_double
             L.orc_hg_sample_mu.argtypes = [C.c_double, C.c_double]
             L.orc_hg_sample_mu.restype = C.c_double
+            L.orc_rayleigh_pdf.argtypes = [C.c_double]
+            L.orc_rayleigh_pdf.restype = C.c_double
+            L.orc_rayleigh_sample_mu.argtypes = [C.c_double]
+            L.orc_rayleigh_sample_mu.restype = C.c_double
             L.orc_hg_sample_dirs.argtypes = [C.c_double, f64p, f64p, C.c_int64, f64p]
             L.orc_transmissivity.argtypes = [sp, f64p, f64p, C.c_uint64, C.c_uint64]
             L.orc_transmissivity.restype = C.c_double
@@ -251,6 +256,7 @@ class Scene:
     n_learned: int = 8
     mis_alpha: float = 0.5
     heights: object = None        # heightfield ground [hny][hnx] float32 km (periodic), or None: flat
+    clear_phase: int = 0          # clear-air phase function: 0 HG (the cloud's g), 1 Rayleigh
     _keep: list = field(default_factory=list, repr=False)
 
     def sun_dir(self):
@@ -297,6 +303,7 @@ class Scene:
             s.mlp = _ptr(mp, C.c_double)
         s.n_learned = self.n_learned
         s.mis_alpha = self.mis_alpha
+        s.clear_phase = self.clear_phase
         if self.heights is not None:
             hf = np.ascontiguousarray(self.heights, dtype=np.float32)
             self._keep.append(hf)
@@ -367,6 +374,14 @@ def dda_bruteforce(scene: Scene, o, d, tmax: float = 1e30, cap: int = 4096):
 # --------------------------------------------------------------------------
 def hg_pdf(g, mu):
     return lib().orc_hg_pdf(float(g), float(mu))
+
+
+def rayleigh_pdf(mu):
+    return lib().orc_rayleigh_pdf(float(mu))
+
+
+def rayleigh_sample_mu(xi):
+    return lib().orc_rayleigh_sample_mu(float(xi))
 
 
 def hg_sample_mu(g, xi):

@@ -259,6 +259,7 @@ typedef struct {
     int32_t hnx, hny;          /* heightfield samples per axis (periodic)  */
     double hmax;               /* largest height                          */
     const float* pyr_min;      /* minorant levels 1..levels (layout of pyr), or NULL: 0 */
+    int32_t clear_phase;       /* phase function of the clear-air part: 0 HG (g), 1 Rayleigh */
 } orc_scene;
 
 static const float* level_ptr(const orc_scene* S, int level, int dims[3])
@@ -638,6 +639,27 @@ double orc_hg_pdf(double g, double mu)
 {
     double den = 1.0 + g * g - 2.0 * g * mu;
     return (1.0 - g * g) / (4.0 * ORC_PI * den * sqrt(den));
+}
+
+/* Rayleigh phase function normalised to 1 over 4 pi sr: 3 (1 + mu^2) / (16 pi). */
+double orc_rayleigh_pdf(double mu)
+{
+    return 3.0 * (1.0 + mu * mu) / (16.0 * ORC_PI);
+}
+
+/* Inverse-CDF Rayleigh cosine for xi in (0, 1].  The cosine's CDF is
+ * (mu^3 + 3 mu + 4) / 8, so mu solves the depressed cubic
+ * mu^3 + 3 mu + 4 - 8 xi = 0, whose one real root (Cardano) is
+ * A^(1/3) - A^(-1/3) with A = 4 xi - 2 + sqrt((4 xi - 2)^2 + 1). */
+double orc_rayleigh_sample_mu(double xi)
+{
+    double b = 4.0 * xi - 2.0;
+    double A = b + sqrt(b * b + 1.0);
+    double c = cbrt(A);
+    double mu = c - 1.0 / c;
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    return mu;
 }
 
 /* Inverse-CDF cosine of the HG distribution for xi in (0, 1]. */
@@ -1047,6 +1069,19 @@ static void vertex_features(const orc_scene* S, const double p[3], const double 
     }
 }
 
+/* Share of the scattering at extinction k_total due to the cloud droplets
+ * (the rest is the clear air): k_c omega_cloud / (k_c omega_cloud +
+ * k_clear omega_clear). */
+static double cloud_scatter_share(const orc_scene* S, double k_total)
+{
+    double k = k_total - S->k_gas;
+    double kc = k - S->k_clear;
+    if (kc < 0.0) kc = 0.0;
+    double kcl = k - kc;
+    double sc = kc * S->ssa_cloud, sr = kcl * S->ssa_clear;
+    return (sc + sr > 0.0) ? sc / (sc + sr) : 1.0;
+}
+
 static double omega_at(const orc_scene* S, double k_total)
 {
     double k = k_total - S->k_gas;          /* cloud + clear */
@@ -1115,12 +1150,20 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 if (kc < 0.0) kc = 0.0;
                 sa += -kc / (k * om);
             }
+            /* clear air with a Rayleigh phase function: the vertex's phase
+             * function is the scattering-weighted mixture (used whole in
+             * the local estimate); the new direction samples the species
+             * first (word 3 of the vertex block), then its phase function */
+            const double pc = S->clear_phase == 1 ? cloud_scatter_share(S, k) : 1.0;
             if (score_it) {
                 double Ts = transmissivity(S, p, s, &rs, C);
                 double mu = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
-                double c = w * om * orc_hg_pdf(S->g, mu) * Ts;
+                double phg = orc_hg_pdf(S->g, mu);
+                double ph = S->clear_phase == 1 ? pc * phg + (1.0 - pc) * orc_rayleigh_pdf(mu) : phg;
+                double c = w * om * ph * Ts;
                 score += c;
-                ds += c * (sg + orc_hg_dlog_dg(S->g, mu));
+                /* d ln ph / dg: only the droplets' share depends on g */
+                ds += c * (sg + pc * phg * orc_hg_dlog_dg(S->g, mu) / ph);
                 da += c * sa;
             }
             w *= om;
@@ -1133,6 +1176,12 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 rng_block(&r, BLOCK_VERTEX - 1u, ul);
                 double um[4] = {uv[0], uv[1], uv[3], ul[0]};
                 w *= orc_mis_sample(raw, S->g, S->mis_alpha, d, um, nd, NULL, NULL);
+            } else if (S->clear_phase == 1) {
+                /* the direction's density is the mixture; its g-score too */
+                double mu = uv[3] > pc ? orc_rayleigh_sample_mu(uv[0]) : orc_hg_sample_mu(S->g, uv[0]);
+                rotate_dir(d, mu, 2.0 * ORC_PI * uv[1], nd);
+                double phg = orc_hg_pdf(S->g, mu);
+                sg += pc * phg * orc_hg_dlog_dg(S->g, mu) / (pc * phg + (1.0 - pc) * orc_rayleigh_pdf(mu));
             } else {
                 double mu = orc_hg_sample_mu(S->g, uv[0]);
                 double phi = 2.0 * ORC_PI * uv[1];

@@ -348,3 +348,66 @@ def test_dT_dalpha_matches_finite_differences(orc):
     sfd = (hi.se[2] + lo.se[2]) / (2 * delta)
     assert fd < 0.0                                       # more absorption, less light
     assert abs(mid.mean[4] - fd) <= 4 * math.hypot(mid.se[4], sfd), (mid.mean[4], mid.se[4], fd, sfd)
+
+
+def test_rayleigh_sampler_and_normalisation(orc):
+    """Rayleigh cosines: E[mu] = 0, E[mu^2] = 2/5, a normalised pdf, binned
+    frequencies following it, and the inverse CDF hitting -1, 0, 1."""
+    from scipy import integrate
+    r = np.random.default_rng(14)
+    xi = 1.0 - r.uniform(size=200000)
+    mu = np.array([orc.rayleigh_sample_mu(x) for x in xi])
+    se1 = mu.std() / math.sqrt(mu.size)
+    se2 = (mu * mu).std() / math.sqrt(mu.size)
+    assert abs(mu.mean()) < 3 * se1
+    assert abs((mu * mu).mean() - 0.4) < 3 * se2
+    total, _ = integrate.quad(lambda m: 2 * math.pi * orc.rayleigh_pdf(m), -1, 1)
+    assert total == pytest.approx(1.0, abs=1e-12)
+    edges = np.linspace(-1, 1, 41)
+    h, _ = np.histogram(mu, bins=edges)
+    e = np.array([integrate.quad(lambda m: 2 * math.pi * orc.rayleigh_pdf(m), a, b)[0]
+                  for a, b in zip(edges[:-1], edges[1:])]) * mu.size
+    assert float(((h - e) ** 2 / e).sum()) < 90.0
+    assert orc.rayleigh_sample_mu(1.0) == pytest.approx(1.0, abs=1e-12)
+    assert orc.rayleigh_sample_mu(0.5) == pytest.approx(0.0, abs=1e-12)
+    assert orc.rayleigh_sample_mu(1e-12) == pytest.approx(-1.0, abs=1e-6)
+
+
+def test_rayleigh_single_scattering_reflected(orc):
+    """A clear-air slab with a Rayleigh phase function, first order, seen from
+    above: omega p_R(Theta) mu0 / (mu0 + mu) (1 - exp(-tau (1/mu0 + 1/mu)))."""
+    k, H, om, th0 = 0.8, 0.8, 0.95, 35.0
+    sp = scenes.homogeneous(16, 16, 8, 0.1, k, levels=1, g=0.85, ssa_cloud=0.5, ssa_clear=om,
+                            sun_zenith_deg=th0, sun_azimuth_deg=0.0)
+    sc = _oscene(orc, sp, max_order=1, k_clear=k, clear_phase=1)      # the whole field is clear air
+    thv = 40.0
+    d = np.array([math.sin(math.radians(thv)), 0.0, -math.cos(math.radians(thv))])
+    pos = np.array([0.8, 0.8, 0.8]) - 20.0 * d
+    cam = orc.Camera(tuple(pos), (0.8, 0.8, 0.8), (0.0, 0.0, 1.0), 1e-3, 1, 1)
+    I, _ = orc.trace_camera(sc, cam, 200000, seed=6)
+    mu0, mu = math.cos(math.radians(th0)), math.cos(math.radians(thv))
+    s = np.array([math.sin(math.radians(th0)), 0.0, mu0])
+    c = float(d @ s)
+    tau = k * 8 * float(np.float32(0.1))
+    want = om * 3 * (1 + c * c) / (16 * math.pi) * mu0 / (mu0 + mu) * (1 - math.exp(-tau * (1 / mu0 + 1 / mu)))
+    assert abs(I.mean[0, 0] - want) < 3.0 * I.se[0, 0], (I.mean[0, 0], want, I.se[0, 0])
+    # and not the HG answer: the phase functions differ a lot at this angle
+    hg = om * _hg(0.85, c) * mu0 / (mu0 + mu) * (1 - math.exp(-tau * (1 / mu0 + 1 / mu)))
+    assert abs(I.mean[0, 0] - hg) > 10 * I.se[0, 0]
+
+
+def test_rayleigh_clear_air_changes_diffuse_not_direct(orc):
+    """Blobs over clear air: switching the clear air's phase function to
+    Rayleigh leaves T_dir unchanged (same paths, same sun rays) and moves
+    T_dif; dT/dg with the mixture score still matches finite differences."""
+    sp = scenes.blobs_small(0)
+    kw = dict(k_clear=0.05)
+    a, _ = orc.trace_flux(_oscene(orc, sp, **kw), 40000, seed=91)
+    b, _ = orc.trace_flux(_oscene(orc, sp, clear_phase=1, **kw), 40000, seed=91)
+    assert a.mean[0] == b.mean[0]
+    delta = 0.03
+    lo, _ = orc.trace_flux(_oscene(orc, sp, clear_phase=1, g=sp.g - delta, **kw), 40000, seed=91)
+    hi, _ = orc.trace_flux(_oscene(orc, sp, clear_phase=1, g=sp.g + delta, **kw), 40000, seed=91)
+    fd = (hi.mean[2] - lo.mean[2]) / (2 * delta)
+    sfd = (hi.se[2] + lo.se[2]) / (2 * delta)
+    assert abs(b.mean[3] - fd) <= 4 * math.hypot(b.se[3], sfd), (b.mean[3], b.se[3], fd, sfd)
