@@ -71,6 +71,10 @@ enum { MCRT_STORAGE_F32 = 0, MCRT_STORAGE_BF16 = 1 };
  * M - m; a voxel leaf is crossed without random draws). */
 enum { MCRT_SUN_RATIO = 0, MCRT_SUN_DELTA = 1, MCRT_SUN_DECOMP = 2 };
 
+/* Phase function of the clear-air part of the field (Sec. 4.1: gas
+ * molecules scatter by Rayleigh, droplets by Henyey-Greenstein). */
+enum { MCRT_PHASE_HG = 0, MCRT_PHASE_RAYLEIGH = 1 };
+
 /* Library version and the ABI version it was built with. */
 MCRT_API int mcrt_version(int32_t* abi_version);
 
@@ -158,6 +162,14 @@ MCRT_API int mcrt_scene_read_minorants(const mcrt_scene* scene, int32_t level, f
 
 /* Flat Lambertian ground of albedo in [0, 1] (Sec. 4.1). */
 MCRT_API int mcrt_scene_set_ground_flat(mcrt_scene* scene, float albedo);
+
+/* Phase function of the clear air (k_clear, omega_clear): MCRT_PHASE_HG
+ * (default: the droplets' g) or MCRT_PHASE_RAYLEIGH, 3 (1 + mu^2) / (16 pi).
+ * With Rayleigh, a scattering vertex uses the mixture of the two species'
+ * phase functions weighted by their scattering coefficients in its local
+ * estimate, and samples the species (Sec. 4.1) before its direction.  Not
+ * available with a learned proposal or in batches. */
+MCRT_API int mcrt_scene_set_clear_sky_phase(mcrt_scene* scene, int32_t phase);
 
 /* Heightfield ground instead of the flat one (an extension of the paper's
  * flat Lambertian ground, Sec. 1 and Sec. 4.1).  heights: hny rows of hnx

@@ -36,6 +36,8 @@ MCRT_STORAGE_BF16 = 1
 MCRT_SUN_RATIO = 0
 MCRT_SUN_DELTA = 1
 MCRT_SUN_DECOMP = 2
+MCRT_PHASE_HG = 0
+MCRT_PHASE_RAYLEIGH = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -106,6 +108,7 @@ def _load():
         "mcrt_scene_read_majorants": [vp, i32, P(f32), C.c_size_t],
         "mcrt_scene_read_minorants": [vp, i32, P(f32), C.c_size_t],
         "mcrt_scene_set_ground_flat": [vp, f32],
+        "mcrt_scene_set_clear_sky_phase": [vp, i32],
         "mcrt_scene_set_ground_heightfield": [vp, vp, i32, i32, i32, f32],
         "mcrt_debug_terrain": [vp, i32, P(f32), P(f32), P(f32)],
         "mcrt_debug_terrain_height": [vp, i32, P(f32), P(f32)],
@@ -237,6 +240,10 @@ def mcrt_scene_read_minorants(ctx, scene, level: int) -> np.ndarray:
     out = np.zeros(dx * dy * dz, dtype=np.float32)
     _check(_load().mcrt_scene_read_minorants(scene, level, _ptr(out, C.c_float), out.size), ctx)
     return out.reshape(dz, dy, dx)
+
+
+def mcrt_scene_set_clear_sky_phase(ctx, scene, phase: int):
+    _check(_load().mcrt_scene_set_clear_sky_phase(scene, phase), ctx)
 
 
 def mcrt_scene_set_ground_flat(ctx, scene, albedo: float):

@@ -83,6 +83,7 @@ DevScene make_dev_scene(const mcrt_scene* sc, float k_gas)
     S.g = sc->g;
     S.k_gas = k_gas;
     S.albedo = sc->albedo;
+    S.rayleigh = sc->clear_phase == MCRT_PHASE_RAYLEIGH;
     for (int a = 0; a < 3; ++a) S.sun[a] = sc->sun[a];
     if (sc->d_hf) {
         S.hf = sc->d_hf;
@@ -332,6 +333,15 @@ int mcrt_scene_read_minorants(const mcrt_scene* sc, int32_t level, float* host_o
     return MCRT_OK;
 }
 
+int mcrt_scene_set_clear_sky_phase(mcrt_scene* sc, int32_t phase)
+{
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_set_clear_sky_phase: NULL scene");
+    if (phase != MCRT_PHASE_HG && phase != MCRT_PHASE_RAYLEIGH)
+        return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_set_clear_sky_phase: bad phase %d", phase);
+    sc->clear_phase = phase;
+    return MCRT_OK;
+}
+
 int mcrt_scene_set_ground_flat(mcrt_scene* sc, float albedo)
 {
     if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_set_ground_flat: NULL scene");
@@ -462,6 +472,8 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
         if (sc->d_hf) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a proposal over a heightfield ground", who);
         if (o->sun_mode == MCRT_SUN_DECOMP)
             return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: decomposition tracking with a proposal", who);
+        if (sc->clear_phase == MCRT_PHASE_RAYLEIGH)
+            return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a proposal with Rayleigh clear air", who);
     }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     return MCRT_OK;
@@ -520,7 +532,7 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;
     int grid = o->grid_size;
-    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP, block);
+    if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP || P.S.rayleigh, block);
     P.s1 = t->d_s1;
     P.s2 = t->d_s2;
     P.counters = t->d_counters;
@@ -843,6 +855,8 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
         if (!(it.sun_zenith_deg >= 0.0f && it.sun_zenith_deg < 90.0f) || !std::isfinite(it.sun_azimuth_deg))
             return fail(ctx, MCRT_ERR_ARG, "%s: item %d: sun zenith must be in [0, 90)", who, i);
         if (sc->d_hf) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: item %d: heightfield ground in batches", who, i);
+        if (sc->clear_phase == MCRT_PHASE_RAYLEIGH)
+            return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: item %d: Rayleigh clear air in batches", who, i);
         if (i > 0 && (sc->storage == MCRT_STORAGE_BF16) != bf16)
             return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: items mix FP32 and BF16 storage", who);
         bf16 = sc->storage == MCRT_STORAGE_BF16;

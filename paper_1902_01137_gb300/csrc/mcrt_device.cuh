@@ -78,6 +78,7 @@ struct DevScene {
     float k_gas;         // extra uniform pure absorber
     float albedo;        // Lambertian ground
     float sun[3];        // unit vector toward the sun
+    int rayleigh;        // clear air scatters with the Rayleigh phase function (else HG with g)
     // heightfield ground (hf null: flat ground at z = 0).  Heights sit at
     // the corners of a periodic grid of hn[0] x hn[1] cells; hpyr holds the
     // cell maxima (level 0: max of a cell's 4 corners) and hlev - 1 coarser
@@ -305,6 +306,31 @@ __device__ __forceinline__ void rotate_dir(const float d[3], float mu, float xi,
     float rz = c * b1z + s * b2z + mu * d[2];
     const float inv = rsqrtf(rx * rx + ry * ry + rz * rz);
     out[0] = rx * inv; out[1] = ry * inv; out[2] = rz * inv;
+}
+
+// Rayleigh phase function normalised over 4 pi sr: 3 (1 + mu^2) / (16 pi).
+__device__ __forceinline__ float rayleigh_pdf(float mu)
+{
+    return (3.0f / (16.0f * kPi)) * (1.0f + mu * mu);
+}
+
+// Inverse-CDF Rayleigh cosine for xi in (0, 1]: the real root of
+// mu^3 + 3 mu + 4 - 8 xi = 0 (Cardano), A^(1/3) - A^(-1/3) with
+// A = 4 xi - 2 + sqrt((4 xi - 2)^2 + 1).
+__device__ __forceinline__ float rayleigh_sample_mu(float xi)
+{
+    const float b = 4.0f * xi - 2.0f;
+    const float c = cbrtf(b + sqrtf(b * b + 1.0f));
+    return fminf(fmaxf(c - __frcp_rn(c), -1.0f), 1.0f);
+}
+
+// Share of the scattering at total extinction k_tot due to the droplets.
+__device__ __forceinline__ float cloud_scatter_share(const DevScene& S, float k_tot)
+{
+    const float k = k_tot - S.k_gas;
+    const float kc = fmaxf(k - S.k_clear, 0.0f);
+    const float sc = kc * S.ssa_cloud, sr = (k - kc) * S.ssa_clear;
+    return sc + sr > 0.0f ? __fdividef(sc, sc + sr) : 1.0f;
 }
 
 // d/dg of ln p_HG(mu) = -2g / (1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu).

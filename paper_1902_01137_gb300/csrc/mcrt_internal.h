@@ -41,6 +41,7 @@ struct mcrt_scene {
     float leaf_tau = 0;
     int leaf_finest = -1;
     float albedo = 0;
+    int clear_phase = 0;              // MCRT_PHASE_HG or MCRT_PHASE_RAYLEIGH
     float sun_zenith = 0, sun_azimuth = 0;
     float sun[3] = {0, 0, 1};
     // heightfield ground (null: flat)
@@ -171,7 +172,7 @@ cudaError_t launch_debug_terrain(const DevScene& S, const float* o, const float*
 cudaError_t launch_debug_terrain_height(const DevScene& S, const float* xy, int n, float* zn, cudaStream_t st);
 cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count, int grid, int block,
                          cudaStream_t st);
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool decomp, int block);
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool extra, int block);
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
 int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);

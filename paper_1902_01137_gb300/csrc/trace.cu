@@ -70,8 +70,11 @@ constexpr int kSections = 9;
 // leaf-entry load and the leaf set-up also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
+// EXTRA: the variants that also handle decomposition tracking of sun rays
+// and Rayleigh clear air (chosen at run time); the others carry neither, so
+// the paper's estimator keeps its registers.
 template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false,
-          bool DECOMP = false>
+          bool EXTRA = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
 {
     // quantities per path: camera radiance; flux T_dir, T_dif, T_tot (+ dT/dg, dT/dalpha in batches)
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const float seg = (TERRAIN ? fminf(R.texit, tg) : R.texit) - R.t;
         // tracking majorant: the leaf's M, or M - m for a sun ray in
         // decomposition tracking (the minorant m is applied exactly)
-        const bool decomp = DECOMP && kind != kMain;
+        const bool decomp = EXTRA && kind != kMain && P.sun_mode == MCRT_SUN_DECOMP;
         const float Mt = decomp ? R.M - R.mn : R.M;
         const float Mseg = Mt * seg;
         const bool tent = ph == PH_STEP && Mt > 0.0f && tau < Mseg;
@@ -451,9 +454,19 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             if (!vground) {
                 const float om = omega_at(S, vk);
                 const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
-                cf = score_it ? w * om * hg_pdf(S.g, mu) : 0.0f;
+                float ph = hg_pdf(S.g, mu);
+                float mu_new;
+                if (EXTRA && S.rayleigh) {
+                    // Rayleigh clear air: the mixture phase function in the estimate;
+                    // the species sampled with word 3 of the vertex block
+                    const float pc = cloud_scatter_share(S, vk);
+                    ph = pc * ph + (1.0f - pc) * rayleigh_pdf(mu);
+                    mu_new = u01(x.w) > pc ? rayleigh_sample_mu(xi1) : hg_sample_mu(S.g, xi1);
+                } else {
+                    mu_new = hg_sample_mu(S.g, xi1);
+                }
+                cf = score_it ? w * om * ph : 0.0f;
                 w *= om;
-                const float mu_new = hg_sample_mu(S.g, xi1);
                 rotate_dir(R.d, mu_new, xi2, nd);
                 if (BATCH) {
                     cfs = hg_dlog_dg(S.g, mu);
@@ -633,7 +646,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 if (P.sun_mode == MCRT_SUN_DELTA) {
                     if (u0 * R.M <= k) { Ts = 0.0f; ended = true; }
                 } else {
-                    if (DECOMP) Ts *= 1.0f - __fdividef(k - R.mn, R.M - R.mn);
+                    if (EXTRA && P.sun_mode == MCRT_SUN_DECOMP) Ts *= 1.0f - __fdividef(k - R.mn, R.M - R.mn);
                     else Ts *= 1.0f - __fdividef(k, R.M);
                     if (!(Ts > 0.0f)) { Ts = 0.0f; ended = true; }
                     else if (Ts < 0.1f) {
@@ -868,10 +881,10 @@ __global__ void debug_philox_kernel(const uint32_t* __restrict__ ctr, const uint
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
 }
 
-template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool TERRAIN = false, bool DECOMP = false>
+template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool TERRAIN = false, bool EXTRA = false>
 const void* kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED, false, TERRAIN, DECOMP>);
+    return reinterpret_cast<const void*>(&trace_kernel<SENSOR, BF16, COUNT, LEARNED, false, TERRAIN, EXTRA>);
 }
 
 template <bool TERRAIN, bool DECOMP>
@@ -890,11 +903,11 @@ const void* pick_t(int sensor, bool bf16, bool count)
 }
 
 // Kernel of a plain trace: sensor, storage, counting, heightfield ground and
-// the sun-ray estimator (decomposition tracking has variants of its own, so
-// the others keep their registers).
-const void* pick(int sensor, bool bf16, bool count, bool terrain, bool decomp)
+// whether decomposition tracking or Rayleigh clear air is in use (those have
+// variants of their own, so the others keep their registers).
+const void* pick(int sensor, bool bf16, bool count, bool terrain, bool extra)
 {
-    if (decomp) return terrain ? pick_t<true, true>(sensor, bf16, count) : pick_t<false, true>(sensor, bf16, count);
+    if (extra) return terrain ? pick_t<true, true>(sensor, bf16, count) : pick_t<false, true>(sensor, bf16, count);
     return terrain ? pick_t<true, false>(sensor, bf16, count) : pick_t<false, false>(sensor, bf16, count);
 }
 
@@ -933,8 +946,8 @@ cudaError_t launch_trace(const TraceParams& P, int sensor, bool bf16, bool count
                          cudaStream_t st)
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
-    return cudaLaunchKernel(pick(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP), dim3(grid),
-                            dim3(block), args, 0, st);
+    const bool extra = P.sun_mode == MCRT_SUN_DECOMP || P.S.rayleigh;
+    return cudaLaunchKernel(pick(sensor, bf16, count, P.S.hf != nullptr, extra), dim3(grid), dim3(block), args, 0, st);
 }
 
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st)
@@ -970,10 +983,10 @@ cudaError_t launch_targets(const float* rec_val, const float* final_score, unsig
     return cudaGetLastError();
 }
 
-int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool decomp, int block)
+int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool extra, int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count, terrain, decomp), block, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(sensor, bf16, count, terrain, extra), block, 0) !=
         cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;

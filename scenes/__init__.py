@@ -273,6 +273,18 @@ def heightfield(n: int = 4096, relief: float = 0.3, seed: int = 0, psd_slope: fl
     return f.astype(np.float32)
 
 
+# Colour bands (nm) for three-band renders: one band per eye cone class
+# stands in for the paper's CIE responsivity integration (Sec. 4.1), whose
+# spectra and k-distribution data are not available here.
+RGB_BANDS_NM = (650.0, 550.0, 450.0)
+
+
+def rayleigh_band_extinction(k_ref: float, lam_ref_nm: float = 550.0, bands_nm=RGB_BANDS_NM) -> list:
+    """Clear-air (molecular) extinction per band, scaled as lambda^-4 from
+    k_ref at lam_ref_nm."""
+    return [k_ref * (lam_ref_nm / lam) ** 4 for lam in bands_nm]
+
+
 def homogeneous(nx: int, ny: int, nz: int, d: float, k: float, **kw) -> SceneSpec:
     """Uniform field (pins: Beer's law, single scattering)."""
     levels = kw.pop("levels", 1)
