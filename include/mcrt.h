@@ -59,7 +59,7 @@ typedef enum {
     MCRT_ERR_CANCELLED = -5,  /* the cancel flag was raised; tallies partial  */
     MCRT_ERR_STATE = -6,      /* call out of order (e.g. no majorants yet)    */
     MCRT_ERR_BOUNDS = -7,     /* an output buffer is too small                */
-    MCRT_ERR_UNSUPPORTED = -8 /* valid request this build does not handle     */
+    MCRT_ERR_UNSUPPORTED = -8 /* valid request the library does not handle    */
 } mcrt_status;
 
 enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };

@@ -567,10 +567,10 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     return MCRT_OK;
 }
 
-// Learned proposal: paths are traced in batches; within a batch, round 0
+// Learned proposal: paths are traced in batches; within a batch, pass 0
 // runs fresh paths up to their first volume vertex, the network evaluates the
-// stopped paths' features, and each later round resumes them (one-sample MIS
-// direction) up to the next learned vertex; after n_learned rounds the paths
+// stopped paths' features, and each later pass resumes them (one-sample MIS
+// direction) up to the next learned vertex; after n_learned passes the paths
 // finish with HG sampling.  With learning on, every batch ends with Adam
 // steps on the vertices its resumed paths recorded.
 int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_trace_opts* o, mcrt_tally* t,
@@ -655,7 +655,7 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
             if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
             if (ws.status) { status = ws.status; break; }
             n_in = n_out;
-            // the outgoing buffers of this round are the incoming ones of the next
+            // the outgoing buffers of this pass are the incoming ones of the next
             qin = (r % 2 == 0) ? qb : qa;
             qout = (r % 2 == 0) ? qa : qb;
             fin_feat = (r % 2 == 0) ? fb : fa;
