@@ -419,106 +419,130 @@ __device__ __forceinline__ float hf_height(const DevScene& S, float x, float y, 
     return c + a * u + b * v;
 }
 
+// Ray-surface walk.  Only the part of the ray o + t d with z <= hmax can
+// hit (it reaches z = 0, at or below every height, last).  The ray's
+// horizontal projection walks the max pyramid over unwrapped cell indices:
+// a cell whose maximum lies below the ray's lowest point over the cell is
+// skipped whole, otherwise the walk descends into its 4 x 4 children; after
+// a step that leaves the parent block it climbs one level.  A ray starting
+// inside the relief layer starts at level 0 (it is near the surface), one
+// entering from above at the top level.  In a level-0 cell the ray crosses
+// at most two triangle pieces (split where u = v); on a piece the ray's
+// height above the plane, f(t), is linear and the hit is where f first
+// reaches 0 (the piece start if f <= 0 there).  A horizontal ray is walked
+// for at most two domain lengths.  The walk is split into a start and
+// single steps so the tracer can interleave it with other lanes' work.
+struct TerrainWalk {
+    int L, i, j;
+    float t, t1;
+};
+
+// Sets up the walk; false when the ray cannot meet the surface.
+__device__ __forceinline__ bool terrain_walk_begin(const DevScene& S, const float o[3], const float d[3],
+                                                   TerrainWalk& W)
+{
+    float t0 = 0.0f;
+    if (o[2] > S.hmax) {
+        if (!(d[2] < 0.0f)) return false;
+        t0 = __fdiv_rn(S.hmax - o[2], d[2]);
+    }
+    if (d[2] < 0.0f) W.t1 = __fdiv_rn(-o[2], d[2]);
+    else if (d[2] > 0.0f) W.t1 = __fdiv_rn(S.hmax - o[2], d[2]);
+    else W.t1 = 2.0f * fmaxf(S.Lper[0], S.Lper[1]);
+    if (W.t1 < t0) return false;
+    W.L = t0 > 0.0f ? S.hlev - 1 : 0;
+    W.t = t0;
+    const float cx = S.hc[0] * (float)(1 << (2 * W.L)), cy = S.hc[1] * (float)(1 << (2 * W.L));
+    const float x = __fmaf_rn(t0, d[0], o[0]), y = __fmaf_rn(t0, d[1], o[1]);
+    W.i = __float2int_rd(__fdiv_rn(x, cx));
+    W.j = __float2int_rd(__fdiv_rn(y, cy));
+    if (d[0] < 0.0f && (float)W.i * cx == x) W.i -= 1;
+    if (d[1] < 0.0f && (float)W.j * cy == y) W.j -= 1;
+    return true;
+}
+
+// One step of the walk (a descent, a cell test and step, or a climb).
+// Returns true when the walk is over, with *t_hit the hit distance or +inf.
+__device__ __forceinline__ bool terrain_walk_step(const DevScene& S, const float o[3], const float d[3],
+                                                  const float inv_d[3], TerrainWalk& W, float* t_hit)
+{
+    const float kInf = __int_as_float(0x7f800000);
+    const int sh = 2 * W.L;
+    const float cx = S.hc[0] * (float)(1 << sh), cy = S.hc[1] * (float)(1 << sh);
+    const float tx = d[0] > 0.0f ? ((float)(W.i + 1) * cx - o[0]) * inv_d[0]
+                   : d[0] < 0.0f ? ((float)W.i * cx - o[0]) * inv_d[0] : kInf;
+    const float ty = d[1] > 0.0f ? ((float)(W.j + 1) * cy - o[1]) * inv_d[1]
+                   : d[1] < 0.0f ? ((float)W.j * cy - o[1]) * inv_d[1] : kInf;
+    const float te = fmaxf(fminf(fminf(tx, ty), W.t1), W.t);
+    const int nx = S.hn[0] >> sh;
+    const float cmax = __ldg(S.hpyr + S.hoff[W.L] + (size_t)hf_wrap(S, 1, W.j, W.L) * nx + hf_wrap(S, 0, W.i, W.L));
+    const float zlo = __fmaf_rn(d[2] < 0.0f ? te : W.t, d[2], o[2]);
+    if (zlo <= cmax) {
+        if (W.L > 0) {
+            // descend into the child holding the point at t (1 / child size:
+            // inv_hc scaled by 4^-(L-1), exact)
+            const float hx = cx * 0.25f, hy = cy * 0.25f;
+            const float x = __fmaf_rn(W.t, d[0], o[0]), y = __fmaf_rn(W.t, d[1], o[1]);
+            const float sc = __int_as_float((127 - 2 * (W.L - 1)) << 23);
+            int ci = __float2int_rd(x * (S.inv_hc[0] * sc)), cj = __float2int_rd(y * (S.inv_hc[1] * sc));
+            if (d[0] < 0.0f && (float)ci * hx == x) ci -= 1;
+            if (d[1] < 0.0f && (float)cj * hy == y) cj -= 1;
+            W.i = min(max(ci, 4 * W.i), 4 * W.i + 3);
+            W.j = min(max(cj, 4 * W.j), 4 * W.j + 3);
+            --W.L;
+            return false;
+        }
+        // level 0: the triangle pieces of [t, te]
+        const float g0 = (o[0] * S.inv_hc[0] - (float)W.i) - (o[1] * S.inv_hc[1] - (float)W.j);
+        const float g1 = d[0] * S.inv_hc[0] - d[1] * S.inv_hc[1];
+        float cut1 = te;
+        int np = 1;
+        if (g1 != 0.0f) {
+            const float tm = __fdividef(-g0, g1);
+            if (tm > W.t && tm < te) { cut1 = tm; np = 2; }
+        }
+        float hc4[4];
+        hf_corners(S, W.i, W.j, hc4);
+        for (int q = 0; q < np; ++q) {
+            const float a0 = q == 0 ? W.t : cut1, b0 = q == 0 ? cut1 : te;
+            const bool triA = __fmaf_rn(g1, 0.5f * (a0 + b0), g0) >= 0.0f;
+            float A, B, Cc;
+            hf_plane(hc4, triA, &A, &B, &Cc);
+            const float ua = __fmaf_rn(a0, d[0], o[0]) * S.inv_hc[0] - (float)W.i;
+            const float va = __fmaf_rn(a0, d[1], o[1]) * S.inv_hc[1] - (float)W.j;
+            const float ub = __fmaf_rn(b0, d[0], o[0]) * S.inv_hc[0] - (float)W.i;
+            const float vb = __fmaf_rn(b0, d[1], o[1]) * S.inv_hc[1] - (float)W.j;
+            const float fa = __fmaf_rn(a0, d[2], o[2]) - (Cc + A * ua + B * va);
+            const float fb = __fmaf_rn(b0, d[2], o[2]) - (Cc + A * ub + B * vb);
+            if (fa <= 0.0f) { *t_hit = a0; return true; }
+            if (fb <= 0.0f) { *t_hit = a0 + fa * __fdividef(b0 - a0, fa - fb); return true; }
+        }
+    }
+    // step to the next cell of this level; climb when leaving the parent block
+    if (te >= W.t1) { *t_hit = kInf; return true; }
+    const int pi = W.i >> 2, pj = W.j >> 2;
+    if (tx <= ty) W.i += d[0] > 0.0f ? 1 : -1;
+    else W.j += d[1] > 0.0f ? 1 : -1;
+    W.t = te;
+    if (W.L < S.hlev - 1 && ((W.i >> 2) != pi || (W.j >> 2) != pj)) {
+        W.i >>= 2;
+        W.j >>= 2;
+        ++W.L;
+    }
+    return false;
+}
+
 // First distance t >= 0 at which the ray o + t d meets the surface, or
-// +inf.  Only the part of the ray with z <= hmax can hit (it reaches z = 0,
-// at or below every height, last).  The ray's horizontal projection walks
-// the max pyramid over unwrapped cell indices: a cell whose maximum lies
-// below the ray's lowest point over the cell is skipped whole, otherwise
-// the walk descends into its 4 x 4 children; after a step that leaves the
-// parent block it climbs one level.  A ray starting inside the relief layer
-// starts the walk at level 0.  In a level-0 cell the ray crosses at
-// most two triangle pieces (split where u = v); on a piece the ray's height
-// above the plane, f(t), is linear and the hit is where f first reaches 0
-// (the piece start if f <= 0 there).
+// +inf (the whole walk at once; at most 2^16 steps).
 static __device__ __forceinline__ float terrain_hit(const DevScene& S, const float o[3], const float d[3])
 {
     const float kInf = __int_as_float(0x7f800000);
-    float t0 = 0.0f, t1;
-    if (o[2] > S.hmax) {
-        if (!(d[2] < 0.0f)) return kInf;
-        t0 = __fdiv_rn(S.hmax - o[2], d[2]);
-    }
-    if (d[2] < 0.0f) t1 = __fdiv_rn(-o[2], d[2]);
-    else if (d[2] > 0.0f) t1 = __fdiv_rn(S.hmax - o[2], d[2]);
-    else t1 = kInf;
-    if (t1 < t0) return kInf;
-    const float inv_dx = d[0] != 0.0f ? __frcp_rn(d[0]) : 0.0f;
-    const float inv_dy = d[1] != 0.0f ? __frcp_rn(d[1]) : 0.0f;
-    // a ray starting inside the relief layer is near the surface: begin at
-    // level 0 and climb; one entering from above begins at the top level
-    int L = t0 > 0.0f ? S.hlev - 1 : 0;
-    float t = t0;
-    int i, j;
-    {
-        const float cx = S.hc[0] * (float)(1 << (2 * L)), cy = S.hc[1] * (float)(1 << (2 * L));
-        const float x = __fmaf_rn(t, d[0], o[0]), y = __fmaf_rn(t, d[1], o[1]);
-        i = __float2int_rd(__fdiv_rn(x, cx));
-        j = __float2int_rd(__fdiv_rn(y, cy));
-        if (d[0] < 0.0f && (float)i * cx == x) i -= 1;
-        if (d[1] < 0.0f && (float)j * cy == y) j -= 1;
-    }
-    for (int it = 0; it < (1 << 16); ++it) {
-        const int sh = 2 * L;
-        const float cx = S.hc[0] * (float)(1 << sh), cy = S.hc[1] * (float)(1 << sh);
-        const float tx = d[0] > 0.0f ? ((float)(i + 1) * cx - o[0]) * inv_dx
-                       : d[0] < 0.0f ? ((float)i * cx - o[0]) * inv_dx : kInf;
-        const float ty = d[1] > 0.0f ? ((float)(j + 1) * cy - o[1]) * inv_dy
-                       : d[1] < 0.0f ? ((float)j * cy - o[1]) * inv_dy : kInf;
-        const float te = fmaxf(fminf(fminf(tx, ty), t1), t);
-        const int nx = S.hn[0] >> sh;
-        const float cmax = __ldg(S.hpyr + S.hoff[L] + (size_t)hf_wrap(S, 1, j, L) * nx + hf_wrap(S, 0, i, L));
-        const float zlo = __fmaf_rn(d[2] < 0.0f ? te : t, d[2], o[2]);
-        if (zlo <= cmax) {
-            if (L > 0) {
-                // descend into the child holding the point at t
-                const float hx = cx * 0.25f, hy = cy * 0.25f;
-                const float x = __fmaf_rn(t, d[0], o[0]), y = __fmaf_rn(t, d[1], o[1]);
-                int ci = __float2int_rd(__fdiv_rn(x, hx)), cj = __float2int_rd(__fdiv_rn(y, hy));
-                if (d[0] < 0.0f && (float)ci * hx == x) ci -= 1;
-                if (d[1] < 0.0f && (float)cj * hy == y) cj -= 1;
-                i = min(max(ci, 4 * i), 4 * i + 3);
-                j = min(max(cj, 4 * j), 4 * j + 3);
-                --L;
-                continue;
-            }
-            // level 0: the triangle pieces of [t, te]
-            const float g0 = (o[0] * S.inv_hc[0] - (float)i) - (o[1] * S.inv_hc[1] - (float)j);
-            const float g1 = d[0] * S.inv_hc[0] - d[1] * S.inv_hc[1];
-            float cut1 = te;
-            int np = 1;
-            if (g1 != 0.0f) {
-                const float tm = __fdiv_rn(-g0, g1);
-                if (tm > t && tm < te) { cut1 = tm; np = 2; }
-            }
-            float hc4[4];
-            hf_corners(S, i, j, hc4);
-            for (int q = 0; q < np; ++q) {
-                const float a0 = q == 0 ? t : cut1, b0 = q == 0 ? cut1 : te;
-                const bool triA = __fmaf_rn(g1, 0.5f * (a0 + b0), g0) >= 0.0f;
-                float A, B, Cc;
-                hf_plane(hc4, triA, &A, &B, &Cc);
-                const float ua = __fmaf_rn(a0, d[0], o[0]) * S.inv_hc[0] - (float)i;
-                const float va = __fmaf_rn(a0, d[1], o[1]) * S.inv_hc[1] - (float)j;
-                const float ub = __fmaf_rn(b0, d[0], o[0]) * S.inv_hc[0] - (float)i;
-                const float vb = __fmaf_rn(b0, d[1], o[1]) * S.inv_hc[1] - (float)j;
-                const float fa = __fmaf_rn(a0, d[2], o[2]) - (Cc + A * ua + B * va);
-                const float fb = __fmaf_rn(b0, d[2], o[2]) - (Cc + A * ub + B * vb);
-                if (fa <= 0.0f) return a0;
-                if (fb <= 0.0f) return a0 + fa * __fdiv_rn(b0 - a0, fa - fb);
-            }
-        }
-        // step to the next cell of this level; climb when leaving the parent block
-        if (te >= t1) return kInf;
-        const int pi = i >> 2, pj = j >> 2;
-        if (tx <= ty) i += d[0] > 0.0f ? 1 : -1;
-        else j += d[1] > 0.0f ? 1 : -1;
-        t = te;
-        if (L < S.hlev - 1 && ((i >> 2) != pi || (j >> 2) != pj)) {
-            i >>= 2;
-            j >>= 2;
-            ++L;
-        }
-    }
+    TerrainWalk W;
+    if (!terrain_walk_begin(S, o, d, W)) return kInf;
+    const float inv_d[3] = {d[0] != 0.0f ? __frcp_rn(d[0]) : 0.0f, d[1] != 0.0f ? __frcp_rn(d[1]) : 0.0f, 0.0f};
+    float th = kInf;
+    for (int it = 0; it < (1 << 16); ++it)
+        if (terrain_walk_step(S, o, d, inv_d, W, &th)) return th;
     return kInf;
 }
 
