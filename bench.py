@@ -53,16 +53,23 @@ METRIC = "paths/s and 1/(variance x time) at 1% rel. std err, learned vs plain, 
 WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x 64 spp, sun 60 deg"
 W, H, SPP = 1024, 1024, 64
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
-# valid only while csrc/trace.cu is the source that was captured
-PROFILED_TRACE_SHA = "f1df80ab1a3cbb7a"
-PROFILED_DRAM_BYTES_PER_PATH = 23.84
+# valid only while the kernel's sources are the ones that were captured
+PROFILED_TRACE_SHA = "unset"
+PROFILED_DRAM_BYTES_PER_PATH = 0.0
+
+
+def trace_sources_sha() -> str:
+    """sha256 prefix over the trace kernel's sources (trace.cu, mcrt_device.cuh)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("trace.cu", "mcrt_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1902_01137_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(paths_per_launch):
-    import hashlib
-    src = os.path.join(ROOT, "paper_1902_01137_gb300", "csrc", "trace.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = trace_sources_sha()
     except OSError:
         return None
     return PROFILED_DRAM_BYTES_PER_PATH * paths_per_launch if sha == PROFILED_TRACE_SHA else None
