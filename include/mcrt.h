@@ -300,7 +300,8 @@ MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, 
  *  - The first call on a device looks up the array's device address; make
  *    that first call before capturing any stream.
  *  - The scene's majorants must be built.  Synchronises the context stream;
- *    errors as mcrt_trace_camera plus MCRT_ERR_BOUNDS. */
+ *    errors as mcrt_trace_camera plus MCRT_ERR_BOUNDS, and
+ *    MCRT_ERR_UNSUPPORTED for a learned proposal (it needs work buffers). */
 MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
                                        const mcrt_trace_opts* opts, double* d_mean, double* d_stderr);
 

@@ -99,6 +99,7 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
         o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
         o->rare_batch < 0 || o->rare_batch > 32)
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);
+    if (o->proposal) return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the learned proposal needs work buffers", who);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return nfail(ctx, MCRT_ERR_ARG, "%s: device index too large", who);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return nfail(ctx, MCRT_ERR_CUDA, "%s: cudaSetDevice: %s", who, cudaGetErrorString(e));
