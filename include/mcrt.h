@@ -252,6 +252,8 @@ typedef struct {
     const volatile int32_t* cancel_flag; /* NULL, or a flag in host-mapped or   */
                                /* device memory; non-zero stops the trace with  */
                                /* MCRT_ERR_CANCELLED                            */
+    int32_t batch_dalpha;      /* batches: 1 also estimates dT/dalpha (the 5th   */
+                               /* quantity; 0 leaves it 0 and runs faster)      */
 } mcrt_trace_opts;
 
 /* Fill `opts` with the defaults listed above. */
@@ -317,7 +319,8 @@ MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc
  * method) and dT_tot/dalpha (with respect to the cloud droplets'
  * absorptivity alpha = 1 - omega_cloud at fixed extinction, the sensitivity
  * of Sec. 6.1: each estimate times the sum of d ln omega / d alpha over the
- * path's volume vertices so far), both along the same paths.  Scenes must have majorants; items must
+ * path's volume vertices so far; only with opts->batch_dalpha, else 0),
+ * both along the same paths.  Scenes must have majorants; items must
  * share FP32 or BF16 storage.  The learned proposal is not used here. */
 typedef struct {
     const mcrt_scene* scene;

@@ -77,7 +77,8 @@ class TraceOpts(C.Structure):
                 ("learn", C.c_int32), ("batch_paths", C.c_int32), ("learning_rate", C.c_float),
                 ("train_steps", C.c_int32),
                 ("deadline_ms", C.c_double),
-                ("cancel_flag", C.c_void_p)]
+                ("cancel_flag", C.c_void_p),
+                ("batch_dalpha", C.c_int32)]
 
 
 _lib = None

@@ -920,7 +920,7 @@ int batch_tally(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, mcrt_tal
 int batch_grid(mcrt_ctx* ctx, const mcrt_trace_opts* o, bool bf16, int* block)
 {
     *block = o->block_size ? o->block_size : 128;
-    return o->grid_size ? o->grid_size : ctx->sm_count * trace_batch_blocks_per_sm(bf16, o->count_events != 0, *block);
+    return o->grid_size ? o->grid_size : ctx->sm_count * trace_batch_blocks_per_sm(bf16, o->count_events != 0, o->batch_dalpha != 0, *block);
 }
 
 }  // namespace
@@ -955,7 +955,7 @@ int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, con
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-    if (e == cudaSuccess) { ctx->launches++; e = launch_trace_batch(P, bf16, o->count_events != 0, grid, block, ctx->stream); }
+    if (e == cudaSuccess) { ctx->launches++; e = launch_trace_batch(P, bf16, o->count_events != 0, o->batch_dalpha != 0, grid, block, ctx->stream); }
     if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
     WorkState ws{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ws, t->d_work, sizeof(ws), cudaMemcpyDeviceToHost, ctx->stream);
@@ -1095,7 +1095,7 @@ int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t 
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_s2, 0, m * sizeof(double), p->st);
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), p->st);
         if (c == cudaSuccess) c = cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), p->st);
-        if (c == cudaSuccess) c = launch_trace_batch(P, bf16, o->count_events != 0, grid, block, p->st);
+        if (c == cudaSuccess) c = launch_trace_batch(P, bf16, o->count_events != 0, o->batch_dalpha != 0, grid, block, p->st);
         if (c == cudaSuccess) c = launch_finalize(t->d_s1, t->d_s2, 0.0, (int)m, t->d_cell_n, 5, t->d_out, p->st);
         if (c == cudaSuccess)
             c = cudaMemcpyAsync(p->h_out, t->d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, p->st);

@@ -176,8 +176,9 @@ int trace_blocks_per_sm(int sensor, bool bf16, bool count, bool terrain, bool ex
 cudaError_t launch_trace_learned(const TraceParams& P, int sensor, bool bf16, int grid, int block, cudaStream_t st);
 int trace_learned_blocks_per_sm(int sensor, bool bf16, int block);
 cudaError_t launch_targets(const float* rec_val, const float* final_score, unsigned n, float* tgt, cudaStream_t st);
-cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, int grid, int block, cudaStream_t st);
-int trace_batch_blocks_per_sm(bool bf16, bool count, int block);
+cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, bool dalpha, int grid, int block,
+                               cudaStream_t st);
+int trace_batch_blocks_per_sm(bool bf16, bool count, bool dalpha, int block);
 cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
                             int nq, double* out, cudaStream_t st);
 cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,

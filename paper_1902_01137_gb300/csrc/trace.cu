@@ -72,7 +72,8 @@ enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_
 
 // EXTRA: the variants that also handle decomposition tracking of sun rays
 // and Rayleigh clear air (chosen at run time); the others carry neither, so
-// the paper's estimator keeps its registers.
+// the paper's estimator keeps its registers.  In batches, EXTRA instead
+// adds the dT/dalpha estimate.
 template <int SENSOR, bool BF16, bool COUNT, bool LEARNED, bool BATCH = false, bool TERRAIN = false,
           bool EXTRA = false>
 __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const __grid_constant__ TraceParams P)
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     cfs = hg_dlog_dg(S.g, mu);
                     sv_pending = hg_dlog_dg(S.g, mu_new);
                     // d ln omega / d alpha = -k_cloud / (k omega) at this vertex
-                    if (om > 0.0f) sa -= __fdividef(fmaxf(vk - S.k_gas - S.k_clear, 0.0f), vk * om);
+                    if (EXTRA && om > 0.0f) sa -= __fdividef(fmaxf(vk - S.k_gas - S.k_clear, 0.0f), vk * om);
                 }
                 if (COUNT) cnt[C_REAL]++;
             } else if constexpr (TERRAIN) {
@@ -679,7 +680,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     score += cf * Ts;
                     if (BATCH) {
                         dscore += cf * Ts * (sg + cfs);
-                        dal += cf * Ts * sa;
+                        if (EXTRA) dal += cf * Ts * sa;
                         sg += sv_pending;
                     }
                     if (LEARNED && cur_rec != 0xFFFFFFFFu) {
@@ -711,8 +712,10 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     if constexpr (BATCH) {
                         const float dt = pi_over_mu0 * dscore;
                         acc[6] += dt; acc[7] += dt * dt;
-                        const float da = pi_over_mu0 * dal;
-                        acc[8] += da; acc[9] += da * da;
+                        if (EXTRA) {
+                            const float da = pi_over_mu0 * dal;
+                            acc[8] += da; acc[9] += da * da;
+                        }
                     }
                 }
                 if (COUNT) {
@@ -911,13 +914,19 @@ const void* pick(int sensor, bool bf16, bool count, bool terrain, bool extra)
     return terrain ? pick_t<true, false>(sensor, bf16, count) : pick_t<false, false>(sensor, bf16, count);
 }
 
-const void* pick_batch(bool bf16, bool count)
+template <bool DALPHA>
+const void* pick_batch_t(bool bf16, bool count)
 {
     if (count)
-        return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, true, false, true>)
-                    : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, true, false, true>);
-    return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, false, false, true>)
-                : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, false, false, true>);
+        return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, true, false, true, false, DALPHA>)
+                    : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, true, false, true, false, DALPHA>);
+    return bf16 ? reinterpret_cast<const void*>(&trace_kernel<kFlux, true, false, false, true, false, DALPHA>)
+                : reinterpret_cast<const void*>(&trace_kernel<kFlux, false, false, false, true, false, DALPHA>);
+}
+
+const void* pick_batch(bool bf16, bool count, bool dalpha)
+{
+    return dalpha ? pick_batch_t<true>(bf16, count) : pick_batch_t<false>(bf16, count);
 }
 
 const void* pick_learned(int sensor, bool bf16)
@@ -963,16 +972,18 @@ int trace_learned_blocks_per_sm(int sensor, bool bf16, int block)
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, int grid, int block, cudaStream_t st)
+cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, bool dalpha, int grid, int block,
+                               cudaStream_t st)
 {
     void* args[] = {const_cast<TraceParams*>(&P)};
-    return cudaLaunchKernel(pick_batch(bf16, count), dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(pick_batch(bf16, count, dalpha), dim3(grid), dim3(block), args, 0, st);
 }
 
-int trace_batch_blocks_per_sm(bool bf16, bool count, int block)
+int trace_batch_blocks_per_sm(bool bf16, bool count, bool dalpha, int block)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_batch(bf16, count), block, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick_batch(bf16, count, dalpha), block, 0) != cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
 }
 

@@ -68,7 +68,7 @@ def test_batch_items_vs_oracle(m, ctx, orc, two_scenes):
     n = 60000
     items = [(sa, 0.0, 30.0, 0.0, n, 11), (sb, 0.05, 60.0, 40.0, n, 12), (sa, 0.6, 75.0, 200.0, n, 13),
              (sb, 0.0, 0.0, 0.0, n, 14)]
-    r = m.trace_batch(ctx, items)
+    r = m.trace_batch(ctx, items, batch_dalpha=1)
     assert r.mean.shape == (4, 5)
     for i, (s, kg, z, az, npaths, seed) in enumerate(items):
         sp = a if s is sa else b
@@ -101,6 +101,17 @@ def test_batch_dg_vs_finite_difference(m, ctx):
     finally:
         for s in sc:
             s.close()
+
+
+def test_batch_dalpha_is_opt_in(m, ctx, two_scenes):
+    """Without batch_dalpha the fifth quantity is 0 and the others are the
+    same paths' estimates as with it (to FP32 chunk-sum rounding)."""
+    (a, sa), _ = two_scenes
+    it = [(sa, 0.01, 40.0, 0.0, 30000, 3)]
+    r0 = m.trace_batch(ctx, it)
+    r1 = m.trace_batch(ctx, it, batch_dalpha=1)
+    assert r0.mean[0, 4] == 0.0 and r1.mean[0, 4] != 0.0
+    np.testing.assert_allclose(r0.mean[0, :4], r1.mean[0, :4], rtol=4e-6, atol=1e-12)
 
 
 def test_batch_matches_single_traces(m, ctx, two_scenes):
@@ -144,8 +155,8 @@ def test_batch_dalpha_scales_each_order(m, ctx):
     sc = m.Scene.from_spec(ctx, sp)
     try:
         it = [(sc, 0.0, 25.0, 0.0, 50000, 71)]
-        one = m.trace_batch(ctx, it, max_order=1)
-        two = m.trace_batch(ctx, it, max_order=2)
+        one = m.trace_batch(ctx, it, max_order=1, batch_dalpha=1)
+        two = m.trace_batch(ctx, it, max_order=2, batch_dalpha=1)
         assert one.mean[0, 1] > 0.01
         assert -om * one.mean[0, 4] == pytest.approx(one.mean[0, 1], rel=2e-5)
         assert -om * two.mean[0, 4] == pytest.approx(2 * two.mean[0, 1] - one.mean[0, 1], rel=2e-5)
