@@ -410,8 +410,8 @@ MCRT_API int mcrt_tally_destroy(mcrt_tally* tally);
 /* p_HG / q, so the estimate stays unbiased for any network.              */
 /* Parameters: 11,560 floats in the order W1[64][9], b1[64], W2[64][64],  */
 /* b2[64], W3[64][64], b3[64], W4[40][64], b4[40] (row = output unit).    */
-/* Inference runs on the tensor cores in BF16 with FP32 accumulation;    */
-/* training keeps FP32 master weights and Adam moments.                   */
+/* Inference and training run on the tensor cores in BF16 with FP32      */
+/* accumulation; training keeps FP32 master weights and Adam moments.     */
 /* --------------------------------------------------------------------- */
 /* Number of network parameters (11,560). */
 MCRT_API int mcrt_proposal_nparams(int32_t* n);
@@ -440,6 +440,14 @@ MCRT_API int mcrt_proposal_eval(mcrt_proposal* proposal, const float* host_featu
  * (beta 0.9, 0.999, eps 1e-8) is applied.  *loss_out gets the loss. */
 MCRT_API int mcrt_proposal_train_step(mcrt_proposal* proposal, const float* host_features, const float* host_dirs,
                                       const float* host_targets, size_t n, float lr, float* loss_out, float* host_grad);
+
+/* Gradient kernel used by training steps (here and in traces that learn):
+ * MCRT_TRAIN_TENSOR (default) runs every dense product of the forward and
+ * backward passes on the tensor cores (BF16 operands, FP32 accumulation);
+ * MCRT_TRAIN_FP32 runs them in FP32 on the CUDA cores.  Master weights and
+ * Adam moments are FP32 either way. */
+enum { MCRT_TRAIN_TENSOR = 0, MCRT_TRAIN_FP32 = 1 };
+MCRT_API int mcrt_proposal_set_training(mcrt_proposal* proposal, int32_t mode);
 
 /* --------------------------------------------------------------------- */
 /* Checks (used by the tests; not on the hot path)                        */

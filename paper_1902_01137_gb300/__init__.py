@@ -38,6 +38,8 @@ MCRT_SUN_DELTA = 1
 MCRT_SUN_DECOMP = 2
 MCRT_PHASE_HG = 0
 MCRT_PHASE_RAYLEIGH = 1
+MCRT_TRAIN_TENSOR = 0
+MCRT_TRAIN_FP32 = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -140,6 +142,7 @@ def _load():
         "mcrt_proposal_get_params": [vp, P(f32), C.c_size_t],
         "mcrt_proposal_eval": [vp, P(f32), C.c_size_t, P(f32), P(f32)],
         "mcrt_proposal_train_step": [vp, P(f32), P(f32), P(f32), C.c_size_t, f32, P(f32), P(f32)],
+        "mcrt_proposal_set_training": [vp, i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -569,11 +572,12 @@ def mcrt_proposal_train_step(ctx, prop, features, dirs, targets, lr=0.0):
 class Proposal:
     """Learned scattering proposal network on the device."""
 
-    def __init__(self, ctx: Context, seed: int = 0, params=None):
+    def __init__(self, ctx: Context, seed: int = 0, params=None, training=MCRT_TRAIN_TENSOR):
         self.ctx = ctx
         self.h = mcrt_proposal_create(ctx.h, seed)
         if params is not None:
             mcrt_proposal_set_params(ctx.h, self.h, params)
+        _check(_load().mcrt_proposal_set_training(self.h, training), ctx.h)
 
     def close(self):
         if self.h:

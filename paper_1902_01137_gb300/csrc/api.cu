@@ -673,8 +673,12 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
                     e = cudaMemsetAsync(prop->d_grad, 0, kMlpParams * sizeof(float), ctx->stream);
                     if (e == cudaSuccess) {
                         ctx->launches += 3;
-                        e = launch_mlp_train(prop->d_params, rfeat, rdir, tgt, (int)nrec, 1.0f / (float)nrec, prop->d_grad,
-                                             prop->d_loss, ctx->sm_count, ctx->stream);
+                        e = prop->train_mode == MCRT_TRAIN_FP32
+                                ? launch_mlp_train(prop->d_params, rfeat, rdir, tgt, (int)nrec, 1.0f / (float)nrec,
+                                                   prop->d_grad, prop->d_loss, ctx->sm_count, ctx->stream)
+                                : launch_mlp_train_tc(prop->d_wbf, prop->d_bias, prop->d_params, rfeat, rdir, tgt,
+                                                      (int)nrec, 1.0f / (float)nrec, prop->d_grad, prop->d_loss,
+                                                      ctx->sm_count, ctx->stream);
                     }
                     if (e == cudaSuccess) {
                         prop->step++;

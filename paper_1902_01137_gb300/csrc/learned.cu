@@ -154,6 +154,15 @@ int mcrt_proposal_set_params(mcrt_proposal* P, const float* host, size_t n)
     return MCRT_OK;
 }
 
+int mcrt_proposal_set_training(mcrt_proposal* P, int32_t mode)
+{
+    if (!P) return lfail(nullptr, MCRT_ERR_ARG, "mcrt_proposal_set_training: NULL proposal");
+    if (mode != MCRT_TRAIN_TENSOR && mode != MCRT_TRAIN_FP32)
+        return lfail(P->ctx, MCRT_ERR_ARG, "mcrt_proposal_set_training: bad mode %d", mode);
+    P->train_mode = mode;
+    return MCRT_OK;
+}
+
 int mcrt_proposal_get_params(const mcrt_proposal* P, float* host, size_t n)
 {
     if (!P || !host) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "mcrt_proposal_get_params: NULL argument");
@@ -219,8 +228,11 @@ int mcrt_proposal_train_step(mcrt_proposal* P, const float* host_feat, const flo
     if (e == cudaSuccess) e = cudaMemsetAsync(P->d_loss, 0, sizeof(float), ctx->stream);
     if (e == cudaSuccess) {
         ctx->launches++;
-        e = launch_mlp_train(P->d_params, d_feat, d_dirs, d_t, (int)n, 1.0f / (float)n, P->d_grad, P->d_loss,
-                             ctx->sm_count, ctx->stream);
+        e = P->train_mode == MCRT_TRAIN_FP32
+                ? launch_mlp_train(P->d_params, d_feat, d_dirs, d_t, (int)n, 1.0f / (float)n, P->d_grad, P->d_loss,
+                                   ctx->sm_count, ctx->stream)
+                : launch_mlp_train_tc(P->d_wbf, P->d_bias, P->d_params, d_feat, d_dirs, d_t, (int)n, 1.0f / (float)n,
+                                      P->d_grad, P->d_loss, ctx->sm_count, ctx->stream);
     }
     if (e == cudaSuccess && host_grad)
         e = cudaMemcpyAsync(host_grad, P->d_grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);

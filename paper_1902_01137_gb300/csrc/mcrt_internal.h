@@ -77,6 +77,7 @@ struct mcrt_proposal {
     void* d_wbf = nullptr;         // padded BF16 inference weights
     float* d_bias = nullptr;       // padded FP32 biases
     int step = 0;                  // Adam steps taken
+    int train_mode = MCRT_TRAIN_TENSOR;   // gradient kernel: tensor cores (BF16) or FP32
 };
 
 namespace mcrt {
@@ -193,6 +194,9 @@ size_t mlp_packed_bf16_elems();
 size_t mlp_packed_bias_elems();
 cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const void* feat, int n, float* mix,
                              float* raw, int sm_count, cudaStream_t st);
+cudaError_t launch_mlp_train_tc(const void* wpacked, const float* bpacked, const float* params, const void* feat,
+                                const float* dirs, const float* tgt, int n, float scale, float* grad, float* loss,
+                                int sm_count, cudaStream_t st);
 cudaError_t launch_mlp_train(const float* params, const void* feat, const float* dirs, const float* tgt, int n,
                              float scale, float* grad, float* loss, int sm_count, cudaStream_t st);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,

@@ -92,7 +92,7 @@ def test_mlp_inference_vs_oracle(env, orc):
 def test_mlp_gradient_and_adam_vs_oracle(env, orc):
     m, ctx = env
     p = _params(orc, 5)
-    prop = m.Proposal(ctx, params=p)
+    prop = m.Proposal(ctx, params=p, training=m.MCRT_TRAIN_FP32)
     try:
         n = 3000
         x = _features(n, 6)
@@ -114,6 +114,40 @@ def test_mlp_gradient_and_adam_vs_oracle(env, orc):
         pp = p.copy(); mm = np.zeros_like(p); vv = np.zeros_like(p)
         orc.adam_step(pp, mm, vv, g2.astype(np.float64), 1, lr=lr)
         np.testing.assert_allclose(newp, pp, rtol=1e-5, atol=1e-7)
+    finally:
+        prop.close()
+
+
+def test_mlp_gradient_on_tensor_cores(env, orc):
+    """The tensor-core gradient (BF16 operands and activations, FP32
+    accumulation) against the FP64 oracle on the same records.  Each
+    product carries BF16 rounding of both operands (relative 2^-8 each,
+    taken as 2^-8 combined after the FP32 sums), compounded over the
+    three hidden layers, so a few per cent of relative error in each
+    parameter block is the expected size: the test asks for a relative L2
+    error below 4 % per weight matrix, a cosine above 0.998 overall, and
+    the same loss to 1e-3 (the loss uses BF16 activations too)."""
+    m, ctx = env
+    p = _params(orc, 5)
+    prop = m.Proposal(ctx, params=p)            # tensor cores by default
+    try:
+        n = 3000
+        x = _features(n, 6)
+        r = np.random.default_rng(7)
+        d = r.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+        t = r.exponential(size=n)
+        t[::7] = 0.0
+        loss, g = prop.train_step(x, d.astype(np.float32), t.astype(np.float32), lr=0.0)
+        xb = bf16(x.astype(np.float64))
+        oloss, og = orc.mlp_loss_grad(p, xb, d.astype(np.float32).astype(np.float64),
+                                      t.astype(np.float32).astype(np.float64))
+        assert loss == pytest.approx(oloss, rel=1e-3)
+        offs = [0, 576, 640, 4736, 4800, 8896, 8960, 11520, 11560]
+        for a, b in zip(offs[:-1:2], offs[1::2]):
+            gg, oo = g[a:b].astype(np.float64), og[a:b]
+            assert np.linalg.norm(gg - oo) <= 0.04 * np.linalg.norm(oo), (a, np.linalg.norm(gg - oo) / np.linalg.norm(oo))
+        cos = float(g.astype(np.float64) @ og / (np.linalg.norm(g) * np.linalg.norm(og)))
+        assert cos > 0.998, cos
     finally:
         prop.close()
 
