@@ -72,6 +72,10 @@ class OrcScene(C.Structure):
         ("hmax", C.c_double),
         ("pyr_min", C.POINTER(C.c_float)),
         ("clear_phase", C.c_int32),
+        ("grid", C.c_int32),
+        ("oct_levels", C.c_int32),
+        ("oct", C.POINTER(C.c_float)),
+        ("oct_min", C.POINTER(C.c_float)),
     ]
 
 
@@ -107,6 +111,10 @@ def lib():
             L.orc_pyramid_size.restype = C.c_int64
             L.orc_build_pyramid.argtypes = [f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f32p]
             L.orc_build_pyramid_min.argtypes = [f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f32p]
+            L.orc_octree_dims.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+            L.orc_octree_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+            L.orc_octree_size.restype = C.c_int64
+            L.orc_build_octree.argtypes = [f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, f32p, f32p]
             L.orc_bf16_round_down.argtypes = [C.c_float]
             L.orc_bf16_round_down.restype = C.c_float
             L.orc_dda_spec.argtypes = [sp, f32p, f32p, C.c_int, i32p, f32p, i32p]
@@ -215,6 +223,43 @@ def build_pyramid_min(k_zyx: np.ndarray, levels: int, round_nearest_bf16: bool =
     return res
 
 
+def octree_levels(shape_xyz) -> int:
+    """Octree levels above the voxels up to the first level with one cell."""
+    L = 0
+    while (1 << L) < max(shape_xyz):
+        L += 1
+    return max(L, 1)
+
+
+def octree_dims(shape_xyz, level):
+    d = (C.c_int * 3)()
+    lib().orc_octree_dims(shape_xyz[0], shape_xyz[1], shape_xyz[2], level, d)
+    return (d[0], d[1], d[2])
+
+
+def build_octree(k_zyx: np.ndarray, levels: int, round_nearest_bf16: bool = False):
+    """The paper's octree (Sec. 3.1.1): per level 1..levels, the max and the
+    min over each aligned block of 2^L voxels per axis.  Returns two lists
+    of arrays [z][y][x]."""
+    k = np.ascontiguousarray(k_zyx, dtype=np.float32)
+    nz, ny, nx = k.shape
+    tot = lib().orc_octree_size(nx, ny, nz, levels)
+    mx = np.zeros(tot, dtype=np.float32)
+    mn = np.zeros(tot, dtype=np.float32)
+    rc = lib().orc_build_octree(_ptr(k, C.c_float), nx, ny, nz, levels, int(round_nearest_bf16),
+                                _ptr(mx, C.c_float), _ptr(mn, C.c_float))
+    if rc != 0:
+        raise ValueError("bad octree request")
+    rmax, rmin, off = [], [], 0
+    for l in range(1, levels + 1):
+        dx, dy, dz = octree_dims((nx, ny, nz), l)
+        n = dx * dy * dz
+        rmax.append(mx[off:off + n].reshape(dz, dy, dx))
+        rmin.append(mn[off:off + n].reshape(dz, dy, dx))
+        off += n
+    return rmax, rmin
+
+
 def bf16_round_down(x: float) -> float:
     return lib().orc_bf16_round_down(float(x))
 
@@ -257,6 +302,7 @@ class Scene:
     mis_alpha: float = 0.5
     heights: object = None        # heightfield ground [hny][hnx] float32 km (periodic), or None: flat
     clear_phase: int = 0          # clear-air phase function: 0 HG (the cloud's g), 1 Rayleigh
+    grid: int = 0                 # tracked grid: 0 the 8^L pyramid, 1 the paper's 2^L octree
     _keep: list = field(default_factory=list, repr=False)
 
     def sun_dir(self):
@@ -304,6 +350,17 @@ class Scene:
         s.n_learned = self.n_learned
         s.mis_alpha = self.mis_alpha
         s.clear_phase = self.clear_phase
+        s.grid = self.grid
+        if self.grid == 1:
+            ol = octree_levels((nx, ny, nz))
+            omax, omin = build_octree(np.ascontiguousarray(self.k, dtype=np.float32), ol,
+                                      round_nearest_bf16=bool(self.bf16))
+            fo = np.ascontiguousarray(np.concatenate([a.ravel() for a in omax]))
+            fm = np.ascontiguousarray(np.concatenate([a.ravel() for a in omin]))
+            self._keep += [fo, fm]
+            s.oct_levels = ol
+            s.oct = _ptr(fo, C.c_float)
+            s.oct_min = _ptr(fm, C.c_float)
         if self.heights is not None:
             hf = np.ascontiguousarray(self.heights, dtype=np.float32)
             self._keep.append(hf)

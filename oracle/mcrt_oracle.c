@@ -13,6 +13,9 @@
  *     definition; the method's random numbers come from it.
  *   - The majorant pyramid: exact max over 8^3 children, level by level
  *     (Sec. 3.1.1 "Construction": merged voxels store the max extinction).
+ *   - The paper's octree (Sec. 3.1.1: groups of 2^3 cells tested
+ *     recursively for merging): the max and min over every aligned 2^L
+ *     voxel block, taken straight from the voxels.
  *   - The leaf criterion of the hierarchical grid: a cell is used for tracking
  *     when the vertical optical depth bound M * h_z of the merged region is
  *     below the threshold tau~ (Sec. 4.2, list after the coarse-graining text).
@@ -232,6 +235,58 @@ int orc_build_pyramid_min(const float* k, int nx, int ny, int nz, int levels, in
     return 0;
 }
 
+/* The paper's octree (Sec. 3.1.1): a level-L cell covers an aligned block
+ * of 2^L voxels per axis (clipped at the field edges) and stores the max
+ * and the min extinction of the voxels it holds.  Written as that
+ * definition: every cell scans its voxels directly.  The stored values are
+ * those of the field the tracer reads: with round_nearest_bf16 != 0 each
+ * voxel is first rounded to nearest bfloat16, and both bounds are taken
+ * over the rounded values. */
+void orc_octree_dims(int nx, int ny, int nz, int level, int out[3])
+{
+    const int f = 1 << level;
+    out[0] = ceil_div(nx, f); out[1] = ceil_div(ny, f); out[2] = ceil_div(nz, f);
+}
+
+int64_t orc_octree_size(int nx, int ny, int nz, int levels)
+{
+    int64_t tot = 0;
+    for (int l = 1; l <= levels; ++l) {
+        int d[3]; orc_octree_dims(nx, ny, nz, l, d);
+        tot += (int64_t)d[0] * d[1] * d[2];
+    }
+    return tot;
+}
+
+int orc_build_octree(const float* k, int nx, int ny, int nz, int levels, int round_nearest_bf16, float* max_out,
+                     float* min_out)
+{
+    if (levels < 1 || levels > 30) return -1;
+    int64_t off = 0;
+    for (int l = 1; l <= levels; ++l) {
+        int d[3]; orc_octree_dims(nx, ny, nz, l, d);
+        const int f = 1 << l;
+        for (int cz = 0; cz < d[2]; ++cz)
+            for (int cy = 0; cy < d[1]; ++cy)
+                for (int cx = 0; cx < d[0]; ++cx) {
+                    float mx = 0.0f, mn = INFINITY;
+                    for (int z = f * cz; z < f * cz + f && z < nz; ++z)
+                        for (int y = f * cy; y < f * cy + f && y < ny; ++y)
+                            for (int x = f * cx; x < f * cx + f && x < nx; ++x) {
+                                float v = k[((int64_t)z * ny + y) * nx + x];
+                                if (round_nearest_bf16) v = orc_bf16_round_nearest(v);
+                                if (v > mx) mx = v;
+                                if (v < mn) mn = v;
+                            }
+                    const int64_t c = off + ((int64_t)cz * d[1] + cy) * d[0] + cx;
+                    max_out[c] = mx;
+                    min_out[c] = mn;
+                }
+        off += (int64_t)d[0] * d[1] * d[2];
+    }
+    return 0;
+}
+
 /* ===================================================================== */
 /* Scene description shared by the traversal and the estimators.          */
 /* ===================================================================== */
@@ -260,7 +315,14 @@ typedef struct {
     double hmax;               /* largest height                          */
     const float* pyr_min;      /* minorant levels 1..levels (layout of pyr), or NULL: 0 */
     int32_t clear_phase;       /* phase function of the clear-air part: 0 HG (g), 1 Rayleigh */
+    int32_t grid;              /* grid tracked: 0 the 8^L pyramid, 1 the 2^L octree */
+    int32_t oct_levels;        /* octree levels above the voxels (grid 1)  */
+    const float* oct;          /* octree maxima, levels 1..oct_levels concatenated */
+    const float* oct_min;      /* octree minima, same layout              */
 } orc_scene;
+
+/* Voxels per axis of a level-L cell of the tracked grid, as a shift. */
+static int cell_shift(const orc_scene* S, int L) { return S->grid == 1 ? L : 3 * L; }
 
 static const float* level_ptr(const orc_scene* S, int level, int dims[3])
 {
@@ -285,8 +347,11 @@ static float kvox(const orc_scene* S, const int v[3])
  * merged cell stores the max, Sec. 3.1.1.)  *m_out (may be NULL) receives
  * the leaf's minorant: the voxel itself for a voxel leaf, else the cell's
  * min rounded down to bfloat16 (the leaf map holds it in 16 bits). */
+static void leaf_of_m_octree(const orc_scene* S, const int v[3], int* lev_out, float* M_out, float* m_out);
+
 static void leaf_of_m(const orc_scene* S, const int v[3], int* lev_out, float* M_out, float* m_out)
 {
+    if (S->grid == 1) { leaf_of_m_octree(S, v, lev_out, M_out, m_out); return; }
     for (int L = S->levels; L > S->finest_level; --L) {
         int d[3];
         const float* P = level_ptr(S, L, d);
@@ -314,6 +379,31 @@ static void leaf_of_m(const orc_scene* S, const int v[3], int* lev_out, float* M
     if (m_out) *m_out = S->pyr_min ? orc_bf16_round_down(S->pyr_min[P - S->pyr + ci]) : 0.0f;
 }
 
+/* The same rule over the octree: the coarsest octree cell at a level >
+ * finest_level with M * h_z <= tau~, h_z = dz * 2^L (FP32 product). */
+static void leaf_of_m_octree(const orc_scene* S, const int v[3], int* lev_out, float* M_out, float* m_out)
+{
+    int64_t off[31];
+    off[1] = 0;
+    for (int L = 1; L < S->oct_levels; ++L) {
+        int d[3]; orc_octree_dims(S->nx, S->ny, S->nz, L, d);
+        off[L + 1] = off[L] + (int64_t)d[0] * d[1] * d[2];
+    }
+    for (int L = S->oct_levels; L >= S->finest_level && L >= 1; --L) {
+        int d[3]; orc_octree_dims(S->nx, S->ny, S->nz, L, d);
+        int64_t ci = off[L] + ((int64_t)(v[2] >> L) * d[1] + (v[1] >> L)) * d[0] + (v[0] >> L);
+        float M = S->oct[ci];
+        float hz = S->dz * (float)(1 << L);
+        if (L == S->finest_level || M * hz <= S->tau_merge) {
+            *lev_out = L; *M_out = M;
+            if (m_out) *m_out = orc_bf16_round_down(S->oct_min[ci]);
+            return;
+        }
+    }
+    *lev_out = 0; *M_out = kvox(S, v);
+    if (m_out) *m_out = *M_out;
+}
+
 static void leaf_of(const orc_scene* S, const int v[3], int* lev_out, float* M_out)
 {
     leaf_of_m(S, v, lev_out, M_out, NULL);
@@ -323,10 +413,11 @@ static void leaf_of(const orc_scene* S, const int v[3], int* lev_out, float* M_o
 static void cell_range(const orc_scene* S, int L, const int v[3], int lo[3], int hi[3])
 {
     const int n[3] = {S->nx, S->ny, S->nz};
+    const int s = cell_shift(S, L);
     for (int a = 0; a < 3; ++a) {
-        int c = v[a] >> (3 * L);
-        lo[a] = c << (3 * L);
-        int e = (c + 1) << (3 * L);
+        int c = v[a] >> s;
+        lo[a] = c << s;
+        int e = (c + 1) << s;
         hi[a] = (e < n[a] ? e : n[a]) - 1;
     }
 }
@@ -401,9 +492,9 @@ int orc_dda_spec(const orc_scene* S, const float o_in[3], const float d[3], int 
         float texit = ta[ax] > t ? ta[ax] : t;
         if (count >= cap) { *status = 3; return count; }
         cells[4 * count + 0] = L;
-        cells[4 * count + 1] = v[0] >> (3 * L);
-        cells[4 * count + 2] = v[1] >> (3 * L);
-        cells[4 * count + 3] = v[2] >> (3 * L);
+        cells[4 * count + 1] = v[0] >> cell_shift(S, L);
+        cells[4 * count + 2] = v[1] >> cell_shift(S, L);
+        cells[4 * count + 3] = v[2] >> cell_shift(S, L);
         tio[2 * count + 0] = tbase + t;
         tio[2 * count + 1] = tbase + texit;
         ++count;
@@ -507,7 +598,8 @@ int orc_dda_bruteforce(const orc_scene* S, const double o[3], const double d[3],
         leaf_of(S, v, &L, &M);
         /* a new record starts at every leaf change and at every periodic
          * wrap (the traversal restarts its segment there) */
-        int leaf[6] = {L, v[0] >> (3 * L), v[1] >> (3 * L), v[2] >> (3 * L), image[0], image[1]};
+        const int sh = cell_shift(S, L);
+        int leaf[6] = {L, v[0] >> sh, v[1] >> sh, v[2] >> sh, image[0], image[1]};
         if (count > 0 && memcmp(leaf, prev_leaf, sizeof(leaf)) == 0) {
             tio[2 * (count - 1) + 1] = tb;
         } else {
