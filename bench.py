@@ -629,11 +629,14 @@ def run_sweep(args):
 
 def run_tau(args):
     """The merge threshold sweep (Sec. 4.2, Sec. 5): the bench image traced
-    with leaves chosen at several tau~ (finest level 0 and 1); per point the
+    with leaves chosen at several tau~ (finest level 0 and 1), over the 8^L
+    pyramid and over the paper's 2^L octree (Sec. 3.1.1); per point the
     trace time and, from a counting run, the traversal work (leaf steps of
     flights and sun rays) and the collision work (tentative collisions, null
     ones among them) -- the paper's partition of the time between the
-    acceleration structure and null collisions."""
+    acceleration structure and null collisions.  tau~ = 0 (voxel leaves) and
+    infinity (one global cell) are the same leaves on both grids and are
+    run once."""
     import torch
     import paper_1902_01137_gb300 as m
     spec, cam = make_workload()
@@ -643,16 +646,25 @@ def run_tau(args):
     clocks = ClockSampler(0)
     clocks.start()
     try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc.build_octree()
+        torch.cuda.synchronize()
+        octree_build_ms = (time.perf_counter() - t0) * 1e3
         sc.trace_camera(cam, 4, seed=1)
-        for fin in (0, 1):
+        sc.trace_camera(cam, 4, seed=1, grid=m.MCRT_GRID_OCTREE)
+        for grid, fin in [(g, f) for g in (m.MCRT_GRID_PYRAMID, m.MCRT_GRID_OCTREE) for f in (0, 1)]:
             for tau in (0.0, 0.1, 0.3, 1.0, 3.0, 10.0, 100.0, float("inf")):
                 if fin == 1 and tau == 0.0:
                     continue
-                ms = [sc.trace_camera(cam, SPP, seed=10 + i, tau_merge=tau, finest_level=fin).kernel_ms
-                      for i in range(2)]
-                c = sc.trace_camera(cam, SPP, seed=10, tau_merge=tau, finest_level=fin, count_events=1).counters
+                if grid == m.MCRT_GRID_OCTREE and (tau == 0.0 or not math.isfinite(tau)):
+                    continue
+                kw = dict(tau_merge=tau, finest_level=fin, grid=grid)
+                ms = [sc.trace_camera(cam, SPP, seed=10 + i, **kw).kernel_ms for i in range(2)]
+                c = sc.trace_camera(cam, SPP, seed=10, count_events=1, **kw).counters
                 P = c["paths"]
-                points.append({"tau_merge": tau if math.isfinite(tau) else "inf", "finest_level": fin,
+                points.append({"grid": "octree 2^L" if grid == m.MCRT_GRID_OCTREE else "pyramid 8^L",
+                               "tau_merge": tau if math.isfinite(tau) else "inf", "finest_level": fin,
                                "ms": min(ms), "paths_per_s": W * H * SPP / (min(ms) / 1e3),
                                "leaf_steps_per_path": (c["leaf_steps"] + c["sun_leaf_steps"]) / P,
                                "tentative_per_path": (c["tentative"] + c["sun_tentative"]) / P,
@@ -663,7 +675,8 @@ def run_tau(args):
         ctx.close()
     clk = clocks.stop()
     print(json.dumps({"metric": METRIC, "workload": "tau~ sweep: " + WORKLOAD, "unit": "paths/s",
-                      "points": points, "clocks": clk, "data": "synthetic"}))
+                      "octree_build_ms": octree_build_ms, "points": points, "clocks": clk,
+                      "data": "synthetic"}))
     return 0
 
 

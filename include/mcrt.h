@@ -75,6 +75,12 @@ enum { MCRT_SUN_RATIO = 0, MCRT_SUN_DELTA = 1, MCRT_SUN_DECOMP = 2 };
  * molecules scatter by Rayleigh, droplets by Henyey-Greenstein). */
 enum { MCRT_PHASE_HG = 0, MCRT_PHASE_RAYLEIGH = 1 };
 
+/* Max grid a trace tracks through (mcrt_trace_opts.grid): the 8^L pyramid
+ * (level-L cells of 8^L voxels per axis), or the paper's octree (Sec.
+ * 3.1.1: groups of 2^3 cells merged recursively, level-L cells of 2^L
+ * voxels per axis), which mcrt_scene_build_octree must have built. */
+enum { MCRT_GRID_PYRAMID = 0, MCRT_GRID_OCTREE = 1 };
+
 /* Library version and the ABI version it was built with. */
 MCRT_API int mcrt_version(int32_t* abi_version);
 
@@ -159,6 +165,28 @@ MCRT_API int mcrt_scene_read_majorants(const mcrt_scene* scene, int32_t level, f
  * decomposition tracking (MCRT_SUN_DECOMP); the paper's octree keeps the
  * min beside the max (Sec. 3.1.1). */
 MCRT_API int mcrt_scene_read_minorants(const mcrt_scene* scene, int32_t level, float* host_out, size_t n);
+
+/* Build the paper's octree (Sec. 3.1.1) beside the pyramid: a level-L cell
+ * covers an aligned block of 2^L voxels per axis (clipped at the field
+ * edges) and holds the max and the min of the voxels it covers, as stored
+ * (for BF16 storage the nearest-bfloat16 values, so the max bounds exactly
+ * what the tracer reads).  `levels` >= 1 levels are built; 0 builds up to
+ * the first level with one cell.  Traces choose it with
+ * mcrt_trace_opts.grid = MCRT_GRID_OCTREE; its leaves follow the same
+ * tau~ rule with h_z = dz 2^L.  Device memory: about 8/7 x (cells of level
+ * 1) x 16 bytes (max, min and the leaf map).  Rebuilding replaces it.
+ * Errors: MCRT_ERR_ARG (levels < 0 or > 20), MCRT_ERR_OOM, MCRT_ERR_CUDA. */
+MCRT_API int mcrt_scene_build_octree(mcrt_scene* scene, int32_t levels);
+
+/* Octree levels built (0 if none), and the cells per axis of one level. */
+MCRT_API int mcrt_scene_octree_levels(const mcrt_scene* scene, int32_t* levels);
+MCRT_API int mcrt_scene_octree_dims(const mcrt_scene* scene, int32_t level, int32_t dims[3]);
+
+/* Copy level `level` (1..levels) of the octree, x fastest, into host
+ * memory: maxima into max_out and minima into min_out (either may be
+ * NULL).  `n` must be at least the level's cell count (else
+ * MCRT_ERR_BOUNDS); MCRT_ERR_STATE before mcrt_scene_build_octree. */
+MCRT_API int mcrt_scene_read_octree(const mcrt_scene* scene, int32_t level, float* max_out, float* min_out, size_t n);
 
 /* Flat Lambertian ground of albedo in [0, 1] (Sec. 4.1). */
 MCRT_API int mcrt_scene_set_ground_flat(mcrt_scene* scene, float albedo);
@@ -254,6 +282,8 @@ typedef struct {
                                /* MCRT_ERR_CANCELLED                            */
     int32_t batch_dalpha;      /* batches: 1 also estimates dT/dalpha (the 5th   */
                                /* quantity; 0 leaves it 0 and runs faster)      */
+    int32_t grid;              /* MCRT_GRID_PYRAMID (default) or                */
+                               /* MCRT_GRID_OCTREE: the max grid tracked        */
 } mcrt_trace_opts;
 
 /* Fill `opts` with the defaults listed above. */
@@ -461,6 +491,12 @@ MCRT_API int mcrt_proposal_set_training(mcrt_proposal* proposal, int32_t mode);
 MCRT_API int mcrt_debug_dda(const mcrt_scene* scene, const float o[3], const float d[3], float tau_merge,
                    int32_t finest_level, int32_t* cells, float* t_in_out, int32_t cap, int32_t* count,
                    int32_t* status);
+
+/* The same over a chosen grid (MCRT_GRID_PYRAMID or MCRT_GRID_OCTREE); a
+ * leaf's (level, ix, iy, iz) are then that grid's level and cell index. */
+MCRT_API int mcrt_debug_dda_grid(const mcrt_scene* scene, const float o[3], const float d[3], float tau_merge,
+                                 int32_t finest_level, int32_t grid, int32_t* cells, float* t_in_out, int32_t cap,
+                                 int32_t* count, int32_t* status);
 
 /* Heightfield checks (MCRT_ERR_STATE on a flat ground): t_out[i] = the
  * distance t along ray i, o + t d (host arrays of n x 3 floats), to its

@@ -40,6 +40,8 @@ MCRT_PHASE_HG = 0
 MCRT_PHASE_RAYLEIGH = 1
 MCRT_TRAIN_TENSOR = 0
 MCRT_TRAIN_FP32 = 1
+MCRT_GRID_PYRAMID = 0
+MCRT_GRID_OCTREE = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -80,7 +82,8 @@ class TraceOpts(C.Structure):
                 ("train_steps", C.c_int32),
                 ("deadline_ms", C.c_double),
                 ("cancel_flag", C.c_void_p),
-                ("batch_dalpha", C.c_int32)]
+                ("batch_dalpha", C.c_int32),
+                ("grid", C.c_int32)]
 
 
 _lib = None
@@ -110,6 +113,10 @@ def _load():
         "mcrt_scene_majorant_dims": [vp, i32, P(i32)],
         "mcrt_scene_read_majorants": [vp, i32, P(f32), C.c_size_t],
         "mcrt_scene_read_minorants": [vp, i32, P(f32), C.c_size_t],
+        "mcrt_scene_build_octree": [vp, i32],
+        "mcrt_scene_octree_levels": [vp, P(i32)],
+        "mcrt_scene_octree_dims": [vp, i32, P(i32)],
+        "mcrt_scene_read_octree": [vp, i32, P(f32), P(f32), C.c_size_t],
         "mcrt_scene_set_ground_flat": [vp, f32],
         "mcrt_scene_set_clear_sky_phase": [vp, i32],
         "mcrt_scene_set_ground_heightfield": [vp, vp, i32, i32, i32, f32],
@@ -127,6 +134,7 @@ def _load():
         "mcrt_tally_kernel_ms": [vp, P(f32)],
         "mcrt_tally_destroy": [vp],
         "mcrt_debug_dda": [vp, P(f32), P(f32), f32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
+        "mcrt_debug_dda_grid": [vp, P(f32), P(f32), f32, i32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
         "mcrt_trace_batch": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
         "mcrt_autotune_batch": [vp, P(BatchItem), i32, C.c_double, P(TraceOpts), P(f32)],
@@ -246,6 +254,31 @@ def mcrt_scene_read_minorants(ctx, scene, level: int) -> np.ndarray:
     return out.reshape(dz, dy, dx)
 
 
+def mcrt_scene_build_octree(ctx, scene, levels: int = 0):
+    _check(_load().mcrt_scene_build_octree(scene, levels), ctx)
+
+
+def mcrt_scene_octree_levels(scene) -> int:
+    v = C.c_int32()
+    _check(_load().mcrt_scene_octree_levels(scene, C.byref(v)))
+    return v.value
+
+
+def mcrt_scene_octree_dims(ctx, scene, level: int):
+    d = (C.c_int32 * 3)()
+    _check(_load().mcrt_scene_octree_dims(scene, level, d), ctx)
+    return (d[0], d[1], d[2])
+
+
+def mcrt_scene_read_octree(ctx, scene, level: int):
+    """(max, min) of octree level ``level``, each [z][y][x]."""
+    dx, dy, dz = mcrt_scene_octree_dims(ctx, scene, level)
+    mx = np.zeros(dx * dy * dz, dtype=np.float32)
+    mn = np.zeros(dx * dy * dz, dtype=np.float32)
+    _check(_load().mcrt_scene_read_octree(scene, level, _ptr(mx, C.c_float), _ptr(mn, C.c_float), mx.size), ctx)
+    return mx.reshape(dz, dy, dx), mn.reshape(dz, dy, dx)
+
+
 def mcrt_scene_set_clear_sky_phase(ctx, scene, phase: int):
     _check(_load().mcrt_scene_set_clear_sky_phase(scene, phase), ctx)
 
@@ -354,14 +387,15 @@ def mcrt_tally_destroy(tally):
     _check(_load().mcrt_tally_destroy(tally))
 
 
-def mcrt_debug_dda(ctx, scene, o, d, tau_merge=1.0, finest_level=1, cap=4096):
+def mcrt_debug_dda(ctx, scene, o, d, tau_merge=1.0, finest_level=1, cap=4096, grid=MCRT_GRID_PYRAMID):
     o32 = np.ascontiguousarray(o, dtype=np.float32)
     d32 = np.ascontiguousarray(d, dtype=np.float32)
     cells = np.zeros((cap, 4), dtype=np.int32)
     tio = np.zeros((cap, 2), dtype=np.float32)
     n, st = C.c_int32(), C.c_int32()
-    _check(_load().mcrt_debug_dda(scene, _ptr(o32, C.c_float), _ptr(d32, C.c_float), tau_merge, finest_level,
-                                  _ptr(cells, C.c_int32), _ptr(tio, C.c_float), cap, C.byref(n), C.byref(st)), ctx)
+    _check(_load().mcrt_debug_dda_grid(scene, _ptr(o32, C.c_float), _ptr(d32, C.c_float), tau_merge, finest_level,
+                                       grid, _ptr(cells, C.c_int32), _ptr(tio, C.c_float), cap, C.byref(n),
+                                       C.byref(st)), ctx)
     return cells[:n.value].copy(), tio[:n.value].copy(), st.value
 
 
@@ -462,6 +496,18 @@ class Scene:
     def minorants(self, level):
         return mcrt_scene_read_minorants(self.ctx.h, self.h, level)
 
+    def build_octree(self, levels=0):
+        """Build the paper's 2^L octree beside the pyramid (traces select it
+        with grid=MCRT_GRID_OCTREE)."""
+        mcrt_scene_build_octree(self.ctx.h, self.h, levels)
+
+    @property
+    def octree_levels(self):
+        return mcrt_scene_octree_levels(self.h)
+
+    def octree(self, level):
+        return mcrt_scene_read_octree(self.ctx.h, self.h, level)
+
     def set_heightfield(self, heights, albedo):
         mcrt_scene_set_ground_heightfield(self.ctx.h, self.h, heights, albedo)
 
@@ -471,8 +517,8 @@ class Scene:
     def terrain_height(self, xy):
         return mcrt_debug_terrain_height(self.ctx.h, self.h, xy)
 
-    def dda(self, o, d, tau_merge=1.0, finest_level=1, cap=4096):
-        return mcrt_debug_dda(self.ctx.h, self.h, o, d, tau_merge, finest_level, cap)
+    def dda(self, o, d, tau_merge=1.0, finest_level=1, cap=4096, grid=MCRT_GRID_PYRAMID):
+        return mcrt_debug_dda(self.ctx.h, self.h, o, d, tau_merge, finest_level, cap, grid)
 
     @staticmethod
     def _opts(**kw):

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI declared in include/mcrt.h: argument checks, device
 // memory ownership, launch configuration and status reporting.  Every device
 // step of the method runs in the kernels of majorant.cu and trace.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -76,7 +77,16 @@ DevScene make_dev_scene(const mcrt_scene* sc, float k_gas)
     S.Lper[1] = (float)sc->n[1] * sc->h[1];
     if (sc->storage == MCRT_STORAGE_BF16) S.vox16 = static_cast<const uint16_t*>(sc->d_vox);
     else S.vox = static_cast<const float*>(sc->d_vox);
-    S.leaf = sc->d_leaf;
+    // the leaf map last built (ensure_leaf) decides the grid tracked
+    if (sc->leaf_grid == MCRT_GRID_OCTREE && sc->oct_levels > 0) {
+        S.leaf = sc->d_oleaf;
+        S.lb = 1;
+        for (int a = 0; a < 3; ++a) S.nl[a] = sc->oct_dims[3 + a];
+    } else {
+        S.leaf = sc->d_leaf;
+        S.lb = 3;
+        for (int a = 0; a < 3; ++a) S.nl[a] = sc->nb[a];
+    }
     S.k_clear = sc->k_clear;
     S.ssa_clear = sc->ssa_clear;
     S.ssa_cloud = sc->ssa_cloud;
@@ -256,6 +266,8 @@ int mcrt_scene_destroy(mcrt_scene* sc)
     dfree(ctx, sc->d_vox);
     dfree(ctx, sc->d_pyr);
     dfree(ctx, sc->d_leaf);
+    dfree(ctx, sc->d_oct);
+    dfree(ctx, sc->d_oleaf);
     dfree(ctx, sc->d_hf);
     dfree(ctx, sc->d_hpyr);
     cudaStreamSynchronize(ctx->stream);
@@ -329,6 +341,96 @@ int mcrt_scene_read_minorants(const mcrt_scene* sc, int32_t level, float* host_o
     if (n < cells) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_scene_read_minorants: need %zu values", cells);
     CK(ctx, cudaMemcpyAsync(host_out, sc->d_pyr + sc->pyr_capacity + sc->lev_off[level], cells * sizeof(float),
                             cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MCRT_OK;
+}
+
+int mcrt_scene_build_octree(mcrt_scene* sc, int32_t levels)
+{
+    const char* who = "mcrt_scene_build_octree";
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "%s: NULL scene", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (levels < 0 || levels > kMaxGridLevels)
+        return fail(ctx, MCRT_ERR_ARG, "%s: levels %d not in [0, %d]", who, levels, kMaxGridLevels);
+    if (levels == 0) {
+        const int nmax = std::max(sc->n[0], std::max(sc->n[1], sc->n[2]));
+        levels = 1;
+        while (levels < kMaxGridLevels && (1 << levels) < nmax) ++levels;
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    std::vector<size_t> off(kMaxGridLevels + 2, 0);
+    std::vector<int> dims(3 * (kMaxGridLevels + 2), 0);
+    size_t tot = 0;
+    for (int L = 1; L <= levels; ++L) {
+        for (int a = 0; a < 3; ++a) dims[3 * L + a] = ceil_div(sc->n[a], 1 << L);
+        off[L] = tot;
+        tot += (size_t)dims[3 * L] * dims[3 * L + 1] * dims[3 * L + 2];
+    }
+    const size_t n1 = (size_t)dims[3] * dims[4] * dims[5];
+    // replace the previous octree (its leaf map goes with it)
+    if (sc->leaf_grid == MCRT_GRID_OCTREE) sc->leaf_valid = false;
+    dfree(ctx, sc->d_oct);
+    dfree(ctx, sc->d_oleaf);
+    sc->d_oct = nullptr;
+    sc->d_oleaf = nullptr;
+    sc->oct_levels = 0;
+    cudaError_t e = dalloc(ctx, &sc->d_oct, 2 * tot * sizeof(float));
+    if (e == cudaSuccess) e = dalloc(ctx, &sc->d_oleaf, n1 * sizeof(uint2));
+    if (e != cudaSuccess) {
+        dfree(ctx, sc->d_oct);
+        dfree(ctx, sc->d_oleaf);
+        sc->d_oct = nullptr;
+        sc->d_oleaf = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, "%s: %s", who,
+                    cudaGetErrorString(e));
+    }
+    sc->oct_off = off;
+    sc->oct_dims = dims;
+    sc->oct_capacity = tot;
+    sc->oct_levels = levels;
+    ctx->launches += (uint64_t)levels;
+    e = launch_octree(sc, make_dev_scene(sc, 0.0f), ctx->stream);
+    if (e != cudaSuccess) {
+        sc->oct_levels = 0;
+        return fail(ctx, MCRT_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
+    }
+    return MCRT_OK;
+}
+
+int mcrt_scene_octree_levels(const mcrt_scene* sc, int32_t* levels)
+{
+    if (!sc || !levels) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_octree_levels: NULL argument");
+    *levels = sc->oct_levels;
+    return MCRT_OK;
+}
+
+int mcrt_scene_octree_dims(const mcrt_scene* sc, int32_t level, int32_t dims[3])
+{
+    if (!sc || !dims) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_octree_dims: NULL argument");
+    if (sc->oct_levels == 0) return fail(sc->ctx, MCRT_ERR_STATE, "mcrt_scene_octree_dims: octree not built");
+    if (level < 1 || level > sc->oct_levels)
+        return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_octree_dims: level %d not in [1, %d]", level, sc->oct_levels);
+    for (int a = 0; a < 3; ++a) dims[a] = sc->oct_dims[3 * level + a];
+    return MCRT_OK;
+}
+
+int mcrt_scene_read_octree(const mcrt_scene* sc, int32_t level, float* max_out, float* min_out, size_t n)
+{
+    const char* who = "mcrt_scene_read_octree";
+    if (!sc) return fail(nullptr, MCRT_ERR_ARG, "%s: NULL scene", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (sc->oct_levels == 0) return fail(ctx, MCRT_ERR_STATE, "%s: octree not built", who);
+    if (level < 1 || level > sc->oct_levels)
+        return fail(ctx, MCRT_ERR_ARG, "%s: level %d not in [1, %d]", who, level, sc->oct_levels);
+    const size_t cells = (size_t)sc->oct_dims[3 * level] * sc->oct_dims[3 * level + 1] * sc->oct_dims[3 * level + 2];
+    if (n < cells) return fail(ctx, MCRT_ERR_BOUNDS, "%s: need %zu values", who, cells);
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (max_out)
+        CK(ctx, cudaMemcpyAsync(max_out, sc->d_oct + sc->oct_off[level], cells * sizeof(float), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+    if (min_out)
+        CK(ctx, cudaMemcpyAsync(min_out, sc->d_oct + sc->oct_capacity + sc->oct_off[level], cells * sizeof(float),
+                                cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return MCRT_OK;
 }
@@ -476,17 +578,21 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
             return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a proposal with Rayleigh clear air", who);
     }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
+    if (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE) return fail(ctx, MCRT_ERR_ARG, "%s: bad grid", who);
+    if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
+        return fail(ctx, MCRT_ERR_STATE, "%s: octree not built (mcrt_scene_build_octree)", who);
     return MCRT_OK;
 }
 
-int ensure_leaf(mcrt_scene* sc, float tau, int finest)
+int ensure_leaf(mcrt_scene* sc, float tau, int finest, int grid)
 {
     mcrt_ctx* ctx = sc->ctx;
-    if (sc->leaf_valid && sc->leaf_tau == tau && sc->leaf_finest == finest) return MCRT_OK;
-    LAUNCH(ctx, launch_leafmap(sc, tau, finest, ctx->stream));
+    if (sc->leaf_valid && sc->leaf_tau == tau && sc->leaf_finest == finest && sc->leaf_grid == grid) return MCRT_OK;
+    LAUNCH(ctx, launch_leafmap(sc, tau, finest, grid, ctx->stream));
     sc->leaf_valid = true;
     sc->leaf_tau = tau;
     sc->leaf_finest = finest;
+    sc->leaf_grid = grid;
     return MCRT_OK;
 }
 
@@ -744,7 +850,7 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
     u[2] = r[0] * f[1] - r[1] * f[0];
     const int ncells = cam->width * cam->height;
     CK(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+    rc = ensure_leaf(sc, o->tau_merge, o->finest_level, o->grid);
     if (rc) return rc;
     rc = get_tally(ctx, ncells, 1, tally, who);
     if (rc) return rc;
@@ -799,7 +905,7 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
     if (rc) return rc;
     if (npaths < 1) return fail(ctx, MCRT_ERR_ARG, "%s: npaths must be >= 1", who);
     CK(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+    rc = ensure_leaf(sc, o->tau_merge, o->finest_level, o->grid);
     if (rc) return rc;
     rc = get_tally(ctx, 1, 3, tally, who);
     if (rc) return rc;
@@ -864,7 +970,7 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
         if (i > 0 && (sc->storage == MCRT_STORAGE_BF16) != bf16)
             return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: items mix FP32 and BF16 storage", who);
         bf16 = sc->storage == MCRT_STORAGE_BF16;
-        rc = ensure_leaf(sc, o->tau_merge, o->finest_level);
+        rc = ensure_leaf(sc, o->tau_merge, o->finest_level, o->grid);
         if (rc) return rc;
         h[i].S = make_dev_scene(sc, it.k_gas);
         const double z = it.sun_zenith_deg * M_PI / 180.0, a = it.sun_azimuth_deg * M_PI / 180.0;
@@ -1260,6 +1366,12 @@ int mcrt_tally_destroy(mcrt_tally* t)
 int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], float tau, int32_t finest,
                    int32_t* cells, float* tio, int32_t cap, int32_t* count, int32_t* status)
 {
+    return mcrt_debug_dda_grid(sc_c, o, d, tau, finest, MCRT_GRID_PYRAMID, cells, tio, cap, count, status);
+}
+
+int mcrt_debug_dda_grid(const mcrt_scene* sc_c, const float o[3], const float d[3], float tau, int32_t finest,
+                        int32_t grid, int32_t* cells, float* tio, int32_t cap, int32_t* count, int32_t* status)
+{
     mcrt_scene* sc = const_cast<mcrt_scene*>(sc_c);
     if (!sc || !o || !d || !cells || !tio || !count || !status)
         return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "mcrt_debug_dda: NULL argument");
@@ -1269,6 +1381,7 @@ int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], f
     mcrt_trace_opts_default(&op);
     op.tau_merge = tau;
     op.finest_level = finest;
+    op.grid = grid;
     int rc = check_opts(sc, &op, "mcrt_debug_dda");
     if (rc) return rc;
     const float n2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -1276,7 +1389,7 @@ int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], f
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(o[a])) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_dda: bad origin");
     CK(ctx, cudaSetDevice(ctx->device));
-    rc = ensure_leaf(sc, tau, finest);
+    rc = ensure_leaf(sc, tau, finest, grid);
     if (rc) return rc;
     int* dcells = nullptr;
     float* dtio = nullptr;

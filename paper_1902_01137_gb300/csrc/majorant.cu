@@ -8,10 +8,14 @@
 // K1 (reduce_level): level L >= 2 cells take the exact max of their (up to)
 // 8x8x8 children (Sec. 3.1.1: merged voxels store the max).  Max is exact and
 // order-free, so the result is bit-identical to any other evaluation order.
-// Leaf map: for each level-1 cell, the coarsest ancestor whose majorant times
-// its height is <= tau~ (Sec. 4.2's merge criterion), with its majorant and
-// its minorant (the min pyramid, built alongside the max: the paper's octree
-// keeps both, Sec. 3.1.1).
+// Octree (oct_level1, oct_reduce2): the paper's own grid, Sec. 3.1.1 --
+// groups of 2^3 cells merged recursively, each cell keeping the max and the
+// min of the voxels it covers.  Level 1 reads the stored voxels (bricks);
+// level L >= 2 reduces 2^3 cells of level L - 1.
+// Leaf map (either grid): for each level-1 cell, the coarsest ancestor whose
+// majorant times its height is <= tau~ (Sec. 4.2's merge criterion), with
+// its majorant, its minorant (the min levels, built alongside the max) and
+// its size as a voxel shift.
 #include <cuda_bf16.h>
 
 #include "mcrt_internal.h"
@@ -135,38 +139,88 @@ __global__ void __launch_bounds__(256) reduce_level_kernel(const float* __restri
 }
 
 struct LevelTable {
-    const float* p[9];
-    const float* pmin[9];
-    int dims[9][3];
-    float hz[9];
+    const float* p[kMaxGridLevels + 1];
+    const float* pmin[kMaxGridLevels + 1];
+    int dims[kMaxGridLevels + 1][3];
+    float hz[kMaxGridLevels + 1];
 };
 
 // Leaf of each level-1 cell: search from the top level down to finest + 1.
-__global__ void __launch_bounds__(256) leafmap_kernel(LevelTable T, int levels, int finest, float tau,
+// lb: log2 of the branching per axis (3 pyramid, 1 octree); a level-L cell
+// spans 2^(lb L) voxels per axis, which is the shift the entry records.
+__global__ void __launch_bounds__(256) leafmap_kernel(LevelTable T, int levels, int finest, float tau, int lb,
                                                       int n1x, int n1y, int n1z, uint2* __restrict__ leaf)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n1x * n1y * n1z) return;
     const int cx = (int)(i % n1x), cy = (int)((i / n1x) % n1y), cz = (int)(i / ((long long)n1x * n1y));
     for (int L = levels; L > finest; --L) {
-        const int s = 3 * (L - 1);
+        const int s = lb * (L - 1);
         const int ax = cx >> s, ay = cy >> s, az = cz >> s;
         const size_t c = ((size_t)az * T.dims[L][1] + ay) * T.dims[L][0] + ax;
         const float M = T.p[L][c];
         if (__fmul_rn(M, T.hz[L]) <= tau) {
-            // .y: the minorant rounded down to bfloat16 (high half) | the level
-            leaf[i] = make_uint2(__float_as_uint(M), (__float_as_uint(T.pmin[L][c]) & 0xFFFF0000u) | (unsigned)L);
+            // .y: the minorant rounded down to bfloat16 (high half) | the shift
+            leaf[i] = make_uint2(__float_as_uint(M),
+                                 (__float_as_uint(T.pmin[L][c]) & 0xFFFF0000u) | (unsigned)(lb * L));
             return;
         }
     }
     if (finest == 0) {
         leaf[i] = make_uint2(0u, 0u);
     } else {
-        const int s = 3 * (finest - 1);
+        const int s = lb * (finest - 1);
         const size_t c = ((size_t)(cz >> s) * T.dims[finest][1] + (cy >> s)) * T.dims[finest][0] + (cx >> s);
         const float M = T.p[finest][c];
-        leaf[i] = make_uint2(__float_as_uint(M), (__float_as_uint(T.pmin[finest][c]) & 0xFFFF0000u) | (unsigned)finest);
+        leaf[i] = make_uint2(__float_as_uint(M),
+                             (__float_as_uint(T.pmin[finest][c]) & 0xFFFF0000u) | (unsigned)(lb * finest));
     }
+}
+
+// Octree level 1: max and min of each 2^3 voxel group, read from the bricks
+// (the stored values: FP32, or the nearest-bfloat16 voxels of a BF16 field,
+// whose max bounds exactly what the tracer reads).
+template <bool BF16>
+__global__ void __launch_bounds__(256) oct_level1_kernel(DevScene S, int dx, int dy, int dz, float* __restrict__ omax,
+                                                         float* __restrict__ omin)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)dx * dy * dz) return;
+    const int cx = (int)(i % dx), cy = (int)((i / dx) % dy), cz = (int)(i / ((long long)dx * dy));
+    float m = 0.0f, mn = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int x = 2 * cx + (c & 1), y = 2 * cy + ((c >> 1) & 1), z = 2 * cz + (c >> 2);
+        if (x < S.n[0] && y < S.n[1] && z < S.n[2]) {
+            const float v = kfetch<BF16>(S, x, y, z);
+            m = fmaxf(m, v);
+            mn = fminf(mn, v);
+        }
+    }
+    omax[i] = m;
+    omin[i] = mn;
+}
+
+// Octree level L >= 2: max and min over the (up to) 2^3 children.
+__global__ void __launch_bounds__(256) oct_reduce2_kernel(const float* __restrict__ pmax, const float* __restrict__ pmin,
+                                                          int px, int py, int pz, float* __restrict__ omax,
+                                                          float* __restrict__ omin, int dx, int dy, int dz)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)dx * dy * dz) return;
+    const int cx = (int)(i % dx), cy = (int)((i / dx) % dy), cz = (int)(i / ((long long)dx * dy));
+    float m = 0.0f, mn = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int x = 2 * cx + (c & 1), y = 2 * cy + ((c >> 1) & 1), z = 2 * cz + (c >> 2);
+        if (x < px && y < py && z < pz) {
+            const size_t j = ((size_t)z * py + y) * (size_t)px + x;
+            m = fmaxf(m, pmax[j]);
+            mn = fminf(mn, pmin[j]);
+        }
+    }
+    omax[i] = m;
+    omin[i] = mn;
 }
 
 }  // namespace
@@ -200,18 +254,52 @@ cudaError_t launch_reduce_level(const float* prev, const int* pd, float* out, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st)
+cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, int grid, cudaStream_t st)
 {
     LevelTable T{};
-    for (int L = 1; L <= sc->levels && L < 9; ++L) {
-        T.p[L] = sc->d_pyr + sc->lev_off[L];
-        T.pmin[L] = sc->d_pyr + sc->pyr_capacity + sc->lev_off[L];
-        for (int a = 0; a < 3; ++a) T.dims[L][a] = sc->lev_dims[3 * L + a];
-        T.hz[L] = sc->h[2] * (float)(1 << (3 * L));
+    const bool oct = grid == MCRT_GRID_OCTREE;
+    const int levels = oct ? sc->oct_levels : sc->levels;
+    const int lb = oct ? 1 : 3;
+    if (levels < 1 || levels > kMaxGridLevels) return cudaErrorInvalidValue;
+    for (int L = 1; L <= levels; ++L) {
+        if (oct) {
+            T.p[L] = sc->d_oct + sc->oct_off[L];
+            T.pmin[L] = sc->d_oct + sc->oct_capacity + sc->oct_off[L];
+            for (int a = 0; a < 3; ++a) T.dims[L][a] = sc->oct_dims[3 * L + a];
+        } else {
+            T.p[L] = sc->d_pyr + sc->lev_off[L];
+            T.pmin[L] = sc->d_pyr + sc->pyr_capacity + sc->lev_off[L];
+            for (int a = 0; a < 3; ++a) T.dims[L][a] = sc->lev_dims[3 * L + a];
+        }
+        T.hz[L] = sc->h[2] * (float)(1 << (lb * L));
     }
-    const long long n1 = (long long)sc->nb[0] * sc->nb[1] * sc->nb[2];
-    leafmap_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(T, sc->levels, finest, tau, sc->nb[0], sc->nb[1],
-                                                                   sc->nb[2], sc->d_leaf);
+    const int* n1 = oct ? &sc->oct_dims[3] : sc->nb;
+    const long long cells = (long long)n1[0] * n1[1] * n1[2];
+    leafmap_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(T, levels, finest, tau, lb, n1[0], n1[1], n1[2],
+                                                                      oct ? sc->d_oleaf : sc->d_leaf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_octree(const mcrt_scene* sc, const DevScene& S, cudaStream_t st)
+{
+    const int* d1 = &sc->oct_dims[3];
+    const long long n1 = (long long)d1[0] * d1[1] * d1[2];
+    float* mx = sc->d_oct;
+    float* mn = sc->d_oct + sc->oct_capacity;
+    if (sc->storage == MCRT_STORAGE_BF16)
+        oct_level1_kernel<true><<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(S, d1[0], d1[1], d1[2], mx + sc->oct_off[1],
+                                                                              mn + sc->oct_off[1]);
+    else
+        oct_level1_kernel<false><<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(S, d1[0], d1[1], d1[2],
+                                                                               mx + sc->oct_off[1], mn + sc->oct_off[1]);
+    for (int L = 2; L <= sc->oct_levels; ++L) {
+        const int* pd = &sc->oct_dims[3 * (L - 1)];
+        const int* d = &sc->oct_dims[3 * L];
+        const long long n = (long long)d[0] * d[1] * d[2];
+        oct_reduce2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            mx + sc->oct_off[L - 1], mn + sc->oct_off[L - 1], pd[0], pd[1], pd[2], mx + sc->oct_off[L],
+            mn + sc->oct_off[L], d[0], d[1], d[2]);
+    }
     return cudaGetLastError();
 }
 

@@ -2,9 +2,11 @@
 //
 //  * Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
 //    per-(path, event, stream) draw sequence.
-//  * The FP32 leaf traversal over the majorant pyramid: the ray steps from
-//    leaf to leaf, a leaf being the coarsest pyramid cell whose majorant times
-//    its height is <= tau~ (Sec. 4.2), or a cell of the finest tracked level.
+//  * The FP32 leaf traversal over a max grid -- the 8^L pyramid or the
+//    paper's 2^L octree (Sec. 3.1.1): the ray steps from leaf to leaf, a leaf
+//    being the coarsest grid cell whose majorant times its height is <= tau~
+//    (Sec. 4.2), or a cell of the finest tracked level.  A leaf is an aligned
+//    block of 2^s voxels per axis; the traversal only sees s.
 //    Every operation is an explicitly rounded IEEE binary32 operation, so the
 //    leaf sequence and distances are reproducible bit for bit.
 //  * Henyey-Greenstein sampling/evaluation and direction frames (Sec. 4.1).
@@ -64,6 +66,7 @@ __device__ __forceinline__ uint4 draw_block(unsigned long long path, uint32_t c2
 // Scene as seen by the kernels
 // --------------------------------------------------------------------------
 constexpr int kMaxHfLevels = 12;
+constexpr int kMaxGridLevels = 20;   // octree levels for fields up to 2^20 voxels per axis
 
 struct DevScene {
     int n[3];            // voxels per axis
@@ -73,7 +76,9 @@ struct DevScene {
     int nb[3];           // bricks (8^3 voxels) per axis == level-1 cells
     const float* __restrict__ vox;       // brick-major FP32 field, or null
     const uint16_t* __restrict__ vox16;  // brick-major BF16 field, or null
-    const uint2* __restrict__ leaf;      // per level-1 cell: {majorant bits, leaf level}
+    const uint2* __restrict__ leaf;      // per level-1 cell: {majorant bits, minorant | leaf shift}
+    int lb;              // log2 of the grid's branching per axis: 3 (8^L pyramid) or 1 (2^L octree)
+    int nl[3];           // level-1 cells per axis of the tracked grid (leaf-map dims)
     float k_clear, ssa_clear, ssa_cloud, g;
     float k_gas;         // extra uniform pure absorber
     float albedo;        // Lambertian ground
@@ -117,7 +122,7 @@ struct Ray {
     float d[3];      // unit direction
     float inv_d[3];  // 1 / d (0 where d == 0)
     int v[3];        // voxel of the current point
-    int lev;         // leaf level
+    int lev;         // leaf size as a shift: the leaf spans 2^lev voxels per axis
     float M;         // leaf majorant (+ k_gas)
     float mn;        // leaf minorant (+ k_gas)
     float t;         // distance of the current point from o
@@ -127,10 +132,10 @@ struct Ray {
 };
 
 // Voxel range [lo, hi] of the current leaf on axis a.
-__device__ __forceinline__ int leaf_lo(const Ray& R, int a) { return (R.v[a] >> (3 * R.lev)) << (3 * R.lev); }
+__device__ __forceinline__ int leaf_lo(const Ray& R, int a) { return (R.v[a] >> R.lev) << R.lev; }
 __device__ __forceinline__ int leaf_hi(const DevScene& S, const Ray& R, int a)
 {
-    return min(leaf_lo(R, a) + (1 << (3 * R.lev)), S.n[a]) - 1;
+    return min(leaf_lo(R, a) + (1 << R.lev), S.n[a]) - 1;
 }
 
 // Voxel of coordinate p on one axis: floor(p / h) by the rounded reciprocal,
@@ -142,24 +147,25 @@ __device__ __forceinline__ int locate(float p, float d, float h, float inv_h, in
     return min(max(i, lo), hi);
 }
 
-// Leaf-map entry of the level-1 cell holding voxel v.
+// Leaf-map entry of the level-1 cell (of the tracked grid) holding voxel v.
 __device__ __forceinline__ const uint2* leaf_entry(const DevScene& S, const int v[3])
 {
-    return S.leaf + ((size_t)(v[2] >> 3) * S.nb[1] + (v[1] >> 3)) * S.nb[0] + (v[0] >> 3);
+    const int b = S.lb;
+    return S.leaf + ((size_t)(v[2] >> b) * S.nl[1] + (v[1] >> b)) * S.nl[0] + (v[0] >> b);
 }
 
-// Finish entering the leaf holding R.v from its leaf-map entry: level,
+// Finish entering the leaf holding R.v from its leaf-map entry: size,
 // majorant and the exit distance / axis.
 template <bool BF16>
 __device__ __forceinline__ void finish_leaf(const DevScene& S, Ray& R, uint2 e)
 {
-    // entry: .x majorant bits, .y = minorant rounded down to bfloat16 | level
+    // entry: .x majorant bits, .y = minorant rounded down to bfloat16 | shift
     R.lev = (int)(e.y & 0xFFFFu);
     float M = __uint_as_float(e.x), mn = __uint_as_float(e.y & 0xFFFF0000u);
     if (R.lev == 0) M = mn = kfetch<BF16>(S, R.v[0], R.v[1], R.v[2]);
     R.M = __fadd_rn(M, S.k_gas);
     R.mn = __fadd_rn(mn, S.k_gas);
-    const int s = 3 * R.lev;
+    const int s = R.lev;
     float ta[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -205,7 +211,7 @@ enum StepResult { kInside = 0, kTop = 1, kGround = 2 };
 // index instead steps across the face (hi + 1 or lo - 1).
 __device__ __forceinline__ void advance(const DevScene& S, const Ray& R, float tn, bool face, float p[3], int nv[3])
 {
-    const int s = 3 * R.lev;
+    const int s = R.lev;
     int lo[3], hi[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {

@@ -35,11 +35,20 @@ struct mcrt_scene {
     size_t pyr_capacity = 0;          // floats allocated
     std::vector<size_t> lev_off;      // offset of level L (index L), floats
     std::vector<int> lev_dims;        // 3 ints per level (index 3L)
-    // leaf map for one (tau~, finest level)
+    // the paper's octree (built on request): 2^L voxels per cell and axis
+    int oct_levels = 0;               // built levels (0 = none)
+    float* d_oct = nullptr;           // max levels, then the min levels at + oct_capacity
+    size_t oct_capacity = 0;
+    std::vector<size_t> oct_off;      // offset of level L (index L), floats
+    std::vector<int> oct_dims;        // 3 ints per level (index 3L)
+    uint2* d_oleaf = nullptr;         // leaf map over the octree's level-1 cells
+    // leaf map for one (tau~, finest level, grid); d_leaf serves the
+    // pyramid, d_oleaf the octree
     uint2* d_leaf = nullptr;
     bool leaf_valid = false;
     float leaf_tau = 0;
     int leaf_finest = -1;
+    int leaf_grid = MCRT_GRID_PYRAMID;
     float albedo = 0;
     int clear_phase = 0;              // MCRT_PHASE_HG or MCRT_PHASE_RAYLEIGH
     float sun_zenith = 0, sun_azimuth = 0;
@@ -166,7 +175,8 @@ enum Sensor { kCamera = 0, kFlux = 1 };
 cudaError_t launch_relayout(const float* src, const mcrt_scene* sc, cudaStream_t st);
 cudaError_t launch_reduce_level(const float* prev, const int* prev_dims, float* out, const int* dims, bool min_level,
                                 cudaStream_t st);
-cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, cudaStream_t st);
+cudaError_t launch_leafmap(const mcrt_scene* sc, float tau, int finest, int grid, cudaStream_t st);
+cudaError_t launch_octree(const mcrt_scene* sc, const DevScene& S, cudaStream_t st);
 cudaError_t launch_hf_pyramid(const float* h, int nx, int ny, float* pyr, const int* off, int levels, cudaStream_t st);
 cudaError_t launch_hf_check(const float* h, long long n, float top, int* bad, cudaStream_t st);
 cudaError_t launch_debug_terrain(const DevScene& S, const float* o, const float* d, int n, float* t, cudaStream_t st);

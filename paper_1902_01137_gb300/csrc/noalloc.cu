@@ -97,8 +97,10 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     if (!(o->tau_merge >= 0.0f) || o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels ||
         o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA && o->sun_mode != MCRT_SUN_DECOMP) || o->block_size < 0 ||
         o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
-        o->rare_batch < 0 || o->rare_batch > 32)
+        o->rare_batch < 0 || o->rare_batch > 32 || (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE))
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);
+    if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
+        return nfail(ctx, MCRT_ERR_STATE, "%s: octree not built", who);
     if (o->proposal) return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the learned proposal needs work buffers", who);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return nfail(ctx, MCRT_ERR_ARG, "%s: device index too large", who);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -134,14 +136,16 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     u[1] = r[2] * f[0] - r[0] * f[2];
     u[2] = r[0] * f[1] - r[1] * f[0];
 
-    // the leaf map of this (tau~, finest level); rebuilt in place, no allocation
-    if (!(sc->leaf_valid && sc->leaf_tau == o->tau_merge && sc->leaf_finest == o->finest_level)) {
+    // the leaf map of this (tau~, finest level, grid); rebuilt in place, no allocation
+    if (!(sc->leaf_valid && sc->leaf_tau == o->tau_merge && sc->leaf_finest == o->finest_level &&
+          sc->leaf_grid == o->grid)) {
         ctx->launches++;
-        e = launch_leafmap(sc, o->tau_merge, o->finest_level, ctx->stream);
+        e = launch_leafmap(sc, o->tau_merge, o->finest_level, o->grid, ctx->stream);
         if (e != cudaSuccess) return nfail(ctx, MCRT_ERR_CUDA, "%s: leaf map: %s", who, cudaGetErrorString(e));
         sc->leaf_valid = true;
         sc->leaf_tau = o->tau_merge;
         sc->leaf_finest = o->finest_level;
+        sc->leaf_grid = o->grid;
     }
 
     // clear what must start at zero: the work state, counters and the sums

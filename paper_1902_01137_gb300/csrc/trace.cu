@@ -834,10 +834,10 @@ __global__ void debug_dda_kernel(DevScene S, float ox, float oy, float oz, float
     int n = 0, status = 0;
     for (;;) {
         if (n >= cap) { status = 3; break; }
-        cells[4 * n + 0] = R.lev;
-        cells[4 * n + 1] = R.v[0] >> (3 * R.lev);
-        cells[4 * n + 2] = R.v[1] >> (3 * R.lev);
-        cells[4 * n + 3] = R.v[2] >> (3 * R.lev);
+        cells[4 * n + 0] = R.lev / S.lb;      // level of the tracked grid
+        cells[4 * n + 1] = R.v[0] >> R.lev;
+        cells[4 * n + 2] = R.v[1] >> R.lev;
+        cells[4 * n + 3] = R.v[2] >> R.lev;
         tio[2 * n + 0] = __fadd_rn(tbase, R.t);
         tio[2 * n + 1] = __fadd_rn(tbase, R.texit);
         ++n;
