@@ -202,6 +202,14 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def ctx_octree_levels(spec) -> int:
+    n = max(spec.shape_xyz)
+    L = 1
+    while (1 << L) < n:
+        L += 1
+    return L
+
+
 def run_gpu(args):
     import torch
     import paper_1902_01137_gb300 as m
@@ -283,6 +291,47 @@ def run_gpu(args):
     paths_per_step = W * H * SPP
     value = world * paths_per_step * args.steps / (total_ms / 1e3)
 
+    # the same steps over the paper's 2^L octree (Sec. 3.1.1), built in each
+    # step beside the pyramid, leaves at tau~ = 1 with 2^3-voxel cells as the
+    # finest level; timed like the steps above
+    oopts = m.mcrt_trace_opts_default()
+    oopts.grid = m.MCRT_GRID_OCTREE
+    oopts.finest_level = 1
+
+    def octree_step(seed, k):
+        sc = new_scene(k)
+        try:
+            sc.build_octree()
+            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, seed, oopts, tally[0])
+            tally[0] = t
+            return m.mcrt_tally_kernel_ms(ctx.h, t)
+        finally:
+            sc.close()
+
+    octree = None
+    if not args.no_octree:
+        for i in range(args.warmup):
+            octree_step(base_seed + 300 + i, k_dev)
+        torch.cuda.synchronize()
+        oct_step_ms, oct_kern_ms = [], []
+        for i in range(args.steps):
+            flush_buf.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            oct_kern_ms.append(octree_step(base_seed + 100 + i, k_dev))
+            e1.record(stream)
+            e1.synchronize()
+            oct_step_ms.append(e0.elapsed_time(e1))
+        oct_total = sum(oct_step_ms)
+        if world > 1:
+            from paper_1902_01137_gb300 import shard
+            oct_total = shard.max_over_ranks(oct_total)
+        octree = {"value": world * paths_per_step * args.steps / (oct_total / 1e3), "unit": "paths/s",
+                  "ms_per_step": oct_total / args.steps, "kernel_ms": statistics.mean(oct_kern_ms),
+                  "grid": "2^L octree (Sec. 3.1.1), %d levels, tau~ 1, finest level 1" % ctx_octree_levels(spec),
+                  "steps": args.steps, "l2": "flushed between steps"}
+
     # e2e: pinned host field in, image mean/SE out, through the C ABI
     e2e_val = None
     h2d = spec.k.nbytes
@@ -334,6 +383,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_val, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk,
             "collision_events_per_s": events / (kavg / 1e3),
+            "octree": octree,
             "fom": fom,
             "counters": cnt}
     if rank == 0:
@@ -440,12 +490,18 @@ def run_batch(args):
         s_.close()
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(fields, seed_off):
+    def step(fields, seed_off, octree=False):
         scs = make_scenes(fields)
         try:
+            kw = dict(shape)
+            if octree:
+                # the paper's 2^L octree (Sec. 3.1.1) per field, finest leaves 2^3 voxels
+                for s_ in scs:
+                    s_.build_octree()
+                kw.update(grid=m.MCRT_GRID_OCTREE, finest_level=1)
             its = [(scs[i], kg, z, a, n, seed + seed_off)
                    for i, (_, kg, z, a, n, seed) in zip(_item_instance(inst), items)]
-            r = m.trace_batch(ctx, its, **shape)
+            r = m.trace_batch(ctx, its, **kw)
         finally:
             for s_ in scs:
                 s_.close()
@@ -479,6 +535,30 @@ def run_batch(args):
         total_ms = shard.max_over_ranks(total_ms)
     clk = clocks.stop()
     value = world * paths * args.steps / (total_ms / 1e3)
+    octree = None
+    if not args.no_octree:
+        for i in range(args.warmup):
+            step(dev_fields, 3000 * (rank + 1) + i, octree=True)
+        torch.cuda.synchronize()
+        o_ms, o_kern = [], []
+        for i in range(args.steps):
+            flush_buf.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step(dev_fields, 1000 * (rank + 1) + 100 + i, octree=True)
+            e1.record(stream)
+            e1.synchronize()
+            o_ms.append(e0.elapsed_time(e1))
+            o_kern.append(r.kernel_ms)
+        o_total = sum(o_ms)
+        if world > 1:
+            from paper_1902_01137_gb300 import shard
+            o_total = shard.max_over_ranks(o_total)
+        octree = {"value": world * paths * args.steps / (o_total / 1e3), "unit": "paths/s",
+                  "ms_per_step": o_total / args.steps, "kernel_ms": statistics.mean(o_kern),
+                  "grid": "2^L octree per field (Sec. 3.1.1), tau~ 1, finest level 1",
+                  "step": "96 scenes (relayout, pyramid, octree, leaf maps) + one batch trace"}
     # e2e: fields from pinned host memory, tallies back to the host
     e2e = None
     if not args.no_e2e:
@@ -515,7 +595,7 @@ def run_batch(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "paths/s", "h2d_bytes_per_step": field_bytes,
                     "d2h_bytes_per_step": len(items) * 4 * 16},
-            "gpu_launches": launches, "clocks": clk, "counters": cnt}
+            "gpu_launches": launches, "clocks": clk, "octree": octree, "counters": cnt}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -597,6 +677,19 @@ def run_sweep(args):
                 row[name] = {"ms": r.kernel_ms, "paths_per_s": npaths / (r.kernel_ms / 1e3),
                              "ns_per_path": r.kernel_ms * 1e6 / npaths, "mean": list(map(float, r.mean)),
                              "se": list(map(float, r.se))}
+                if storage == m.MCRT_STORAGE_F32:
+                    # the same paths over the paper's 2^L octree (Sec. 3.1.1)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    sc.build_octree()
+                    torch.cuda.synchronize()
+                    build_ms = (time.perf_counter() - t0) * 1e3
+                    kw = dict(grid=m.MCRT_GRID_OCTREE, finest_level=1)
+                    sc.trace_flux(1 << 20, seed=1, **kw)
+                    r = sc.trace_flux(npaths, seed=7, **kw)
+                    row["f32_octree"] = {"ms": r.kernel_ms, "paths_per_s": npaths / (r.kernel_ms / 1e3),
+                                         "ns_per_path": r.kernel_ms * 1e6 / npaths, "build_ms": build_ms,
+                                         "mean": list(map(float, r.mean)), "se": list(map(float, r.se))}
             finally:
                 sc.close()
         f, b = row["f32"], row["bf16"]
@@ -711,6 +804,7 @@ def main():
     ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep", "tau"])
     ap.add_argument("--sweep-paths", type=int, default=100_000_000)
     ap.add_argument("--no-fom", action="store_true")
+    ap.add_argument("--no-octree", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
