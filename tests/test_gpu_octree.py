@@ -203,3 +203,68 @@ def test_octree_refusals(m, ctx):
         assert np.all(np.isfinite(r.mean))
     finally:
         sc.close()
+
+
+# ---------------------------------------------------------------------------
+# the other kernel variants over the octree (terrain walk, Rayleigh species,
+# learned proposal): the grid changes only the leaves, so each must still
+# match the oracle over the same octree
+# ---------------------------------------------------------------------------
+def test_octree_with_terrain_vs_oracle(m, ctx, orc):
+    sp = scenes.blobs_small(0)
+    sp.sun_zenith_deg = 50.0
+    sp.sun_azimuth_deg = 30.0
+    h = scenes.heightfield(256, 0.3, seed=7)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        sc.set_heightfield(h, sp.ground_albedo)
+        sc.build_octree()
+        n = 60000
+        g = sc.trace_flux(n, seed=13, grid=m.MCRT_GRID_OCTREE)
+        o, _ = orc.trace_flux(oscene(orc, sp, heights=h, grid=1), n, seed=13)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean, o.mean)
+        assert abs(g.mean[2] - o.mean[2]) < 0.5 * o.se[2]
+    finally:
+        sc.close()
+
+
+def test_octree_with_rayleigh_vs_oracle(m, ctx, orc):
+    sp = scenes.blobs_small(0)
+    sp.k = sp.k + np.float32(0.04)
+    sp.k_clear = 0.05
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        m.mcrt_scene_set_clear_sky_phase(ctx.h, sc.h, m.MCRT_PHASE_RAYLEIGH)
+        sc.build_octree()
+        n = 60000
+        g = sc.trace_flux(n, seed=15, grid=m.MCRT_GRID_OCTREE, tau_merge=3.0)
+        o, _ = orc.trace_flux(oscene(orc, sp, clear_phase=1, grid=1, tau_merge=3.0), n, seed=15)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean, o.mean)
+        assert abs(g.mean[2] - o.mean[2]) < 0.25 * o.se[2]
+    finally:
+        sc.close()
+
+
+def test_octree_with_learned_proposal_vs_oracle(m, ctx, orc):
+    """A fixed network over the octree (its features still read the
+    pyramid's levels 1 and 2): the oracle with the same parameters over the
+    same octree agrees within 4 combined SE."""
+    sp = scenes.blobs_small(0)
+    p = orc.xavier_init(21)
+    r = np.random.default_rng(21)
+    p[p.size - 40:] = r.normal(size=40) * 0.5
+    p = p.astype(np.float32).astype(np.float64)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        sc.build_octree()
+        n = 100000
+        g = sc.trace_flux(n, seed=42, proposal=prop, batch_paths=30000, grid=m.MCRT_GRID_OCTREE)
+        o, _ = orc.trace_flux(oscene(orc, sp, mlp=p, grid=1), n, seed=42)
+        for q in range(3):
+            assert close_4se(g.mean[q], g.se[q], o.mean[q], o.se[q]), (q, g.mean, o.mean)
+    finally:
+        prop.close()
+        sc.close()
