@@ -379,7 +379,11 @@ MCRT_API int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, in
  * copies of the results and the status to pinned host memory) is captured
  * into one CUDA graph, so a run costs one graph launch.  The scenes must
  * outlive the plan and keep their majorants; a run traces the same paths
- * again unless mcrt_batch_plan_set_seeds changes the seeds.  Deadline and
+ * again unless mcrt_batch_plan_set_seeds changes the seeds.  A run checks
+ * its scenes first: if one changed since the plan was made (a trace with
+ * another tau~, finest level or grid rebuilt its leaf map, its octree or
+ * pyramid was rebuilt, its ground or phase function was set), the plan's
+ * leaf maps are rebuilt and its item records remade before the launch.  Deadline and
  * cancel flag are not available in plans (MCRT_ERR_UNSUPPORTED).
  * mcrt_batch_plan_run: mean and se (either may be NULL) receive n x 5
  * entries in the order of mcrt_trace_batch; *kernel_ms the graph's device

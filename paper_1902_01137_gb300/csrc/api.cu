@@ -297,6 +297,7 @@ int mcrt_scene_build_majorants(mcrt_scene* sc, int32_t levels)
     }
     sc->levels = levels;
     sc->leaf_valid = false;
+    sc->gen++;
     return MCRT_OK;
 }
 
@@ -369,6 +370,7 @@ int mcrt_scene_build_octree(mcrt_scene* sc, int32_t levels)
     const size_t n1 = (size_t)dims[3] * dims[4] * dims[5];
     // replace the previous octree (its leaf map goes with it)
     if (sc->leaf_grid == MCRT_GRID_OCTREE) sc->leaf_valid = false;
+    sc->gen++;
     dfree(ctx, sc->d_oct);
     dfree(ctx, sc->d_oleaf);
     sc->d_oct = nullptr;
@@ -441,6 +443,7 @@ int mcrt_scene_set_clear_sky_phase(mcrt_scene* sc, int32_t phase)
     if (phase != MCRT_PHASE_HG && phase != MCRT_PHASE_RAYLEIGH)
         return fail(sc->ctx, MCRT_ERR_ARG, "mcrt_scene_set_clear_sky_phase: bad phase %d", phase);
     sc->clear_phase = phase;
+    sc->gen++;
     return MCRT_OK;
 }
 
@@ -454,6 +457,7 @@ int mcrt_scene_set_ground_flat(mcrt_scene* sc, float albedo)
     dfree(sc->ctx, sc->d_hpyr);
     sc->d_hf = sc->d_hpyr = nullptr;
     sc->hlev = 0;
+    sc->gen++;
     return MCRT_OK;
 }
 
@@ -517,6 +521,7 @@ int mcrt_scene_set_ground_heightfield(mcrt_scene* sc, const float* heights, int3
     for (float v : tops) hm = std::fmax(hm, v);
     sc->hmax = hm;
     sc->albedo = albedo;
+    sc->gen++;
     return MCRT_OK;
 }
 
@@ -589,6 +594,7 @@ int ensure_leaf(mcrt_scene* sc, float tau, int finest, int grid)
     mcrt_ctx* ctx = sc->ctx;
     if (sc->leaf_valid && sc->leaf_tau == tau && sc->leaf_finest == finest && sc->leaf_grid == grid) return MCRT_OK;
     LAUNCH(ctx, launch_leafmap(sc, tau, finest, grid, ctx->stream));
+    sc->gen++;
     sc->leaf_valid = true;
     sc->leaf_tau = tau;
     sc->leaf_finest = finest;
@@ -1128,6 +1134,10 @@ int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, 
 struct mcrt_batch_plan {
     mcrt_ctx* ctx = nullptr;
     mcrt_trace_opts opts{};
+    std::vector<mcrt_batch_item> items;   // the caller's items (scenes borrowed)
+    std::vector<uint64_t> gens;           // each item's scene state when its record was made
+    unsigned long long total = 0;
+    bool bf16 = false;
     std::vector<BatchItem> h;
     BatchItem* d_items = nullptr;
     mcrt_tally* t = nullptr;
@@ -1180,6 +1190,11 @@ int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t 
     int rc = prepare_batch(ctx, items, n, o, who, p->h, total, bf16);
     if (rc == MCRT_OK) rc = batch_tally(ctx, items, n, &p->t, who);
     if (rc) { plan_free(p); return rc; }
+    p->items.assign(items, items + n);
+    p->gens.resize((size_t)n);
+    for (int i = 0; i < n; ++i) p->gens[i] = items[i].scene->gen;
+    p->total = total;
+    p->bf16 = bf16;
     const size_t m = (size_t)n * 5;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
@@ -1236,11 +1251,37 @@ int mcrt_batch_plan_set_seeds(mcrt_batch_plan* p, const uint64_t* seeds, int32_t
 
 int mcrt_batch_plan_run(mcrt_batch_plan* p, double* mean, double* se, size_t count, float* kernel_ms)
 {
-    if (!p) return fail(nullptr, MCRT_ERR_ARG, "mcrt_batch_plan_run: NULL plan");
+    const char* who = "mcrt_batch_plan_run";
+    if (!p) return fail(nullptr, MCRT_ERR_ARG, "%s: NULL plan", who);
     mcrt_ctx* ctx = p->ctx;
     const size_t m = p->h.size() * 5;
-    if ((mean || se) && count < m) return fail(ctx, MCRT_ERR_BOUNDS, "mcrt_batch_plan_run: need %zu entries", m);
+    if ((mean || se) && count < m) return fail(ctx, MCRT_ERR_BOUNDS, "%s: need %zu entries", who, m);
     CK(ctx, cudaSetDevice(ctx->device));
+    // the scenes may have changed since the records were made (another
+    // tau~ or grid traced in between rebuilt a leaf map, the octree was
+    // rebuilt elsewhere in memory, the ground changed): bring the leaf maps
+    // back to the plan's options and, if any scene changed, remake and
+    // upload the item records before the graph reads them
+    bool stale = false;
+    for (size_t i = 0; i < p->items.size(); ++i) {
+        mcrt_scene* sc = const_cast<mcrt_scene*>(p->items[i].scene);
+        int rc = ensure_leaf(sc, p->opts.tau_merge, p->opts.finest_level, p->opts.grid);
+        if (rc) return rc;
+        if (sc->gen != p->gens[i]) stale = true;
+    }
+    if (stale) {
+        std::vector<BatchItem> hh;
+        unsigned long long total = 0;
+        bool bf16 = false;
+        int rc = prepare_batch(ctx, p->items.data(), (int32_t)p->items.size(), &p->opts, who, hh, total, bf16);
+        if (rc) return rc;
+        if (total != p->total || bf16 != p->bf16) return fail(ctx, MCRT_ERR_STATE, "%s: the items changed shape", who);
+        for (size_t i = 0; i < hh.size(); ++i) hh[i].key = p->h[i].key;     // seeds set on the plan
+        CK(ctx, cudaStreamSynchronize(p->st));
+        p->h.swap(hh);
+        CK(ctx, cudaMemcpy(p->d_items, p->h.data(), sizeof(BatchItem) * p->h.size(), cudaMemcpyHostToDevice));
+        for (size_t i = 0; i < p->items.size(); ++i) p->gens[i] = p->items[i].scene->gen;
+    }
     CK(ctx, cudaStreamSynchronize(ctx->stream));      // work queued before the call (e.g. field uploads)
     ctx->launches += 2;                               // trace + finalize
     CK(ctx, cudaEventRecord(p->e0, p->st));

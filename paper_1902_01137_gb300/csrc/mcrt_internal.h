@@ -49,6 +49,10 @@ struct mcrt_scene {
     float leaf_tau = 0;
     int leaf_finest = -1;
     int leaf_grid = MCRT_GRID_PYRAMID;
+    // bumped whenever something a device scene record holds changes (leaf
+    // map rebuilt, octree or pyramid rebuilt, ground or phase changed), so
+    // that saved records (batch plans) know to refresh
+    uint64_t gen = 0;
     float albedo = 0;
     int clear_phase = 0;              // MCRT_PHASE_HG or MCRT_PHASE_RAYLEIGH
     float sun_zenith = 0, sun_azimuth = 0;

@@ -268,3 +268,31 @@ def test_octree_with_learned_proposal_vs_oracle(m, ctx, orc):
     finally:
         prop.close()
         sc.close()
+
+
+def test_batch_plan_survives_scene_changes(m, ctx):
+    """A plan keeps its own options: a trace with another tau~ or grid in
+    between, or the octree rebuilt elsewhere in memory, does not change
+    what the plan traces (its records are remade before the launch)."""
+    sp = scenes.blobs_small(0)
+    sc = m.Scene.from_spec(ctx, sp)
+    try:
+        sc.build_octree()
+        items = [(sc, 0.0, 20.0, 10.0, 20000, 5), (sc, 0.01, 40.0, 0.0, 9000, 6)]
+        for grid in (m.MCRT_GRID_PYRAMID, m.MCRT_GRID_OCTREE):
+            plan = m.BatchPlan(ctx, items, grid=grid, tau_merge=1.0)
+            try:
+                r1 = plan.run()
+                sc.trace_flux(5000, seed=3, tau_merge=10.0, grid=m.MCRT_GRID_OCTREE)
+                sc.trace_flux(5000, seed=3, tau_merge=0.0)
+                r2 = plan.run()
+                np.testing.assert_allclose(r2.mean, r1.mean, rtol=4e-6, atol=1e-12)
+                sc.build_octree()                  # new device buffers for the octree
+                r3 = plan.run()
+                np.testing.assert_allclose(r3.mean, r1.mean, rtol=4e-6, atol=1e-12)
+                direct = m.trace_batch(ctx, items, grid=grid, tau_merge=1.0)
+                np.testing.assert_allclose(r1.mean, direct.mean, rtol=4e-6, atol=1e-12)
+            finally:
+                plan.close()
+    finally:
+        sc.close()
