@@ -486,29 +486,40 @@ class Tally:
 
     @property
     def mean(self):
-        return self.s1 / self.n
+        with np.errstate(invalid="ignore", divide="ignore"):      # cells with no paths: nan
+            return self.s1 / self.n
 
     @property
     def se(self):
-        m = self.s1 / self.n
-        var = np.maximum(self.s2 / self.n - m * m, 0.0) * self.n / np.maximum(self.n - 1, 1)
-        return np.sqrt(var / self.n)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            m = self.s1 / self.n
+            var = np.maximum(self.s2 / self.n - m * m, 0.0) * self.n / np.maximum(self.n - 1, 1)
+            return np.sqrt(var / self.n)
 
 
-def trace_camera(scene: Scene, cam: Camera, spp: int, seed: int, pix_range=None, nthreads: int = 0):
-    """Per-pixel radiance tallies [height][width] (units of F0 per sr)."""
+def trace_camera(scene: Scene, cam: Camera, spp: int, seed: int, pix_range=None, nthreads: int = 0,
+                 pixels=None):
+    """Per-pixel radiance tallies [height][width] (units of F0 per sr).
+    ``pix_range`` (begin, end) or ``pixels`` (flat indices) restrict the
+    trace to those pixels (same path ids as the whole image); the others
+    are left at zero with a path count of 0."""
     st = scene.struct()
     cs = cam.struct()
     npix = cam.width * cam.height
-    p0, p1 = (0, npix) if pix_range is None else pix_range
     sums = np.zeros((npix, 2), dtype=np.float64)
     stats = np.zeros(4, dtype=np.int64)
-    rc = lib().orc_trace_camera(C.byref(st), C.byref(cs), spp, seed, p0, p1, _ptr(sums, C.c_double),
-                                nthreads or default_threads(), _ptr(stats, C.c_int64))
-    if rc != 0:
-        raise ValueError("bad camera request")
     n = np.zeros(npix)
-    n[p0:p1] = spp
+    ranges = [(0, npix) if pix_range is None else tuple(pix_range)]
+    if pixels is not None:
+        ranges = [(int(p), int(p) + 1) for p in pixels]
+    for p0, p1 in ranges:
+        st_i = np.zeros(4, dtype=np.int64)
+        rc = lib().orc_trace_camera(C.byref(st), C.byref(cs), spp, seed, p0, p1, _ptr(sums, C.c_double),
+                                    nthreads or default_threads(), _ptr(st_i, C.c_int64))
+        if rc != 0:
+            raise ValueError("bad camera request")
+        stats += st_i
+        n[p0:p1] = spp
     t = Tally(sums[:, 0].reshape(cam.height, cam.width), sums[:, 1].reshape(cam.height, cam.width),
               n.reshape(cam.height, cam.width))
     return t, stats
