@@ -773,10 +773,11 @@ def run_tau(args):
     return 0
 
 
-def run_profile_case():
+def run_profile_case(grid="pyramid"):
     """A small case of the bench kernel for ncu: the same 512x512x160 field
     (160 MiB, larger than L2), a 512 x 512 image at 16 spp (4,194,304
-    paths), two launches."""
+    paths), two launches; over the 8^L pyramid (the bench line) or over the
+    paper's 2^L octree (the line's `octree` figure: tau~ 1, finest level 1)."""
     import torch
     import paper_1902_01137_gb300 as m
     spec, _ = make_workload()
@@ -784,8 +785,12 @@ def run_profile_case():
     cam = scenes.nadir_camera(spec, 512, 512)
     ctx = m.Context(0)
     sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    kw = {}
+    if grid == "octree":
+        sc.build_octree()
+        kw = dict(grid=m.MCRT_GRID_OCTREE, finest_level=1)
     for i in range(2):
-        r = sc.trace_camera(cam, 16, seed=7 + i)
+        r = sc.trace_camera(cam, 16, seed=7 + i, **kw)
         print("launch", i, "kernel_ms", r.kernel_ms, "mean", float(r.mean.mean()), flush=True)
     sc.close()
     ctx.close()
@@ -807,6 +812,8 @@ def main():
     ap.add_argument("--no-octree", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
+    ap.add_argument("--profile-grid", default="pyramid", choices=["pyramid", "octree"],
+                    help="grid the profile case traces over")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per trace launch, if captured for this kernel version")
     args = ap.parse_args()
@@ -815,7 +822,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
-        return run_profile_case()
+        return run_profile_case(args.profile_grid)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "sweep":
