@@ -133,8 +133,11 @@ typedef struct {
  *   omega = ((k - k_clear) * ssa_cloud + k_clear * ssa_clear) / k
  * (cloud droplets and clear air mixed in proportion to their extinction,
  * Sec. 4.1 species sampling in expectation).  The ground is black and the
- * sun at zenith until set.  Errors: MCRT_ERR_ARG, MCRT_ERR_OOM,
- * MCRT_ERR_CUDA. */
+ * sun at zenith until set.  A host field in page-locked memory mapped
+ * into the device's address space (cudaHostAlloc, or cudaHostRegister with
+ * cudaHostRegisterMapped) is read by the relayout kernel directly; other
+ * host memory is copied to a device staging buffer first.  Errors:
+ * MCRT_ERR_ARG, MCRT_ERR_OOM, MCRT_ERR_CUDA. */
 MCRT_API int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* desc, mcrt_scene** out);
 
 /* Destroy a scene (synchronises the context stream). */

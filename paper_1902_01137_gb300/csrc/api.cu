@@ -235,10 +235,24 @@ int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* d, mcrt_scene** out)
     float* staging = nullptr;
     const size_t nvox = (size_t)d->nx * d->ny * d->nz;
     if (e == cudaSuccess && d->ext_mem == MCRT_MEM_HOST) {
-        e = dalloc(ctx, &staging, nvox * sizeof(float));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(staging, d->ext, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
-        src = staging;
+        // page-locked host memory mapped into the device's address space is
+        // read by the relayout kernel itself, over the host link, in the
+        // same pass that writes the bricks; other host memory goes through
+        // a device staging copy
+        cudaPointerAttributes pa{};
+        const float* mapped = nullptr;
+        if (cudaPointerGetAttributes(&pa, d->ext) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            mapped = static_cast<const float*>(pa.devicePointer);
+        else
+            (void)cudaGetLastError();
+        if (mapped) {
+            src = mapped;
+        } else {
+            e = dalloc(ctx, &staging, nvox * sizeof(float));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(staging, d->ext, nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+            src = staging;
+        }
     }
     if (e == cudaSuccess) {
         ctx->launches++;

@@ -430,3 +430,29 @@ def test_bf16_error_against_fp64_oracle_of_fp32_field(m, ctx, orc, capsys):
               "bf16-oracle %s (se %s)" % (np.round(o.mean[:3], 6), np.round(res["f32"].mean, 6),
                                            np.round(res["bf16"].mean, 6),
                                            np.round(res["bf16"].mean - o.mean[:3], 6), np.round(o.se[:3], 6)))
+
+
+def test_scene_from_pinned_host_field(m, ctx, orc):
+    """A page-locked host field is read by the relayout kernel in place (no
+    staging copy): bricks and majorants equal those of the same field from
+    pageable host memory and from device memory, and the oracle's."""
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(77)
+    shape = (40, 72, 72)
+    k = (r.lognormal(0.0, 2.0, shape) * (r.uniform(size=shape) < 0.4)).astype(np.float32)
+    pinned = torch.from_numpy(k).pin_memory()
+    assert pinned.is_pinned()
+    want = orc.build_pyramid(k, 3)
+    for src in (pinned, k, torch.from_numpy(k).cuda()):
+        sc = m.Scene(ctx, src, 0.1, 0.1, 0.1, levels=3)
+        try:
+            for L in range(1, 4):
+                assert np.array_equal(sc.majorants(L).view(np.uint32), want[L - 1].view(np.uint32)), (type(src), L)
+            cam = scenes.nadir_camera(scenes.homogeneous(72, 72, 40, 0.1, 1.0), 16, 16)
+            res = sc.trace_camera(cam, 4, seed=3)
+            if src is pinned:
+                ref = res.mean
+            else:
+                np.testing.assert_allclose(res.mean, ref, rtol=1e-12, atol=0)   # FP64 atomics: order only
+        finally:
+            sc.close()
