@@ -81,6 +81,9 @@ enum { MCRT_PHASE_HG = 0, MCRT_PHASE_RAYLEIGH = 1 };
  * voxels per axis), which mcrt_scene_build_octree must have built. */
 enum { MCRT_GRID_PYRAMID = 0, MCRT_GRID_OCTREE = 1 };
 
+/* Order in which a camera trace claims its pixels (mcrt_trace_opts.pixel_order). */
+enum { MCRT_ORDER_COST = 0, MCRT_ORDER_RASTER = 1 };
+
 /* Library version and the ABI version it was built with. */
 MCRT_API int mcrt_version(int32_t* abi_version);
 
@@ -287,6 +290,13 @@ typedef struct {
                                /* quantity; 0 leaves it 0 and runs faster)      */
     int32_t grid;              /* MCRT_GRID_PYRAMID (default) or                */
                                /* MCRT_GRID_OCTREE: the max grid tracked        */
+    int32_t pixel_order;       /* camera traces: MCRT_ORDER_COST (default)      */
+                               /* claims the pixels whose view ray crosses the  */
+                               /* most majorant optical depth first (a short    */
+                               /* pre-pass per 8x8 tile), so the longest paths  */
+                               /* do not start last; MCRT_ORDER_RASTER claims   */
+                               /* them row by row.  Launch shape only: a path's */
+                               /* id, draws and result do not depend on it      */
 } mcrt_trace_opts;
 
 /* Fill `opts` with the defaults listed above. */

@@ -42,6 +42,8 @@ MCRT_TRAIN_TENSOR = 0
 MCRT_TRAIN_FP32 = 1
 MCRT_GRID_PYRAMID = 0
 MCRT_GRID_OCTREE = 1
+MCRT_ORDER_COST = 0
+MCRT_ORDER_RASTER = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -83,7 +85,8 @@ class TraceOpts(C.Structure):
                 ("deadline_ms", C.c_double),
                 ("cancel_flag", C.c_void_p),
                 ("batch_dalpha", C.c_int32),
-                ("grid", C.c_int32)]
+                ("grid", C.c_int32),
+                ("pixel_order", C.c_int32)]
 
 
 _lib = None

@@ -598,6 +598,8 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
     }
     if (!(o->deadline_ms >= 0.0)) return fail(ctx, MCRT_ERR_ARG, "%s: deadline_ms must be >= 0", who);
     if (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE) return fail(ctx, MCRT_ERR_ARG, "%s: bad grid", who);
+    if (o->pixel_order != MCRT_ORDER_COST && o->pixel_order != MCRT_ORDER_RASTER)
+        return fail(ctx, MCRT_ERR_ARG, "%s: bad pixel_order", who);
     if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
         return fail(ctx, MCRT_ERR_STATE, "%s: octree not built (mcrt_scene_build_octree)", who);
     return MCRT_OK;
@@ -648,6 +650,58 @@ int get_tally(mcrt_ctx* ctx, int ncells, int nq, mcrt_tally** inout, const char*
     CK(ctx, cudaMemsetAsync(t->d_s2, 0, m * sizeof(double), ctx->stream));
     CK(ctx, cudaMemsetAsync(t->d_counters, 0, kNumCounters * sizeof(unsigned long long), ctx->stream));
     CK(ctx, cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), ctx->stream));
+    return MCRT_OK;
+}
+
+// Claim order of a camera trace (MCRT_ORDER_COST): per tile of pixels the
+// majorant optical depth along its central view ray, tiles sorted by it
+// (largest first, ties in raster order), expanded to one pixel per claim
+// rank in *d_order (device, freed by the caller with dfree).
+int make_claim_order(mcrt_scene* sc, const TraceParams& P, uint32_t** d_order, const char* who)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    int tx = 0;
+    const int n = order_tiles(P.width, P.height, &tx);
+    float* d_cost = nullptr;
+    uint32_t* d_tiles = nullptr;
+    CK(ctx, dalloc(ctx, &d_cost, (size_t)n * sizeof(float)));
+    ctx->launches++;
+    cudaError_t e = launch_view_cost(P, sc->storage == MCRT_STORAGE_BF16, d_cost, ctx->stream);
+    std::vector<float> cost((size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cost.data(), d_cost, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost,
+                                              ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d_cost);
+    if (e != cudaSuccess) return fail(ctx, MCRT_ERR_CUDA, "%s: claim order: %s", who, cudaGetErrorString(e));
+    std::vector<uint32_t> tiles((size_t)2 * n);
+    for (int i = 0; i < n; ++i) {
+        tiles[i] = (uint32_t)i;
+        if (!(cost[i] >= 0.0f)) cost[i] = 3.0e38f;     // NaN: treat as the most costly
+    }
+    std::stable_sort(tiles.begin(), tiles.begin() + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    uint32_t acc = 0;
+    for (int b = 0; b < n; ++b) {
+        const int x0 = (int)(tiles[b] % (uint32_t)tx) * 8, y0 = (int)(tiles[b] / (uint32_t)tx) * 8;
+        tiles[n + b] = acc;
+        acc += (uint32_t)(std::min(8, P.width - x0) * std::min(8, P.height - y0));
+    }
+    e = dalloc(ctx, &d_tiles, (size_t)2 * n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = dalloc(ctx, d_order, (size_t)P.width * P.height * sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tiles, tiles.data(), (size_t)2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->launches++;
+        e = launch_expand_order(d_tiles, d_tiles + n, n, P.width, P.height, *d_order, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);    // the host vector is read by the copy
+    dfree(ctx, d_tiles);
+    if (e != cudaSuccess) {
+        dfree(ctx, *d_order);
+        *d_order = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, "%s: claim order: %s", who,
+                    cudaGetErrorString(e));
+    }
     return MCRT_OK;
 }
 
@@ -909,7 +963,15 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
         P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
         return run_learned(sc, P, kCamera, o, t, spp, who);
     }
-    return run_trace(sc, P, kCamera, o, t, who);
+    uint32_t* d_order = nullptr;
+    if (o->pixel_order == MCRT_ORDER_COST) {
+        rc = make_claim_order(sc, P, &d_order, who);
+        if (rc) return rc;
+        P.pix_order = d_order;
+    }
+    rc = run_trace(sc, P, kCamera, o, t, who);
+    dfree(ctx, d_order);
+    return rc;
 }
 
 int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_trace_opts* opts, mcrt_tally** tally)

@@ -163,6 +163,8 @@ struct TraceParams {
     // batches (flux sensor): items sorted by begin
     const BatchItem* items;
     int n_items;
+    // camera: pixel of each claim rank (null: raster order)
+    const uint32_t* pix_order;
     // outputs
     double* s1;
     double* s2;
@@ -196,6 +198,10 @@ cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, bool
 int trace_batch_blocks_per_sm(bool bf16, bool count, bool dalpha, int block);
 cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
                             int nq, double* out, cudaStream_t st);
+int order_tiles(int width, int height, int* tiles_x);
+cudaError_t launch_view_cost(const TraceParams& P, bool bf16, float* cost, cudaStream_t st);
+cudaError_t launch_expand_order(const uint32_t* tiles, const uint32_t* prefix, int n, int width, int height,
+                                uint32_t* order, cudaStream_t st);
 cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,
                              float* tio, int* count_status, bool bf16, cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,

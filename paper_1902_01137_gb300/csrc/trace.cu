@@ -188,7 +188,16 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                         if (pid >= np) { chunk = false; phase = PH_IDLE; }
                     }
                     if constexpr (SENSOR == kCamera) {
-                        const unsigned long long pix = pid / P.spp;
+                        unsigned long long pix = pid / P.spp;
+                        if (!LEARNED && P.pix_order) {
+                            // claims walk the pixels in the given order (costly
+                            // ones first); a path keeps its id, so its draws and
+                            // its result do not depend on the order
+                            const unsigned long long off = pid - pix * P.spp;
+                            pix = __ldg(P.pix_order + pix);
+                            pid = pix * P.spp + off;
+                            pend = pid + P.chunk;          // a chunk never straddles two pixels
+                        }
                         cell = (unsigned)pix;
                         px = (int)(pix % (unsigned long long)P.width);
                         py = (int)(pix / (unsigned long long)P.width);
@@ -853,6 +862,79 @@ __global__ void debug_dda_kernel(DevScene S, float ox, float oy, float oz, float
     count_status[1] = status;
 }
 
+// Claim order of a camera trace: the cost of each tile of kOrderTile^2
+// pixels is estimated by the majorant optical depth along the view ray
+// through the tile's centre (the sum of M times the length over the leaves
+// it crosses, capped): paths that enter thick cloud scatter many times and
+// run longest.  Tracing the costly tiles first leaves cheap paths for the
+// end of the launch, where a long path would otherwise run alone.
+constexpr int kOrderTile = 8;
+
+template <bool BF16>
+__global__ void view_cost_kernel(TraceParams P, int tiles_x, int tiles_y, float* __restrict__ cost)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tiles_x * tiles_y) return;
+    const DevScene& S = P.S;
+    const float cx = fminf((float)((i % tiles_x) * kOrderTile) + 0.5f * kOrderTile, (float)P.width - 0.5f);
+    const float cy = fminf((float)((i / tiles_x) * kOrderTile) + 0.5f * kOrderTile, (float)P.height - 0.5f);
+    const float sx = (2.0f * cx * P.inv_width - 1.0f) * P.tan_half;
+    const float sy = (2.0f * cy * P.inv_height - 1.0f) * P.tan_half * P.aspect;
+    float d[3], q[3] = {P.cam_pos[0], P.cam_pos[1], P.cam_pos[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = P.cam_f[a] + sx * P.cam_r[a] + sy * P.cam_u[a];
+    const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] *= inv;
+    float c = 0.0f;
+    bool enters = true;
+    if (q[2] > P.Lz) {
+        if (d[2] < 0.0f) {
+            const float t = (P.Lz - q[2]) / d[2];
+            q[0] += t * d[0];
+            q[1] += t * d[1];
+            q[2] = P.Lz;
+        } else {
+            enters = false;
+        }
+    } else if (q[2] < 0.0f) {
+        enters = false;
+    }
+    if (enters) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            q[a] -= floorf(q[a] / S.Lper[a]) * S.Lper[a];
+            if (!(q[a] < S.Lper[a]) || q[a] < 0.0f) q[a] = 0.0f;
+        }
+        Ray R;
+        ray_begin<BF16>(S, R, q, d);
+        for (int n = 0; n < 4096 && c < 1e4f; ++n) {
+            c += R.M * (R.texit - R.t);
+            float wdt, p[3];
+            const int st = step_face(S, R, p, &wdt);
+            if (st != kInside) break;
+            finish_leaf<BF16>(S, R, __ldg(leaf_entry(S, R.v)));
+        }
+    }
+    cost[i] = c;
+}
+
+// order[prefix[b] + j] = the j-th pixel (row-major inside the tile) of the
+// b-th tile in claim order.
+__global__ void expand_order_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ prefix, int n,
+                                    int tiles_x, int width, int height, uint32_t* __restrict__ order)
+{
+    const int b = blockIdx.x;
+    if (b >= n) return;
+    const uint32_t tile = tiles[b];
+    const int x0 = (int)(tile % (uint32_t)tiles_x) * kOrderTile, y0 = (int)(tile / (uint32_t)tiles_x) * kOrderTile;
+    const int tw = min(kOrderTile, width - x0), th = min(kOrderTile, height - y0);
+    const int t = threadIdx.x;
+    if (t >= tw * th) return;
+    const int tx = t % tw, ty = t / tw;
+    order[prefix[b] + t] = (uint32_t)((y0 + ty) * width + x0 + tx);
+}
+
 // One thread per ray: the heightfield hit distance (terrain check).
 __global__ void debug_terrain_kernel(DevScene S, const float* __restrict__ o, const float* __restrict__ d, int n,
                                      float* __restrict__ t)
@@ -1019,6 +1101,31 @@ cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, 
     else
         debug_dda_kernel<false><<<1, 32, 0, st>>>(S, o[0], o[1], o[2], d[0], d[1], d[2], cap, cells, tio,
                                                    count_status);
+    return cudaGetLastError();
+}
+
+int order_tiles(int width, int height, int* tiles_x)
+{
+    *tiles_x = (width + kOrderTile - 1) / kOrderTile;
+    return *tiles_x * ((height + kOrderTile - 1) / kOrderTile);
+}
+
+cudaError_t launch_view_cost(const TraceParams& P, bool bf16, float* cost, cudaStream_t st)
+{
+    int tx = 0;
+    const int n = order_tiles(P.width, P.height, &tx);
+    const int ty = n / tx;
+    if (bf16) view_cost_kernel<true><<<(n + 127) / 128, 128, 0, st>>>(P, tx, ty, cost);
+    else view_cost_kernel<false><<<(n + 127) / 128, 128, 0, st>>>(P, tx, ty, cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_order(const uint32_t* tiles, const uint32_t* prefix, int n, int width, int height,
+                                uint32_t* order, cudaStream_t st)
+{
+    int tx = 0;
+    order_tiles(width, height, &tx);
+    expand_order_kernel<<<n, kOrderTile * kOrderTile, 0, st>>>(tiles, prefix, n, tx, width, height, order);
     return cudaGetLastError();
 }
 
