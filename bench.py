@@ -54,8 +54,8 @@ WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x
 W, H, SPP = 1024, 1024, 64
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
-PROFILED_TRACE_SHA = "e50215c719d839bf"
-PROFILED_DRAM_BYTES_PER_PATH = 23.80
+PROFILED_TRACE_SHA = "57cf5627c682072d"
+PROFILED_DRAM_BYTES_PER_PATH = 24.14
 
 
 def trace_sources_sha() -> str:
