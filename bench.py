@@ -56,6 +56,12 @@ W, H, SPP = 1024, 1024, 64
 # valid only while the kernel's sources are the ones that were captured
 PROFILED_TRACE_SHA = "57cf5627c682072d"
 PROFILED_DRAM_BYTES_PER_PATH = 24.14
+# issue-slot figures of the same capture (smsp__issue_active, threads per
+# warp instruction); the kernel is issue-bound, so these locate it against
+# its real ceiling: 152 SMs x 4 schedulers x 1 warp instruction per cycle
+PROFILED_ISSUE_ACTIVE = 0.7355
+PROFILED_THREADS_PER_INST = 13.07
+PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
 
 
 def trace_sources_sha() -> str:
@@ -73,6 +79,22 @@ def profiled_traffic(paths_per_launch):
     except OSError:
         return None
     return PROFILED_DRAM_BYTES_PER_PATH * paths_per_launch if sha == PROFILED_TRACE_SHA else None
+
+
+def profiled_issue(sm_mhz):
+    """Secondary roofline of the trace kernel against its issue ceiling,
+    from the committed ncu capture (None once the kernel sources changed)."""
+    try:
+        if trace_sources_sha() != PROFILED_TRACE_SHA:
+            return None
+    except OSError:
+        return None
+    peak = 152 * 4 * (sm_mhz or 2070.0) * 1e6
+    return {"bound": "issue", "achieved": PROFILED_ISSUE_ACTIVE * peak, "peak": peak,
+            "unit": "warp instructions/s", "frac": PROFILED_ISSUE_ACTIVE,
+            "simt_efficiency": PROFILED_THREADS_PER_INST / 32.0,
+            "peak_derivation": "152 SMs x 4 schedulers x 1 issue/cycle x SM clock",
+            "source": "ncu capture of the small case: " + PROFILED_SOURCE}
 
 
 def peaks():
@@ -379,7 +401,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "paths_per_step": paths_per_step, "l2": "flushed between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_issue": profiled_issue(clk.get("sm_mhz") if clk else None),
+            "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk,
             "collision_events_per_s": events / (kavg / 1e3),
