@@ -9,9 +9,10 @@ size:
   whole field bit-exact; 512 sampled pixels traced by the oracle with the
   same path ids, paired per pixel (same random numbers) and within 4
   combined SE over the sample.
-* The bench batch (96 instances, 814 items, autotuned launch shape):
-  sampled items against the oracle's trace of the same item's first paths
-  (same seeds and path ids), within 4 combined SE.
+* The bench batch (96 instances, 814 items, autotuned launch shape, over
+  the octree as the bench traces it): sampled items against the oracle's
+  trace of the same item's first paths over the same octree (same seeds
+  and path ids), within 4 combined SE.
 * The largest sweep field (2048^2 x 640, 2.7e9 voxels, over the 4096^2
   heightfield): sampled pyramid and octree cells bit-exact against the
   oracle's reduction of their voxel blocks; the pyramid, the octree and
@@ -104,11 +105,16 @@ def test_bench_batch_full_size(env, orc):
     scs = [m.Scene(ctx, sp.k, sp.dx, sp.dy, sp.dz, k_clear=sp.k_clear, ssa_clear=sp.ssa_clear,
                    ssa_cloud=sp.ssa_cloud, g=sp.g, levels=sp.levels, albedo=sp.ground_albedo) for sp in specs]
     try:
+        for s in scs:
+            s.build_octree()
         items = scenes.batch_items(inst, lambda i: scs[i])
         assert len(items) == 814
-        opts, _ = m.mcrt_autotune_batch(ctx.h, m.make_batch_items(items), 0.25, m.mcrt_trace_opts_default())
+        topts = m.mcrt_trace_opts_default()
+        topts.grid = m.MCRT_GRID_OCTREE
+        topts.finest_level = 1
+        opts, _ = m.mcrt_autotune_batch(ctx.h, m.make_batch_items(items), 0.25, topts)
         shape = dict(chunk=opts.chunk, rare_batch=opts.rare_batch, block_size=opts.block_size)
-        res = m.trace_batch(ctx, items, **shape)
+        res = m.trace_batch(ctx, items, grid=m.MCRT_GRID_OCTREE, finest_level=1, **shape)
         owner = bench._item_instance(inst)
         r = np.random.default_rng(4)
         # sampled items: two of the smallest fields, one mid-size, one of the largest
@@ -122,7 +128,7 @@ def test_bench_batch_full_size(env, orc):
             k = sp.k.cpu().numpy()
             osc = orc.Scene(k=k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=sp.k_clear,
                             ssa_clear=sp.ssa_clear, ssa_cloud=sp.ssa_cloud, g=sp.g, ground_albedo=sp.ground_albedo,
-                            sun_zenith_deg=z, sun_azimuth_deg=az, k_gas=kg)
+                            sun_zenith_deg=z, sun_azimuth_deg=az, k_gas=kg, grid=1, finest_level=1)
             n = min(npaths, 20000)
             o, st = orc.trace_flux(osc, n, seed=seed)
             assert st[0] == 0
