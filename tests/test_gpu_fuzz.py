@@ -1,4 +1,5 @@
-"""Randomised bit-exact parity of the grids and the traversal.
+"""Randomised parity with the oracle: the grids and the traversal bit for
+bit, then the estimators on random scenes.
 
 Thirty seeded cases, each drawn at random:
 - field shape (1 to 40 voxels per axis, so levels are clipped at ragged edges);
@@ -11,6 +12,12 @@ Each of its rays must then give the same leaves and the same t bits as the
 oracle's FP32 traversal spec. The rays are random, plus hard ones: starting
 exactly on voxel faces, on the ground and top faces, along the axes, and
 nearly parallel to a face.
+
+Sixteen more seeded cases draw the scene constants and the options (g,
+both single-scattering albedos, clear-sky extinction, ground albedo, sun
+position, ratio / delta / decomposition tracking, grid, finest level, tau~,
+storage); their flux tallies and image means must agree with the oracle's
+within 4 combined SE on the same seeds.
 """
 import numpy as np
 import pytest
@@ -111,5 +118,67 @@ def test_random_case_bit_exact(env, orc, i):
             assert sg == so, (i, j, sg, so, c["k"].shape)
             assert np.array_equal(cg, co), (i, j)
             assert np.array_equal(tg.view(np.uint32), to.view(np.uint32)), (i, j)
+    finally:
+        sc.close()
+
+
+# ---------------------------------------------------------------------------
+# estimators: random scene constants and options against the oracle
+# ---------------------------------------------------------------------------
+TALLY_CASES = 16
+
+
+def _scene_case(i):
+    r = np.random.default_rng(9100 + i)
+    nx, ny, nz = (int(v) for v in r.integers(8, 33, 3))
+    h = float(np.float32(r.choice([0.05, 0.1, 0.2])))
+    k = r.lognormal(r.uniform(-1.0, 2.0), 1.2, (nz, ny, nx))
+    k[r.uniform(size=k.shape) < r.uniform(0.3, 0.9)] = 0.0
+    k_clear = float(r.choice([0.0, 0.01, 0.2]))
+    k = (k + k_clear).astype(np.float32)
+    levels = 1
+    while 8 ** levels < max(nx, ny, nz):
+        levels += 1
+    return dict(k=k, h=h, levels=levels, k_clear=k_clear, ssa_clear=float(r.uniform(0.5, 1.0)),
+                ssa_cloud=float(r.uniform(0.6, 1.0)), g=float(r.uniform(-0.5, 0.95)),
+                albedo=float(r.uniform(0.0, 0.9)), zenith=float(r.uniform(0.0, 80.0)),
+                azimuth=float(r.uniform(0.0, 360.0)), sun_mode=int(r.integers(0, 3)), grid=int(r.integers(0, 2)),
+                finest=int(r.integers(0, 2)), tau=float(r.choice((0.3, 1.0, 5.0))), bf16=bool(r.integers(0, 2)))
+
+
+@pytest.mark.parametrize("i", range(TALLY_CASES))
+def test_random_scene_tallies(env, orc, i):
+    m, ctx = env
+    c = _scene_case(i)
+    sc = m.Scene(ctx, c["k"], c["h"], c["h"], c["h"], k_clear=c["k_clear"], ssa_clear=c["ssa_clear"],
+                 ssa_cloud=c["ssa_cloud"], g=c["g"], levels=c["levels"], albedo=c["albedo"],
+                 sun_zenith_deg=c["zenith"], sun_azimuth_deg=c["azimuth"],
+                 storage=m.MCRT_STORAGE_BF16 if c["bf16"] else m.MCRT_STORAGE_F32)
+    try:
+        if c["grid"] == 1:
+            sc.build_octree()
+        kw = dict(tau_merge=c["tau"], finest_level=c["finest"], sun_mode=c["sun_mode"], grid=c["grid"])
+        osc = orc.Scene(k=c["k"], dx=c["h"], dy=c["h"], dz=c["h"], levels=c["levels"], k_clear=c["k_clear"],
+                        ssa_clear=c["ssa_clear"], ssa_cloud=c["ssa_cloud"], g=c["g"], ground_albedo=c["albedo"],
+                        sun_zenith_deg=c["zenith"], sun_azimuth_deg=c["azimuth"], bf16=c["bf16"],
+                        tau_merge=c["tau"], finest_level=c["finest"], sun_mode=c["sun_mode"], grid=c["grid"])
+        n = 30000
+        g = sc.trace_flux(n, seed=100 + i, **kw)
+        o, st = orc.trace_flux(osc, n, seed=100 + i)
+        assert st[0] == 0
+        for q in range(3):
+            s = float(np.hypot(g.se[q], o.se[q]))
+            assert abs(g.mean[q] - o.mean[q]) <= 4.0 * s + 1e-12, (i, q, g.mean[:3], o.mean[:3], c)
+        nz, ny, nx = c["k"].shape
+        spec = scenes.SceneSpec("fuzz", c["k"], c["h"], c["h"], c["h"], c["levels"], c["k_clear"], c["ssa_clear"],
+                                c["ssa_cloud"], c["g"], c["albedo"], c["zenith"], c["azimuth"])
+        cam = scenes.nadir_camera(spec, 12, 10)
+        gi = sc.trace_camera(cam, 16, seed=200 + i, **kw)
+        oi, _ = orc.trace_camera(osc, orc.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, cam.width, cam.height),
+                                 16, seed=200 + i)
+        sg = float(np.sqrt(np.sum(gi.se ** 2))) / gi.se.size
+        so = float(np.sqrt(np.sum(oi.se ** 2))) / oi.se.size
+        assert abs(gi.mean.mean() - oi.mean.mean()) <= 4.0 * np.hypot(sg, so) + 1e-12, (i, gi.mean.mean(),
+                                                                                      oi.mean.mean(), c)
     finally:
         sc.close()
