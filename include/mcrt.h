@@ -344,6 +344,8 @@ MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, 
  *    race.  Issue them one after another on one stream.
  *  - The first call on a device looks up the array's device address; make
  *    that first call before capturing any stream.
+ *  - Pixels are claimed in raster order whatever opts->pixel_order says (the
+ *    cost order needs work buffers); results are the same either way.
  *  - The scene's majorants must be built.  Synchronises the context stream;
  *    errors as mcrt_trace_camera plus MCRT_ERR_BOUNDS, and
  *    MCRT_ERR_UNSUPPORTED for a learned proposal (it needs work buffers). */

@@ -97,7 +97,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     if (!(o->tau_merge >= 0.0f) || o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels ||
         o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA && o->sun_mode != MCRT_SUN_DECOMP) || o->block_size < 0 ||
         o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
-        o->rare_batch < 0 || o->rare_batch > 32 || (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE))
+        o->rare_batch < 0 || o->rare_batch > 32 || (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE) ||
+        (o->pixel_order != MCRT_ORDER_COST && o->pixel_order != MCRT_ORDER_RASTER))
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);
     if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
         return nfail(ctx, MCRT_ERR_STATE, "%s: octree not built", who);
