@@ -423,16 +423,18 @@ def _fom(rel, ms):
 
 def learned_fom(m, ctx):
     """Learned proposal vs plain HG sampling (1/(rel. variance x time)) on
-    the 64x64x32 blob field, sun zenith 60 deg.  The flux figure uses T_tot
-    over 2^24 paths; the image figure the mean pixel relative variance of a
-    512 x 512 image at 16 spp.  'online' counts the network's training
-    (2^26 paths in batches of 2^20, 2 Adam steps each) in the time of the
-    estimate those paths give; 'frozen' reuses the trained network."""
+    the bench's cumulus field (512x512x160 at 25 m), sun zenith 60 deg.  The
+    flux figure uses T_tot over 2^24 paths; the image figure the mean pixel
+    relative variance of a 512 x 512 nadir image at 16 spp.  'online' counts
+    the network's training (2^26 paths in batches of 2^20, 2 Adam steps
+    each) in the time of the estimate those paths give; 'frozen' reuses the
+    trained network."""
     import scenes
-    spec = scenes.blobs_small(0)
-    spec.sun_zenith_deg = 60.0
-    sc = m.Scene.from_spec(ctx, spec)
-    out = {"field": "blobs 64x64x32 @100m, sun 60 deg", "quantity": "T_tot flux; 512x512 image @16 spp"}
+    import torch
+    spec, _ = make_workload()
+    sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    out = {"field": "cumulus 512x512x160 @25m (the bench field), sun 60 deg",
+           "quantity": "T_tot flux; 512x512 image @16 spp"}
     try:
         N = 1 << 24
         sc.trace_flux(1 << 20, seed=1)
