@@ -520,9 +520,40 @@ def run_batch(args):
     grid_kw = dict(grid=m.MCRT_GRID_OCTREE, finest_level=1)
     cr = m.trace_batch(ctx, items, count_events=1, **shape, **grid_kw)
     cnt = cr.counters
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # the same batch as a CUDA-graph plan over these scenes (set up once):
+    # one graph launch per step, new seeds each step
+    plan_fig = None
+    plan = m.BatchPlan(ctx, items, **shape, **grid_kw)
+    try:
+        base = np.array(seeds0, dtype=np.uint64)
+        for i in range(args.warmup):
+            plan.set_seeds(base + np.uint64(7000 * (rank + 1) + i))
+            plan.run()
+        torch.cuda.synchronize()
+        p_ms, g_ms = [], []
+        for i in range(args.steps):
+            flush_buf.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.set_seeds(base + np.uint64(1000 * (rank + 1) + 100 + i))
+            r = plan.run()
+            e1.record(stream)
+            e1.synchronize()
+            p_ms.append(e0.elapsed_time(e1))
+            g_ms.append(r.kernel_ms)
+        p_total = sum(p_ms)
+        if world > 1:
+            from paper_1902_01137_gb300 import shard
+            p_total = shard.max_over_ranks(p_total)
+        plan_fig = {"value": world * paths * args.steps / (p_total / 1e3), "unit": "paths/s",
+                    "ms_per_step": p_total / args.steps, "graph_ms": statistics.mean(g_ms),
+                    "step": "new seeds + one graph launch (tally reset, trace, finalize, copies); scenes set up once"}
+    finally:
+        plan.close()
     for s_ in sc:
         s_.close()
-    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(fields, seed_off, octree=True):
         scs = make_scenes(fields)
@@ -630,7 +661,7 @@ def run_batch(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "paths/s", "h2d_bytes_per_step": field_bytes,
                     "d2h_bytes_per_step": len(items) * 4 * 16},
-            "gpu_launches": launches, "clocks": clk, "pyramid": pyramid, "counters": cnt}
+            "gpu_launches": launches, "clocks": clk, "pyramid": pyramid, "graph_plan": plan_fig, "counters": cnt}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
