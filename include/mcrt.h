@@ -490,6 +490,14 @@ MCRT_API int mcrt_proposal_eval(mcrt_proposal* proposal, const float* host_featu
 MCRT_API int mcrt_proposal_train_step(mcrt_proposal* proposal, const float* host_features, const float* host_dirs,
                                       const float* host_targets, size_t n, float lr, float* loss_out, float* host_grad);
 
+/* One Adam step (beta 0.9, 0.999, eps 1e-8, learning rate lr > 0) with a
+ * gradient the caller supplies (host, 11,560 floats, all finite): with
+ * several processes, each computes its gradient with
+ * mcrt_proposal_train_step(lr = 0), the processes average them, and each
+ * applies the same average here, so every copy of the network stays the
+ * same (data-parallel training).  Errors: MCRT_ERR_ARG. */
+MCRT_API int mcrt_proposal_apply_gradient(mcrt_proposal* proposal, const float* host_grad, float lr);
+
 /* Gradient kernel used by training steps (here and in traces that learn):
  * MCRT_TRAIN_TENSOR (default) runs every dense product of the forward and
  * backward passes on the tensor cores (BF16 operands, FP32 accumulation);

@@ -153,6 +153,7 @@ def _load():
         "mcrt_proposal_get_params": [vp, P(f32), C.c_size_t],
         "mcrt_proposal_eval": [vp, P(f32), C.c_size_t, P(f32), P(f32)],
         "mcrt_proposal_train_step": [vp, P(f32), P(f32), P(f32), C.c_size_t, f32, P(f32), P(f32)],
+        "mcrt_proposal_apply_gradient": [vp, P(f32), f32],
         "mcrt_proposal_set_training": [vp, i32],
     }
     for name, args in sig.items():
@@ -646,6 +647,13 @@ class Proposal:
 
     def train_step(self, features, dirs, targets, lr=0.0):
         return mcrt_proposal_train_step(self.ctx.h, self.h, features, dirs, targets, lr)
+
+    def apply_gradient(self, grad, lr=1e-3):
+        """One Adam step with a given gradient (data-parallel training)."""
+        g = np.ascontiguousarray(grad, dtype=np.float32).ravel()
+        if g.size != 11560:
+            raise ValueError("gradient must have 11,560 entries")
+        _check(_load().mcrt_proposal_apply_gradient(self.h, _ptr(g, C.c_float), float(lr)), self.ctx.h)
 
 
 # ---------------------------------------------------------------------------

@@ -255,4 +255,27 @@ int mcrt_proposal_train_step(mcrt_proposal* P, const float* host_feat, const flo
     return MCRT_OK;
 }
 
+int mcrt_proposal_apply_gradient(mcrt_proposal* P, const float* host_grad, float lr)
+{
+    const char* who = "mcrt_proposal_apply_gradient";
+    if (!P || !host_grad) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = P->ctx;
+    if (!(lr > 0.0f)) return lfail(ctx, MCRT_ERR_ARG, "%s: lr must be > 0", who);
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(host_grad[i])) return lfail(ctx, MCRT_ERR_ARG, "%s: gradient entry %d not finite", who, i);
+    LCK(ctx, cudaSetDevice(ctx->device));
+    cudaError_t e = cudaMemcpyAsync(P->d_grad, host_grad, kMlpParams * sizeof(float), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) {
+        P->step++;
+        ctx->launches += 2;
+        e = launch_adam(P->d_params, P->d_m, P->d_v, P->d_grad, kMlpParams, lr, 0.9f, 0.999f, 1e-8f, P->step,
+                        ctx->stream);
+        if (e == cudaSuccess) e = launch_pack(P->d_params, P->d_wbf, P->d_bias, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    LCK(ctx, e);
+    return MCRT_OK;
+}
+
 }  // extern "C"

@@ -2,7 +2,8 @@
 
 Paths are independent, so a tally shards by contiguous path-id ranges with
 no exchange during tracing; the only collective is one reduction of the
-per-rank FP64 sums at the end.  The reduction gathers every rank's sums and
+per-rank FP64 sums at the end.  Online training of the proposal network is
+data-parallel: one gradient average per Adam step (average_gradient).  The reduction gathers every rank's sums and
 adds them in rank order, so its result is the same on every rank and from
 run to run, whatever the transport (gloo on CPU, NCCL on GPUs).
 """
@@ -54,6 +55,20 @@ def reduce_sums(arrays, group=None):
         out.append(total[off:off + n].reshape(np.shape(a)))
         off += n
     return out
+
+
+def average_gradient(grad, counts, group=None):
+    """Data-parallel training of the proposal network: each rank holds the
+    gradient of its own mean loss over `counts` records; the gradient of the
+    mean loss over all ranks' records is the count-weighted average.  The
+    ranks' gradients are gathered and combined in rank order in FP64, so
+    every rank gets the same result (which it then applies with
+    Proposal.apply_gradient, keeping the copies of the network equal)."""
+    g = np.ascontiguousarray(grad, dtype=np.float64).ravel()
+    weighted, n = reduce_sums([g * float(counts), np.array([float(counts)])], group=group)
+    if not n[0] > 0:
+        raise ValueError("no training records on any rank")
+    return (weighted / n[0]).astype(np.float32)
 
 
 def max_over_ranks(x: float, group=None) -> float:

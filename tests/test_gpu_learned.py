@@ -220,3 +220,36 @@ def test_online_training_changes_network_and_stays_unbiased(env, orc):
     finally:
         prop.close()
         sc.close()
+
+
+def test_apply_gradient_matches_oracle_adam(env, orc):
+    """Data-parallel building block: a gradient taken with lr = 0 and then
+    applied with apply_gradient gives the oracle's Adam step on that same
+    gradient.  (Two gradient calls on the same records agree only to FP32
+    rounding -- the kernel adds its partial sums with atomics in varying
+    order -- which is why every rank applies one averaged copy.)"""
+    m, ctx = env
+    p = _params(orc, 9)
+    a = m.Proposal(ctx, params=p, training=m.MCRT_TRAIN_FP32)
+    b = m.Proposal(ctx, params=p, training=m.MCRT_TRAIN_FP32)
+    try:
+        n = 2000
+        x = _features(n, 10)
+        r = np.random.default_rng(11)
+        d = r.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+        d = d.astype(np.float32)
+        t = r.exponential(size=n).astype(np.float32)
+        _, ga = a.train_step(x, d, t, lr=0.0)
+        _, gb = b.train_step(x, d, t, lr=0.0)
+        np.testing.assert_allclose(ga, gb, rtol=0, atol=1e-6 * np.abs(gb).max())
+        b.apply_gradient(gb, lr=1e-3)
+        a.apply_gradient(gb, lr=1e-3)
+        np.testing.assert_array_equal(a.params, b.params)     # same gradient, same step
+        pp = p.copy(); mm = np.zeros_like(p); vv = np.zeros_like(p)
+        orc.adam_step(pp, mm, vv, gb.astype(np.float64), 1, lr=1e-3)
+        np.testing.assert_allclose(b.params.astype(np.float64), pp, rtol=1e-5, atol=1e-7)
+        with pytest.raises(m.McrtError):
+            b.apply_gradient(np.full(11560, np.nan, dtype=np.float32))
+    finally:
+        a.close()
+        b.close()

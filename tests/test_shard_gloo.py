@@ -48,6 +48,38 @@ def _worker(rank, world, port, total, out_dir):
         dist.destroy_process_group()
 
 
+def _records(n, seed):
+    r = np.random.default_rng(seed)
+    x = np.concatenate([r.uniform(-1, 1, (n, 3)), r.normal(size=(n, 3)), r.uniform(-8, 6, (n, 3))], axis=1)
+    d = r.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return x, d, r.exponential(size=n)
+
+
+def _dp_worker(rank, world, port, out_dir):
+    """Data-parallel training step of the proposal network: each rank takes
+    the gradient of its own records (the oracle's FP64 gradient stands in
+    for the GPU kernel here), the ranks average them by record count, and
+    each applies the same Adam step."""
+    import torch.distributed as dist
+    import oracle
+    from paper_1902_01137_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        x, d, t = _records(1200, 3)
+        lo, hi = (0, 700) if rank == 0 else (700, 1200)       # uneven shares
+        p = oracle.xavier_init(5)
+        _, g = oracle.mlp_loss_grad(p, x[lo:hi], d[lo:hi], t[lo:hi])
+        avg = shard.average_gradient(g, hi - lo)
+        pp, m, v = p.copy(), np.zeros_like(p), np.zeros_like(p)
+        oracle.adam_step(pp, m, v, avg.astype(np.float64), 1, lr=1e-3)
+        np.savez(os.path.join(out_dir, "dp%d.npz" % rank), avg=avg, params=pp)
+    finally:
+        dist.destroy_process_group()
+
+
 def test_shard_ranges_cover_and_align():
     from paper_1902_01137_gb300 import shard
     for total in (0, 1, 1023, 1024, 5000, 10 ** 6 + 7):
@@ -83,3 +115,20 @@ def test_two_ranks_gloo_match_one_process(tmp_path):
     m, se = shard.mean_se(a["rs1"], a["rs2"], a["rn"][0])
     for q in range(3):
         assert abs(m[q] - one.mean[q]) <= 4 * math.hypot(se[q], one.se[q])
+
+
+def test_data_parallel_training_step_gloo(tmp_path):
+    """Two ranks with 700 and 500 records: the count-weighted gradient
+    average equals the gradient of the mean loss over all 1,200 records,
+    and both ranks end the Adam step with identical parameters."""
+    import torch.multiprocessing as mp
+    import oracle
+    port = 30500 + (os.getpid() % 1000)
+    mp.start_processes(_dp_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
+    a = np.load(tmp_path / "dp0.npz")
+    b = np.load(tmp_path / "dp1.npz")
+    assert np.array_equal(a["avg"], b["avg"]) and np.array_equal(a["params"], b["params"])
+    x, d, t = _records(1200, 3)
+    _, g_all = oracle.mlp_loss_grad(oracle.xavier_init(5), x, d, t)
+    scale = np.abs(g_all).max()
+    np.testing.assert_allclose(a["avg"], g_all, rtol=1e-6, atol=1e-7 * scale)
