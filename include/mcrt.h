@@ -475,6 +475,17 @@ MCRT_API int mcrt_proposal_destroy(mcrt_proposal* proposal);
 MCRT_API int mcrt_proposal_set_params(mcrt_proposal* proposal, const float* host, size_t n);
 MCRT_API int mcrt_proposal_get_params(const mcrt_proposal* proposal, float* host, size_t n);
 
+/* The Adam state (first and second moments, n = 11,560 each, and the step
+ * count) out to / in from host memory, for checkpoints: a network restored
+ * with mcrt_proposal_set_params and then this call continues training
+ * exactly where it stopped.  Set after the parameters (setting those clears
+ * the state).  Errors: MCRT_ERR_BOUNDS (n too small), MCRT_ERR_ARG (a
+ * moment not finite, a negative second moment, a bad step count). */
+MCRT_API int mcrt_proposal_get_adam(const mcrt_proposal* proposal, float* host_m, float* host_v, size_t n,
+                                    int64_t* step);
+MCRT_API int mcrt_proposal_set_adam(mcrt_proposal* proposal, const float* host_m, const float* host_v, size_t n,
+                                    int64_t step);
+
 /* Evaluate the network on n feature rows (host, n x 9 floats, rounded to
  * BF16 on the device as in the tracer).  host_mix receives n x 40 mixture
  * parameters (per lobe: unit axis (3), concentration, weight); host_raw, if

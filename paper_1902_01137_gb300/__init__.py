@@ -154,6 +154,8 @@ def _load():
         "mcrt_proposal_eval": [vp, P(f32), C.c_size_t, P(f32), P(f32)],
         "mcrt_proposal_train_step": [vp, P(f32), P(f32), P(f32), C.c_size_t, f32, P(f32), P(f32)],
         "mcrt_proposal_apply_gradient": [vp, P(f32), f32],
+        "mcrt_proposal_get_adam": [vp, P(f32), P(f32), C.c_size_t, P(C.c_int64)],
+        "mcrt_proposal_set_adam": [vp, P(f32), P(f32), C.c_size_t, C.c_int64],
         "mcrt_proposal_set_training": [vp, i32],
     }
     for name, args in sig.items():
@@ -647,6 +649,24 @@ class Proposal:
 
     def train_step(self, features, dirs, targets, lr=0.0):
         return mcrt_proposal_train_step(self.ctx.h, self.h, features, dirs, targets, lr)
+
+    @property
+    def adam_state(self):
+        """(first moments, second moments, step count) of Adam."""
+        mm = np.zeros(11560, dtype=np.float32)
+        vv = np.zeros(11560, dtype=np.float32)
+        st = C.c_int64()
+        _check(_load().mcrt_proposal_get_adam(self.h, _ptr(mm, C.c_float), _ptr(vv, C.c_float), 11560,
+                                              C.byref(st)), self.ctx.h)
+        return mm, vv, int(st.value)
+
+    @adam_state.setter
+    def adam_state(self, state):
+        mm, vv, st = state
+        mm = np.ascontiguousarray(mm, dtype=np.float32)
+        vv = np.ascontiguousarray(vv, dtype=np.float32)
+        _check(_load().mcrt_proposal_set_adam(self.h, _ptr(mm, C.c_float), _ptr(vv, C.c_float), mm.size, int(st)),
+               self.ctx.h)
 
     def apply_gradient(self, grad, lr=1e-3):
         """One Adam step with a given gradient (data-parallel training)."""

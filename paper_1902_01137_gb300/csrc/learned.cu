@@ -173,6 +173,38 @@ int mcrt_proposal_get_params(const mcrt_proposal* P, float* host, size_t n)
     return MCRT_OK;
 }
 
+int mcrt_proposal_get_adam(const mcrt_proposal* P, float* host_m, float* host_v, size_t n, int64_t* step)
+{
+    const char* who = "mcrt_proposal_get_adam";
+    if (!P || !host_m || !host_v || !step) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = P->ctx;
+    if (n < (size_t)kMlpParams) return lfail(ctx, MCRT_ERR_BOUNDS, "%s: need %d values", who, kMlpParams);
+    LCK(ctx, cudaSetDevice(ctx->device));
+    LCK(ctx, cudaMemcpyAsync(host_m, P->d_m, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    LCK(ctx, cudaMemcpyAsync(host_v, P->d_v, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    LCK(ctx, cudaStreamSynchronize(ctx->stream));
+    *step = P->step;
+    return MCRT_OK;
+}
+
+int mcrt_proposal_set_adam(mcrt_proposal* P, const float* host_m, const float* host_v, size_t n, int64_t step)
+{
+    const char* who = "mcrt_proposal_set_adam";
+    if (!P || !host_m || !host_v) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = P->ctx;
+    if (n < (size_t)kMlpParams) return lfail(ctx, MCRT_ERR_BOUNDS, "%s: need %d values", who, kMlpParams);
+    if (step < 0 || step > (int64_t)1 << 30) return lfail(ctx, MCRT_ERR_ARG, "%s: bad step count", who);
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(host_m[i]) || !(host_v[i] >= 0.0f) || !std::isfinite(host_v[i]))
+            return lfail(ctx, MCRT_ERR_ARG, "%s: moment %d not finite (or second moment < 0)", who, i);
+    LCK(ctx, cudaSetDevice(ctx->device));
+    LCK(ctx, cudaMemcpyAsync(P->d_m, host_m, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    LCK(ctx, cudaMemcpyAsync(P->d_v, host_v, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    LCK(ctx, cudaStreamSynchronize(ctx->stream));
+    P->step = (int)step;
+    return MCRT_OK;
+}
+
 int mcrt_proposal_eval(mcrt_proposal* P, const float* host_feat, size_t n, float* host_mix, float* host_raw)
 {
     if (!P || !host_feat || !host_mix) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "mcrt_proposal_eval: NULL argument");

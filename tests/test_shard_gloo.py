@@ -132,3 +132,54 @@ def test_data_parallel_training_step_gloo(tmp_path):
     _, g_all = oracle.mlp_loss_grad(oracle.xavier_init(5), x, d, t)
     scale = np.abs(g_all).max()
     np.testing.assert_allclose(a["avg"], g_all, rtol=1e-6, atol=1e-7 * scale)
+
+
+_DYING = r'''
+import os, sys, time, json
+from datetime import timedelta
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch.distributed as dist
+from paper_1902_01137_gb300 import shard
+rank = int(sys.argv[1])
+os.environ["MASTER_ADDR"] = "127.0.0.1"
+os.environ["MASTER_PORT"] = {port!r}
+dist.init_process_group("gloo", rank=rank, world_size=2, timeout=timedelta(seconds=4))
+shard.reduce_sums([np.ones(3)])                # one step together
+if rank == 1:
+    os._exit(0)                                # this rank leaves between steps
+t0 = time.time()
+try:
+    shard.reduce_sums([np.ones(3)])
+    out = "returned"
+except Exception as e:                         # the survivor learns of it
+    out = "raised " + type(e).__name__
+with open({res!r}, "w") as f:
+    json.dump({{"result": out, "seconds": time.time() - t0}}, f)
+os._exit(0)
+'''
+
+
+def test_rank_leaving_is_detected_not_hung(tmp_path):
+    """A rank that exits between steps: the other rank's next reduction
+    ends with an error within the process group's timeout (4 s here)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    port = str(31500 + (os.getpid() % 1000))
+    res = str(tmp_path / "survivor.json")
+    script = tmp_path / "dying.py"
+    script.write_text(_DYING.format(root=root, port=port, res=res))
+    procs = [subprocess.Popen([sys.executable, str(script), str(r)]) for r in (0, 1)]
+    try:
+        for p in procs:
+            p.wait(timeout=90)
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()                                 # our own child, by handle
+    with open(res) as f:
+        out = json.load(f)
+    assert out["result"].startswith("raised"), out
+    assert out["seconds"] < 60, out
