@@ -543,6 +543,16 @@ MCRT_API int mcrt_debug_dda_grid(const mcrt_scene* scene, const float o[3], cons
 MCRT_API int mcrt_debug_terrain(const mcrt_scene* scene, int32_t n, const float* o, const float* d, float* t_out);
 MCRT_API int mcrt_debug_terrain_height(const mcrt_scene* scene, int32_t n, const float* xy, float* zn_out);
 
+/* Bounds-checked build (built with -DMCRT_CHECKED): *checked_build = 1 and
+ * *count = the index violations the trace kernels have recorded since the
+ * last call (then cleared), *first_code the first one's kind (1 voxel,
+ * 2 leaf-map entry, 3 tally entry, 4 heightfield corner, 5 heightfield
+ * pyramid cell); such an index is clamped, never followed.  In the normal
+ * build *checked_build = 0 and *count = 0.  Synchronises the context
+ * stream. */
+MCRT_API int mcrt_debug_bounds_violations(mcrt_ctx* ctx, int32_t* checked_build, uint64_t* count,
+                                          int32_t* first_code);
+
 /* Philox4x32-10 evaluated on the device for n (counter[4], key[2]) pairs
  * (host arrays); out receives 4 words per pair. */
 MCRT_API int mcrt_debug_philox(mcrt_ctx* ctx, const uint32_t* counters, const uint32_t* keys, uint32_t* out, size_t n);

@@ -18,7 +18,9 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# MCRT_LIBRARY selects another build of the same library (e.g. the
+# bounds-checked variant, build(checked=True)); default: the in-tree build.
+LIB_PATH = os.environ.get("MCRT_LIBRARY") or _build.LIB
 
 MCRT_OK = 0
 MCRT_ERR_ARG = -1
@@ -139,6 +141,7 @@ def _load():
         "mcrt_debug_dda": [vp, P(f32), P(f32), f32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_dda_grid": [vp, P(f32), P(f32), f32, i32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
+        "mcrt_debug_bounds_violations": [vp, P(i32), P(u64), P(i32)],
         "mcrt_trace_batch": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
         "mcrt_autotune_batch": [vp, P(BatchItem), i32, C.c_double, P(TraceOpts), P(f32)],
         "mcrt_batch_plan_create": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
@@ -403,6 +406,13 @@ def mcrt_debug_dda(ctx, scene, o, d, tau_merge=1.0, finest_level=1, cap=4096, gr
                                        grid, _ptr(cells, C.c_int32), _ptr(tio, C.c_float), cap, C.byref(n),
                                        C.byref(st)), ctx)
     return cells[:n.value].copy(), tio[:n.value].copy(), st.value
+
+
+def mcrt_debug_bounds_violations(ctx):
+    """(checked build?, violations since the last call, first code)."""
+    chk, n, code = C.c_int32(), C.c_uint64(), C.c_int32()
+    _check(_load().mcrt_debug_bounds_violations(ctx, C.byref(chk), C.byref(n), C.byref(code)), ctx)
+    return bool(chk.value), int(n.value), int(code.value)
 
 
 def mcrt_debug_philox(ctx, ctr, key) -> np.ndarray:

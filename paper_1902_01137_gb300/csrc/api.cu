@@ -1480,6 +1480,20 @@ int mcrt_tally_destroy(mcrt_tally* t)
 // ---------------------------------------------------------------------------
 // Checks
 // ---------------------------------------------------------------------------
+int mcrt_debug_bounds_violations(mcrt_ctx* ctx, int32_t* checked_build, uint64_t* count, int32_t* first_code)
+{
+    if (!ctx || !checked_build || !count || !first_code)
+        return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_bounds_violations: NULL argument");
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    unsigned n = 0, code = 0;
+    CK(ctx, read_bounds_violations(&n, &code));
+    *checked_build = bounds_checked_build() ? 1 : 0;
+    *count = n;
+    *first_code = (int32_t)code;
+    return MCRT_OK;
+}
+
 int mcrt_debug_dda(const mcrt_scene* sc_c, const float o[3], const float d[3], float tau, int32_t finest,
                    int32_t* cells, float* tio, int32_t cap, int32_t* count, int32_t* status)
 {

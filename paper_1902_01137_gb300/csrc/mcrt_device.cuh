@@ -20,6 +20,24 @@
 
 namespace mcrt {
 
+// Bounds-checked build (-DMCRT_CHECKED; the default build compiles every
+// check away): MCRT_CHECK(cond, code) counts a violated index condition in
+// a device word of this translation unit and keeps the first code; the
+// caller then clamps the index, so nothing faults.  Codes: 1 voxel, 2
+// leaf-map entry, 3 tally entry, 4 heightfield corner, 5 heightfield
+// pyramid cell.
+#ifdef MCRT_CHECKED
+static __device__ unsigned int g_mcrt_bounds[2];   // violations, first code
+__device__ __forceinline__ void mcrt_bounds_fail(unsigned code)
+{
+    atomicAdd(&g_mcrt_bounds[0], 1u);
+    atomicCAS(&g_mcrt_bounds[1], 0u, code);
+}
+#define MCRT_CHECK(cond, code) do { if (!(cond)) mcrt_bounds_fail(code); } while (0)
+#else
+#define MCRT_CHECK(cond, code) do { } while (0)
+#endif
+
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInv4Pi = 0.0795774715459476679f;
 
@@ -109,6 +127,12 @@ __device__ __forceinline__ size_t brick_index(const DevScene& S, int i, int j, i
 template <bool BF16>
 __device__ __forceinline__ float kfetch(const DevScene& S, int i, int j, int k)
 {
+#ifdef MCRT_CHECKED
+    MCRT_CHECK(i >= 0 && i < S.n[0] && j >= 0 && j < S.n[1] && k >= 0 && k < S.n[2], 1);
+    i = min(max(i, 0), S.n[0] - 1);
+    j = min(max(j, 0), S.n[1] - 1);
+    k = min(max(k, 0), S.n[2] - 1);
+#endif
     const size_t idx = brick_index(S, i, j, k);
     if (BF16) return __uint_as_float((uint32_t)__ldg(S.vox16 + idx) << 16);
     return __ldg(S.vox + idx);
@@ -151,7 +175,16 @@ __device__ __forceinline__ int locate(float p, float d, float h, float inv_h, in
 __device__ __forceinline__ const uint2* leaf_entry(const DevScene& S, const int v[3])
 {
     const int b = S.lb;
+#ifdef MCRT_CHECKED
+    int w[3];
+    for (int a = 0; a < 3; ++a) {
+        MCRT_CHECK(v[a] >= 0 && v[a] < S.n[a] && (v[a] >> b) < S.nl[a], 2);
+        w[a] = min(max(v[a], 0), S.n[a] - 1);
+    }
+    return S.leaf + ((size_t)(w[2] >> b) * S.nl[1] + (w[1] >> b)) * S.nl[0] + (w[0] >> b);
+#else
     return S.leaf + ((size_t)(v[2] >> b) * S.nl[1] + (v[1] >> b)) * S.nl[0] + (v[0] >> b);
+#endif
 }
 
 // Finish entering the leaf holding R.v from its leaf-map entry: size,
@@ -396,6 +429,8 @@ __device__ __forceinline__ void hf_corners(const DevScene& S, int i, int j, floa
 {
     const int i0 = hf_wrap(S, 0, i, 0), i1 = hf_wrap(S, 0, i + 1, 0);
     const size_t r0 = (size_t)hf_wrap(S, 1, j, 0) * S.hn[0], r1 = (size_t)hf_wrap(S, 1, j + 1, 0) * S.hn[0];
+    MCRT_CHECK(i0 >= 0 && i0 < S.hn[0] && i1 >= 0 && i1 < S.hn[0] && r0 < (size_t)S.hn[0] * S.hn[1] &&
+                   r1 < (size_t)S.hn[0] * S.hn[1], 4);
     h[0] = __ldg(S.hf + r0 + i0);
     h[1] = __ldg(S.hf + r0 + i1);
     h[2] = __ldg(S.hf + r1 + i0);
@@ -481,6 +516,8 @@ __device__ __forceinline__ bool terrain_walk_step(const DevScene& S, const float
                    : d[1] < 0.0f ? ((float)W.j * cy - o[1]) * inv_d[1] : kInf;
     const float te = fmaxf(fminf(fminf(tx, ty), W.t1), W.t);
     const int nx = S.hn[0] >> sh;
+    MCRT_CHECK(W.L >= 0 && W.L < S.hlev && hf_wrap(S, 0, W.i, W.L) < nx && hf_wrap(S, 1, W.j, W.L) < (S.hn[1] >> sh) &&
+                   hf_wrap(S, 0, W.i, W.L) >= 0 && hf_wrap(S, 1, W.j, W.L) >= 0, 5);
     const float cmax = __ldg(S.hpyr + S.hoff[W.L] + (size_t)hf_wrap(S, 1, W.j, W.L) * nx + hf_wrap(S, 0, W.i, W.L));
     const float zlo = __fmaf_rn(d[2] < 0.0f ? te : W.t, d[2], o[2]);
     if (zlo <= cmax) {

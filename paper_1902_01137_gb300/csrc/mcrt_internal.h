@@ -198,6 +198,8 @@ cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, bool
 int trace_batch_blocks_per_sm(bool bf16, bool count, bool dalpha, int block);
 cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
                             int nq, double* out, cudaStream_t st);
+bool bounds_checked_build();
+cudaError_t read_bounds_violations(unsigned* count, unsigned* first_code);
 int order_tiles(int width, int height, int* tiles_x);
 cudaError_t launch_view_cost(const TraceParams& P, bool bf16, float* cost, cudaStream_t st);
 cudaError_t launch_expand_order(const uint32_t* tiles, const uint32_t* prefix, int n, int width, int height,

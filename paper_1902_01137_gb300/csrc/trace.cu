@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         while (fmask) {
             const int src = __ffs(fmask) - 1;
             const unsigned c = __shfl_sync(kFull, cell, src);
+            MCRT_CHECK(c < (SENSOR == kCamera ? (unsigned)(P.width * P.height) : (BATCH ? (unsigned)P.n_items : 1u)), 3);
             const bool mine = pending && cell == c;
 #pragma unroll
             for (int q = 0; q < 2 * NQ; ++q) {
@@ -1102,6 +1103,34 @@ cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, 
         debug_dda_kernel<false><<<1, 32, 0, st>>>(S, o[0], o[1], o[2], d[0], d[1], d[2], cap, cells, tio,
                                                    count_status);
     return cudaGetLastError();
+}
+
+// Bounds-checked build: read (and clear) this unit's violation word.
+bool bounds_checked_build()
+{
+#ifdef MCRT_CHECKED
+    return true;
+#else
+    return false;
+#endif
+}
+
+cudaError_t read_bounds_violations(unsigned* count, unsigned* first_code)
+{
+    *count = 0;
+    *first_code = 0;
+#ifdef MCRT_CHECKED
+    unsigned h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_mcrt_bounds, sizeof(h));
+    if (e != cudaSuccess) return e;
+    const unsigned zero[2] = {0, 0};
+    e = cudaMemcpyToSymbol(g_mcrt_bounds, zero, sizeof(zero));
+    *count = h[0];
+    *first_code = h[1];
+    return e;
+#else
+    return cudaSuccess;
+#endif
 }
 
 int order_tiles(int width, int height, int* tiles_x)
