@@ -188,6 +188,7 @@ int mcrt_launch_count(const mcrt_ctx* ctx, uint64_t* count)
 // ---------------------------------------------------------------------------
 int mcrt_scene_create(mcrt_ctx* ctx, const mcrt_field_desc* d, mcrt_scene** out)
 {
+    NvtxRange nvtx_range("mcrt_scene_create");
     if (!ctx || !d || !out) return fail(ctx, MCRT_ERR_ARG, "mcrt_scene_create: NULL argument");
     *out = nullptr;
     ctx->err.clear();
@@ -291,6 +292,7 @@ int mcrt_scene_destroy(mcrt_scene* sc)
 
 int mcrt_scene_build_majorants(mcrt_scene* sc, int32_t levels)
 {
+    NvtxRange nvtx_range("mcrt_scene_build_majorants");
     if (!sc) return fail(nullptr, MCRT_ERR_ARG, "mcrt_scene_build_majorants: NULL scene");
     mcrt_ctx* ctx = sc->ctx;
     if (levels < 0 || levels > 8)
@@ -362,6 +364,7 @@ int mcrt_scene_read_minorants(const mcrt_scene* sc, int32_t level, float* host_o
 
 int mcrt_scene_build_octree(mcrt_scene* sc, int32_t levels)
 {
+    NvtxRange nvtx_range("mcrt_scene_build_octree");
     const char* who = "mcrt_scene_build_octree";
     if (!sc) return fail(nullptr, MCRT_ERR_ARG, "%s: NULL scene", who);
     mcrt_ctx* ctx = sc->ctx;
@@ -478,6 +481,7 @@ int mcrt_scene_set_ground_flat(mcrt_scene* sc, float albedo)
 int mcrt_scene_set_ground_heightfield(mcrt_scene* sc, const float* heights, int32_t hnx, int32_t hny, int32_t mem,
                                       float albedo)
 {
+    NvtxRange nvtx_range("mcrt_scene_set_ground_heightfield");
     const char* who = "mcrt_scene_set_ground_heightfield";
     if (!sc || !heights) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
     mcrt_ctx* ctx = sc->ctx;
@@ -890,6 +894,7 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
 int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp, uint64_t seed,
                       const mcrt_trace_opts* opts, mcrt_tally** tally)
 {
+    NvtxRange nvtx_range("mcrt_trace_camera");
     const char* who = "mcrt_trace_camera";
     if (!sc || !cam || !tally) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
     mcrt_ctx* ctx = sc->ctx;
@@ -976,6 +981,7 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
 
 int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_trace_opts* opts, mcrt_tally** tally)
 {
+    NvtxRange nvtx_range("mcrt_trace_flux");
     const char* who = "mcrt_trace_flux";
     if (!sc || !tally) return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
     mcrt_ctx* ctx = sc->ctx;
@@ -1122,6 +1128,7 @@ extern "C" {
 int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const mcrt_trace_opts* opts,
                      mcrt_tally** tally)
 {
+    NvtxRange nvtx_range("mcrt_trace_batch");
     const char* who = "mcrt_trace_batch";
     if (!ctx || !items || !tally) return fail(ctx, MCRT_ERR_ARG, "%s: NULL argument", who);
     ctx->err.clear();
@@ -1168,6 +1175,7 @@ int mcrt_trace_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, con
 int mcrt_autotune_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, double path_fraction,
                         mcrt_trace_opts* opts_inout, float* best_ms)
 {
+    NvtxRange nvtx_range("mcrt_autotune_batch");
     const char* who = "mcrt_autotune_batch";
     if (!ctx || !items || !opts_inout) return fail(ctx, MCRT_ERR_ARG, "%s: NULL argument", who);
     if (!(path_fraction > 0.0 && path_fraction <= 1.0)) return fail(ctx, MCRT_ERR_ARG, "%s: path_fraction in (0, 1]", who);
@@ -1248,6 +1256,7 @@ void plan_free(mcrt_batch_plan* p)
 int mcrt_batch_plan_create(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const mcrt_trace_opts* opts,
                            mcrt_batch_plan** out)
 {
+    NvtxRange nvtx_range("mcrt_batch_plan_create");
     const char* who = "mcrt_batch_plan_create";
     if (!ctx || !items || !out) return fail(ctx, MCRT_ERR_ARG, "%s: NULL argument", who);
     *out = nullptr;
@@ -1327,6 +1336,7 @@ int mcrt_batch_plan_set_seeds(mcrt_batch_plan* p, const uint64_t* seeds, int32_t
 
 int mcrt_batch_plan_run(mcrt_batch_plan* p, double* mean, double* se, size_t count, float* kernel_ms)
 {
+    NvtxRange nvtx_range("mcrt_batch_plan_run");
     const char* who = "mcrt_batch_plan_run";
     if (!p) return fail(nullptr, MCRT_ERR_ARG, "%s: NULL plan", who);
     mcrt_ctx* ctx = p->ctx;

@@ -207,6 +207,7 @@ int mcrt_proposal_set_adam(mcrt_proposal* P, const float* host_m, const float* h
 
 int mcrt_proposal_eval(mcrt_proposal* P, const float* host_feat, size_t n, float* host_mix, float* host_raw)
 {
+    NvtxRange nvtx_range("mcrt_proposal_eval");
     if (!P || !host_feat || !host_mix) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "mcrt_proposal_eval: NULL argument");
     mcrt_ctx* ctx = P->ctx;
     if (n == 0) return MCRT_OK;
@@ -240,6 +241,7 @@ int mcrt_proposal_eval(mcrt_proposal* P, const float* host_feat, size_t n, float
 int mcrt_proposal_train_step(mcrt_proposal* P, const float* host_feat, const float* host_dirs,
                              const float* host_targets, size_t n, float lr, float* loss_out, float* host_grad)
 {
+    NvtxRange nvtx_range("mcrt_proposal_train_step");
     if (!P || !host_feat || !host_dirs || !host_targets)
         return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "mcrt_proposal_train_step: NULL argument");
     mcrt_ctx* ctx = P->ctx;
@@ -289,6 +291,7 @@ int mcrt_proposal_train_step(mcrt_proposal* P, const float* host_feat, const flo
 
 int mcrt_proposal_apply_gradient(mcrt_proposal* P, const float* host_grad, float lr)
 {
+    NvtxRange nvtx_range("mcrt_proposal_apply_gradient");
     const char* who = "mcrt_proposal_apply_gradient";
     if (!P || !host_grad) return lfail(P ? P->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
     mcrt_ctx* ctx = P->ctx;

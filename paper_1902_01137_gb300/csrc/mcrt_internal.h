@@ -8,8 +8,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mcrt.h"
 #include "mcrt_device.cuh"
+
+// One NVTX range per public call (named after it), so a profiler's timeline
+// and its kernel filters (ncu --nvtx --nvtx-include "mcrt_trace_camera/")
+// see the library's calls; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct mcrt_ctx {
     int device = 0;

@@ -79,6 +79,7 @@ __global__ void noalloc_finalize_kernel(double n, int count, double* __restrict_
 extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp, uint64_t seed,
                                          const mcrt_trace_opts* opts, double* d_mean, double* d_stderr)
 {
+    NvtxRange nvtx_range("mcrt_trace_camera_noalloc");
     const char* who = "mcrt_trace_camera_noalloc";
     if (!sc || !cam || !d_mean || !d_stderr) return nfail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
     mcrt_ctx* ctx = sc->ctx;
