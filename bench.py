@@ -54,13 +54,13 @@ WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x
 W, H, SPP = 1024, 1024, 64
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
-PROFILED_TRACE_SHA = "57cf5627c682072d"
-PROFILED_DRAM_BYTES_PER_PATH = 24.14
+PROFILED_TRACE_SHA = "a962f2fa6c79b4d0"
+PROFILED_DRAM_BYTES_PER_PATH = 24.29
 # issue-slot figures of the same capture (smsp__issue_active, threads per
 # warp instruction); the kernel is issue-bound, so these locate it against
 # its real ceiling: 152 SMs x 4 schedulers x 1 warp instruction per cycle
-PROFILED_ISSUE_ACTIVE = 0.7355
-PROFILED_THREADS_PER_INST = 13.07
+PROFILED_ISSUE_ACTIVE = 0.7216
+PROFILED_THREADS_PER_INST = 13.09
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
 
 
