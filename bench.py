@@ -49,9 +49,11 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from scenes.configs import CONFIGS  # noqa: E402
+
 METRIC = "paths/s and 1/(variance x time) at 1% rel. std err, learned vs plain, 1 GB300"
 WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x 64 spp, sun 60 deg"
-W, H, SPP = 1024, 1024, 64
+W, H, SPP = CONFIGS[1].image.width, CONFIGS[1].image.height, CONFIGS[1].image.spp
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
 PROFILED_TRACE_SHA = "a962f2fa6c79b4d0"
@@ -157,10 +159,8 @@ class ClockSampler:
 
 
 def make_workload():
-    import scenes
-    spec = scenes.cumulus(512, 512, 160, seed=0)
-    cam = scenes.nadir_camera(spec, W, H)
-    return spec, cam
+    spec = CONFIGS[1].scene()
+    return spec, CONFIGS[1].camera(spec)
 
 
 # ---------------------------------------------------------------------------
@@ -712,7 +712,7 @@ def batch_oracle_sample(inst, target_s=12.0):
 # ---------------------------------------------------------------------------
 # Refinement sweep with a heightfield ground
 # ---------------------------------------------------------------------------
-SWEEP = ((128, 40), (256, 80), (512, 160), (1024, 320), (2048, 640))
+SWEEP = CONFIGS[2].sizes
 
 
 def run_sweep(args):
