@@ -717,6 +717,7 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     const int block = o->block_size ? o->block_size : 128;
     int grid = o->grid_size;
     if (!grid) grid = ctx->sm_count * trace_blocks_per_sm(sensor, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP || P.S.rayleigh, block);
+    if (!o->chunk) P.chunk = auto_chunk(P.total, (unsigned long long)grid * block, sensor == kCamera ? P.spp : 0u);
     P.s1 = t->d_s1;
     P.s2 = t->d_s2;
     P.counters = t->d_counters;

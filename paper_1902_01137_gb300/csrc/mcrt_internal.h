@@ -210,6 +210,23 @@ cudaError_t launch_trace_batch(const TraceParams& P, bool bf16, bool count, bool
 int trace_batch_blocks_per_sm(bool bf16, bool count, bool dalpha, int block);
 cudaError_t launch_finalize(const double* s1, const double* s2, double n, int count, const unsigned long long* cell_n,
                             int nq, double* out, cudaStream_t st);
+// Default paths per claim (mcrt_trace_opts.chunk = 0).  A lane traces the
+// paths of its chunk one after another, so with few paths per resident
+// lane long chunks stretch the launch's tail (a chunk of one cloudy pixel
+// holds several long random walks); with many, short chunks cost claims.
+// Thresholds from GB300 measurements on the cumulus field: chunk 1 below
+// 48 paths per lane, 2 below 160, else 4; camera chunks divide spp.
+inline uint32_t auto_chunk(unsigned long long total, unsigned long long lanes, uint32_t spp)
+{
+    const double per_lane = lanes ? (double)total / (double)lanes : 0.0;
+    uint32_t c = per_lane < 48.0 ? 1u : (per_lane < 160.0 ? 2u : 4u);
+    if (spp) {
+        if (c > spp) c = spp;
+        while (spp % c) --c;
+    }
+    return c;
+}
+
 bool bounds_checked_build();
 cudaError_t read_bounds_violations(unsigned* count, unsigned* first_code);
 int order_tiles(int width, int height, int* tiles_x);

@@ -194,6 +194,7 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;
     const int grid = o->grid_size ? o->grid_size : ctx->sm_count * trace_blocks_per_sm(kCamera, bf16, count, P.S.hf != nullptr, P.sun_mode == MCRT_SUN_DECOMP || P.S.rayleigh, block);
+    if (!o->chunk) P.chunk = auto_chunk(P.total, (unsigned long long)grid * block, spp);
     ctx->launches++;
     e = launch_trace(P, kCamera, bf16, count, grid, block, ctx->stream);
     if (e != cudaSuccess) return nfail(ctx, MCRT_ERR_CUDA, "%s: trace launch: %s", who, cudaGetErrorString(e));
