@@ -822,7 +822,10 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
         for (int r = 0; r <= NL && e == cudaSuccess; ++r) {
             P.resume = r > 0;
             P.total = r == 0 ? nb : n_in;
-            P.chunk = r == 0 ? P0.chunk : 1u;
+            P.chunk = r > 0 ? 1u
+                            : (o->chunk ? P0.chunk
+                                        : auto_chunk(nb, (unsigned long long)grid * block,
+                                                     sensor == kCamera ? (uint32_t)spp : 0u));
             P.qin = qin; P.qin_feat = fin_feat; P.qin_mix = mix;
             P.qout = qout; P.qout_feat = fout; P.qout_count = cnt; P.qout_cap = (unsigned)nb;
             if (P.total == 0) break;
