@@ -8,7 +8,8 @@ size:
   64 spp, default options): the majorant pyramid and the octree of the
   whole field bit-exact; 512 sampled pixels traced by the oracle with the
   same path ids, paired per pixel (same random numbers) and within 4
-  combined SE over the sample.
+  combined SE over the sample -- over the pyramid (the headline) and over
+  the octree (the line's octree figure).
 * The bench batch (96 instances, 814 items, autotuned launch shape, over
   the octree as the bench traces it): sampled items against the oracle's
   trace of the same item's first paths over the same octree (same seeds
@@ -91,6 +92,18 @@ def test_bench_image_full_size(env, orc):
         sg = math.sqrt(np.sum(gs ** 2)) / pix.size
         so = math.sqrt(np.sum(os_ ** 2)) / pix.size
         assert close_4se(gm.mean(), sg, om.mean(), so), (gm.mean(), om.mean(), sg, so)
+        # the bench line's octree figure: the same image over the octree,
+        # finest leaves 2^3 voxels, against the oracle over the same octree
+        g2 = sc.trace_camera(cam, bench.SPP, seed=seed, grid=m.MCRT_GRID_OCTREE, finest_level=1)
+        o2, st2 = orc.trace_camera(_oscene(orc, spec, grid=1, finest_level=1), oc, bench.SPP, seed, pixels=pix)
+        assert st2[0] == 0
+        gm2, gs2 = g2.mean.ravel()[pix], g2.se.ravel()[pix]
+        om2, os2 = o2.mean.ravel()[pix], o2.se.ravel()[pix]
+        rel2 = np.abs(gm2 - om2) / np.maximum(np.abs(om2), 1e-3)
+        assert np.median(rel2) < 1e-3, np.median(rel2)
+        sg2 = math.sqrt(np.sum(gs2 ** 2)) / pix.size
+        so2 = math.sqrt(np.sum(os2 ** 2)) / pix.size
+        assert close_4se(gm2.mean(), sg2, om2.mean(), so2), (gm2.mean(), om2.mean(), sg2, so2)
     finally:
         sc.close()
 
