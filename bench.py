@@ -64,6 +64,8 @@ PROFILED_DRAM_BYTES_PER_PATH = 24.29
 PROFILED_ISSUE_ACTIVE = 0.7216
 PROFILED_THREADS_PER_INST = 13.09
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
+# the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
+PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.26
 
 
 def trace_sources_sha() -> str:
@@ -349,10 +351,36 @@ def run_gpu(args):
         if world > 1:
             from paper_1902_01137_gb300 import shard
             oct_total = shard.max_over_ranks(oct_total)
+        # its own roofline: algorithmic bytes from a counting run on the same seed
+        sc = new_scene(k_dev)
+        try:
+            sc.build_octree()
+            oc = m.mcrt_trace_opts_default()
+            oc.grid, oc.finest_level, oc.count_events = m.MCRT_GRID_OCTREE, 1, 1
+            ct = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, base_seed + 100, oc)
+            ocnt = m.mcrt_tally_counters(ctx.h, ct)
+            m.mcrt_tally_destroy(ct)
+        finally:
+            sc.close()
+        o_alg = 4 * (ocnt["tentative"] + ocnt["sun_tentative"]) + 4 * (ocnt["leaf_steps"] + ocnt["sun_leaf_steps"] +
+                                                                      ocnt["sun_rays"] + ocnt.get("flights", 0))
+        o_kavg = statistics.mean(oct_kern_ms)
+        o_ach = o_alg / (o_kavg / 1e3) / 1e9
+        o_peak = peaks()["hbm_gbs"] if peaks() else 6800.0
+        o_traffic = None
+        try:
+            if trace_sources_sha() == PROFILED_TRACE_SHA:
+                o_traffic = PROFILED_OCTREE_DRAM_BYTES_PER_PATH * paths_per_step
+        except OSError:
+            pass
         octree = {"value": world * paths_per_step * args.steps / (oct_total / 1e3), "unit": "paths/s",
-                  "ms_per_step": oct_total / args.steps, "kernel_ms": statistics.mean(oct_kern_ms),
+                  "ms_per_step": oct_total / args.steps, "kernel_ms": o_kavg,
                   "grid": "2^L octree (Sec. 3.1.1), %d levels, tau~ 1, finest level 1" % ctx_octree_levels(spec),
-                  "steps": args.steps, "l2": "flushed between steps"}
+                  "steps": args.steps, "l2": "flushed between steps",
+                  "roofline": {"bound": "hbm", "achieved": o_ach, "peak": o_peak, "unit": "GB/s",
+                               "frac": o_ach / o_peak, "traffic": o_traffic, "alg_bytes_per_launch": o_alg,
+                               "leaf_steps_per_path": (ocnt["leaf_steps"] + ocnt["sun_leaf_steps"]) / paths_per_step,
+                               "tentative_per_path": (ocnt["tentative"] + ocnt["sun_tentative"]) / paths_per_step}}
 
     # e2e: pinned host field in, image mean/SE out, through the C ABI
     e2e_val = None
