@@ -49,11 +49,11 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from scenes.configs import CONFIGS  # noqa: E402
+from scenes.configs import CUMULUS, REFINEMENT_SWEEP  # noqa: E402
 
 METRIC = "paths/s and 1/(variance x time) at 1% rel. std err, learned vs plain, 1 GB300"
 WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x 64 spp, sun 60 deg"
-W, H, SPP = CONFIGS[1].image.width, CONFIGS[1].image.height, CONFIGS[1].image.spp
+W, H, SPP = CUMULUS.image.width, CUMULUS.image.height, CUMULUS.image.spp
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
 PROFILED_TRACE_SHA = "a962f2fa6c79b4d0"
@@ -161,8 +161,8 @@ class ClockSampler:
 
 
 def make_workload():
-    spec = CONFIGS[1].scene()
-    return spec, CONFIGS[1].camera(spec)
+    spec = CUMULUS.scene()
+    return spec, CUMULUS.camera(spec)
 
 
 # ---------------------------------------------------------------------------
@@ -740,7 +740,7 @@ def batch_oracle_sample(inst, target_s=12.0):
 # ---------------------------------------------------------------------------
 # Refinement sweep with a heightfield ground
 # ---------------------------------------------------------------------------
-SWEEP = CONFIGS[2].sizes
+SWEEP = REFINEMENT_SWEEP.sizes
 
 
 def run_sweep(args):

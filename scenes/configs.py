@@ -1,13 +1,13 @@
-"""The five benchmark configurations as data: every constant of a workload
-in one place, with its seed.  The scene generators in this package build
-the fields; bench.py and the tests read sizes, sample counts and options
-from here.
+"""The five benchmark workloads as data: every constant of a workload in
+one place, with its seed.  The scene generators in this package build the
+fields; bench.py and the tests read sizes, sample counts and options from
+here.
 
-C0  plain method, small: the blob field, a 64 x 64 image and ground flux.
-C1  plain method, LES-like cumulus: the bench image.
-C2  refinement sweep plus precision: five resolutions over a heightfield.
-C3  batching: 96 uneven flux problems in one launch.
-C4  learned proposal on the C1 field.
+PLAIN_SMALL       plain method on the blob field: a 64 x 64 image and ground flux.
+CUMULUS           plain method on the LES-like cumulus: the bench image.
+REFINEMENT_SWEEP  five resolutions of the cumulus over a heightfield, FP32 and BF16.
+BATCHING          96 uneven flux problems in one launch.
+LEARNED_PROPOSAL  the learned scattering proposal on the cumulus field.
 """
 from __future__ import annotations
 
@@ -26,7 +26,7 @@ class ImageConfig:
 
 @dataclass(frozen=True)
 class PlainSmall:
-    """C0: 64x64x32 voxels of 100 m, three Gaussian blobs (peak 50 km^-1)
+    """64x64x32 voxels of 100 m, three Gaussian blobs (peak 50 km^-1)
     over clear sky 0.01 km^-1; albedo 1 in cloud, 0.9 in clear sky; HG
     g 0.85; Lambertian ground 0.2; sun zenith 30 deg; 2-level pyramid."""
     field_seed: int = 0
@@ -40,7 +40,7 @@ class PlainSmall:
 
 @dataclass(frozen=True)
 class Cumulus:
-    """C1: 512x512x160 voxels of 25 m (20 % cover, spectral slope -5/3,
+    """512x512x160 voxels of 25 m (20 % cover, spectral slope -5/3,
     base 800 m, log-normal LWC median 0.3 g/m^3, r_eff 10 um); albedo 0.999
     in cloud; HG g 0.86; ground 0.1; sun zenith 60 deg; 3-level pyramid;
     a 1024 x 1024 nadir image at 64 paths per pixel."""
@@ -58,7 +58,7 @@ class Cumulus:
 
 @dataclass(frozen=True)
 class RefinementSweep:
-    """C2: the cumulus statistics at five resolutions of the same 12.8 km
+    """The cumulus statistics at five resolutions of the same 12.8 km
     domain, over a 4096 x 4096 fractal heightfield (0-300 m relief), 1e8
     flux paths per point, FP32 and BF16 storage, sun zenith 60 deg."""
     sizes: tuple = ((128, 40), (256, 80), (512, 160), (1024, 320), (2048, 640))
@@ -74,7 +74,7 @@ class RefinementSweep:
 
 @dataclass(frozen=True)
 class Batching:
-    """C3: 96 instances, fields from 64^2x32 to 1024^2x160, 1-16 bands with
+    """96 instances, fields from 64^2x32 to 1024^2x160, 1-16 bands with
     log-normal gas absorption (median 1e-3 km^-1, sigma_ln 2), sun zenith
     uniform in [0, 75] deg, 1e5-1e7 paths each; tallies T_dir, T_dif and
     dT/dg; launch shapes from the autotuner."""
@@ -89,7 +89,7 @@ class Batching:
 
 @dataclass(frozen=True)
 class LearnedProposal:
-    """C4: the C1 field; MLP 9 -> 64 -> 64 -> 64 -> 40 (GELU), an 8-lobe vMF
+    """The cumulus field; MLP 9 -> 64 -> 64 -> 64 -> 40 (GELU), an 8-lobe vMF
     mixture MIS-mixed with HG at alpha 0.5; online Adam (lr 1e-3, 2^20
     vertices per step); 1/(variance x time) for the ground flux and a
     512 x 512 image at sun zenith 60 deg, against plain HG."""
@@ -101,4 +101,8 @@ class LearnedProposal:
     flux_paths: int = 1 << 24
 
 
-CONFIGS = {0: PlainSmall(), 1: Cumulus(), 2: RefinementSweep(), 3: Batching(), 4: LearnedProposal()}
+PLAIN_SMALL = PlainSmall()
+CUMULUS = Cumulus()
+REFINEMENT_SWEEP = RefinementSweep()
+BATCHING = Batching()
+LEARNED_PROPOSAL = LearnedProposal()
