@@ -453,10 +453,12 @@ def learned_fom(m, ctx):
     """Learned proposal vs plain HG sampling (1/(rel. variance x time)) on
     the bench's cumulus field (512x512x160 at 25 m), sun zenith 60 deg.  The
     flux figure uses T_tot over 2^24 paths; the image figure the mean pixel
-    relative variance of a 512 x 512 nadir image at 16 spp.  'online' counts
-    the network's training (2^26 paths in batches of 2^20, 2 Adam steps
-    each) in the time of the estimate those paths give; 'frozen' reuses the
-    trained network."""
+    relative variance of a 512 x 512 nadir image at 16 spp.  Each estimate
+    has its own network, trained online on its own kind of path: flux paths
+    for the flux, camera paths for the image (2^26 paths in batches of 2^20,
+    2 Adam steps each).  'online' counts that training in the time of the
+    estimate its paths give; 'frozen' reuses the trained network.  The image
+    traced with the flux-trained network is reported beside it."""
     import scenes
     import torch
     spec, _ = make_workload()
@@ -485,16 +487,31 @@ def learned_fom(m, ctx):
                 fr = sc.trace_flux(N, seed=5, proposal=prop, learn=0, batch_paths=1 << 24, n_learned=nl,
                                    mis_alpha=alpha)
                 rel_f = fr.se[2] / fr.mean[2]
-                fi = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=nl,
+                fx = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=nl,
                                      mis_alpha=alpha)
+                # the image's own network: trained online on camera paths
+                prop_i = m.Proposal(ctx, seed=7)
+                try:
+                    ti = sc.trace_camera(cam, 256, seed=4, proposal=prop_i, learn=1, batch_paths=1 << 20,
+                                         n_learned=nl, mis_alpha=alpha, train_steps=2)
+                    fi = sc.trace_camera(cam, 16, seed=5, proposal=prop_i, learn=0, batch_paths=1 << 22,
+                                         n_learned=nl, mis_alpha=alpha)
+                finally:
+                    prop_i.close()
+                fom_ip = _fom(img_rel(ip), ip.kernel_ms)
                 out[tag] = {
                     "online": {"fom": _fom(rel_t, tr.kernel_ms), "rel_se": rel_t, "ms": tr.kernel_ms,
                                "paths": 1 << 26, "adam_steps": 128},
                     "frozen": {"fom": _fom(rel_f, fr.kernel_ms), "rel_se": rel_f, "ms": fr.kernel_ms},
+                    "online_image": {"fom": _fom(img_rel(ti), ti.kernel_ms), "rel_se": img_rel(ti),
+                                     "ms": ti.kernel_ms, "spp": 256, "adam_steps": 128},
                     "frozen_image": {"fom": _fom(img_rel(fi), fi.kernel_ms), "rel_se": img_rel(fi),
                                      "ms": fi.kernel_ms},
+                    "frozen_image_flux_network": {"fom": _fom(img_rel(fx), fx.kernel_ms), "rel_se": img_rel(fx),
+                                                  "ms": fx.kernel_ms},
                     "ratio_frozen_vs_plain": _fom(rel_f, fr.kernel_ms) / _fom(rel_p, plain.kernel_ms),
-                    "ratio_image_vs_plain": _fom(img_rel(fi), fi.kernel_ms) / _fom(img_rel(ip), ip.kernel_ms),
+                    "ratio_image_vs_plain": _fom(img_rel(fi), fi.kernel_ms) / fom_ip,
+                    "ratio_online_image_vs_plain": _fom(img_rel(ti), ti.kernel_ms) / fom_ip,
                 }
             finally:
                 prop.close()

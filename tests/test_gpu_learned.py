@@ -201,6 +201,70 @@ def test_learned_tracer_unbiased_and_matches_oracle(env, orc):
         sc.close()
 
 
+def test_learned_result_independent_of_batches(env, orc):
+    """A frozen network's estimate depends only on the path ids: one pixel
+    (or one path) per batch, three pixels per batch and the whole image in
+    one batch give the same tallies up to the order of the additions.  The
+    batches change which paths share a pass and which vertices share a
+    network tile, so this also checks that no path is lost or repeated
+    between passes and that a row's network output does not depend on the
+    rows beside it."""
+    import scenes
+    m, ctx = env
+    sp = scenes.blobs_small(0)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, params=_params(orc, 23))
+    try:
+        cam = scenes.nadir_camera(sp, 16, 16)
+        kw = dict(seed=61, proposal=prop, n_learned=3, mis_alpha=0.5)
+        one = sc.trace_camera(cam, 32, batch_paths=32, **kw)          # a pixel per batch
+        three = sc.trace_camera(cam, 32, batch_paths=32 * 3, **kw)    # 3 pixels per batch
+        whole = sc.trace_camera(cam, 32, batch_paths=1 << 20, **kw)   # one batch
+        assert one.mean.max() > 0.0
+        for r in (three, whole):
+            np.testing.assert_allclose(r.mean, one.mean, rtol=2e-6, atol=1e-9)
+            np.testing.assert_allclose(r.se, one.se, rtol=1e-4, atol=1e-8)
+        f1 = sc.trace_flux(4099, seed=62, proposal=prop, batch_paths=1, n_learned=3)
+        f4 = sc.trace_flux(4099, seed=62, proposal=prop, batch_paths=1 << 20, n_learned=3)
+        np.testing.assert_allclose(f4.mean, f1.mean, rtol=2e-6, atol=1e-9)
+    finally:
+        prop.close()
+        sc.close()
+
+
+def test_camera_trained_network_lowers_image_variance(env):
+    """What the trained network gains over the method without it: on the
+    512x512x160 cumulus field (sun 60 deg), a network trained online on
+    camera paths (2^26 paths, 128 Adam steps) with 8 learned vertices lowers
+    the mean pixel relative variance of a 512 x 512 nadir image at 16 spp
+    below plain HG sampling's (measured 0.88x in relative SE, i.e. 1.3x in
+    variance), and the two images agree in their mean."""
+    import scenes
+    import torch
+    m, ctx = env
+    spec = scenes.cumulus(512, 512, 160, seed=0, device=torch.device("cuda", 0))
+    sc = m.Scene.from_spec(ctx, spec, k=spec.k)
+    prop = m.Proposal(ctx, seed=7)
+    try:
+        cam = scenes.nadir_camera(spec, 512, 512)
+
+        def rel(r):
+            ok = r.mean > 1e-3 * r.mean.max()
+            return float(np.sqrt(np.mean((r.se[ok] / r.mean[ok]) ** 2)))
+        plain = sc.trace_camera(cam, 16, seed=3)
+        sc.trace_camera(cam, 256, seed=4, proposal=prop, learn=1, batch_paths=1 << 20, n_learned=8,
+                        mis_alpha=0.5, train_steps=2)
+        learned = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=8,
+                                  mis_alpha=0.5)
+        assert rel(learned) < 0.95 * rel(plain), (rel(learned), rel(plain))
+        sp = math.sqrt(float((plain.se ** 2).sum())) / plain.se.size
+        sl = math.sqrt(float((learned.se ** 2).sum())) / learned.se.size
+        assert _close(float(learned.mean.mean()), sl, float(plain.mean.mean()), sp)
+    finally:
+        prop.close()
+        sc.close()
+
+
 def test_online_training_changes_network_and_stays_unbiased(env, orc):
     import scenes
     m, ctx = env
