@@ -908,6 +908,27 @@ def run_profile_case(grid="pyramid"):
     return 0
 
 
+def run_profile_learned():
+    """A case of the learned proposal's passes for ncu: the bench field, a
+    512 x 512 image at 16 spp, 8 learned vertices, MIS alpha 0.5, a fixed
+    (Xavier-initialised, seed 7) network, one batch: trace launches 0..8 are
+    passes 0..8, with a network evaluation before each resumed pass."""
+    import torch
+    import paper_1902_01137_gb300 as m
+    import scenes
+    spec, _ = make_workload()
+    cam = scenes.nadir_camera(spec, 512, 512)
+    ctx = m.Context(0)
+    sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    prop = m.Proposal(ctx, seed=7)
+    r = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=8, mis_alpha=0.5)
+    print("learned image kernel_ms", r.kernel_ms, "mean", float(r.mean.mean()), flush=True)
+    prop.close()
+    sc.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -923,6 +944,8 @@ def main():
     ap.add_argument("--no-octree", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
+    ap.add_argument("--profile-learned", action="store_true",
+                    help="trace one learned-proposal image (8 learned vertices, fixed network) and exit (for ncu)")
     ap.add_argument("--profile-grid", default="pyramid", choices=["pyramid", "octree"],
                     help="grid the profile case traces over")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
@@ -934,6 +957,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return run_profile_case(args.profile_grid)
+    if args.profile_learned:
+        return run_profile_learned()
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "sweep":
