@@ -929,6 +929,32 @@ def run_profile_learned():
     return 0
 
 
+def run_profile_train():
+    """The proposal network's training kernels for ncu: 2^20 synthetic
+    records (features in the tracer's ranges, unit directions, exponential
+    targets; seed 1), one Adam-free gradient step per call, five calls per
+    mode (FP32 SIMT, then BF16 tensor cores) after one warm-up call on 4096
+    records."""
+    import paper_1902_01137_gb300 as m
+    r = np.random.default_rng(1)
+    n = 1 << 20
+    x = np.concatenate([r.uniform(-1, 1, (n, 3)), r.normal(size=(n, 3)), r.uniform(-8, 6, (n, 3))], axis=1)
+    x[:, 3:6] /= np.linalg.norm(x[:, 3:6], axis=1, keepdims=True)
+    d = r.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t = r.exponential(size=n)
+    ctx = m.Context(0)
+    for mode in (m.MCRT_TRAIN_FP32, m.MCRT_TRAIN_TENSOR):
+        prop = m.Proposal(ctx, seed=3, training=mode)
+        prop.train_step(x[:4096], d[:4096], t[:4096])
+        for _ in range(5):
+            loss, _g = prop.train_step(x, d, t)
+        print("mode", mode, "loss", loss, flush=True)
+        prop.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -946,6 +972,8 @@ def main():
                     help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
     ap.add_argument("--profile-learned", action="store_true",
                     help="trace one learned-proposal image (8 learned vertices, fixed network) and exit (for ncu)")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="run the network's training kernels on 2^20 synthetic records and exit (for ncu)")
     ap.add_argument("--profile-grid", default="pyramid", choices=["pyramid", "octree"],
                     help="grid the profile case traces over")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
@@ -959,6 +987,8 @@ def main():
         return run_profile_case(args.profile_grid)
     if args.profile_learned:
         return run_profile_learned()
+    if args.profile_train:
+        return run_profile_train()
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "sweep":
