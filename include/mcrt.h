@@ -556,6 +556,34 @@ MCRT_API int mcrt_debug_terrain_height(const mcrt_scene* scene, int32_t n, const
 MCRT_API int mcrt_debug_bounds_violations(mcrt_ctx* ctx, int32_t* checked_build, uint64_t* count,
                                           int32_t* first_code);
 
+/* Device memory held by the allocations of the context's device's current
+ * stream-ordered memory pool (the pool every allocation of this library
+ * draws from, except a batch plan's item table): *used_current now and
+ * *used_high the most since the last reset; reset_high != 0 then resets the
+ * high mark to the current use.  Lets a caller check that a call allocated
+ * nothing (the paper has no counterpart).  Synchronises the context
+ * stream. */
+/* The online-training records of one learned trace, for checks against an
+ * independent implementation: the trace runs as mcrt_trace_camera
+ * (camera != NULL, n = samples per pixel) or mcrt_trace_flux (n paths) with
+ * opts->proposal and opts' n_learned and mis_alpha, in one batch of at most
+ * 2^24 paths, without training the network.  Every learned vertex of a
+ * path (one-sample MIS, the project's addition to the method of Sec. 4.1)
+ * yields a record; the first min(cap, *count) are written in the order the
+ * vertices were reached within each pass: feat (cap x 9) the vertex
+ * features as the network saw them (BF16 values), dir (cap x 3) the sampled
+ * direction, val (cap x 4) the path's score before the vertex, w * omega,
+ * the vertex's own local estimate, and the target of the KL estimator
+ * (score after the vertex without its own estimate, over w * omega), path
+ * (cap) the path id.  Each path records at most one vertex per pass, at
+ * most the first 2^20 / n_learned paths reaching a pass.  All buffers are
+ * host memory owned by the caller.  MCRT_ERR_BOUNDS beyond 2^24 paths. */
+MCRT_API int mcrt_debug_learned_records(mcrt_scene* scene, const mcrt_camera_desc* camera, uint64_t n, uint64_t seed,
+                                        const mcrt_trace_opts* opts, int32_t cap, float* feat, float* dir,
+                                        float* val, uint64_t* path, int32_t* count);
+
+MCRT_API int mcrt_debug_pool_usage(mcrt_ctx* ctx, int32_t reset_high, uint64_t* used_current, uint64_t* used_high);
+
 /* Philox4x32-10 evaluated on the device for n (counter[4], key[2]) pairs
  * (host arrays); out receives 4 words per pair. */
 MCRT_API int mcrt_debug_philox(mcrt_ctx* ctx, const uint32_t* counters, const uint32_t* keys, uint32_t* out, size_t n);

@@ -601,6 +601,36 @@ def _learned_sigs():
 
 MLP_SHAPES = [(64, 9), (64,), (64, 64), (64,), (64, 64), (64,), (40, 64), (40,)]
 
+# One online-training record of a learned vertex (orc_record in the C file).
+RECORD_DTYPE = np.dtype([("path", np.uint64), ("vertex", np.int32), ("pad", np.int32), ("x", np.float64, 9),
+                         ("dir", np.float64, 3), ("before", np.float64), ("w_omega", np.float64),
+                         ("own", np.float64), ("target", np.float64)])
+
+
+def learned_records(scene: Scene, cam, spp: int, seed: int, begin: int, end: int, cap: int = 1 << 20):
+    """The learned proposal's online-training records of camera paths
+    [begin, end) (``cam`` a Camera, ``spp`` samples per pixel) or of ground
+    flux paths (``cam`` None), in path order, plus each path's backward
+    score.  Each record holds the vertex's features, the sampled direction,
+    the score before the vertex, w * omega, the vertex's own estimate and the
+    KL target (score after the vertex excluding its own estimate, over
+    w * omega)."""
+    if scene.mlp is None:
+        raise ValueError("learned_records needs a scene with a network (mlp=...)")
+    L = lib()
+    L.orc_learned_records.restype = C.c_int64
+    L.orc_learned_records.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64,
+                                      C.c_void_p, C.c_int64, C.POINTER(C.c_double)]
+    st = scene.struct()
+    cs = cam.struct() if cam is not None else None
+    out = np.zeros(cap, dtype=RECORD_DTYPE)
+    scores = np.zeros(end - begin, dtype=np.float64)
+    n = L.orc_learned_records(C.addressof(st), C.addressof(cs) if cs is not None else None, spp if cam else 0,
+                              seed, begin, end, out.ctypes.data, cap, _ptr(scores, C.c_double))
+    if n < 0:
+        raise ValueError("bad learned-records request")
+    return out[:min(n, cap)].copy(), scores
+
 
 def mlp_nparam() -> int:
     return _learned_sigs().orc_mlp_nparam()

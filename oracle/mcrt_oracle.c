@@ -1161,6 +1161,29 @@ static void vertex_features(const orc_scene* S, const double p[3], const double 
     }
 }
 
+/* Online-training record of one learned vertex (the training set of the
+ * learned proposal): the vertex's features, the direction sampled there,
+ * the path's score before the vertex, the weight times omega at the vertex,
+ * the vertex's own local estimate, and the target of the KL estimator:
+ * the score the path gained after the vertex, excluding its own estimate,
+ * divided by w * omega.  That ratio equals p_HG(w') L(w') / q_mix(w'), the
+ * density ratio p* / q_mix of the target distribution p* ~ p_HG L whose
+ * KL divergence to the network's mixture is minimised. */
+typedef struct {
+    uint64_t path;
+    int32_t vertex;             /* learned-vertex index along the path */
+    int32_t pad;
+    double x[MLP_IN];
+    double dir[3];
+    double before, w_omega, own, target;
+} orc_record;
+
+typedef struct {
+    orc_record* rec;
+    int64_t cap;
+    int64_t n;                  /* records emitted (may exceed cap: the rest are dropped) */
+} orc_rec_sink;
+
 /* Share of the scattering at extinction k_total due to the cloud droplets
  * (the rest is the clear air): k_c omega_cloud / (k_c omega_cloud +
  * k_clear omega_clear). */
@@ -1203,8 +1226,15 @@ double orc_hg_dlog_dg(double g, double mu)
  * of d ln omega / d alpha = -k_c / (k omega).  (Roulette keeps this form:
  * a survival's probability w / 0.01 carries the same logarithmic
  * derivative as the weight it replaces.) */
+static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
+                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha,
+                               orc_rec_sink* sink);
+
 static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
-                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha);
+                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha)
+{
+    return trace_backward_r(S, p, d, seed, path, C, aborted, dscore, dalpha, NULL);
+}
 
 static double trace_backward(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                              orc_counts* C, int64_t* aborted)
@@ -1212,9 +1242,12 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
     return trace_backward_d(S, p, d, seed, path, C, aborted, NULL, NULL);
 }
 
-static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
-                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha)
+/* sink (may be NULL): receives one record per learned vertex of the path. */
+static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
+                               orc_counts* C, int64_t* aborted, double* dscore, double* dalpha,
+                               orc_rec_sink* sink)
 {
+    const int64_t rec0 = sink ? sink->n : 0;   /* this path's first record */
     double sg = 0.0, ds = 0.0;
     double sa = 0.0, da = 0.0;
     double w = 1.0, score = 0.0;
@@ -1236,6 +1269,8 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
         double uv[4];
         rng_block(&r, BLOCK_VERTEX, uv);
         if (ev == EV_VOLUME) {
+            const double before = score, w_vertex = w;
+            double own = 0.0;
             double om = omega_at(S, k);
             if (om > 0.0) {
                 double kc = k - S->k_gas - S->k_clear;
@@ -1254,6 +1289,7 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 double ph = S->clear_phase == 1 ? pc * phg + (1.0 - pc) * orc_rayleigh_pdf(mu) : phg;
                 double c = w * om * ph * Ts;
                 score += c;
+                own = c;
                 /* d ln ph / dg: only the droplets' share depends on g */
                 ds += c * (sg + pc * phg * orc_hg_dlog_dg(S->g, mu) / ph);
                 da += c * sa;
@@ -1268,6 +1304,21 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
                 rng_block(&r, BLOCK_VERTEX - 1u, ul);
                 double um[4] = {uv[0], uv[1], uv[3], ul[0]};
                 w *= orc_mis_sample(raw, S->g, S->mis_alpha, d, um, nd, NULL, NULL);
+                if (sink) {
+                    if (sink->n < sink->cap) {
+                        orc_record* R = &sink->rec[sink->n];
+                        R->path = path;
+                        R->vertex = lv;
+                        R->pad = 0;
+                        for (int a = 0; a < MLP_IN; ++a) R->x[a] = x[a];
+                        for (int a = 0; a < 3; ++a) R->dir[a] = nd[a];
+                        R->before = before;
+                        R->w_omega = w_vertex * om;
+                        R->own = own;
+                        R->target = 0.0;
+                    }
+                    sink->n++;
+                }
             } else if (S->clear_phase == 1) {
                 /* the direction's density is the mixture; its g-score too */
                 double mu = uv[3] > pc ? orc_rayleigh_sample_mu(uv[0]) : orc_hg_sample_mu(S->g, uv[0]);
@@ -1314,6 +1365,13 @@ static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uin
     }
     if (dscore) *dscore = ds;
     if (dalpha) *dalpha = da;
+    if (sink) {
+        /* targets: what the path scored after each learned vertex, per unit w * omega */
+        for (int64_t i = rec0; i < sink->n && i < sink->cap; ++i) {
+            orc_record* R = &sink->rec[i];
+            R->target = R->w_omega > 0.0 ? (score - R->before - R->own) / R->w_omega : 0.0;
+        }
+    }
     return score;
 }
 
@@ -1354,8 +1412,17 @@ static void wrap_xy(const orc_scene* S, double p[3])
 
 /* One camera path (Sec. 4.1: pinhole camera, direction jittered in the
  * pixel).  Stream (0, 2) gives the two jitter draws. */
+static double camera_path_r(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed, uint64_t path,
+                            orc_counts* cnt, int64_t* aborted, orc_rec_sink* sink);
+
 static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed, uint64_t path,
                           orc_counts* cnt, int64_t* aborted)
+{
+    return camera_path_r(S, C, spp, seed, path, cnt, aborted, NULL);
+}
+
+static double camera_path_r(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed, uint64_t path,
+                            orc_counts* cnt, int64_t* aborted, orc_rec_sink* sink)
 {
     uint64_t pix = path / spp;
     int px = (int)(pix % (uint64_t)C->width), py = (int)(pix / (uint64_t)C->width);
@@ -1384,14 +1451,23 @@ static double camera_path(const orc_scene* S, const orc_camera* C, uint32_t spp,
         return 0.0;
     }
     wrap_xy(S, p);
-    return trace_backward(S, p, d, seed, path, cnt, aborted);
+    return trace_backward_r(S, p, d, seed, path, cnt, aborted, NULL, NULL, sink);
 }
 
 /* One ground-flux path: uniform ground point, cosine-weighted upward
  * direction (stream (0, 2): four draws); direct part from stream (0, 3).
  * out[0] = T_dir, out[1] = T_dif = pi / mu0 * sum of local estimates. */
+static void flux_path_r(const orc_scene* S, uint64_t seed, uint64_t path, double out[4],
+                        orc_counts* cnt, int64_t* aborted, orc_rec_sink* sink);
+
 static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double out[4],
                       orc_counts* cnt, int64_t* aborted)
+{
+    flux_path_r(S, seed, path, out, cnt, aborted, NULL);
+}
+
+static void flux_path_r(const orc_scene* S, uint64_t seed, uint64_t path, double out[4],
+                        orc_counts* cnt, int64_t* aborted, orc_rec_sink* sink)
 {
     rng_t r;
     rng_init(&r, seed, path, 0, 2);
@@ -1429,7 +1505,7 @@ static void flux_path(const orc_scene* S, uint64_t seed, uint64_t path, double o
     double q[3] = {p[0], p[1], p[2]};
     double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
     double dsc = 0.0, dal = 0.0;
-    double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc, &dal);
+    double score = trace_backward_r(S, p, d, seed, path, cnt, aborted, &dsc, &dal, sink);
     out[0] = Tdir;
     out[1] = ORC_PI / mu0 * score;
     out[2] = ORC_PI / mu0 * dsc;
@@ -1628,6 +1704,34 @@ int orc_trace_flux(const orc_scene* S, uint64_t seed, uint64_t begin, uint64_t e
     if (stats) { stats[0] = ab; stats[1] = tot.tentative; stats[2] = tot.real; stats[3] = tot.leaves; }
     free(J.out); free(J.aborted); free(J.counts);
     return 0;
+}
+
+/* Online-training records of the learned proposal (see orc_record) for
+ * camera paths [begin, end) of a spp-per-pixel image (C != NULL) or for
+ * ground-flux paths [begin, end) (C == NULL), traced one after another in
+ * path order with the scene's network; at most cap records are stored,
+ * scores[i] (may be NULL) receives path begin + i's backward score (the
+ * sum of its local estimates).  Returns the number of records the paths
+ * produced (all of them, also beyond cap). */
+int64_t orc_learned_records(const orc_scene* S, const orc_camera* C, uint32_t spp, uint64_t seed, uint64_t begin,
+                            uint64_t end, orc_record* out, int64_t cap, double* scores)
+{
+    if (!S->mlp || end < begin || (C && spp == 0)) return -1;
+    orc_rec_sink sink = {out, cap, 0};
+    orc_counts cnt = {0, 0, 0};
+    int64_t ab = 0;
+    for (uint64_t path = begin; path < end; ++path) {
+        double sc;
+        if (C) {
+            sc = camera_path_r(S, C, spp, seed, path, &cnt, &ab, &sink);
+        } else {
+            double o[4];
+            flux_path_r(S, seed, path, o, &cnt, &ab, &sink);
+            sc = o[1] * S->sun[2] / ORC_PI;
+        }
+        if (scores) scores[path - begin] = sc;
+    }
+    return sink.n;
 }
 
 /* Forward analog: sums[12] = (sum, sum^2) of R, T_dir, T_dif, A_vol,

@@ -142,6 +142,8 @@ def _load():
         "mcrt_debug_dda_grid": [vp, P(f32), P(f32), f32, i32, i32, P(i32), P(f32), i32, P(i32), P(i32)],
         "mcrt_debug_philox": [vp, P(u32), P(u32), P(u32), C.c_size_t],
         "mcrt_debug_bounds_violations": [vp, P(i32), P(u64), P(i32)],
+        "mcrt_debug_pool_usage": [vp, i32, P(u64), P(u64)],
+        "mcrt_debug_learned_records": [vp, vp, u64, u64, P(TraceOpts), i32, P(f32), P(f32), P(f32), P(u64), P(i32)],
         "mcrt_trace_batch": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
         "mcrt_autotune_batch": [vp, P(BatchItem), i32, C.c_double, P(TraceOpts), P(f32)],
         "mcrt_batch_plan_create": [vp, P(BatchItem), i32, P(TraceOpts), P(vp)],
@@ -415,6 +417,33 @@ def mcrt_debug_bounds_violations(ctx):
     return bool(chk.value), int(n.value), int(code.value)
 
 
+def mcrt_debug_learned_records(ctx, scene, cam, n: int, seed: int, opts, cap: int = 1 << 16):
+    """Online-training records of one learned trace (no training): a dict of
+    feat (k x 9), dir (k x 3), before, w_omega, own, target, path, and the
+    number of records the trace produced.  ``cam`` a CameraDesc (n = spp) or
+    None for ground flux (n = paths)."""
+    feat = np.zeros((cap, 9), np.float32)
+    dirs = np.zeros((cap, 3), np.float32)
+    val = np.zeros((cap, 4), np.float32)
+    path = np.zeros(cap, np.uint64)
+    cnt = C.c_int32()
+    camp = C.byref(cam) if cam is not None else None
+    _check(_load().mcrt_debug_learned_records(scene, camp, n, seed, C.byref(opts), cap, _ptr(feat, C.c_float),
+                                              _ptr(dirs, C.c_float), _ptr(val, C.c_float),
+                                              _ptr(path, C.c_uint64), C.byref(cnt)), ctx)
+    k = min(cap, cnt.value)
+    return {"feat": feat[:k], "dir": dirs[:k], "before": val[:k, 0], "w_omega": val[:k, 1], "own": val[:k, 2],
+            "target": val[:k, 3], "path": path[:k], "count": int(cnt.value)}
+
+
+def mcrt_debug_pool_usage(ctx, reset_high: bool = False):
+    """(bytes in use, most bytes in use since the last reset) of the device's
+    stream-ordered memory pool; reset_high then resets the high mark."""
+    cur, high = C.c_uint64(), C.c_uint64()
+    _check(_load().mcrt_debug_pool_usage(ctx, 1 if reset_high else 0, C.byref(cur), C.byref(high)), ctx)
+    return int(cur.value), int(high.value)
+
+
 def mcrt_debug_philox(ctx, ctr, key) -> np.ndarray:
     ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
     key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
@@ -553,6 +582,17 @@ class Scene:
         ms = mcrt_tally_kernel_ms(self.ctx.h, t)
         cnt = mcrt_tally_counters(self.ctx.h, t) if read_counters else {}
         return Result(mean, se, n, ms, cnt)
+
+    def learned_records(self, cam, n, seed, cap=1 << 16, **opts):
+        """Online-training records of one learned trace (no training) of a
+        camera (``cam``, n = spp) or of ground flux (``cam`` None, n paths)."""
+        cd = None
+        if cam is not None:
+            cd = CameraDesc()
+            for i in range(3):
+                cd.pos[i], cd.target[i], cd.up[i] = cam.pos[i], cam.target[i], cam.up[i]
+            cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
+        return mcrt_debug_learned_records(self.ctx.h, self.h, cd, n, seed, self._opts(**opts), cap)
 
     def trace_camera(self, cam, spp, seed, tally=None, **opts):
         cd = CameraDesc()

@@ -570,8 +570,10 @@ int mcrt_trace_opts_default(mcrt_trace_opts* o)
     return MCRT_OK;
 }
 
-namespace {
+extern "C++" {
+namespace mcrt {
 
+// Shared by every trace entry point (the no-allocation call included).
 int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
 {
     mcrt_ctx* ctx = sc->ctx;
@@ -621,6 +623,11 @@ int ensure_leaf(mcrt_scene* sc, float tau, int finest, int grid)
     sc->leaf_grid = grid;
     return MCRT_OK;
 }
+
+}  // namespace mcrt
+}  // extern "C++"
+
+namespace {
 
 int get_tally(mcrt_ctx* ctx, int ncells, int nq, mcrt_tally** inout, const char* who)
 {
@@ -772,8 +779,10 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
     if (B < spp) B = spp;
     B = (B / spp) * spp;                                 // batches hold whole pixels
     const unsigned long long total = P0.total;
+    RecordDump* dump = ctx->rec_dump;                   // records to the host, no training
+    if (dump) B = total;
     if (B > total) B = total;
-    const unsigned rec_cap = o->learn ? (1u << 20) : 0u;
+    const unsigned rec_cap = (o->learn || dump) ? (1u << 20) : 0u;
     const int block = o->block_size ? o->block_size : 128;
     const int grid = o->grid_size ? o->grid_size : ctx->sm_count * trace_learned_blocks_per_sm(sensor, bf16, block);
     // work buffers
@@ -801,7 +810,7 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
     const int lev2 = sc->levels >= 2 ? 2 : sc->levels;
     for (unsigned long long b0 = 0; b0 < total && e == cudaSuccess && status == 0; b0 += B) {
         const unsigned long long nb = (total - b0 < B) ? total - b0 : B;
-        const bool warm = o->learn && prop->step == 0;   // untrained network: HG only, records collected
+        const bool warm = o->learn && prop->step == 0 && !dump;   // untrained network: HG only, records collected
         TraceParams P = P0;
         P.learned = 1;
         P.n_learned = NL;
@@ -857,7 +866,34 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
             if (e == cudaSuccess && nrec > 0) {
                 ctx->launches++;
                 e = launch_targets(rval, fin, nrec, tgt, ctx->stream);
-                for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+                if (dump && e == cudaSuccess) {
+                    const unsigned nc = nrec < (unsigned)dump->cap ? nrec : (unsigned)dump->cap;
+                    std::vector<uint16_t> hf((size_t)nc * 16);
+                    std::vector<float> hv((size_t)nc * 4), ht(nc);
+                    e = cudaMemcpyAsync(hf.data(), rfeat, hf.size() * 2, cudaMemcpyDeviceToHost, ctx->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(dump->dir, rdir, (size_t)nc * 12, cudaMemcpyDeviceToHost, ctx->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(hv.data(), rval, hv.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(ht.data(), tgt, ht.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+                    for (unsigned i = 0; e == cudaSuccess && i < nc; ++i) {
+                        for (int a = 0; a < 9; ++a) {
+                            const uint32_t bits = (uint32_t)hf[(size_t)i * 16 + a] << 16;
+                            std::memcpy(&dump->feat[(size_t)i * 9 + a], &bits, 4);
+                        }
+                        uint32_t pid;
+                        std::memcpy(&pid, &hv[(size_t)i * 4 + 3], 4);
+                        dump->path[i] = b0 + pid;
+                        dump->val[(size_t)i * 4] = hv[(size_t)i * 4];
+                        dump->val[(size_t)i * 4 + 1] = hv[(size_t)i * 4 + 1];
+                        dump->val[(size_t)i * 4 + 2] = hv[(size_t)i * 4 + 2];
+                        dump->val[(size_t)i * 4 + 3] = ht[i];
+                    }
+                }
+                if (dump) dump->count = (int32_t)nrec;
+                for (int k = 0; k < steps && e == cudaSuccess && !dump; ++k) {
                     e = cudaMemsetAsync(prop->d_grad, 0, kMlpParams * sizeof(float), ctx->stream);
                     if (e == cudaSuccess) {
                         ctx->launches += 3;
@@ -1505,6 +1541,52 @@ int mcrt_debug_bounds_violations(mcrt_ctx* ctx, int32_t* checked_build, uint64_t
     *checked_build = bounds_checked_build() ? 1 : 0;
     *count = n;
     *first_code = (int32_t)code;
+    return MCRT_OK;
+}
+
+int mcrt_debug_learned_records(mcrt_scene* sc, const mcrt_camera_desc* cam, uint64_t n, uint64_t seed,
+                               const mcrt_trace_opts* opts, int32_t cap, float* feat, float* dir, float* val,
+                               uint64_t* path, int32_t* count)
+{
+    const char* who = "mcrt_debug_learned_records";
+    if (!sc || !opts || !count || cap < 0 || (cap > 0 && (!feat || !dir || !val || !path)))
+        return fail(sc ? sc->ctx : nullptr, MCRT_ERR_ARG, "%s: NULL argument", who);
+    mcrt_ctx* ctx = sc->ctx;
+    if (!opts->proposal) return fail(ctx, MCRT_ERR_ARG, "%s: opts->proposal is NULL", who);
+    const unsigned long long paths = cam ? n * (unsigned long long)(cam->width > 0 ? cam->width : 0) *
+                                               (unsigned long long)(cam->height > 0 ? cam->height : 0)
+                                         : n;
+    if (paths > (1ull << 24)) return fail(ctx, MCRT_ERR_BOUNDS, "%s: at most 2^24 paths", who);
+    if (cam && n > 0xFFFFFFFFull) return fail(ctx, MCRT_ERR_ARG, "%s: spp too large", who);
+    RecordDump d;
+    d.cap = cap; d.feat = feat; d.dir = dir; d.val = val; d.path = path;
+    mcrt_trace_opts o = *opts;
+    o.learn = 0;
+    mcrt_tally* t = nullptr;
+    ctx->rec_dump = &d;
+    int rc = cam ? mcrt_trace_camera(sc, cam, (uint32_t)n, seed, &o, &t) : mcrt_trace_flux(sc, n, seed, &o, &t);
+    ctx->rec_dump = nullptr;
+    if (t) mcrt_tally_destroy(t);
+    *count = d.count;
+    return rc;
+}
+
+int mcrt_debug_pool_usage(mcrt_ctx* ctx, int32_t reset_high, uint64_t* used_current, uint64_t* used_high)
+{
+    if (!ctx || !used_current || !used_high) return fail(ctx, MCRT_ERR_ARG, "mcrt_debug_pool_usage: NULL argument");
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaMemPool_t pool;
+    CK(ctx, cudaDeviceGetMemPool(&pool, ctx->device));
+    unsigned long long cur = 0, high = 0;
+    CK(ctx, cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur));
+    CK(ctx, cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+    if (reset_high) {
+        unsigned long long zero = 0;
+        CK(ctx, cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    *used_current = (uint64_t)cur;
+    *used_high = (uint64_t)high;
     return MCRT_OK;
 }
 

@@ -23,6 +23,17 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Host buffers that receive the online-training records of one learned
+// trace (mcrt_debug_learned_records); the trace then skips its training.
+struct RecordDump {
+    int32_t cap = 0;
+    float* feat = nullptr;       // cap x 9
+    float* dir = nullptr;        // cap x 3
+    float* val = nullptr;        // cap x 4: score before, w * omega, own estimate, target
+    uint64_t* path = nullptr;    // cap
+    int32_t count = 0;           // records the trace produced (may exceed cap)
+};
+
 struct mcrt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -30,6 +41,7 @@ struct mcrt_ctx {
     size_t l2_bytes = 0;
     uint64_t launches = 0;
     std::string err;
+    RecordDump* rec_dump = nullptr;   // set only inside mcrt_debug_learned_records
 };
 
 struct mcrt_scene {
@@ -239,6 +251,12 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32
                                 cudaStream_t st);
 
 DevScene make_dev_scene(const mcrt_scene* sc, float k_gas);
+
+// Option checks shared by the trace entry points (status and message as
+// mcrt_trace_camera reports them), and the leaf map of (tau~, finest level,
+// grid), rebuilt in place when another one is current.
+int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who);
+int ensure_leaf(mcrt_scene* sc, float tau, int finest, int grid);
 
 // learned proposal network
 size_t mlp_packed_bf16_elems();

@@ -62,11 +62,17 @@ int nfail(mcrt_ctx* ctx, int code, const char* fmt, ...)
 }
 
 // Mean and standard error straight from the static sums into the caller's
-// device buffers.
+// device buffers; NaN in both when the trace stopped early (deadline or
+// cancel flag), whose partial sums estimate nothing.
 __global__ void noalloc_finalize_kernel(double n, int count, double* __restrict__ mean, double* __restrict__ se)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
+    if (g_noalloc_scratch.work.status != 0) {
+        mean[i] = __longlong_as_double(0x7ff8000000000000ll);
+        se[i] = mean[i];
+        return;
+    }
     const double m = g_noalloc_scratch.s1[i] / n;
     double var = g_noalloc_scratch.s2[i] / n - m * m;
     if (var < 0.0) var = 0.0;
@@ -87,7 +93,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     mcrt_trace_opts dflt;
     mcrt_trace_opts_default(&dflt);
     const mcrt_trace_opts* o = opts ? opts : &dflt;
-    if (sc->levels == 0) return nfail(ctx, MCRT_ERR_STATE, "%s: majorants not built", who);
+    int rc = check_opts(sc, o, who);
+    if (rc != MCRT_OK) return rc;
     if (cam->width < 1 || cam->height < 1)
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad image size %d x %d", who, cam->width, cam->height);
     if ((long long)cam->width * cam->height > kNoAllocMaxPixels)
@@ -95,14 +102,6 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
                      cam->width, cam->height, kNoAllocMaxPixels);
     if (spp < 1) return nfail(ctx, MCRT_ERR_ARG, "%s: spp must be >= 1", who);
     if (!(cam->fov_deg > 0.0f && cam->fov_deg < 180.0f)) return nfail(ctx, MCRT_ERR_ARG, "%s: fov must be in (0, 180)", who);
-    if (!(o->tau_merge >= 0.0f) || o->finest_level < 0 || o->finest_level > 1 || o->finest_level > sc->levels ||
-        o->max_order < 0 || (o->sun_mode != MCRT_SUN_RATIO && o->sun_mode != MCRT_SUN_DELTA && o->sun_mode != MCRT_SUN_DECOMP) || o->block_size < 0 ||
-        o->block_size > 128 || (o->block_size % 32) != 0 || o->grid_size < 0 || o->chunk < 0 || !(o->deadline_ms >= 0.0) ||
-        o->rare_batch < 0 || o->rare_batch > 32 || (o->grid != MCRT_GRID_PYRAMID && o->grid != MCRT_GRID_OCTREE) ||
-        (o->pixel_order != MCRT_ORDER_COST && o->pixel_order != MCRT_ORDER_RASTER))
-        return nfail(ctx, MCRT_ERR_ARG, "%s: bad trace options", who);
-    if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
-        return nfail(ctx, MCRT_ERR_STATE, "%s: octree not built", who);
     if (o->proposal) return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the learned proposal needs work buffers", who);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return nfail(ctx, MCRT_ERR_ARG, "%s: device index too large", who);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -139,16 +138,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     u[2] = r[0] * f[1] - r[1] * f[0];
 
     // the leaf map of this (tau~, finest level, grid); rebuilt in place, no allocation
-    if (!(sc->leaf_valid && sc->leaf_tau == o->tau_merge && sc->leaf_finest == o->finest_level &&
-          sc->leaf_grid == o->grid)) {
-        ctx->launches++;
-        e = launch_leafmap(sc, o->tau_merge, o->finest_level, o->grid, ctx->stream);
-        if (e != cudaSuccess) return nfail(ctx, MCRT_ERR_CUDA, "%s: leaf map: %s", who, cudaGetErrorString(e));
-        sc->leaf_valid = true;
-        sc->leaf_tau = o->tau_merge;
-        sc->leaf_finest = o->finest_level;
-        sc->leaf_grid = o->grid;
-    }
+    rc = ensure_leaf(sc, o->tau_merge, o->finest_level, o->grid);
+    if (rc != MCRT_OK) return rc;
 
     // clear what must start at zero: the work state, counters and the sums
     const int npix = cam->width * cam->height;

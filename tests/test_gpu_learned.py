@@ -374,3 +374,113 @@ def test_training_learns_a_known_direction_field(env):
         assert np.mean(cos) > 0.95 and np.quantile(cos, 0.05) > 0.8, (np.mean(cos), np.quantile(cos, 0.05))
     finally:
         prop.close()
+
+
+# ---------------------------------------------------------------------------
+# Online-training records against the oracle's, path by path
+# ---------------------------------------------------------------------------
+def _pair_records(g, o):
+    """Group GPU records (in pass order) and oracle records (in vertex
+    order) by path; return (paths with equal counts / all paths, list of
+    (gpu index, oracle index) pairs for those paths)."""
+    go = {}
+    for i, pth in enumerate(g["path"].tolist()):
+        go.setdefault(pth, []).append(i)
+    oo = {}
+    for i, pth in enumerate(o["path"].tolist()):
+        oo.setdefault(pth, []).append(i)
+    paths = set(go) | set(oo)
+    same = [p for p in paths if len(go.get(p, [])) == len(oo.get(p, []))]
+    pairs = [(gi, oi) for p in same for gi, oi in zip(go[p], oo[p])]
+    return len(same) / max(1, len(paths)), np.array(pairs, dtype=np.int64).reshape(-1, 2)
+
+
+@pytest.mark.parametrize("sensor", ["camera", "flux"])
+def test_training_records_match_oracle(env, orc, sensor):
+    """Every learned vertex's record -- features, sampled direction, score
+    before it, w * omega, its own estimate and the KL target -- against the
+    oracle's records of the same path ids (HG directions, alpha = 1, so the
+    paths draw the same numbers on both sides and differ only by FP32
+    rounding): features to one BF16 step, directions and weights to FP32
+    rounding, targets to a tolerance scaled by the score they are the
+    difference of.  The oracle's targets are pinned by the single-scatter
+    closed form in the oracle tests."""
+    import scenes
+    m, ctx = env
+    sp = scenes.blobs_small(0)
+    p = _params(orc, 31)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        osc = _oscene(orc, sp, mlp=p, n_learned=3, mis_alpha=1.0)
+        if sensor == "camera":
+            cam = scenes.nadir_camera(sp, 32, 32)
+            spp = 4
+            g = sc.learned_records(cam, spp, seed=71, proposal=prop, n_learned=3, mis_alpha=1.0)
+            o, _ = orc.learned_records(osc, orc.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, 32, 32), spp,
+                                       seed=71, begin=0, end=32 * 32 * spp)
+        else:
+            n = 4096
+            g = sc.learned_records(None, n, seed=72, proposal=prop, n_learned=3, mis_alpha=1.0)
+            o, _ = orc.learned_records(osc, None, 0, seed=72, begin=0, end=n)
+        assert g["count"] == len(g["path"]) and len(o) > 1000
+        assert abs(len(g["path"]) - len(o)) <= 0.03 * len(o), (len(g["path"]), len(o))
+        frac_paths, pairs = _pair_records(g, o)
+        assert frac_paths >= 0.97, frac_paths
+        gi, oi = pairs[:, 0], pairs[:, 1]
+        # features: the oracle's FP64 values rounded to BF16, within one BF16 step
+        of = bf16(o["x"][oi].astype(np.float32))
+        gf = g["feat"][gi].astype(np.float64)
+        step = np.maximum(np.abs(of), 1e-30) * 2.0 ** -7
+        feat_ok = np.all(np.abs(gf - of) <= step + 1e-6, axis=1)
+        dir_ok = np.all(np.abs(g["dir"][gi] - o["dir"][oi]) <= 2e-4, axis=1)
+        w_ok = np.abs(g["w_omega"][gi] - o["w_omega"][oi]) <= 1e-4 * o["w_omega"][oi] + 1e-9
+        scale = o["before"][oi] + o["own"][oi] + o["w_omega"][oi] * o["target"][oi]
+        b_ok = np.abs(g["before"][gi] - o["before"][oi]) <= 1e-3 * scale + 1e-9
+        own_ok = np.abs(g["own"][gi] - o["own"][oi]) <= 1e-3 * np.abs(o["own"][oi]) + 1e-4 * scale + 1e-9
+        t_tol = 2e-3 * scale / np.maximum(o["w_omega"][oi], 1e-12) + 1e-3 * o["target"][oi] + 1e-9
+        t_ok = np.abs(g["target"][gi] - o["target"][oi]) <= t_tol
+        for name, ok in (("feat", feat_ok), ("dir", dir_ok), ("w_omega", w_ok), ("before", b_ok),
+                         ("own", own_ok), ("target", t_ok)):
+            assert ok.mean() >= 0.97, (name, ok.mean())
+        # the targets' sum over all records agrees too (no systematic factor)
+        st = float(g["target"].sum()), float(o["target"].sum())
+        assert abs(st[0] - st[1]) <= 0.02 * abs(st[1]), st
+    finally:
+        prop.close()
+        sc.close()
+
+
+def test_training_records_with_network_match_oracle(env, orc):
+    """With the network in the mixture (alpha = 0.5) the GPU's BF16 network
+    and the oracle's FP64 one sample slightly different directions, so paths
+    part after their first learned vertex: the first vertex's features still
+    pair up exactly, and the mean KL target of all records agrees within 4
+    combined standard errors."""
+    import scenes
+    m, ctx = env
+    sp = scenes.blobs_small(0)
+    p = _params(orc, 33)
+    sc = m.Scene.from_spec(ctx, sp)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        n = 16384
+        g = sc.learned_records(None, n, seed=73, proposal=prop, n_learned=3, mis_alpha=0.5, cap=1 << 17)
+        o, _ = orc.learned_records(_oscene(orc, sp, mlp=p, n_learned=3, mis_alpha=0.5), None, 0, seed=73,
+                                   begin=0, end=n, cap=1 << 17)
+        first_o = o[o["vertex"] == 0]
+        gpos = {}
+        for i, pth in enumerate(g["path"].tolist()):
+            gpos.setdefault(pth, i)          # a path's first record comes from the first pass
+        idx = [(gpos[int(pth)], j) for j, pth in enumerate(first_o["path"].tolist()) if int(pth) in gpos]
+        assert len(idx) >= 0.97 * len(first_o)
+        gi, oi = np.array(idx).T
+        of = bf16(first_o["x"][oi].astype(np.float32))
+        feat_ok = np.all(np.abs(g["feat"][gi] - of) <= np.maximum(np.abs(of), 1e-30) * 2.0 ** -7 + 1e-6, axis=1)
+        assert feat_ok.mean() >= 0.97
+        tg, to = g["target"].astype(np.float64), o["target"]
+        se = math.hypot(tg.std() / math.sqrt(len(tg)), to.std() / math.sqrt(len(to)))
+        assert abs(tg.mean() - to.mean()) <= 4 * se, (tg.mean(), to.mean(), se)
+    finally:
+        prop.close()
+        sc.close()

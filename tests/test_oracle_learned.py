@@ -159,3 +159,75 @@ def test_learned_tracer_unbiased(orc):
     ma, mb = a.mean.mean(), b.mean.mean()
     sa, sb = math.sqrt((a.se ** 2).sum()) / a.se.size, math.sqrt((b.se ** 2).sum()) / b.se.size
     assert abs(ma - mb) < 4 * math.hypot(sa, sb)
+
+
+# ---------------------------------------------------------------------------
+# Online-training records and their KL targets
+# ---------------------------------------------------------------------------
+def _hg(g, mu):
+    return (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * mu) ** 1.5)
+
+
+def _slab_record_expectation(orc, recs, k, H, om, g, s, alpha, params):
+    """E[target | vertex height z, incoming d, sampled w] for the first
+    learned vertex of a path in a homogeneous slab (extinction k, height H,
+    albedo om, black ground) when only two orders are scored: the next
+    vertex's estimate over w * omega, i.e. p_HG(d.w) / q_mix(w) times the
+    single-scattered radiance arriving from w,
+        om p_HG(w.s) k exp(-k (H - z) / mu0) (1 - exp(-a t_max)) / a,
+    a = k (1 - w_z / mu0), t_max the distance to the slab's top or bottom
+    along w (a bottom exit meets the black ground and scores nothing)."""
+    mu0 = s[2]
+    z = (recs["x"][:, 2] + 1.0) * 0.5 * H
+    d = recs["x"][:, 3:6]
+    w = recs["dir"]
+    wz = w[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tmax = np.where(wz > 0, (H - z) / wz, np.where(wz < 0, z / -wz, np.inf))
+    a = k * (1.0 - wz / mu0)
+    integ = np.where(np.abs(a) > 1e-12, -np.expm1(-a * tmax) / np.where(np.abs(a) > 1e-12, a, 1.0), tmax)
+    L1 = om * _hg(g, w @ s) * k * np.exp(-k * (H - z) / mu0) * integ
+    phg = _hg(g, np.einsum("ij,ij->i", d, w))
+    if alpha >= 1.0:
+        return L1
+    raw = orc.mlp_forward(params, recs["x"])
+    qv = np.array([orc.mixture_pdf(raw[i], w[i]) for i in range(len(w))])
+    return phg / (alpha * phg + (1 - alpha) * qv) * L1
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+def test_record_targets_match_single_scatter_radiance(orc, alpha):
+    """The records' targets are the radiance the sampled direction brought
+    back, weighted by p_HG / q_mix: in a homogeneous slab scored to order 2
+    their mean matches the closed form of the single-scattered radiance
+    arriving along each record's direction, and a second learned vertex,
+    after which nothing is scored, has target 0 exactly."""
+    k, H, om, g, th0 = 1.0, 1.0, 0.9, 0.7, 30.0
+    sp = scenes.homogeneous(16, 16, 10, 0.1, k, levels=1, g=g, ssa_cloud=om, ssa_clear=om,
+                            sun_zenith_deg=th0)
+    p = orc.xavier_init(11)
+    p[-40:] = np.random.default_rng(12).normal(size=40) * 0.5
+    sc = orc.Scene(k=sp.k, dx=sp.dx, dy=sp.dy, dz=sp.dz, levels=sp.levels, k_clear=0.0, ssa_clear=om,
+                   ssa_cloud=om, g=g, ground_albedo=0.0, sun_zenith_deg=th0, max_order=2, mlp=p, n_learned=2,
+                   mis_alpha=alpha)
+    recs, scores = orc.learned_records(sc, None, 0, seed=5, begin=0, end=60000, cap=1 << 18)
+    first = recs[recs["vertex"] == 0]
+    second = recs[recs["vertex"] == 1]
+    assert len(first) > 20000 and len(second) > 5000
+    # before the first vertex nothing has been scored; after the second, nothing is
+    assert np.all(first["before"] == 0.0)
+    # (target 0 up to the rounding of score - before - own in FP64)
+    assert np.all(np.abs(second["target"] * second["w_omega"]) <= 1e-14 * (second["before"] + second["own"]))
+    mu0 = math.cos(math.radians(th0))
+    s = np.array([math.sin(math.radians(th0)), 0.0, mu0])
+    want = _slab_record_expectation(orc, first, k, H, om, g, s, alpha, p)
+    r = first["target"] - want
+    se = r.std() / math.sqrt(len(r))
+    assert abs(r.mean()) < 4 * se, (r.mean(), se, first["target"].mean(), want.mean())
+    for sel in (first["dir"][:, 2] > 0, first["dir"][:, 2] < 0):
+        rs = r[sel]
+        assert abs(rs.mean()) < 4 * rs.std() / math.sqrt(len(rs))
+    # the record's pieces add up to the path's score (before + own + w omega target)
+    idx = first["path"].astype(np.int64)
+    total = first["before"] + first["own"] + first["w_omega"] * first["target"]
+    np.testing.assert_allclose(total, scores[idx], rtol=1e-12, atol=1e-15)
