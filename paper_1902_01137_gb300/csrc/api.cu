@@ -924,6 +924,9 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
     CK(ctx, e);
     CK(ctx, se);
     t->kernel_ms = ms;
+    int terr = 0;
+    CK(ctx, tc5_take_error(&terr, ctx->stream));
+    if (terr) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: a tensor-core wait of the proposal network ran out", who);
     if (status == 1) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: deadline of %g ms expired", who, o->deadline_ms);
     if (status == 2) return fail(ctx, MCRT_ERR_CANCELLED, "%s: cancelled", who);
     return MCRT_OK;

@@ -235,6 +235,9 @@ int mcrt_proposal_eval(mcrt_proposal* P, const float* host_feat, size_t n, float
     cudaFreeAsync(d_mix, ctx->stream);
     if (d_raw) cudaFreeAsync(d_raw, ctx->stream);
     LCK(ctx, e);
+    int terr = 0;
+    LCK(ctx, tc5_take_error(&terr, ctx->stream));
+    if (terr) return lfail(ctx, MCRT_ERR_TIMEOUT, "mcrt_proposal_eval: a tensor-core wait ran out");
     return MCRT_OK;
 }
 
@@ -285,6 +288,9 @@ int mcrt_proposal_train_step(mcrt_proposal* P, const float* host_feat, const flo
     cudaFreeAsync(d_dirs, ctx->stream);
     cudaFreeAsync(d_t, ctx->stream);
     LCK(ctx, e);
+    int terr = 0;
+    LCK(ctx, tc5_take_error(&terr, ctx->stream));
+    if (terr) return lfail(ctx, MCRT_ERR_TIMEOUT, "mcrt_proposal_train_step: a tensor-core wait ran out");
     if (loss_out) *loss_out = loss;
     return MCRT_OK;
 }

@@ -266,6 +266,9 @@ cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const vo
 cudaError_t launch_mlp_train_tc(const void* wpacked, const float* bpacked, const float* params, const void* feat,
                                 const float* dirs, const float* tgt, int n, float scale, float* grad, float* loss,
                                 int sm_count, cudaStream_t st);
+// 1 in *err if an MMA wait of the tensor-core network kernels ran out since
+// the last call (then cleared); synchronises the stream.
+cudaError_t tc5_take_error(int* err, cudaStream_t st);
 cudaError_t launch_mlp_train(const float* params, const void* feat, const float* dirs, const float* tgt, int n,
                              float scale, float* grad, float* loss, int sm_count, cudaStream_t st);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,

@@ -59,7 +59,7 @@ def test_mlp_inference_vs_oracle(env, orc):
     p = _params(orc, 3)
     prop = m.Proposal(ctx, params=p)
     try:
-        n = 1000                                   # 31 full warp tiles and a ragged tail
+        n = 1000                                   # 7 full 128-row tiles and a ragged tail
         x = _features(n, 4)
         mix, raw = prop.eval(x)
         W1, b1, W2, b2, W3, b3, W4, b4 = orc.mlp_split(p)
@@ -67,14 +67,17 @@ def test_mlp_inference_vs_oracle(env, orc):
         a = bf16(x.astype(np.float64))
         ref = orc.mlp_forward(np.concatenate([Wb[0].ravel(), b1, Wb[1].ravel(), b2, Wb[2].ravel(), b3,
                                               Wb[3].ravel(), b4]), a)
-        # error bound through the layers
+        # error bound through the layers: the propagated error (GELU
+        # Lipschitz 1.13), BF16 rounding of each activation (2^-8 relative),
+        # and the hardware tanh inside GELU (tanh.approx.f32, relative error
+        # below 2^-10.9 of |tanh| <= 1, so at most 0.5 |z| 2^-10.9 in GELU)
         da = np.zeros_like(a)
         h = a
         for W, b in ((Wb[0], b1), (Wb[1], b2), (Wb[2], b3)):
             z = h @ W.T + b
             dz = (np.abs(da) @ np.abs(W).T) + 64 * 2.0 ** -23 * (np.abs(h) @ np.abs(W).T + np.abs(b))
             h = gelu(z)
-            da = 1.13 * dz + 2.0 ** -8 * np.abs(h)
+            da = 1.13 * dz + 2.0 ** -8 * np.abs(h) + 0.5 * np.abs(z) * 2.0 ** -10.9
         bound = np.abs(da) @ np.abs(Wb[3]).T + 64 * 2.0 ** -23 * (np.abs(h) @ np.abs(Wb[3]).T + np.abs(b4))
         err = np.abs(raw - ref)
         assert np.all(err <= bound + 1e-6), (err.max(), (err - bound).max())
