@@ -11,9 +11,13 @@ per pixel (67,108,864 paths), mean/SE finalize.
   e2e        the same through the C ABI from a pinned host field, host->device
              copy of the field and device->host read of the image (mean, SE)
              inside the timed region
-  roofline   trace kernel: algorithmic bytes (4 B per voxel read at a
-             tentative collision + 4 B of majorant per leaf entered, counted by a separate
-             counting run with the same seed) / kernel time, over measured HBM
+  roofline   trace kernel against instruction issue, the ceiling that binds
+             it: warp instructions per launch (ncu count per path x paths) /
+             kernel time, over 152 SMs x 4 schedulers x the sampled SM clock
+  roofline_hbm  the memory roofline: algorithmic bytes (4 B per voxel read at
+             a tentative collision + 4 B of majorant per leaf entered, counted
+             by a separate counting run with the same seed) / kernel time,
+             over measured HBM
   cpu_baseline  the CPU oracle on a bounded pixel sample of the same image
 
   fom        1/(relative variance x time) of the learned proposal against
@@ -28,9 +32,11 @@ shape chosen by the autotuner.  ``--workload sweep``: the refinement sweep
 point, FP32 and BF16 storage, FP64 oracle difference at the two smallest).
 
 ``--impl reference`` times the CPU oracle alone on the same workload.
-Multi-GPU (torchrun): every rank renders an independent replica of the image
-with its own seed (paths are independent: weak scaling, no collective on the
-data path); rank 0 prints the max-over-ranks timing.
+Multi-GPU (torchrun): the job is one image with 64 x N samples per pixel;
+rank r traces every N-th pixel of the claim order (64 x W x H paths per rank:
+weak scaling) and the ranks' per-pixel FP64 sums are added in rank order at
+the end of each step (the only collective); rank 0 prints the max-over-ranks
+timing.  The line's `strong` figure splits the single 64-spp image instead.
 """
 from __future__ import annotations
 
@@ -63,6 +69,7 @@ PROFILED_DRAM_BYTES_PER_PATH = 24.29
 # its real ceiling: 152 SMs x 4 schedulers x 1 warp instruction per cycle
 PROFILED_ISSUE_ACTIVE = 0.7216
 PROFILED_THREADS_PER_INST = 13.09
+PROFILED_WARP_INST_PER_PATH = 7921.0
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
 # the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
 PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.26
@@ -85,20 +92,28 @@ def profiled_traffic(paths_per_launch):
     return PROFILED_DRAM_BYTES_PER_PATH * paths_per_launch if sha == PROFILED_TRACE_SHA else None
 
 
-def profiled_issue(sm_mhz):
-    """Secondary roofline of the trace kernel against its issue ceiling,
-    from the committed ncu capture (None once the kernel sources changed)."""
+def issue_roofline(kernel_ms, paths, sm_mhz, traffic):
+    """Roofline of the trace kernel against the ceiling that binds it,
+    instruction issue: warp instructions per launch (the committed ncu
+    capture's count per path times the launch's paths) over the live kernel
+    time, against 152 SMs x 4 schedulers x 1 warp instruction per cycle at
+    the SM clock sampled during the timed steps.  None once the kernel's
+    sources differ from the captured ones."""
     try:
         if trace_sources_sha() != PROFILED_TRACE_SHA:
             return None
     except OSError:
         return None
-    peak = 152 * 4 * (sm_mhz or 2070.0) * 1e6
-    return {"bound": "issue", "achieved": PROFILED_ISSUE_ACTIVE * peak, "peak": peak,
-            "unit": "warp instructions/s", "frac": PROFILED_ISSUE_ACTIVE,
+    mhz = sm_mhz or 2070.0
+    peak = 152 * 4 * mhz * 1e6
+    achieved = PROFILED_WARP_INST_PER_PATH * paths / (kernel_ms / 1e3)
+    return {"bound": "alu", "resource": "warp-instruction issue", "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak, "traffic": traffic,
             "simt_efficiency": PROFILED_THREADS_PER_INST / 32.0,
-            "peak_derivation": "152 SMs x 4 schedulers x 1 issue/cycle x SM clock",
-            "source": "ncu capture of the small case: " + PROFILED_SOURCE}
+            "lane_frac": achieved / peak * PROFILED_THREADS_PER_INST / 32.0,
+            "inst_per_path": PROFILED_WARP_INST_PER_PATH, "sm_mhz": mhz,
+            "peak_derivation": "152 SMs x 4 schedulers x 1 warp instruction/cycle x sampled SM clock",
+            "source": "instructions per path from " + PROFILED_SOURCE}
 
 
 def peaks():
@@ -198,24 +213,34 @@ def oracle_sample(spec, cam, target_s=12.0, seed=0):
 
 
 def run_reference(args):
+    """The CPU oracle on the bench workload: each step traces a bounded row
+    sample of the image (the whole run stays within a few minutes); value is
+    the paths per second over what ran, ms_per_step the time a step took.
+    The time a whole image would take is only extrapolated, in its own
+    labelled field."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     spec, cam = make_workload()
-    vals = []
+    per_step = max(2.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
     for _ in range(args.warmup):
-        oracle_sample(spec, cam, target_s=2.0)
-    descs = []
+        oracle_sample(spec, cam, target_s=min(2.0, per_step))
+    descs, paths_all, dts = [], 0, []
     cores = 1
     for _ in range(args.steps):
-        v, cores, desc, paths, dt = oracle_sample(spec, cam, target_s=args.ref_seconds)
-        vals.append(v)
+        v, cores, desc, paths, dt = oracle_sample(spec, cam, target_s=per_step)
         descs.append(desc)
-    value = statistics.median(vals)
+        paths_all += paths
+        dts.append(dt)
+    value = paths_all / sum(dts)
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": W * H * SPP / value * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "timed": "CPU oracle on a row sample, paths/s extrapolated"},
+            "config": {"workload": WORKLOAD,
+                       "timed": "each step: the CPU oracle on a row sample of the image (about %.0f s of work)"
+                                % per_step,
+                       "paths_per_step": paths_all // max(1, args.steps)},
+            "full_image_ms_extrapolated": W * H * SPP / value * 1e3,
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
                              "sample": descs[0]},
             "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -263,12 +288,25 @@ def run_gpu(args):
     cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
     opts = m.mcrt_trace_opts_default()
     tally = [None]
+    # N > 1: one image whose samples grow with the ranks (SPP x N per pixel,
+    # weak scaling: every rank traces SPP x W x H paths), split by pixels
+    # (every N-th pixel of the claim order per rank) and combined by a
+    # rank-ordered FP64 reduction of the per-pixel sums
+    spp_job = SPP * world
+    if world > 1:
+        opts.shard_index, opts.shard_count = rank, world
+    from paper_1902_01137_gb300 import shard
 
-    def step(seed, k):
+    def step(seed, k, spp=None, o=None):
+        spp = spp_job if spp is None else spp
+        o = opts if o is None else o
         sc = new_scene(k)
         try:
-            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, seed, opts, tally[0])
+            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp, seed, o, tally[0])
             tally[0] = t
+            if o.shard_count > 1:
+                s1, s2 = m.mcrt_tally_read_sums(ctx.h, t)
+                shard.combine_image(s1[:, 0], s2[:, 0], spp)
             return m.mcrt_tally_kernel_ms(ctx.h, t)
         finally:
             sc.close()
@@ -281,8 +319,9 @@ def run_gpu(args):
     # counting run (same seed as the first timed step) for algorithmic bytes
     copts = m.mcrt_trace_opts_default()
     copts.count_events = 1
+    copts.shard_index, copts.shard_count = opts.shard_index, opts.shard_count
     sc = new_scene(k_dev)
-    ct = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, base_seed + 100, copts)
+    ct = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp_job, base_seed + 100, copts)
     cnt = m.mcrt_tally_counters(ctx.h, ct)
     m.mcrt_tally_destroy(ct)
     sc.close()
@@ -315,19 +354,45 @@ def run_gpu(args):
     paths_per_step = W * H * SPP
     value = world * paths_per_step * args.steps / (total_ms / 1e3)
 
+    # N > 1 also: the single SPP image split over the ranks (strong scaling)
+    strong = None
+    if world > 1:
+        for i in range(args.warmup):
+            step(base_seed + 400 + i, k_dev, spp=SPP)
+        torch.distributed.barrier()
+        torch.cuda.synchronize()
+        st_ms = []
+        for i in range(args.steps):
+            flush_buf.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(base_seed + 500 + i, k_dev, spp=SPP)
+            e1.record(stream)
+            e1.synchronize()
+            st_ms.append(e0.elapsed_time(e1))
+        st_total = shard.max_over_ranks(sum(st_ms))
+        strong = {"value": paths_per_step * args.steps / (st_total / 1e3), "unit": "paths/s",
+                  "ms_per_step": st_total / args.steps,
+                  "workload": "the %dx%d x %d spp image split by pixels over %d ranks" % (W, H, SPP, world)}
+
     # the same steps over the paper's 2^L octree (Sec. 3.1.1), built in each
     # step beside the pyramid, leaves at tau~ = 1 with 2^3-voxel cells as the
     # finest level; timed like the steps above
     oopts = m.mcrt_trace_opts_default()
     oopts.grid = m.MCRT_GRID_OCTREE
     oopts.finest_level = 1
+    oopts.shard_index, oopts.shard_count = opts.shard_index, opts.shard_count
 
     def octree_step(seed, k):
         sc = new_scene(k)
         try:
             sc.build_octree()
-            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, seed, oopts, tally[0])
+            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp_job, seed, oopts, tally[0])
             tally[0] = t
+            if oopts.shard_count > 1:
+                s1, s2 = m.mcrt_tally_read_sums(ctx.h, t)
+                shard.combine_image(s1[:, 0], s2[:, 0], spp_job)
             return m.mcrt_tally_kernel_ms(ctx.h, t)
         finally:
             sc.close()
@@ -357,7 +422,8 @@ def run_gpu(args):
             sc.build_octree()
             oc = m.mcrt_trace_opts_default()
             oc.grid, oc.finest_level, oc.count_events = m.MCRT_GRID_OCTREE, 1, 1
-            ct = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, base_seed + 100, oc)
+            oc.shard_index, oc.shard_count = opts.shard_index, opts.shard_count
+            ct = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp_job, base_seed + 100, oc)
             ocnt = m.mcrt_tally_counters(ctx.h, ct)
             m.mcrt_tally_destroy(ct)
         finally:
@@ -388,14 +454,18 @@ def run_gpu(args):
     d2h = W * H * 16
     if not args.no_e2e:
         e2e_ms = []
-        for i in range(max(1, min(args.steps, 3))):
+        for i in range(args.steps):
             flush_buf.fill_(float(i))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sc = new_scene(k_host)                     # H2D copy of the field inside
             try:
-                t = m.mcrt_trace_camera(ctx.h, sc.h, cd, SPP, base_seed + 200 + i, opts, tally[0])
-                mean, se, _ = m.mcrt_tally_read(ctx.h, t)   # D2H of the image
+                t = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp_job, base_seed + 200 + i, opts, tally[0])
+                if world > 1:                              # D2H of this rank's sums, then the reduction
+                    s1, s2 = m.mcrt_tally_read_sums(ctx.h, t)
+                    shard.combine_image(s1[:, 0], s2[:, 0], spp_job)
+                else:
+                    mean, se, _ = m.mcrt_tally_read(ctx.h, t)   # D2H of the image
             finally:
                 sc.close()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -409,11 +479,15 @@ def run_gpu(args):
     kavg = statistics.mean(kern_ms)
     achieved = alg_bytes / (kavg / 1e3) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": args.traffic_bytes if args.traffic_bytes else profiled_traffic(W * H * SPP),
-            "peak_source": "measured" if pk else "fallback",
-            "kernel": "trace_kernel<camera,f32>", "kernel_ms": kavg,
-            "alg_bytes_per_launch": alg_bytes, "vox_reads": vox_reads, "leaf_entries": leaf_entries}
+    traffic = args.traffic_bytes if args.traffic_bytes else profiled_traffic(W * H * SPP)
+    roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": "measured" if pk else "fallback",
+                "kernel": "trace_kernel<camera,f32>", "kernel_ms": kavg,
+                "alg_bytes_per_launch": alg_bytes, "vox_reads": vox_reads, "leaf_entries": leaf_entries}
+    # the kernel is bound by instruction issue, not by HBM: the line's
+    # roofline is the issue ceiling, the memory roofline is reported beside it
+    roof = issue_roofline(kavg, W * H * SPP, clk.get("sm_mhz") if clk else None, traffic) or roof_hbm
+    roof["kernel"], roof["kernel_ms"] = "trace_kernel<camera,f32>", kavg
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,9 +501,13 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "paths_per_step": paths_per_step, "l2": "flushed between steps",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "roofline_issue": profiled_issue(clk.get("sm_mhz") if clk else None),
+            "config": {"workload": WORKLOAD if world == 1 else
+                       WORKLOAD.replace("x %d spp" % SPP, "x %d spp (%d per rank)" % (spp_job, SPP)),
+                       "paths_per_step": paths_per_step, "l2": "flushed between steps",
+                       "parallelism": "pixel shards over %d ranks, rank-ordered FP64 reduction" % world
+                       if world > 1 else "single"},
+            "strong": strong,
+            "roofline": roof, "roofline_hbm": roof_hbm,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk,

@@ -300,6 +300,18 @@ typedef struct {
                                /* do not start last; MCRT_ORDER_RASTER claims   */
                                /* them row by row.  Launch shape only: a path's */
                                /* id, draws and result do not depend on it      */
+    int32_t shard_index;       /* shard_count > 1: trace one shard of the paths */
+    int32_t shard_count;       /* (one process per GPU, Sec. 3's independent    */
+                               /* paths).  Camera: the pixels at positions      */
+                               /* shard_index, + shard_count, ... of the claim  */
+                               /* order (pixel_order), all spp paths of each;   */
+                               /* flux: path ids [n*i/c, n*(i+1)/c).  Paths keep */
+                               /* their global ids, so the shards' FP64 sums    */
+                               /* (mcrt_tally_read_sums) add up to the whole    */
+                               /* trace's; a shard's own mean divides by the   */
+                               /* whole path count.  0 or 1: no sharding.  Not  */
+                               /* with a proposal, in batches or without        */
+                               /* allocation (MCRT_ERR_UNSUPPORTED)             */
 } mcrt_trace_opts;
 
 /* Fill `opts` with the defaults listed above. */

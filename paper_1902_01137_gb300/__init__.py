@@ -88,7 +88,9 @@ class TraceOpts(C.Structure):
                 ("cancel_flag", C.c_void_p),
                 ("batch_dalpha", C.c_int32),
                 ("grid", C.c_int32),
-                ("pixel_order", C.c_int32)]
+                ("pixel_order", C.c_int32),
+                ("shard_index", C.c_int32),
+                ("shard_count", C.c_int32)]
 
 
 _lib = None

@@ -608,6 +608,10 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
         return fail(ctx, MCRT_ERR_ARG, "%s: bad pixel_order", who);
     if (o->grid == MCRT_GRID_OCTREE && sc->oct_levels == 0)
         return fail(ctx, MCRT_ERR_STATE, "%s: octree not built (mcrt_scene_build_octree)", who);
+    if (o->shard_count < 0 || o->shard_index < 0 || o->shard_index >= (o->shard_count > 1 ? o->shard_count : 1))
+        return fail(ctx, MCRT_ERR_ARG, "%s: shard_index %d of %d", who, o->shard_index, o->shard_count);
+    if (o->shard_count > 1 && o->proposal)
+        return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: sharding with a proposal", who);
     return MCRT_OK;
 }
 
@@ -1017,6 +1021,26 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
         if (rc) return rc;
         P.pix_order = d_order;
     }
+    if (o->shard_count > 1) {
+        // this shard's pixels: every shard_count-th position of the claim order
+        const uint32_t nsh = (uint32_t)o->shard_count, idx = (uint32_t)o->shard_index, npix = (uint32_t)ncells;
+        const uint32_t n_r = idx < npix ? (npix - idx + nsh - 1) / nsh : 0u;
+        uint32_t* d_sh = nullptr;
+        cudaError_t e = dalloc(ctx, &d_sh, (size_t)(n_r ? n_r : 1) * sizeof(uint32_t));
+        if (e == cudaSuccess) {
+            ctx->launches++;
+            e = launch_shard_order(d_order, n_r, nsh, idx, d_sh, ctx->stream);
+        }
+        dfree(ctx, d_order);
+        d_order = d_sh;
+        if (e != cudaSuccess) {
+            dfree(ctx, d_order);
+            return fail(ctx, e == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, "%s: shard order: %s", who,
+                        cudaGetErrorString(e));
+        }
+        P.pix_order = d_order;
+        P.total = (unsigned long long)n_r * spp;
+    }
     rc = run_trace(sc, P, kCamera, o, t, who);
     dfree(ctx, d_order);
     return rc;
@@ -1060,6 +1084,14 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
         P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
         return run_learned(sc, P, kFlux, o, t, 1ull, who);
     }
+    if (o->shard_count > 1) {
+        // this shard's path ids: [n i / c, n (i + 1) / c)
+        const unsigned __int128 n = npaths;
+        const unsigned long long b = (unsigned long long)(n * (unsigned)o->shard_index / (unsigned)o->shard_count);
+        const unsigned long long e = (unsigned long long)(n * (unsigned)(o->shard_index + 1) / (unsigned)o->shard_count);
+        P.path_base = b;
+        P.total = e - b;
+    }
     return run_trace(sc, P, kFlux, o, t, who);
 }
 
@@ -1078,6 +1110,7 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
 {
     if (n < 1 || n > (1 << 20)) return fail(ctx, MCRT_ERR_ARG, "%s: item count %d not in [1, 2^20]", who, n);
     if (o->proposal) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: learned proposal in batches", who);
+    if (o->shard_count > 1) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: sharding in batches (items are the unit)", who);
     if (o->sun_mode == MCRT_SUN_DECOMP) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: decomposition tracking in batches", who);
     const uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     h.assign((size_t)n, BatchItem{});

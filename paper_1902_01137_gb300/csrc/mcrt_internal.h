@@ -245,6 +245,8 @@ int order_tiles(int width, int height, int* tiles_x);
 cudaError_t launch_view_cost(const TraceParams& P, bool bf16, float* cost, cudaStream_t st);
 cudaError_t launch_expand_order(const uint32_t* tiles, const uint32_t* prefix, int n, int width, int height,
                                 uint32_t* order, cudaStream_t st);
+cudaError_t launch_shard_order(const uint32_t* order, uint32_t n_out, uint32_t stride, uint32_t offset,
+                               uint32_t* out, cudaStream_t st);
 cudaError_t launch_debug_dda(const DevScene& S, const float* o, const float* d, int cap, int* cells,
                              float* tio, int* count_status, bool bf16, cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,

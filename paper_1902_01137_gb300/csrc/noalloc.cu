@@ -103,6 +103,7 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     if (spp < 1) return nfail(ctx, MCRT_ERR_ARG, "%s: spp must be >= 1", who);
     if (!(cam->fov_deg > 0.0f && cam->fov_deg < 180.0f)) return nfail(ctx, MCRT_ERR_ARG, "%s: fov must be in (0, 180)", who);
     if (o->proposal) return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the learned proposal needs work buffers", who);
+    if (o->shard_count > 1) return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: a shard needs its own claim order", who);
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return nfail(ctx, MCRT_ERR_ARG, "%s: device index too large", who);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return nfail(ctx, MCRT_ERR_CUDA, "%s: cudaSetDevice: %s", who, cudaGetErrorString(e));

@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     int phase = PH_IDLE;
     unsigned cell = 0;                      // tally cell of the chunk
     int px = 0, py = 0;                     // camera pixel of the chunk
-    float acc[2 * NQ];                      // chunk sums of x and x^2
+    double acc[2 * NQ];                     // chunk sums of x and x^2 (FP64; x^2 of an FP32 x is exact)
 #pragma unroll
-    for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
+    for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0;
     Ray R;
     int kind = kMain;
     uint32_t c2 = 0, blk = 1, ev = 0;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             const bool mine = pending && cell == c;
 #pragma unroll
             for (int q = 0; q < 2 * NQ; ++q) {
-                double a = mine ? (double)acc[q] : 0.0;
+                double a = mine ? acc[q] : 0.0;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
                 if (lane == src) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)c * NQ + (q >> 1), a);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             if (mine) {
                 pending = false;
 #pragma unroll
-                for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
+                for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0;
             }
             fmask = __ballot_sync(kFull, pending);
         }
@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                     pend = min(pid + (unsigned long long)P.chunk, P.total);
                     chunk = true;
                     phase = (LEARNED && P.resume) ? PH_RESUME : PH_START;
-                    if (LEARNED && !P.resume) { pid += P.path_base; pend += P.path_base; }
+                    // the batch (learned mode) or shard (flux) this launch traces
+                    if (!BATCH && !(LEARNED && P.resume)) { pid += P.path_base; pend += P.path_base; }
                     if constexpr (BATCH) {
                         // items own chunk-aligned id ranges: find the item, use its local ids
                         int lo = 0, hi = P.n_items - 1;
@@ -710,20 +711,21 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             if (evc == EV_ESCAPE) path_done = true;
             if (path_done) {
                 if constexpr (SENSOR == kCamera) {
-                    acc[0] += score;
-                    acc[1] += score * score;
+                    const double x = score;
+                    acc[0] += x;
+                    acc[1] += x * x;
                 } else {
                     const float pi_over_mu0 = __fdividef(kPi, TERRAIN ? fz * S.sun[2] : S.sun[2]);
-                    const float tf = pi_over_mu0 * score;
-                    const float tt = tdir + tf;
-                    acc[0] += tdir; acc[1] += tdir * tdir;
+                    const double td = tdir, tf = pi_over_mu0 * score;
+                    const double tt = td + tf;
+                    acc[0] += td; acc[1] += td * td;
                     acc[2] += tf; acc[3] += tf * tf;
                     acc[4] += tt; acc[5] += tt * tt;
                     if constexpr (BATCH) {
-                        const float dt = pi_over_mu0 * dscore;
+                        const double dt = pi_over_mu0 * dscore;
                         acc[6] += dt; acc[7] += dt * dt;
                         if (EXTRA) {
-                            const float da = pi_over_mu0 * dal;
+                            const double da = pi_over_mu0 * dal;
                             acc[8] += da; acc[9] += da * da;
                         }
                     }
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     if (chunk) {
 #pragma unroll
         for (int q = 0; q < 2 * NQ; ++q)
-            if (acc[q] != 0.0f) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)cell * NQ + (q >> 1), (double)acc[q]);
+            if (acc[q] != 0.0) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)cell * NQ + (q >> 1), acc[q]);
     }
     if (COUNT) {
 #pragma unroll
@@ -922,6 +924,17 @@ __global__ void view_cost_kernel(TraceParams P, int tiles_x, int tiles_y, float*
 
 // order[prefix[b] + j] = the j-th pixel (row-major inside the tile) of the
 // b-th tile in claim order.
+// One shard of a claim order: out[i] = order[i * stride + offset] (the
+// identity order when order is NULL).
+__global__ void shard_order_kernel(const uint32_t* __restrict__ order, uint32_t n_out, uint32_t stride,
+                                   uint32_t offset, uint32_t* __restrict__ out)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    const uint32_t j = i * stride + offset;
+    out[i] = order ? order[j] : j;
+}
+
 __global__ void expand_order_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ prefix, int n,
                                     int tiles_x, int width, int height, uint32_t* __restrict__ order)
 {
@@ -1146,6 +1159,14 @@ cudaError_t launch_view_cost(const TraceParams& P, bool bf16, float* cost, cudaS
     const int ty = n / tx;
     if (bf16) view_cost_kernel<true><<<(n + 127) / 128, 128, 0, st>>>(P, tx, ty, cost);
     else view_cost_kernel<false><<<(n + 127) / 128, 128, 0, st>>>(P, tx, ty, cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_order(const uint32_t* order, uint32_t n_out, uint32_t stride, uint32_t offset,
+                               uint32_t* out, cudaStream_t st)
+{
+    if (n_out == 0) return cudaSuccess;
+    shard_order_kernel<<<(n_out + 255) / 256, 256, 0, st>>>(order, n_out, stride, offset, out);
     return cudaGetLastError();
 }
 

@@ -2,10 +2,13 @@
 
 Paths are independent, so a tally shards by contiguous path-id ranges with
 no exchange during tracing; the only collective is one reduction of the
-per-rank FP64 sums at the end.  Online training of the proposal network is
-data-parallel: one gradient average per Adam step (average_gradient).  The reduction gathers every rank's sums and
-adds them in rank order, so its result is the same on every rank and from
-run to run, whatever the transport (gloo on CPU, NCCL on GPUs).
+per-rank FP64 sums at the end.  An image shards by pixels (every world-th
+pixel of the claim order per rank, which keeps the ranks' loads even); a
+flux by contiguous path-id ranges.  Online training of the proposal network
+is data-parallel: one gradient average per Adam step (average_gradient).
+The reduction gathers every rank's sums and adds them in rank order, so its
+result is the same on every rank and from run to run, whatever the
+transport (gloo on CPU, NCCL on GPUs).
 """
 from __future__ import annotations
 
@@ -26,6 +29,26 @@ def shard_range(total: int, rank: int, world: int, align: int = 1):
     lo = units * rank // world
     hi = units * (rank + 1) // world
     return min(lo * align, total), min(hi * align, total)
+
+
+def image_shard_pixels(npix: int, rank: int, world: int):
+    """Pixels of `rank`'s shard of an image traced in raster order
+    (mcrt_trace_opts shard_index / shard_count with MCRT_ORDER_RASTER):
+    every world-th pixel starting at rank.  With the cost order the library
+    interleaves the same way over its claim order instead."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank %d of %d" % (rank, world))
+    return np.arange(rank, npix, world, dtype=np.int64)
+
+
+def combine_image(s1, s2, n_per_pixel, group=None):
+    """One image from its shards: every rank holds per-pixel FP64 sums
+    (Sum x, Sum x^2) of its own pixels (zeros elsewhere); the sums are added
+    in rank order and the mean and standard error formed from them, the same
+    on every rank."""
+    t1, t2 = reduce_sums([s1, s2], group=group)
+    m, se = mean_se(t1, t2, np.full(np.shape(t1), float(n_per_pixel)))
+    return t1, t2, m, se
 
 
 def replica_seed(seed: int, rank: int) -> int:

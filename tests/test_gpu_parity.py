@@ -476,3 +476,47 @@ def test_pixel_order_changes_speed_not_results(m, small):
             assert ca[k] == cb[k], k
     with pytest.raises(m.McrtError):
         sc.trace_camera(scenes.nadir_camera(sp, 8, 8), 1, seed=1, pixel_order=5)
+
+
+def test_shards_add_up_to_the_whole_trace(m, ctx, small):
+    """One image or flux traced as shards (one per process in a multi-GPU
+    run): every path keeps its global id, so the shards' per-pixel sums add
+    up to the unsharded trace's (to the order of the FP64 adds) and their
+    pixel sets partition the image, in cost and in raster claim order; the
+    flux shards cover [0, n) with no path twice."""
+    sp, sc = small
+    cam = scenes.nadir_camera(sp, 37, 21)
+    cd = m.CameraDesc()
+    for i in range(3):
+        cd.pos[i], cd.target[i], cd.up[i] = cam.pos[i], cam.target[i], cam.up[i]
+    cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
+
+    def sums(fn, **kw):
+        o = m.mcrt_trace_opts_default()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        t = fn(o)
+        try:
+            return m.mcrt_tally_read_sums(ctx.h, t)
+        finally:
+            m.mcrt_tally_destroy(t)
+
+    cam_fn = lambda o: m.mcrt_trace_camera(ctx.h, sc.h, cd, 8, 5, o)
+    for order in (m.MCRT_ORDER_COST, m.MCRT_ORDER_RASTER):
+        w1, w2 = sums(cam_fn, pixel_order=order)
+        parts = [sums(cam_fn, pixel_order=order, shard_index=r, shard_count=3) for r in range(3)]
+        owner = np.stack([(p[0][:, 0] != 0) | (p[1][:, 0] != 0) for p in parts])
+        assert owner.sum(axis=0).max() <= 1                 # no pixel in two shards
+        if order == m.MCRT_ORDER_RASTER:
+            for r in range(3):                              # raster shards: every third pixel
+                assert not owner[r][np.setdiff1d(np.arange(37 * 21), np.arange(r, 37 * 21, 3))].any()
+        np.testing.assert_allclose(sum(p[0] for p in parts), w1, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(sum(p[1] for p in parts), w2, rtol=1e-12, atol=0)
+    flux_fn = lambda o: m.mcrt_trace_flux(ctx.h, sc.h, 10007, 6, o)
+    f1, f2 = sums(flux_fn)
+    parts = [sums(flux_fn, shard_index=r, shard_count=4) for r in range(4)]
+    np.testing.assert_allclose(sum(p[0] for p in parts), f1, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(sum(p[1] for p in parts), f2, rtol=1e-12, atol=0)
+    with pytest.raises(m.McrtError) as e:
+        sums(flux_fn, shard_index=4, shard_count=4)
+    assert e.value.status == m.MCRT_ERR_ARG

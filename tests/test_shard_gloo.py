@@ -48,6 +48,29 @@ def _worker(rank, world, port, total, out_dir):
         dist.destroy_process_group()
 
 
+def _image_worker(rank, world, port, out_dir):
+    """One image split by pixels over the ranks (the bench's multi-GPU step),
+    the CPU oracle tracing each rank's shard, combined by shard.combine_image."""
+    import torch.distributed as dist
+    import oracle
+    import scenes
+    from paper_1902_01137_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        S = _scene()
+        sp = scenes.blobs_small(0)
+        cam = scenes.nadir_camera(sp, 12, 10)
+        oc = oracle.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, 12, 10)
+        px = shard.image_shard_pixels(120, rank, world)
+        t, _ = oracle.trace_camera(S, oc, 8, seed=9, pixels=px, nthreads=2)
+        s1, s2, mean, se = shard.combine_image(t.s1.ravel(), t.s2.ravel(), 8)
+        np.savez(os.path.join(out_dir, "img%d.npz" % rank), s1=s1, s2=s2, mean=mean, se=se, px=px)
+    finally:
+        dist.destroy_process_group()
+
+
 def _records(n, seed):
     r = np.random.default_rng(seed)
     x = np.concatenate([r.uniform(-1, 1, (n, 3)), r.normal(size=(n, 3)), r.uniform(-8, 6, (n, 3))], axis=1)
@@ -115,6 +138,29 @@ def test_two_ranks_gloo_match_one_process(tmp_path):
     m, se = shard.mean_se(a["rs1"], a["rs2"], a["rn"][0])
     for q in range(3):
         assert abs(m[q] - one.mean[q]) <= 4 * math.hypot(se[q], one.se[q])
+
+
+def test_image_split_over_two_ranks_equals_one_process(tmp_path):
+    """A 2-rank pixel split of one image, combined in rank order, gives the
+    one-process image's sums bit for bit (each pixel's sums come from one
+    rank, the other adds exact zeros), on both ranks."""
+    import torch.multiprocessing as mp
+    import oracle
+    import scenes
+    port = 30600 + (os.getpid() % 1000)
+    mp.start_processes(_image_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
+    a = np.load(tmp_path / "img0.npz")
+    b = np.load(tmp_path / "img1.npz")
+    for k in ("s1", "s2", "mean", "se"):
+        assert np.array_equal(a[k], b[k]), k
+    assert sorted(np.concatenate([a["px"], b["px"]]).tolist()) == list(range(120))
+    sp = scenes.blobs_small(0)
+    cam = scenes.nadir_camera(sp, 12, 10)
+    one, _ = oracle.trace_camera(_scene(), oracle.Camera(cam.pos, cam.target, cam.up, cam.fov_deg, 12, 10), 8,
+                                 seed=9, nthreads=2)
+    assert np.array_equal(a["s1"], one.s1.ravel()) and np.array_equal(a["s2"], one.s2.ravel())
+    np.testing.assert_array_equal(a["mean"], one.mean.ravel())
+    assert a["mean"].max() > 0.0
 
 
 def test_data_parallel_training_step_gloo(tmp_path):
