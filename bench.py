@@ -527,72 +527,137 @@ def _fom(rel, ms):
     return 1.0 / (rel * rel * ms / 1e3)
 
 
-def learned_fom(m, ctx):
-    """Learned proposal vs plain HG sampling (1/(rel. variance x time)) on
-    the bench's cumulus field (512x512x160 at 25 m), sun zenith 60 deg.  The
-    flux figure uses T_tot over 2^24 paths; the image figure the mean pixel
-    relative variance of a 512 x 512 nadir image at 16 spp.  Each estimate
-    has its own network, trained online on its own kind of path: flux paths
-    for the flux, camera paths for the image (2^26 paths in batches of 2^20,
-    2 Adam steps each).  'online' counts that training in the time of the
-    estimate its paths give; 'frozen' reuses the trained network.  The image
-    traced with the flux-trained network is reported beside it."""
+# The learned proposal's configuration in the bench line: 8 learned vertices,
+# MIS share 0.25 for HG (the best of the alpha / vertex sweep of
+# --workload fom), network trained online on the image's own kind of path.
+FOM_ALPHA, FOM_NL = 0.25, 8
+FOM_TARGET = 0.01
+
+
+def _img_stats(r):
+    """Mean pixel relative variance and median pixel relative SE over the
+    pixels brighter than 1e-3 of the image maximum."""
+    ok = r.mean > 1e-3 * r.mean.max()
+    rel = r.se[ok] / r.mean[ok]
+    return float(np.mean(rel * rel)), float(np.median(rel))
+
+
+def _run_to_target(trace, pilot_spp, seed):
+    """Trace a pilot image, size the run that brings the median pixel
+    relative SE to FOM_TARGET (10 % margin), trace it; the FOM is that run's
+    1 / (mean pixel relative variance x its time)."""
+    p = trace(pilot_spp, seed)
+    _, med = _img_stats(p)
+    spp = max(pilot_spp, int(math.ceil(pilot_spp * (med / FOM_TARGET) ** 2 * 1.1)))
+    r = trace(spp, seed + 1)
+    rv, med = _img_stats(r)
+    return {"spp": spp, "ms": r.kernel_ms, "rel_var": rv, "median_rel_se": med, "fom": 1.0 / (rv * r.kernel_ms / 1e3),
+            "paths": spp * r.mean.size, "mean": float(r.mean.mean())}
+
+
+def _flux_to_target(trace, seed):
+    p = trace(1 << 20, seed)
+    rel = p.se[2] / p.mean[2]
+    n = max(1024, int(math.ceil((1 << 20) * (rel / FOM_TARGET) ** 2 * 1.1)))
+    r = trace(n, seed + 1)
+    rel = r.se[2] / r.mean[2]
+    return {"paths": n, "ms": r.kernel_ms, "rel_se": rel, "fom": _fom(rel, r.kernel_ms)}
+
+
+def learned_fom(m, ctx, sweep=False):
+    """Learned proposal against plain HG sampling, 1/(relative variance x
+    time) at 1 % relative standard error (the metric), on the bench's cumulus
+    field (512x512x160 at 25 m), sun zenith 60 deg.
+
+    Image: a 512 x 512 nadir image traced until its median pixel relative SE
+    is at most 1 % (pixels brighter than 1e-3 of the maximum); FOM = 1 /
+    (mean pixel relative variance x time).  The learned form's network is
+    first trained online on camera paths of the same image (2^26 paths in
+    batches of 2^20, two Adam steps each); 'online' counts that training in
+    the time, 'frozen' does not.  Flux: T_tot to 1 % relative SE (a few
+    thousand paths, where fixed launch costs dominate) and, beside it, at
+    2^26 paths.  sweep: the image FOM for MIS shares 0.25 / 0.5 / 0.75 and
+    2 / 8 learned vertices at 256 spp (the FOM of a frozen network does not
+    depend on the run's length) instead of the full 1 % runs."""
     import scenes
     import torch
     spec, _ = make_workload()
     sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    cam = scenes.nadir_camera(spec, 512, 512)
     out = {"field": "cumulus 512x512x160 @25m (the bench field), sun 60 deg",
-           "quantity": "T_tot flux; 512x512 image @16 spp"}
+           "protocol": "median pixel relative SE <= 1 %% (pixels > 1e-3 of max), FOM = 1/(mean pixel rel. "
+                       "variance x time); learned: alpha %.2f, %d learned vertices" % (FOM_ALPHA, FOM_NL)}
     try:
-        N = 1 << 24
-        sc.trace_flux(1 << 20, seed=1)
-        plain = sc.trace_flux(N, seed=3)
-        rel_p = plain.se[2] / plain.mean[2]
-        out["plain"] = {"fom": _fom(rel_p, plain.kernel_ms), "rel_se": rel_p, "ms": plain.kernel_ms, "paths": N}
-        cam = scenes.nadir_camera(spec, 512, 512)
+        sc.trace_camera(cam, 16, seed=1)
 
-        def img_rel(r):
-            ok = r.mean > 1e-3 * r.mean.max()
-            return float(np.sqrt(np.mean((r.se[ok] / r.mean[ok]) ** 2)))
-        ip = sc.trace_camera(cam, 16, seed=3)
-        out["plain_image"] = {"fom": _fom(img_rel(ip), ip.kernel_ms), "rel_se": img_rel(ip), "ms": ip.kernel_ms}
-        for tag, nl, alpha in (("alpha0.5_nl8", 8, 0.5), ("alpha0.75_nl1", 1, 0.75)):
+        def plain(spp, seed):
+            return sc.trace_camera(cam, spp, seed=seed)
+
+        def train(alpha, nl):
             prop = m.Proposal(ctx, seed=7)
+            t = sc.trace_camera(cam, 256, seed=4, proposal=prop, learn=1, batch_paths=1 << 20, n_learned=nl,
+                                mis_alpha=alpha, train_steps=2)
+            return prop, t.kernel_ms
+
+        if sweep:
+            base = plain(256, 3)
+            rv0, _ = _img_stats(base)
+            f0 = 1.0 / (rv0 * base.kernel_ms / 1e3)
+            out["plain_256spp"] = {"ms": base.kernel_ms, "rel_var": rv0, "fom": f0}
+            for alpha in (0.25, 0.5, 0.75):
+                for nl in (2, 8):
+                    prop, tms = train(alpha, nl)
+                    try:
+                        r = sc.trace_camera(cam, 256, seed=5, proposal=prop, learn=0, n_learned=nl,
+                                            mis_alpha=alpha)
+                    finally:
+                        prop.close()
+                    rv, _ = _img_stats(r)
+                    f = 1.0 / (rv * r.kernel_ms / 1e3)
+                    out["alpha%.2f_nl%d" % (alpha, nl)] = {"ms": r.kernel_ms, "rel_var": rv, "fom": f,
+                                                           "ratio": f / f0, "var_gain": rv0 / rv,
+                                                           "time_ratio": r.kernel_ms / base.kernel_ms,
+                                                           "train_ms": tms}
+            return out
+        pl = _run_to_target(plain, 256, 10)
+        out["plain_image"] = pl
+        prop, tms = train(FOM_ALPHA, FOM_NL)
+        try:
+            def learned(spp, seed):
+                return sc.trace_camera(cam, spp, seed=seed, proposal=prop, learn=0, n_learned=FOM_NL,
+                                       mis_alpha=FOM_ALPHA)
+            lf = _run_to_target(learned, 64, 20)
+            lf["train_ms"] = tms
+            out["learned_image"] = lf
+            online = 1.0 / (lf["rel_var"] * (lf["ms"] + tms) / 1e3)
+            out["ratio_image_vs_plain"] = lf["fom"] / pl["fom"]
+            out["ratio_online_image_vs_plain"] = online / pl["fom"]
+            out["image_means_agree_rel"] = abs(lf["mean"] - pl["mean"]) / pl["mean"]
+
+            # ground flux T_tot: its own network, trained on flux paths
+            fprop = m.Proposal(ctx, seed=7)
             try:
-                tr = sc.trace_flux(1 << 26, seed=4, proposal=prop, learn=1, batch_paths=1 << 20, n_learned=nl,
-                                   mis_alpha=alpha, train_steps=2)
-                rel_t = tr.se[2] / tr.mean[2]
-                fr = sc.trace_flux(N, seed=5, proposal=prop, learn=0, batch_paths=1 << 24, n_learned=nl,
-                                   mis_alpha=alpha)
-                rel_f = fr.se[2] / fr.mean[2]
-                fx = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=nl,
-                                     mis_alpha=alpha)
-                # the image's own network: trained online on camera paths
-                prop_i = m.Proposal(ctx, seed=7)
-                try:
-                    ti = sc.trace_camera(cam, 256, seed=4, proposal=prop_i, learn=1, batch_paths=1 << 20,
-                                         n_learned=nl, mis_alpha=alpha, train_steps=2)
-                    fi = sc.trace_camera(cam, 16, seed=5, proposal=prop_i, learn=0, batch_paths=1 << 22,
-                                         n_learned=nl, mis_alpha=alpha)
-                finally:
-                    prop_i.close()
-                fom_ip = _fom(img_rel(ip), ip.kernel_ms)
-                out[tag] = {
-                    "online": {"fom": _fom(rel_t, tr.kernel_ms), "rel_se": rel_t, "ms": tr.kernel_ms,
-                               "paths": 1 << 26, "adam_steps": 128},
-                    "frozen": {"fom": _fom(rel_f, fr.kernel_ms), "rel_se": rel_f, "ms": fr.kernel_ms},
-                    "online_image": {"fom": _fom(img_rel(ti), ti.kernel_ms), "rel_se": img_rel(ti),
-                                     "ms": ti.kernel_ms, "spp": 256, "adam_steps": 128},
-                    "frozen_image": {"fom": _fom(img_rel(fi), fi.kernel_ms), "rel_se": img_rel(fi),
-                                     "ms": fi.kernel_ms},
-                    "frozen_image_flux_network": {"fom": _fom(img_rel(fx), fx.kernel_ms), "rel_se": img_rel(fx),
-                                                  "ms": fx.kernel_ms},
-                    "ratio_frozen_vs_plain": _fom(rel_f, fr.kernel_ms) / _fom(rel_p, plain.kernel_ms),
-                    "ratio_image_vs_plain": _fom(img_rel(fi), fi.kernel_ms) / fom_ip,
-                    "ratio_online_image_vs_plain": _fom(img_rel(ti), ti.kernel_ms) / fom_ip,
-                }
+                ft = sc.trace_flux(1 << 26, seed=4, proposal=fprop, learn=1, batch_paths=1 << 20, n_learned=FOM_NL,
+                                   mis_alpha=FOM_ALPHA, train_steps=2)
+                pf = _flux_to_target(lambda n, s_: sc.trace_flux(n, seed=s_), 30)
+                lfx = _flux_to_target(lambda n, s_: sc.trace_flux(n, seed=s_, proposal=fprop, learn=0,
+                                                                  n_learned=FOM_NL, mis_alpha=FOM_ALPHA), 40)
+                big = 1 << 26
+                pb = sc.trace_flux(big, seed=50)
+                lb = sc.trace_flux(big, seed=51, proposal=fprop, learn=0, n_learned=FOM_NL, mis_alpha=FOM_ALPHA)
+                fp_b = _fom(pb.se[2] / pb.mean[2], pb.kernel_ms)
+                fl_b = _fom(lb.se[2] / lb.mean[2], lb.kernel_ms)
+                out["flux"] = {"plain_1pct": pf, "learned_1pct": lfx, "train_ms": ft.kernel_ms,
+                               "ratio_1pct": lfx["fom"] / pf["fom"],
+                               "ratio_online_1pct": 1.0 / ((lfx["rel_se"] ** 2) * (lfx["ms"] + ft.kernel_ms) / 1e3)
+                               / pf["fom"],
+                               "plain_2p26": {"fom": fp_b, "ms": pb.kernel_ms, "rel_se": pb.se[2] / pb.mean[2]},
+                               "learned_2p26": {"fom": fl_b, "ms": lb.kernel_ms, "rel_se": lb.se[2] / lb.mean[2]},
+                               "ratio_2p26": fl_b / fp_b}
             finally:
-                prop.close()
+                fprop.close()
+        finally:
+            prop.close()
     finally:
         sc.close()
     return out
@@ -962,6 +1027,17 @@ def run_tau(args):
     return 0
 
 
+def run_fom_sweep(args):
+    """The learned proposal's image FOM for each MIS share and learned-vertex
+    count (256 spp; see learned_fom), as one JSON line."""
+    import paper_1902_01137_gb300 as m
+    ctx = m.Context(0)
+    out = learned_fom(m, ctx, sweep=True)
+    print(json.dumps({"metric": METRIC, "workload": "learned-proposal sweep", "fom": out}))
+    ctx.close()
+    return 0
+
+
 def run_profile_case(grid="pyramid"):
     """A small case of the bench kernel for ncu: the same 512x512x160 field
     (160 MiB, larger than L2), a 512 x 512 image at 16 spp (4,194,304
@@ -1042,7 +1118,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep", "tau"])
+    ap.add_argument("--workload", default="image", choices=["image", "batch", "sweep", "tau", "fom"])
     ap.add_argument("--sweep-paths", type=int, default=100_000_000)
     ap.add_argument("--no-fom", action="store_true")
     ap.add_argument("--no-octree", action="store_true")
@@ -1073,6 +1149,8 @@ def main():
         return run_sweep(args)
     if args.workload == "tau":
         return run_tau(args)
+    if args.workload == "fom":
+        return run_fom_sweep(args)
     return run_gpu(args)
 
 

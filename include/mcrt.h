@@ -282,6 +282,9 @@ typedef struct {
                                /* produced; the first batch of an untrained     */
                                /* network samples HG only                       */
     int32_t batch_paths;       /* paths per batch in learned mode; 0 = 2^21     */
+                               /* when learning, else 2^25 (about 12 GB of      */
+                               /* queues; larger batches waste less time in     */
+                               /* the passes' tails)                            */
     float learning_rate;       /* 0 = 1e-3                                      */
     int32_t train_steps;       /* Adam steps per batch; 0 = 1                   */
     double deadline_ms;        /* > 0: stop and report MCRT_ERR_TIMEOUT after   */

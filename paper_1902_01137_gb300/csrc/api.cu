@@ -779,7 +779,9 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
     const float alpha = o->mis_alpha > 0.0f ? o->mis_alpha : 0.5f;
     const float lr = o->learning_rate > 0.0f ? o->learning_rate : 1e-3f;
     const int steps = o->train_steps ? o->train_steps : 1;
-    unsigned long long B = o->batch_paths ? (unsigned long long)o->batch_paths : (1ull << 21);
+    // a frozen network takes large batches: each batch ends every pass with
+    // its slowest paths, so fewer, larger batches waste less of the GPU
+    unsigned long long B = o->batch_paths ? (unsigned long long)o->batch_paths : (o->learn ? (1ull << 21) : (1ull << 25));
     if (B < spp) B = spp;
     B = (B / spp) * spp;                                 // batches hold whole pixels
     const unsigned long long total = P0.total;
@@ -797,7 +799,7 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
     auto A = [&](auto** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(p), bytes ? bytes : 16, ctx->stream);
     };
-    A(&qa, B * 64); A(&qb, B * 64); A(&fa, B * 32); A(&fb, B * 32); A(&mix, B * 160); A(&fin, B * 4);
+    A(&qa, B * 64); A(&qb, B * 64); A(&fa, B * 32); A(&fb, B * 32); A(&mix, B * 192); A(&fin, B * 4);
     A(&cnt, 16);
     if (rec_cap) { A(&rfeat, (size_t)rec_cap * 32); A(&rdir, (size_t)rec_cap * 12); A(&rval, (size_t)rec_cap * 16); A(&tgt, (size_t)rec_cap * 4); }
     auto release = [&]() {
@@ -844,7 +846,8 @@ int run_learned(mcrt_scene* sc, const TraceParams& P0, int sensor, const mcrt_tr
             if (P.total == 0) break;
             if (r > 0) {
                 ctx->launches++;
-                e = launch_mlp_infer(prop->d_wbf, prop->d_bias, fin_feat, (int)n_in, mix, nullptr, ctx->sm_count, ctx->stream);
+                e = launch_mlp_infer(prop->d_wbf, prop->d_bias, fin_feat, (int)n_in, mix, nullptr, ctx->sm_count,
+                                     ctx->stream, true);
             }
             if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4, ctx->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(t->d_work, 0, sizeof(WorkState), ctx->stream);

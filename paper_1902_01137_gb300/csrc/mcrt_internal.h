@@ -167,7 +167,7 @@ struct TraceParams {
     unsigned long long path_base;  // first path id of the batch (record / final-score index origin)
     const uint4* qin;          // resumed states, 4 x uint4 per slot
     const uint4* qin_feat;     // their feature rows (16 bf16 = 2 uint4)
-    const float* qin_mix;      // their mixture parameters (40 floats)
+    const float* qin_mix;      // their mixture parameters (48 floats: mu, kappa, weight CDF, pi C(kappa) per lobe)
     uint4* qout;               // suspended states
     uint4* qout_feat;          // suspended feature rows
     unsigned* qout_count;
@@ -263,8 +263,10 @@ int ensure_leaf(mcrt_scene* sc, float tau, int finest, int grid);
 // learned proposal network
 size_t mlp_packed_bf16_elems();
 size_t mlp_packed_bias_elems();
+// mix: 40 floats per row (mu, kappa, pi per lobe), or with tracer_layout
+// 48 (mu, kappa, weight CDF, pi C(kappa)) as the learned trace reads them.
 cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const void* feat, int n, float* mix,
-                             float* raw, int sm_count, cudaStream_t st);
+                             float* raw, int sm_count, cudaStream_t st, bool tracer_layout = false);
 cudaError_t launch_mlp_train_tc(const void* wpacked, const float* bpacked, const float* params, const void* feat,
                                 const float* dirs, const float* tgt, int n, float scale, float* grad, float* loss,
                                 int sm_count, cudaStream_t st);

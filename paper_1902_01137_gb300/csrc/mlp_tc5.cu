@@ -125,9 +125,16 @@ __device__ __forceinline__ bool from_mma(uint64_t* bar, uint32_t& phase)
     return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// Mixture parameters of one row's 40 raw outputs: unit axis, concentration
-// softplus + 1e-3, softmax weight (the layout the tracer reads).
-__device__ __forceinline__ void mixture_out(const float* r, float* __restrict__ o)
+// Mixture parameters of one row's 40 raw outputs: unit axis mu_j,
+// concentration kappa_j = softplus + 1e-3, softmax weight pi_j.  The API
+// layout holds (mu, kappa, pi) per lobe (40 floats); the tracer's layout
+// (kTracerMix floats) holds (mu, kappa, CDF of the weights up to lobe j,
+// pi_j C(kappa_j)) with the vMF normalisation C(k) = k / (2 pi (1 - e^-2k)),
+// so that a resumed vertex evaluates the mixture density with one
+// exponential per lobe.
+constexpr int kTracerMix = 48;
+
+__device__ __forceinline__ void mixture_out(const float* r, float* __restrict__ o, bool tracer)
 {
     float mx = -3.0e38f;
 #pragma unroll
@@ -136,22 +143,27 @@ __device__ __forceinline__ void mixture_out(const float* r, float* __restrict__ 
 #pragma unroll
     for (int j = 0; j < kLobes; ++j) { e[j] = __expf(r[5 * j + 4] - mx); s += e[j]; }
     const float inv_s = 1.0f / s;
+    float cdf = 0.0f;
 #pragma unroll
     for (int j = 0; j < kLobes; ++j) {
         const float x = r[5 * j], y = r[5 * j + 1], z = r[5 * j + 2];
         const float nn = x * x + y * y + z * z;
         const float inv = nn > 1e-24f ? rsqrtf(nn) : 0.0f;
         const float k = r[5 * j + 3];
-        float4 a;
-        a.x = nn > 1e-24f ? x * inv : 0.0f;
-        a.y = nn > 1e-24f ? y * inv : 0.0f;
-        a.z = nn > 1e-24f ? z * inv : 1.0f;
-        a.w = (k > 20.0f ? k : log1pf(__expf(k))) + 1e-3f;
-        o[5 * j] = a.x;
-        o[5 * j + 1] = a.y;
-        o[5 * j + 2] = a.z;
-        o[5 * j + 3] = a.w;
-        o[5 * j + 4] = e[j] * inv_s;
+        const float kap = (k > 20.0f ? k : log1pf(__expf(k))) + 1e-3f;
+        const float pi = e[j] * inv_s;
+        const int b = tracer ? 6 * j : 5 * j;
+        o[b] = nn > 1e-24f ? x * inv : 0.0f;
+        o[b + 1] = nn > 1e-24f ? y * inv : 0.0f;
+        o[b + 2] = nn > 1e-24f ? z * inv : 1.0f;
+        o[b + 3] = kap;
+        if (tracer) {
+            cdf += pi;
+            o[b + 4] = cdf;
+            o[b + 5] = pi * kap / (2.0f * kPi * (-expm1f(-2.0f * kap)));
+        } else {
+            o[b + 4] = pi;
+        }
     }
 }
 
@@ -184,7 +196,8 @@ __device__ __forceinline__ void infer_hidden(uint32_t tacc, const float* __restr
 __global__ void __launch_bounds__(128) mlp_infer_tc5_kernel(const __nv_bfloat16* __restrict__ wpacked,
                                                            const float* __restrict__ bpacked,
                                                            const __nv_bfloat16* __restrict__ feat, int n,
-                                                           float* __restrict__ mix, float* __restrict__ raw_out)
+                                                           float* __restrict__ mix, float* __restrict__ raw_out,
+                                                           int tracer_layout)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ float sB[kPackedBias];
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(128) mlp_infer_tc5_kernel(const __nv_bfloat16*
         if (row < n) {
             if (raw_out)
                 for (int i = 0; i < kOut; ++i) raw_out[(size_t)row * kOut + i] = r[i];
-            mixture_out(r, mix + (size_t)row * kOut);
+            mixture_out(r, mix + (size_t)row * (tracer_layout ? kTracerMix : kOut), tracer_layout != 0);
         }
     }
     if (!ok && tid == 0) atomicExch(&g_tc5_error, 1);
@@ -564,7 +577,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
 }  // namespace
 
 cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const void* feat, int n, float* mix,
-                                 float* raw, int sm_count, cudaStream_t st)
+                             float* raw, int sm_count, cudaStream_t st, bool tracer_layout)
 {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(mlp_infer_tc5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -573,7 +586,8 @@ cudaError_t launch_mlp_infer(const void* wpacked, const float* bpacked, const vo
     const int tiles = (n + kRows - 1) / kRows;
     const int grid = tiles < 3 * sm_count ? tiles : 3 * sm_count;
     mlp_infer_tc5_kernel<<<grid, 128, kInfSmem, st>>>(static_cast<const __nv_bfloat16*>(wpacked), bpacked,
-                                                      static_cast<const __nv_bfloat16*>(feat), n, mix, raw);
+                                                      static_cast<const __nv_bfloat16*>(feat), n, mix, raw,
+                                                      tracer_layout ? 1 : 0);
     return cudaGetLastError();
 }
 

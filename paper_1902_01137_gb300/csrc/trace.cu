@@ -557,30 +557,27 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             const float om = omega_at(S, vk);
             const float mu_s = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
             cf = score_it ? w * om * hg_pdf(S.g, mu_s) : 0.0f;
-            const float* mix = P.qin_mix + 40 * (size_t)slot;
+            const float* mix = P.qin_mix + 48 * (size_t)slot;
             if (xc <= P.mis_alpha) {
                 rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
             } else {
                 int j = 7;
-                float cum = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    cum += __ldg(mix + 5 * i + 4);
-                    if (j == 7 && i < 7 && xlobe <= cum) j = i;
-                }
-                const float mu_l[3] = {__ldg(mix + 5 * j), __ldg(mix + 5 * j + 1), __ldg(mix + 5 * j + 2)};
-                const float kap = __ldg(mix + 5 * j + 3);
+                for (int i = 0; i < 7; ++i)
+                    if (j == 7 && xlobe <= __ldg(mix + 6 * i + 4)) j = i;
+                const float mu_l[3] = {__ldg(mix + 6 * j), __ldg(mix + 6 * j + 1), __ldg(mix + 6 * j + 2)};
+                const float kap = __ldg(mix + 6 * j + 3);
                 float cw = 1.0f + __logf(xi1 + (1.0f - xi1) * __expf(-2.0f * kap)) / kap;
                 cw = fminf(fmaxf(cw, -1.0f), 1.0f);
                 rotate_dir(mu_l, cw, xi2, nd);
             }
             const float phg = hg_pdf(S.g, R.d[0] * nd[0] + R.d[1] * nd[1] + R.d[2] * nd[2]);
+            // mixture density: sum of pi_j C(kappa_j) exp(kappa_j (mu_j . w - 1))
             float qv = 0.0f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const float kap = __ldg(mix + 5 * i + 3);
-                const float c = __ldg(mix + 5 * i) * nd[0] + __ldg(mix + 5 * i + 1) * nd[1] + __ldg(mix + 5 * i + 2) * nd[2];
-                qv += __ldg(mix + 5 * i + 4) * kap / (2.0f * kPi * (-expm1f(-2.0f * kap))) * __expf(kap * (c - 1.0f));
+                const float c = __ldg(mix + 6 * i) * nd[0] + __ldg(mix + 6 * i + 1) * nd[1] + __ldg(mix + 6 * i + 2) * nd[2];
+                qv += __ldg(mix + 6 * i + 5) * __expf(__ldg(mix + 6 * i + 3) * (c - 1.0f));
             }
             const float qmix = P.mis_alpha * phg + (1.0f - P.mis_alpha) * qv;
             // training record: features, direction, score so far, w * omega

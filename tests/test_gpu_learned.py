@@ -235,39 +235,48 @@ def test_learned_result_independent_of_batches(env, orc):
         sc.close()
 
 
-def test_camera_trained_network_lowers_image_variance(env):
-    """What the trained network gains over the method without it: on the
-    512x512x160 cumulus field (sun 60 deg), a network trained online on
-    camera paths (2^26 paths, 128 Adam steps) with 8 learned vertices lowers
-    the mean pixel relative variance of a 512 x 512 nadir image at 16 spp
-    below plain HG sampling's (measured 0.88-0.92x in relative SE over
-    trainings, which are not bit-reproducible: the gradient sums use FP32
-    atomics), and the two images agree in their mean.  The relative SE
-    averaged over ~250k pixels is precise to about 0.3 %, so the bound of
-    0.97 still asks for a clearly lower variance."""
+def test_training_gains_where_directions_matter(env):
+    """What the trained network gains over the method without it, on a scene
+    whose radiance hinges on the scattering direction: a nadir view of a
+    homogeneous slab (tau = 2, albedo 1, g = 0.85) over a black ground with
+    the sun at 30 deg, scored to order 2.  Most of the second-order radiance
+    arrives from near the sun direction, which the forward-peaked HG phase
+    function rarely samples from a downward path (a back-scatter), so plain
+    sampling has a heavy-tailed, high variance.  A network trained online
+    on camera paths of that view (one learned vertex, MIS share 0.5) must
+    cut the per-path variance of the image at least 10-fold against plain
+    HG sampling and 3-fold against the same untrained network (measured:
+    55-fold and 6.5-fold; a hand-set lobe toward the sun cuts it 40- to
+    80-fold on the oracle), and the three images must agree in their mean.  Variances are pooled over the 64
+    pixels of 2^18 paths each, so they are estimated from 2^24 paths."""
     import scenes
-    import torch
     m, ctx = env
-    spec = scenes.cumulus(512, 512, 160, seed=0, device=torch.device("cuda", 0))
-    sc = m.Scene.from_spec(ctx, spec, k=spec.k)
-    prop = m.Proposal(ctx, seed=7)
-    try:
-        cam = scenes.nadir_camera(spec, 512, 512)
+    sp = scenes.homogeneous(16, 16, 10, 0.1, 2.0, levels=1, g=0.85, ssa_cloud=1.0, ssa_clear=1.0,
+                            sun_zenith_deg=30.0)
+    sc = m.Scene.from_spec(ctx, sp)
+    cam = scenes.nadir_camera(sp, 8, 8)
+    spp = 1 << 18
+    kw = dict(max_order=2)
 
-        def rel(r):
-            ok = r.mean > 1e-3 * r.mean.max()
-            return float(np.sqrt(np.mean((r.se[ok] / r.mean[ok]) ** 2)))
-        plain = sc.trace_camera(cam, 16, seed=3)
-        sc.trace_camera(cam, 256, seed=4, proposal=prop, learn=1, batch_paths=1 << 20, n_learned=8,
-                        mis_alpha=0.5, train_steps=2)
-        learned = sc.trace_camera(cam, 16, seed=5, proposal=prop, learn=0, batch_paths=1 << 22, n_learned=8,
-                                  mis_alpha=0.5)
-        assert rel(learned) < 0.97 * rel(plain), (rel(learned), rel(plain))
-        sp = math.sqrt(float((plain.se ** 2).sum())) / plain.se.size
-        sl = math.sqrt(float((learned.se ** 2).sum())) / learned.se.size
-        assert _close(float(learned.mean.mean()), sl, float(plain.mean.mean()), sp)
+    def pooled(r):
+        return float(r.mean.mean()), float(np.mean(r.se ** 2) * spp), math.sqrt(float(np.mean(r.se ** 2)) / r.se.size)
+
+    trained = m.Proposal(ctx, seed=7)
+    untrained = m.Proposal(ctx, seed=7)
+    try:
+        sc.trace_camera(cam, 1 << 16, seed=1, proposal=trained, learn=1, batch_paths=1 << 18, n_learned=1,
+                        mis_alpha=0.5, train_steps=8, learning_rate=3e-3, **kw)
+        plain = pooled(sc.trace_camera(cam, spp, seed=2, **kw))
+        lt = pooled(sc.trace_camera(cam, spp, seed=3, proposal=trained, learn=0, n_learned=1, mis_alpha=0.5, **kw))
+        lu = pooled(sc.trace_camera(cam, spp, seed=4, proposal=untrained, learn=0, n_learned=1, mis_alpha=0.5,
+                                    **kw))
+        assert lt[1] < plain[1] / 10.0, (lt[1], plain[1])
+        assert lt[1] < lu[1] / 3.0, (lt[1], lu[1])
+        for other in (plain, lu):
+            assert abs(lt[0] - other[0]) <= 4.0 * math.hypot(lt[2], other[2]), (lt[0], other[0])
     finally:
-        prop.close()
+        trained.close()
+        untrained.close()
         sc.close()
 
 
