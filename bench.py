@@ -527,10 +527,11 @@ def _fom(rel, ms):
     return 1.0 / (rel * rel * ms / 1e3)
 
 
-# The learned proposal's configuration in the bench line: 8 learned vertices,
-# MIS share 0.25 for HG (the best of the alpha / vertex sweep of
-# --workload fom), network trained online on the image's own kind of path.
-FOM_ALPHA, FOM_NL = 0.25, 8
+# The learned proposal's configuration in the bench line: 2 learned vertices,
+# MIS share 0.75 for HG (the best figure of merit of the alpha / vertex sweep
+# of --workload fom at 256 spp), network trained online on the image's own
+# kind of path.
+FOM_ALPHA, FOM_NL = 0.75, 2
 FOM_TARGET = 0.01
 
 

@@ -457,7 +457,11 @@ MCRT_API int mcrt_tally_read_sums(const mcrt_tally* tally, double* s1, double* s
  * longest time in ns a warp ran in total, and when n >= 22, [13..21] SM
  * clock cycles summed over warps spent in the sections of the trace loop
  * (loop top, random block, path start, ray start, step, vertex, load,
- * after-load, ray/path end).  n >= 10. */
+ * after-load, ray/path end), and when n >= 30, [22..29] lane occupancy
+ * summed over warp iterations: iterations, lanes holding a path, lanes
+ * taking a traversal step, of those at a tentative collision, lanes running
+ * a batched rare phase (path start, ray start, vertex), lanes waiting for
+ * one, iterations that ran rare phases, lanes with no path.  n >= 10. */
 MCRT_API int mcrt_tally_counters(const mcrt_tally* tally, uint64_t* counters, size_t n);
 
 /* Device time of the trace kernel that filled the tally, in ms. */

@@ -50,7 +50,8 @@ MCRT_ORDER_RASTER = 1
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
                  "clk_top", "clk_philox", "clk_start", "clk_begin", "clk_step", "clk_vertex", "clk_load",
-                 "clk_after", "clk_end")
+                 "clk_after", "clk_end", "occ_iters", "occ_busy", "occ_step", "occ_tent", "occ_rare", "occ_wait",
+                 "occ_rare_iters", "occ_empty")
 
 
 class McrtError(RuntimeError):

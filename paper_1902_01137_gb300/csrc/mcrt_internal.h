@@ -119,7 +119,7 @@ struct mcrt_proposal {
 
 namespace mcrt {
 
-constexpr int kNumCounters = 24;
+constexpr int kNumCounters = 32;
 constexpr int kMlpParams = 11560;
 
 // Work distribution and status shared by all blocks of a trace launch.

@@ -62,6 +62,11 @@ enum { C_MAX_ITERS = 10, C_T_DRY = 11, C_T_END = 12 };
 // ray start, step, vertex, load, after-load, ray/path end.
 constexpr int C_SEC = 13;
 constexpr int kSections = 9;
+// ... and, per warp iteration, lane occupancy (slots 22..29): iterations,
+// lanes holding a path, stepping, at a tentative collision, running a rare
+// phase, waiting for one, iterations that ran rare phases, lanes without a path.
+constexpr int C_OCC = 22;
+constexpr int kOcc = 8;
 
 // Each lane is in one phase per iteration: it starts a path, starts a ray
 // (flight or sun ray), takes one traversal step, or handles the vertex that
@@ -90,9 +95,11 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     int phase = PH_IDLE;
     unsigned cell = 0;                      // tally cell of the chunk
     int px = 0, py = 0;                     // camera pixel of the chunk
-    double acc[2 * NQ];                     // chunk sums of x and x^2 (FP64; x^2 of an FP32 x is exact)
+    // chunk sums of x and x^2 in FP32 (a chunk is at most 8 paths: relative
+    // error below 7 * 2^-24 of the sum of |x| before the FP64 atomic add)
+    float acc[2 * NQ];
 #pragma unroll
-    for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
     Ray R;
     int kind = kMain;
     uint32_t c2 = 0, blk = 1, ev = 0;
@@ -113,6 +120,9 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     unsigned long long sec[kSections];
 #pragma unroll
     for (int q = 0; q < kSections; ++q) sec[q] = 0;
+    unsigned long long occ[kOcc];
+#pragma unroll
+    for (int q = 0; q < kOcc; ++q) occ[q] = 0;
     long long tclk = COUNT ? clock64() : 0;
     auto mark = [&](int q) {
         if (COUNT) {
@@ -142,7 +152,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             const bool mine = pending && cell == c;
 #pragma unroll
             for (int q = 0; q < 2 * NQ; ++q) {
-                double a = mine ? acc[q] : 0.0;
+                double a = mine ? (double)acc[q] : 0.0;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
                 if (lane == src) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)c * NQ + (q >> 1), a);
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             if (mine) {
                 pending = false;
 #pragma unroll
-                for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0;
+                for (int q = 0; q < 2 * NQ; ++q) acc[q] = 0.0f;
             }
             fmask = __ballot_sync(kFull, pending);
         }
@@ -239,7 +249,15 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
-        const int ph = (phase == PH_STEP || (rare && run_rare)) ? phase : PH_IDLE;
+        // of the rare kinds (ray start, vertex, the rest) only the one most
+        // lanes wait for runs in this iteration: the warp then executes one
+        // rare branch with more lanes instead of several with few
+        const int nb_ = __popc(__ballot_sync(kFull, phase == PH_BEGIN));
+        const int nv_ = __popc(__ballot_sync(kFull, phase == PH_VERTEX));
+        const int ns_ = __popc(rare_mask) - nb_ - nv_;
+        const int sel = (nb_ >= nv_ && nb_ >= ns_) ? PH_BEGIN : (nv_ >= ns_ ? PH_VERTEX : -1);
+        const bool mine = sel < 0 ? (phase != PH_BEGIN && phase != PH_VERTEX) : phase == sel;
+        const int ph = (phase == PH_STEP || (rare && run_rare && mine)) ? phase : PH_IDLE;
 
         // ---- the scene of the lane's chunk (one per batch item) ---------------
         const DevScene& S = BATCH ? P.items[item].S : P.S;
@@ -252,6 +270,13 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const float Mt = decomp ? R.M - R.mn : R.M;
         const float Mseg = Mt * seg;
         const bool tent = ph == PH_STEP && Mt > 0.0f && tau < Mseg;
+        if (COUNT) {
+            const unsigned busy = __ballot_sync(kFull, chunk), tm = __ballot_sync(kFull, tent);
+            const unsigned rr = __ballot_sync(kFull, rare && ph != PH_IDLE);
+            occ[0] += 1; occ[1] += __popc(busy); occ[2] += __popc(step_mask); occ[3] += __popc(tm);
+            occ[4] += __popc(rr); occ[5] += __popc(rare_mask) - __popc(rr); occ[6] += rr ? 1 : 0;
+            occ[7] += 32 - __popc(busy);
+        }
         uint32_t xc2 = c2, xblk = 0u;
         if (ph == PH_START) xc2 = 2u;
         else if (ph == PH_STEP) xblk = blk;
@@ -708,21 +733,20 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             if (evc == EV_ESCAPE) path_done = true;
             if (path_done) {
                 if constexpr (SENSOR == kCamera) {
-                    const double x = score;
-                    acc[0] += x;
-                    acc[1] += x * x;
+                    acc[0] += score;
+                    acc[1] += score * score;
                 } else {
                     const float pi_over_mu0 = __fdividef(kPi, TERRAIN ? fz * S.sun[2] : S.sun[2]);
-                    const double td = tdir, tf = pi_over_mu0 * score;
-                    const double tt = td + tf;
-                    acc[0] += td; acc[1] += td * td;
+                    const float tf = pi_over_mu0 * score;
+                    const float tt = tdir + tf;
+                    acc[0] += tdir; acc[1] += tdir * tdir;
                     acc[2] += tf; acc[3] += tf * tf;
                     acc[4] += tt; acc[5] += tt * tt;
                     if constexpr (BATCH) {
-                        const double dt = pi_over_mu0 * dscore;
+                        const float dt = pi_over_mu0 * dscore;
                         acc[6] += dt; acc[7] += dt * dt;
                         if (EXTRA) {
-                            const double da = pi_over_mu0 * dal;
+                            const float da = pi_over_mu0 * dal;
                             acc[8] += da; acc[9] += da * da;
                         }
                     }
@@ -792,7 +816,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
     if (chunk) {
 #pragma unroll
         for (int q = 0; q < 2 * NQ; ++q)
-            if (acc[q] != 0.0) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)cell * NQ + (q >> 1), acc[q]);
+            if (acc[q] != 0.0f) atomicAdd(((q & 1) ? P.s2 : P.s1) + (size_t)cell * NQ + (q >> 1), (double)acc[q]);
     }
     if (COUNT) {
 #pragma unroll
@@ -806,6 +830,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < kSections; ++q) atomicAdd(P.counters + C_SEC + q, sec[q]);
+#pragma unroll
+            for (int q = 0; q < kOcc; ++q) atomicAdd(P.counters + C_OCC + q, occ[q]);
             const uint64_t t_end = globaltimer_ns();
             atomicMax(P.counters + C_MAX_ITERS, (unsigned long long)mi);
             if (t_dry) atomicMax(P.counters + C_T_DRY, (unsigned long long)(t_dry - t_start));

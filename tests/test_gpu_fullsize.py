@@ -212,3 +212,40 @@ def test_largest_sweep_field(env, orc):
             sb.close()
         del spec
         torch.cuda.empty_cache()
+
+
+def test_lane_sums_stay_within_their_fp32_bound(env):
+    """Each lane sums the scores x and x^2 of its chunk (at most 8 paths) in
+    FP32 before one FP64 atomic add, so a pixel's sums may differ from exact
+    FP64 sums of the same FP32 path scores by at most (chunk - 1) 2^-24 of
+    themselves (all terms are >= 0).  Tracing the same paths with one path
+    per claim (every score reaches the FP64 sums alone) and with 8 per claim
+    checks that bound pixel by pixel on the bench field (cumulus
+    512x512x160, 64 x 64 nadir image at 64 spp: cloudy and clear pixels,
+    scores spread over orders of magnitude)."""
+    import bench
+    torch, m, ctx = env
+    spec, _ = bench.make_workload()
+    sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    cd = m.CameraDesc()
+    cam = scenes.nadir_camera(spec, 64, 64)
+    for i in range(3):
+        cd.pos[i], cd.target[i], cd.up[i] = cam.pos[i], cam.target[i], cam.up[i]
+    cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
+    try:
+        sums = {}
+        for chunk in (1, 8):
+            o = m.mcrt_trace_opts_default()
+            o.chunk = chunk
+            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, 64, 9, o)
+            try:
+                sums[chunk] = m.mcrt_tally_read_sums(ctx.h, t)
+            finally:
+                m.mcrt_tally_destroy(t)
+        for q in range(2):
+            exact, grouped = sums[1][q][:, 0], sums[8][q][:, 0]
+            assert exact.max() > 0.0
+            bound = 7 * 2.0 ** -24 * exact + 1e-15 * exact.max()
+            assert np.all(np.abs(grouped - exact) <= bound), float(np.max(np.abs(grouped - exact) / np.maximum(exact, 1e-300)))
+    finally:
+        sc.close()
