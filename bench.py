@@ -62,17 +62,17 @@ WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x
 W, H, SPP = CUMULUS.image.width, CUMULUS.image.height, CUMULUS.image.spp
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
-PROFILED_TRACE_SHA = "a962f2fa6c79b4d0"
-PROFILED_DRAM_BYTES_PER_PATH = 24.29
+PROFILED_TRACE_SHA = "d51f4b474eabd20e"
+PROFILED_DRAM_BYTES_PER_PATH = 24.01
 # issue-slot figures of the same capture (smsp__issue_active, threads per
 # warp instruction); the kernel is issue-bound, so these locate it against
 # its real ceiling: 152 SMs x 4 schedulers x 1 warp instruction per cycle
-PROFILED_ISSUE_ACTIVE = 0.7216
-PROFILED_THREADS_PER_INST = 13.09
-PROFILED_WARP_INST_PER_PATH = 7921.0
+PROFILED_ISSUE_ACTIVE = 0.7210
+PROFILED_THREADS_PER_INST = 14.79
+PROFILED_WARP_INST_PER_PATH = 7805.9
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
 # the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
-PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.26
+PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.32
 
 
 def trace_sources_sha() -> str:
