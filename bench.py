@@ -543,17 +543,34 @@ def _img_stats(r):
     return float(np.mean(rel * rel)), float(np.median(rel))
 
 
-def _run_to_target(trace, pilot_spp, seed):
-    """Trace a pilot image, size the run that brings the median pixel
-    relative SE to FOM_TARGET (10 % margin), trace it; the FOM is that run's
-    1 / (mean pixel relative variance x its time)."""
-    p = trace(pilot_spp, seed)
-    _, med = _img_stats(p)
-    spp = max(pilot_spp, int(math.ceil(pilot_spp * (med / FOM_TARGET) ** 2 * 1.1)))
-    r = trace(spp, seed + 1)
-    rv, med = _img_stats(r)
-    return {"spp": spp, "ms": r.kernel_ms, "rel_var": rv, "median_rel_se": med, "fom": 1.0 / (rv * r.kernel_ms / 1e3),
-            "paths": spp * r.mean.size, "mean": float(r.mean.mean())}
+def _sum_stats(s1, s2, n):
+    mean = s1 / n
+    var = np.maximum(s2 / n - mean * mean, 0.0) * n / max(n - 1, 1)
+    se = np.sqrt(var / n)
+    ok = mean > 1e-3 * mean.max()
+    rel = se[ok] / mean[ok]
+    return float(np.mean(rel * rel)), float(np.median(rel)), float(mean.mean())
+
+
+def _run_to_target(trace, pilot_spp, seed, max_rounds=8):
+    """Trace the image in segments (fresh seeds), adding their per-pixel FP64
+    sums, until the median pixel relative SE is at most FOM_TARGET: each
+    next segment is sized from the current median (10 % margin).  The FOM is
+    1 / (mean pixel relative variance x the time of all segments)."""
+    s1 = s2 = 0.0
+    n, ms, segs = 0, 0.0, []
+    spp = pilot_spp
+    rv = med = mean = float("nan")
+    for r in range(max_rounds):
+        a1, a2, t = trace(spp, seed + r)
+        s1, s2, n, ms = s1 + a1, s2 + a2, n + spp, ms + t
+        segs.append(spp)
+        rv, med, mean = _sum_stats(s1, s2, n)
+        if med <= FOM_TARGET:
+            break
+        spp = max(pilot_spp, int(math.ceil(n * (med / FOM_TARGET) ** 2 * 1.1)) - n)
+    return {"spp": n, "segments_spp": segs, "ms": ms, "rel_var": rv, "median_rel_se": med,
+            "fom": 1.0 / (rv * ms / 1e3), "paths": n * int(np.size(s1)), "mean": mean}
 
 
 def _flux_to_target(trace, seed):
@@ -590,6 +607,18 @@ def learned_fom(m, ctx, sweep=False):
                        "variance x time); learned: alpha %.2f, %d learned vertices" % (FOM_ALPHA, FOM_NL)}
     try:
         sc.trace_camera(cam, 16, seed=1)
+        cd = m.CameraDesc()
+        for i in range(3):
+            cd.pos[i], cd.target[i], cd.up[i] = cam.pos[i], cam.target[i], cam.up[i]
+        cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
+
+        def sums(spp, seed, **kw):
+            t = m.mcrt_trace_camera(ctx.h, sc.h, cd, spp, seed, m.Scene._opts(**kw))
+            try:
+                a1, a2 = m.mcrt_tally_read_sums(ctx.h, t)
+                return a1[:, 0], a2[:, 0], m.mcrt_tally_kernel_ms(ctx.h, t)
+            finally:
+                m.mcrt_tally_destroy(t)
 
         def plain(spp, seed):
             return sc.trace_camera(cam, spp, seed=seed)
@@ -620,14 +649,12 @@ def learned_fom(m, ctx, sweep=False):
                                                            "time_ratio": r.kernel_ms / base.kernel_ms,
                                                            "train_ms": tms}
             return out
-        pl = _run_to_target(plain, 256, 10)
+        pl = _run_to_target(lambda spp, seed: sums(spp, seed), 256, 10)
         out["plain_image"] = pl
         prop, tms = train(FOM_ALPHA, FOM_NL)
         try:
-            def learned(spp, seed):
-                return sc.trace_camera(cam, spp, seed=seed, proposal=prop, learn=0, n_learned=FOM_NL,
-                                       mis_alpha=FOM_ALPHA)
-            lf = _run_to_target(learned, 64, 20)
+            lf = _run_to_target(lambda spp, seed: sums(spp, seed, proposal=prop, learn=0, n_learned=FOM_NL,
+                                                      mis_alpha=FOM_ALPHA), 256, 20)
             lf["train_ms"] = tms
             out["learned_image"] = lf
             online = 1.0 / (lf["rel_var"] * (lf["ms"] + tms) / 1e3)
