@@ -291,14 +291,17 @@ constexpr uint32_t kTrOffH2 = kTrOffH1 + kSzH, kTrOffH3 = kTrOffH2 + kSzH;
 constexpr uint32_t kTrOffDO = kTrOffH3 + kSzH, kTrOffDZ = kTrOffDO + kRows * kCD * 2;
 constexpr uint32_t kTrainSmem = kTrOffDZ + kRows * kCD * 2;        // 116,736 bytes: one CTA per SM
 constexpr uint32_t kTrCols = 512;
+constexpr int kTrThreads = 256;    // two threads per row: warps w and w + 4 share TMEM lane quarter w
 
-// Forward epilogue of hidden layer l: bias + GELU to the operand rows (BF16),
-// GELU derivative to TMEM.
-__device__ __forceinline__ void train_hidden(uint32_t tl, uint32_t cgp, const float* __restrict__ bias, uint8_t* H,
-                                             int row)
+// Forward epilogue of hidden layer l over the thread's 32 columns
+// [c1, c1 + 32): bias + GELU to the operand rows (BF16), the GELU derivative
+// to TMEM.
+__device__ __forceinline__ void train_hidden(uint32_t tl, uint32_t cgp, int c1, const float* __restrict__ bias,
+                                             uint8_t* H, int row)
 {
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
+    for (int c = 0; c < 32; c += 16) {
+        const int c0 = c1 + c;
         uint32_t v[16];
         tmem_ld16(tl + cACC + c0, v);
         tmem_wait_ld(v);
@@ -319,11 +322,13 @@ __device__ __forceinline__ void train_hidden(uint32_t tl, uint32_t cgp, const fl
     tmem_wait_st();
 }
 
-// Backward epilogue: dZ = dA * GELU'(Z) to the operand rows (BF16).
-__device__ __forceinline__ void train_dz(uint32_t tl, uint32_t cgp, uint8_t* DZ, int row)
+// Backward epilogue over the thread's 32 columns: dZ = dA * GELU'(Z) to the
+// operand rows (BF16).
+__device__ __forceinline__ void train_dz(uint32_t tl, uint32_t cgp, int c1, uint8_t* DZ, int row)
 {
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
+    for (int c = 0; c < 32; c += 16) {
+        const int c0 = c1 + c;
         uint32_t a[16], g[16];
         tmem_ld16(tl + cACC + c0, a);
         tmem_wait_ld(a);
@@ -339,14 +344,89 @@ __device__ __forceinline__ void train_dz(uint32_t tl, uint32_t cgp, uint8_t* DZ,
     }
 }
 
-// Add one M = 64 gradient block (rows 16w + lane of warp w's lanes 0..15)
-// to the global gradient: W[m][c] for c < ncols at wofs + m * ncols, and the
-// bias (column bcol) at bofs + m, for rows m < nrows.
-__device__ __forceinline__ void flush_block(uint32_t tl, uint32_t col, int nload, int ncols, int bcol, int nrows,
-                                            int wofs, int bofs, float* __restrict__ grad, int warp, int lane)
+// Gradient of -t log q_vMF(w) with respect to the 20 raw outputs of lobes
+// 4h .. 4h + 3 of one row (the row's other lobes are the other thread's):
+// the softmax maximum and sum and the mixture density are combined through
+// shared memory (xch[step][half][row]; every thread of the CTA passes the
+// same two barriers); the 20 gradients go to the output-gradient rows as
+// BF16.  Returns this half's loss term (the first half carries it).
+__device__ __forceinline__ float train_loss_half(uint32_t tl, const float* __restrict__ sB, float (*xch)[2][kRows],
+                                                 int row, int h, const float w[3], float t, uint8_t* DO)
 {
-    const int m = 16 * warp + lane;
-    for (int c0 = 0; c0 < nload; c0 += 16) {
+    const int C0 = 20 * h;
+    float raw[20];
+    {
+        float r48[48];
+#pragma unroll
+        for (int c0 = 0; c0 < 48; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tl + cACC + c0, v);
+            tmem_wait_ld(v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) r48[c0 + j] = __uint_as_float(v[j]);
+        }
+#pragma unroll
+        for (int c = 0; c < 20; ++c) raw[c] = (h ? r48[20 + c] : r48[c]) + sB[192 + C0 + c];
+    }
+    float mx = -3.0e38f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mx = fmaxf(mx, raw[5 * j + 4]);
+    xch[0][h][row] = mx;
+    __syncthreads();
+    mx = fmaxf(xch[0][0][row], xch[0][1][row]);
+    float pi[4], s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { pi[j] = __expf(raw[5 * j + 4] - mx); s += pi[j]; }
+    float mu[4][3], kap[4], nrm[4], cc[4], f[4];
+    float q = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float x = raw[5 * j], y = raw[5 * j + 1], z = raw[5 * j + 2];
+        nrm[j] = sqrtf(x * x + y * y + z * z);
+        const float in = nrm[j] < 1e-12f ? 0.0f : 1.0f / nrm[j];
+        mu[j][0] = x * in; mu[j][1] = y * in; mu[j][2] = nrm[j] < 1e-12f ? 1.0f : z * in;
+        const float r3 = raw[5 * j + 3];
+        kap[j] = (r3 > 20.0f ? r3 : log1pf(__expf(r3))) + 1e-3f;
+        cc[j] = mu[j][0] * w[0] + mu[j][1] * w[1] + mu[j][2] * w[2];
+        f[j] = kap[j] / (2.0f * kPi * (-expm1f(-2.0f * kap[j]))) * __expf(kap[j] * (cc[j] - 1.0f));
+        q += pi[j] * f[j];                      // weights not yet normalised
+    }
+    xch[1][h][row] = s;
+    xch[2][h][row] = q;
+    __syncthreads();
+    const float inv_s = 1.0f / (xch[1][0][row] + xch[1][1][row]);
+    const float qs = fmaxf((xch[2][0][row] + xch[2][1][row]) * inv_s, 1e-30f);
+    float d[20];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pi[j] *= inv_s;
+        const float resp = pi[j] * f[j] / qs;
+        const float k = kap[j];
+        const float sc = nrm[j] < 1e-12f ? 0.0f : -t * resp * k / nrm[j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[5 * j + a] = sc * (w[a] - cc[j] * mu[j][a]);
+        const float e2 = __expf(-2.0f * k);
+        const float dk = 1.0f / k - 2.0f * e2 / (-expm1f(-2.0f * k)) + (cc[j] - 1.0f);
+        const float sig = 1.0f / (1.0f + __expf(-raw[5 * j + 3]));
+        d[5 * j + 3] = -t * resp * dk * sig;
+        d[5 * j + 4] = -t * (resp - pi[j]);
+    }
+#pragma unroll
+    for (int c = 0; c < 20; ++c)
+        *reinterpret_cast<__nv_bfloat16*>(DO + core_off(row, C0 + c, kCD)) = __float2bfloat16_rn(d[c]);
+    return (h == 0 && t != 0.0f) ? -t * __logf(qs) : 0.0f;
+}
+
+// Add one M = 64 gradient block (rows 16q + lane of lane quarter q's lanes
+// 0..15) to the global gradient: W[m][c] for c < ncols at wofs + m * ncols,
+// and the bias (column bcol) at bofs + m, for rows m < nrows; the thread
+// loads the 16-column chunks [cfrom, cto).
+__device__ __forceinline__ void flush_block(uint32_t tl, uint32_t col, int cfrom, int cto, int ncols, int bcol,
+                                            int nrows, int wofs, int bofs, float* __restrict__ grad, int quarter,
+                                            int lane)
+{
+    const int m = 16 * quarter + lane;
+    for (int c0 = cfrom; c0 < cto; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tl + col + c0, v);
         tmem_wait_ld(v);
@@ -362,36 +442,43 @@ __device__ __forceinline__ void flush_block(uint32_t tl, uint32_t col, int nload
     }
 }
 
-__global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat16* __restrict__ wpacked,
-                                                              const float* __restrict__ bpacked,
-                                                              const __nv_bfloat16* __restrict__ feat,
-                                                              const float* __restrict__ dirs,
-                                                              const float* __restrict__ tgt, int n, float scale,
-                                                              float* __restrict__ grad, float* __restrict__ loss_out)
+__global__ void __launch_bounds__(kTrThreads, 1) mlp_train_tc5_kernel(const __nv_bfloat16* __restrict__ wpacked,
+                                                                     const float* __restrict__ bpacked,
+                                                                     const __nv_bfloat16* __restrict__ feat,
+                                                                     const float* __restrict__ dirs,
+                                                                     const float* __restrict__ tgt, int n, float scale,
+                                                                     float* __restrict__ grad,
+                                                                     float* __restrict__ loss_out)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ float sB[kPackedBias];
+    __shared__ float xch[3][2][kRows];
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
     __shared__ float sloss;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    stage_weights(sm, wpacked, tid, 128);
-    for (int i = tid; i < kPackedBias; i += 128) sB[i] = bpacked[i];
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = 32 * quarter + lane;           // this thread's row (= TMEM lane)
+    const int c1 = 32 * half;                      // its 32 columns of a 64-column block
+    stage_weights(sm, wpacked, tid, kTrThreads);
+    for (int i = tid; i < kPackedBias; i += kTrThreads) sB[i] = bpacked[i];
     // constant columns: a one after each hidden layer's 64 outputs (bias
-    // gradients), zeros in the output-gradient columns 48..63
-    {
+    // gradients); zeros in the output-gradient columns 40..63
+    if (half == 0) {
         const uint32_t one = 0x3F80u;                              // BF16 1.0
-        st16(sm + kTrOffH1, core_off(tid, 64, kCH), one, 0u, 0u, 0u);
-        st16(sm + kTrOffH2, core_off(tid, 64, kCH), one, 0u, 0u, 0u);
-        st16(sm + kTrOffH3, core_off(tid, 64, kCH), one, 0u, 0u, 0u);
-        st16(sm + kTrOffDO, core_off(tid, 48, kCD), 0u, 0u, 0u, 0u);
-        st16(sm + kTrOffDO, core_off(tid, 56, kCD), 0u, 0u, 0u, 0u);
+        st16(sm + kTrOffH1, core_off(row, 64, kCH), one, 0u, 0u, 0u);
+        st16(sm + kTrOffH2, core_off(row, 64, kCH), one, 0u, 0u, 0u);
+        st16(sm + kTrOffH3, core_off(row, 64, kCH), one, 0u, 0u, 0u);
+    } else {
+        st16(sm + kTrOffDO, core_off(row, 40, kCD), 0u, 0u, 0u, 0u);
+        st16(sm + kTrOffDO, core_off(row, 48, kCD), 0u, 0u, 0u, 0u);
+        st16(sm + kTrOffDO, core_off(row, 56, kCD), 0u, 0u, 0u, 0u);
     }
     if (tid == 0) { sloss = 0.0f; mbar_init(&bar, 1); fence_mbar_init(); }
     if (warp == 0) { tmem_alloc(&tbase, kTrCols); tmem_relinquish(); }
     to_mma();
     const uint32_t T = tbase;
-    const uint32_t tl = T + ((uint32_t)(32 * warp) << 16);       // this warp's lane quarter
+    const uint32_t tl = T + ((uint32_t)(32 * quarter) << 16);    // this warp's lane quarter
     const uint32_t aW1 = smem_addr(sm + kOffSW1), aW2 = smem_addr(sm + kOffSW2), aW3 = smem_addr(sm + kOffSW3);
     const uint32_t aW4 = smem_addr(sm + kOffSW4), aX = smem_addr(sm + kOffSX);
     const uint32_t aH1 = smem_addr(sm + kTrOffH1), aH2 = smem_addr(sm + kTrOffH2), aH3 = smem_addr(sm + kTrOffH3);
@@ -406,21 +493,18 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
     float lsum = 0.0f;
     const int tiles = (n + kRows - 1) / kRows;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int row = tile * kRows + tid;
-        uint4 f0 = make_uint4(0u, 0u, 0u, 0u), f1 = f0;
+        const int r = tile * kRows + row;
+        uint4 fq = make_uint4(0u, 0u, 0u, 0u);
         float w[3] = {0.0f, 0.0f, 1.0f}, t = 0.0f;
-        if (row < n) {
-            const uint4* fp = reinterpret_cast<const uint4*>(feat + (size_t)row * 16);
-            f0 = __ldg(fp);
-            f1 = __ldg(fp + 1);
-            f1.x = (f1.x & 0xFFFFu) | (0x3F80u << 16);              // feature 9 := 1 (bias of layer 1)
-            w[0] = __ldg(dirs + 3 * (size_t)row);
-            w[1] = __ldg(dirs + 3 * (size_t)row + 1);
-            w[2] = __ldg(dirs + 3 * (size_t)row + 2);
-            t = __ldg(tgt + row) * scale;
+        if (r < n) {
+            fq = __ldg(reinterpret_cast<const uint4*>(feat + (size_t)r * 16) + half);
+            if (half) fq.x = (fq.x & 0xFFFFu) | (0x3F80u << 16);      // feature 9 := 1 (bias of layer 1)
+            w[0] = __ldg(dirs + 3 * (size_t)r);
+            w[1] = __ldg(dirs + 3 * (size_t)r + 1);
+            w[2] = __ldg(dirs + 3 * (size_t)r + 2);
+            t = __ldg(tgt + r) * scale;
         }
-        *reinterpret_cast<uint4*>(sm + kOffSX + core_off(tid, 0, kCX)) = f0;
-        *reinterpret_cast<uint4*>(sm + kOffSX + core_off(tid, 8, kCX)) = f1;
+        *reinterpret_cast<uint4*>(sm + kOffSX + core_off(row, 8 * half, kCX)) = fq;
         // ---- forward
         to_mma();
         if (tid == 0) {
@@ -428,7 +512,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
             mma_commit(&bar);
         }
         if (!(ok = from_mma(&bar, phase))) break;
-        train_hidden(tl, cGP1, sB, sm + kTrOffH1, tid);
+        train_hidden(tl, cGP1, c1, sB, sm + kTrOffH1, row);
         for (int L = 0; L < 2 && ok; ++L) {
             const uint32_t aIn = L == 0 ? aH1 : aH2, aWl = L == 0 ? aW2 : aW3;
             to_mma();
@@ -440,7 +524,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
                 mma_commit(&bar);
             }
             if (!(ok = from_mma(&bar, phase))) break;
-            train_hidden(tl, L == 0 ? cGP2 : cGP3, sB + 64 * (L + 1), sm + (L == 0 ? kTrOffH2 : kTrOffH3), tid);
+            train_hidden(tl, L == 0 ? cGP2 : cGP3, c1, sB + 64 * (L + 1), sm + (L == 0 ? kTrOffH2 : kTrOffH3), row);
         }
         if (!ok) break;
         to_mma();
@@ -452,62 +536,8 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
             mma_commit(&bar);
         }
         if (!(ok = from_mma(&bar, phase))) break;
-        // ---- d(-t log q_vMF)/d outputs, FP32, one row per thread
-        {
-            float raw[48];
-#pragma unroll
-            for (int c0 = 0; c0 < 48; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tl + cACC + c0, v);
-                tmem_wait_ld(v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) raw[c0 + j] = __uint_as_float(v[j]) + sB[192 + c0 + j];
-            }
-            float mx = -3.0e38f;
-#pragma unroll
-            for (int j = 0; j < kLobes; ++j) mx = fmaxf(mx, raw[5 * j + 4]);
-            float pi[kLobes], f[kLobes], s = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kLobes; ++j) { pi[j] = __expf(raw[5 * j + 4] - mx); s += pi[j]; }
-            const float inv_s = 1.0f / s;
-            float q = 0.0f;
-            float mu[kLobes][3], kap[kLobes], nrm[kLobes], cc[kLobes];
-#pragma unroll
-            for (int j = 0; j < kLobes; ++j) {
-                pi[j] *= inv_s;
-                const float x = raw[5 * j], y = raw[5 * j + 1], z = raw[5 * j + 2];
-                nrm[j] = sqrtf(x * x + y * y + z * z);
-                const float in = nrm[j] < 1e-12f ? 0.0f : 1.0f / nrm[j];
-                mu[j][0] = x * in; mu[j][1] = y * in; mu[j][2] = nrm[j] < 1e-12f ? 1.0f : z * in;
-                const float r3 = raw[5 * j + 3];
-                kap[j] = (r3 > 20.0f ? r3 : log1pf(__expf(r3))) + 1e-3f;
-                cc[j] = mu[j][0] * w[0] + mu[j][1] * w[1] + mu[j][2] * w[2];
-                f[j] = kap[j] / (2.0f * kPi * (-expm1f(-2.0f * kap[j]))) * __expf(kap[j] * (cc[j] - 1.0f));
-                q += pi[j] * f[j];
-            }
-            const float qs = fmaxf(q, 1e-30f);
-            if (t != 0.0f) lsum -= t * __logf(qs);
-            float d[48];
-#pragma unroll
-            for (int j = 0; j < kLobes; ++j) {
-                const float resp = pi[j] * f[j] / qs;
-                const float k = kap[j];
-                const float sc = nrm[j] < 1e-12f ? 0.0f : -t * resp * k / nrm[j];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) d[5 * j + a] = sc * (w[a] - cc[j] * mu[j][a]);
-                const float e2 = __expf(-2.0f * k);
-                const float dk = 1.0f / k - 2.0f * e2 / (-expm1f(-2.0f * k)) + (cc[j] - 1.0f);
-                const float sig = 1.0f / (1.0f + __expf(-raw[5 * j + 3]));
-                d[5 * j + 3] = -t * resp * dk * sig;
-                d[5 * j + 4] = -t * (resp - pi[j]);
-            }
-#pragma unroll
-            for (int c = kOut; c < 48; ++c) d[c] = 0.0f;
-#pragma unroll
-            for (int c0 = 0; c0 < 48; c0 += 8)
-                st16(sm + kTrOffDO, core_off(tid, c0, kCD), pack2(d[c0], d[c0 + 1]), pack2(d[c0 + 2], d[c0 + 3]),
-                     pack2(d[c0 + 4], d[c0 + 5]), pack2(d[c0 + 6], d[c0 + 7]));
-        }
+        // ---- d(-t log q_vMF)/d outputs, FP32, half the lobes of a row per thread
+        lsum += train_loss_half(tl, sB, xch, row, half, w, t, sm + kTrOffDO);
         // ---- backward, layer 4: dW4 += dO^T [H3 1]; dA3 = dO W4 (K = 48)
         to_mma();
         if (tid == 0) {
@@ -522,7 +552,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
             mma_commit(&bar);
         }
         if (!(ok = from_mma(&bar, phase))) break;
-        train_dz(tl, cGP3, sm + kTrOffDZ, tid);
+        train_dz(tl, cGP3, c1, sm + kTrOffDZ, row);
         // ---- layers 3 and 2: dW_l += dZ^T [A_{l-1} 1]; dA_{l-1} = dZ W_l
         for (int L = 0; L < 2 && ok; ++L) {
             const uint32_t aIn = L == 0 ? aH2 : aH1, aWl = L == 0 ? aW3 : aW2, cG = L == 0 ? cG3 : cG2;
@@ -539,7 +569,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
                 mma_commit(&bar);
             }
             if (!(ok = from_mma(&bar, phase))) break;
-            train_dz(tl, L == 0 ? cGP2 : cGP1, sm + kTrOffDZ, tid);
+            train_dz(tl, L == 0 ? cGP2 : cGP1, c1, sm + kTrOffDZ, row);
         }
         if (!ok) break;
         // ---- layer 1: dW1 += dZ1^T [X 1] (features 0..8, the one at 9)
@@ -554,15 +584,16 @@ __global__ void __launch_bounds__(128, 1) mlp_train_tc5_kernel(const __nv_bfloat
         if (!(ok = from_mma(&bar, phase))) break;   // the next tile overwrites X, H, dO and dZ
         acc_g = 1u;
     }
-    // ---- loss and gradient blocks to global memory
+    // ---- loss and gradient blocks to global memory (the two threads of a
+    // lane split the column chunks of each block)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0) atomicAdd(&sloss, lsum);
     if (ok && acc_g) {
-        flush_block(tl, cG1, 16, kIn, 9, 64, kOffW1, kOffB1, grad, warp, lane);
-        flush_block(tl, cG2, 80, kH, 64, 64, kOffW2, kOffB2, grad, warp, lane);
-        flush_block(tl, cG3, 80, kH, 64, 64, kOffW3, kOffB3, grad, warp, lane);
-        flush_block(tl, cG4, 80, kH, 64, kOut, kOffW4, kOffB4, grad, warp, lane);
+        if (half == 0) flush_block(tl, cG1, 0, 16, kIn, 9, 64, kOffW1, kOffB1, grad, quarter, lane);
+        flush_block(tl, cG2, half ? 48 : 0, half ? 80 : 48, kH, 64, 64, kOffW2, kOffB2, grad, quarter, lane);
+        flush_block(tl, cG3, half ? 48 : 0, half ? 80 : 48, kH, 64, 64, kOffW3, kOffB3, grad, quarter, lane);
+        flush_block(tl, cG4, half ? 48 : 0, half ? 80 : 48, kH, 64, kOut, kOffW4, kOffB4, grad, quarter, lane);
     }
     if (!ok && tid == 0) atomicExch(&g_tc5_error, 1);
     fence_before_sync();
@@ -601,7 +632,7 @@ cudaError_t launch_mlp_train_tc(const void* wpacked, const float* bpacked, const
     if (e != cudaSuccess) return e;
     const int tiles = (n + kRows - 1) / kRows;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    mlp_train_tc5_kernel<<<grid, 128, kTrainSmem, st>>>(static_cast<const __nv_bfloat16*>(wpacked), bpacked,
+    mlp_train_tc5_kernel<<<grid, kTrThreads, kTrainSmem, st>>>(static_cast<const __nv_bfloat16*>(wpacked), bpacked,
                                                          static_cast<const __nv_bfloat16*>(feat), dirs, tgt, n, scale,
                                                          grad, loss);
     return cudaGetLastError();
