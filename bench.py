@@ -62,17 +62,19 @@ WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x
 W, H, SPP = CUMULUS.image.width, CUMULUS.image.height, CUMULUS.image.spp
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
-PROFILED_TRACE_SHA = "d51f4b474eabd20e"
-PROFILED_DRAM_BYTES_PER_PATH = 24.01
-# issue-slot figures of the same capture (smsp__issue_active, threads per
-# warp instruction); the kernel is issue-bound, so these locate it against
-# its real ceiling: 152 SMs x 4 schedulers x 1 warp instruction per cycle
-PROFILED_ISSUE_ACTIVE = 0.7210
-PROFILED_THREADS_PER_INST = 14.79
-PROFILED_WARP_INST_PER_PATH = 7805.9
-PROFILED_SOURCE = "profiles/trace_kernel_cumulus_512px16spp_ncu_full.md"
+PROFILED_TRACE_SHA = "179067b3dd62c720"
+PROFILED_DRAM_BYTES_PER_PATH = 24.06
+# issue figures: warp instructions per path and threads per warp instruction
+# from a one-pass count of a bench launch (1024^2 x 64 spp), the small
+# capture's issue-active fraction; the kernel is issue-bound, so these
+# locate it against its real ceiling: 152 SMs x 4 schedulers x 1 warp
+# instruction per cycle
+PROFILED_ISSUE_ACTIVE = 0.7252
+PROFILED_THREADS_PER_INST = 15.87
+PROFILED_WARP_INST_PER_PATH = 5895.9
+PROFILED_SOURCE = "profiles/trace_kernel_cumulus_1024px64spp_launches.md"
 # the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
-PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.32
+PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 43.46
 
 
 def trace_sources_sha() -> str:
@@ -495,7 +497,7 @@ def run_gpu(args):
         cpu = {"value": v, "unit": "paths/s", "cores": cores, "kind": "oracle", "sample": desc}
 
     fom = None
-    if rank == 0 and not args.no_fom:
+    if world == 1 and not args.no_fom:         # the learned proposal's FOM: one GPU (minutes of tracing)
         fom = learned_fom(m, ctx)
     events = cnt["tentative"] + cnt["sun_tentative"]
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,

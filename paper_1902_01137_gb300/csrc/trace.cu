@@ -441,9 +441,14 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 phase = PH_VERTEX;
             } else if (tent) {
                 R.t = tn;
-                const size_t idx = brick_index(S, nv[0], nv[1], nv[2]);
-                if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
-                else { ptr = reinterpret_cast<const uint2*>(S.vox) + (idx >> 1); sub = (uint32_t)idx & 1u; }
+                // a voxel leaf's majorant is the voxel itself: its tentative
+                // collision needs no load (k = M, so it is real; a sun ray's
+                // ratio 1 - k/M is 0)
+                if (R.lev != 0) {
+                    const size_t idx = brick_index(S, nv[0], nv[1], nv[2]);
+                    if (BF16) { ptr = reinterpret_cast<const uint2*>(S.vox16) + (idx >> 2); sub = (uint32_t)idx & 3u; }
+                    else { ptr = reinterpret_cast<const uint2*>(S.vox) + (idx >> 1); sub = (uint32_t)idx & 1u; }
+                }
             } else {
                 tau -= Mseg;
                 float wdt;
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             } else {
                 kv = __uint_as_float(sub ? val.y : val.x);
             }
-            const float k = __fadd_rn(kv, S.k_gas);
+            const float k = R.lev == 0 ? R.M : __fadd_rn(kv, S.k_gas);
             ++blk;
             const float u0 = u01(x.x);
             const float nt = -__logf(u01(x.y));
