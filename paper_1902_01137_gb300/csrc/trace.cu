@@ -35,7 +35,7 @@
 #include "mcrt_internal.h"
 
 #ifndef MCRT_TRACE_MIN_BLOCKS
-#define MCRT_TRACE_MIN_BLOCKS 8   // resident blocks of 128 threads the register budget must allow
+#define MCRT_TRACE_MIN_BLOCKS 7   // resident blocks of 128 threads the register budget must allow (72 registers)
 #endif
 
 namespace mcrt {
