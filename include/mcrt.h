@@ -366,7 +366,9 @@ MCRT_API int mcrt_trace_flux(mcrt_scene* scene, uint64_t npaths, uint64_t seed, 
  *    cost order needs work buffers); results are the same either way.
  *  - The scene's majorants must be built.  Synchronises the context stream;
  *    errors as mcrt_trace_camera plus MCRT_ERR_BOUNDS, and
- *    MCRT_ERR_UNSUPPORTED for a learned proposal (it needs work buffers). */
+ *    MCRT_ERR_UNSUPPORTED for a learned proposal or a shard (they need work
+ *    buffers).  After MCRT_ERR_TIMEOUT or MCRT_ERR_CANCELLED both output
+ *    buffers hold NaN (the partial sums estimate nothing). */
 MCRT_API int mcrt_trace_camera_noalloc(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
                                        const mcrt_trace_opts* opts, double* d_mean, double* d_stderr);
 

@@ -173,6 +173,7 @@ __device__ __forceinline__ void mixture_out(const float* r, float* __restrict__ 
 constexpr uint32_t kInfOffHa = kOffSX + kSzX, kInfOffHb = kInfOffHa + kRows * 64 * 2;
 constexpr uint32_t kInfSmem = kInfOffHb + kRows * 64 * 2;          // 61,440 bytes
 constexpr uint32_t kInfCols = 64;
+static_assert(kRows * (48 + 1) * 4 <= kInfSmem - kInfOffHa, "output staging fits in the two activation buffers");
 
 // One forward epilogue: bias + GELU of the 64 accumulator columns, BF16 to
 // the next layer's operand rows.
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(128) mlp_infer_tc5_kernel(const __nv_bfloat16*
     __shared__ float sB[kPackedBias];
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     stage_weights(sm, wpacked, tid, 128);
     for (int i = tid; i < kPackedBias; i += 128) sB[i] = bpacked[i];
     if (tid == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
@@ -268,11 +269,21 @@ __global__ void __launch_bounds__(128) mlp_infer_tc5_kernel(const __nv_bfloat16*
 #pragma unroll
             for (int j = 0; j < 16; ++j) r[c0 + j] = __uint_as_float(v[j]) + sB[192 + c0 + j];
         }
+        // the rows' mixtures go through shared memory (the activation
+        // buffers are free once layer 4 has run; stride W + 1 words: no bank
+        // conflicts) and out with a warp per row, so the stores coalesce
+        const int W = tracer_layout ? kTracerMix : kOut;
+        float* stage = reinterpret_cast<float*>(sm + kInfOffHa);
         if (row < n) {
             if (raw_out)
                 for (int i = 0; i < kOut; ++i) raw_out[(size_t)row * kOut + i] = r[i];
-            mixture_out(r, mix + (size_t)row * (tracer_layout ? kTracerMix : kOut), tracer_layout != 0);
+            mixture_out(r, stage + tid * (W + 1), tracer_layout != 0);
         }
+        __syncthreads();
+        const int nrows = min(kRows, n - tile * kRows);
+        for (int rr = warp; rr < nrows; rr += 4)
+            for (int c = lane; c < W; c += 32)
+                mix[(size_t)(tile * kRows + rr) * W + c] = stage[rr * (W + 1) + c];
     }
     if (!ok && tid == 0) atomicExch(&g_tc5_error, 1);
     fence_before_sync();

@@ -92,6 +92,30 @@ def test_mlp_inference_vs_oracle(env, orc):
         prop.close()
 
 
+@pytest.mark.parametrize("n", [1, 127, 129, 4097])
+def test_mlp_inference_tile_edges(env, orc, n):
+    """Row counts around the 128-row tile: every row's raw outputs equal the
+    same rows evaluated in a larger batch bit for bit (a row's result does
+    not depend on its tile neighbours), and the mixture of each row matches
+    the oracle's mixture of its raw outputs."""
+    m, ctx = env
+    p = _params(orc, 9)
+    prop = m.Proposal(ctx, params=p)
+    try:
+        x = _features(5000, 10)
+        mix_all, raw_all = prop.eval(x)
+        mix, raw = prop.eval(x[:n])
+        np.testing.assert_array_equal(raw, raw_all[:n])
+        np.testing.assert_array_equal(mix, mix_all[:n])
+        for i in sorted({0, n // 2, n - 1}):
+            mu, ka, pi = orc.mixture(raw[i].astype(np.float64))
+            got = mix[i].reshape(8, 5)
+            np.testing.assert_allclose(got[:, :3], mu, rtol=1e-5, atol=1e-6)
+            np.testing.assert_allclose(got[:, 4], pi, rtol=1e-4, atol=1e-7)
+    finally:
+        prop.close()
+
+
 def test_mlp_gradient_and_adam_vs_oracle(env, orc):
     m, ctx = env
     p = _params(orc, 5)

@@ -492,9 +492,7 @@ def test_shards_add_up_to_the_whole_trace(m, ctx, small):
     cd.fov_deg, cd.width, cd.height = cam.fov_deg, cam.width, cam.height
 
     def sums(fn, **kw):
-        o = m.mcrt_trace_opts_default()
-        for k, v in kw.items():
-            setattr(o, k, v)
+        o = m.Scene._opts(**kw)
         t = fn(o)
         try:
             return m.mcrt_tally_read_sums(ctx.h, t)
@@ -520,3 +518,22 @@ def test_shards_add_up_to_the_whole_trace(m, ctx, small):
     with pytest.raises(m.McrtError) as e:
         sums(flux_fn, shard_index=4, shard_count=4)
     assert e.value.status == m.MCRT_ERR_ARG
+    # more shards than pixels: the surplus shards trace nothing
+    tiny = scenes.nadir_camera(sp, 3, 2)
+    td = m.CameraDesc()
+    for i in range(3):
+        td.pos[i], td.target[i], td.up[i] = tiny.pos[i], tiny.target[i], tiny.up[i]
+    td.fov_deg, td.width, td.height = tiny.fov_deg, tiny.width, tiny.height
+    tiny_fn = lambda o: m.mcrt_trace_camera(ctx.h, sc.h, td, 16, 7, o)
+    t1, t2 = sums(tiny_fn)
+    parts = [sums(tiny_fn, shard_index=r, shard_count=9) for r in range(9)]
+    assert all(not p[0].any() for p in parts[6:])
+    np.testing.assert_allclose(sum(p[0] for p in parts), t1, rtol=1e-12, atol=0)
+    # shards are for plain traces: not with a proposal or in batches
+    prop = m.Proposal(ctx, seed=1)
+    try:
+        with pytest.raises(m.McrtError) as e:
+            sums(flux_fn, shard_index=0, shard_count=2, proposal=prop.h)
+        assert e.value.status == m.MCRT_ERR_UNSUPPORTED
+    finally:
+        prop.close()
