@@ -305,54 +305,46 @@ constexpr uint32_t kTrCols = 512;
 constexpr int kTrThreads = 256;    // two threads per row: warps w and w + 4 share TMEM lane quarter w
 
 // Forward epilogue of hidden layer l over the thread's 32 columns
-// [c1, c1 + 32): bias + GELU to the operand rows (BF16), the GELU derivative
-// to TMEM.
+// [c1, c1 + 32) (one TMEM load, one wait): bias + GELU to the operand rows
+// (BF16), the GELU derivative to TMEM.
 __device__ __forceinline__ void train_hidden(uint32_t tl, uint32_t cgp, int c1, const float* __restrict__ bias,
                                              uint8_t* H, int row)
 {
+    uint32_t v[32];
+    tmem_ld32(tl + cACC + c1, v);
+    tmem_wait_ld32(v);
+    uint32_t p[16], g[32];
 #pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-        const int c0 = c1 + c;
-        uint32_t v[16];
-        tmem_ld16(tl + cACC + c0, v);
-        tmem_wait_ld(v);
-        uint32_t p[8], g[16];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            float h0, h1, g0, g1;
-            gelu2(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], h0, g0);
-            gelu2(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], h1, g1);
-            p[j] = pack2(h0, h1);
-            g[2 * j] = __float_as_uint(g0);
-            g[2 * j + 1] = __float_as_uint(g1);
-        }
-        st16(H, core_off(row, c0, kCH), p[0], p[1], p[2], p[3]);
-        st16(H, core_off(row, c0 + 8, kCH), p[4], p[5], p[6], p[7]);
-        tmem_st16(tl + cgp + c0, g);
+    for (int j = 0; j < 16; ++j) {
+        float h0, h1, g0, g1;
+        gelu2(__uint_as_float(v[2 * j]) + bias[c1 + 2 * j], h0, g0);
+        gelu2(__uint_as_float(v[2 * j + 1]) + bias[c1 + 2 * j + 1], h1, g1);
+        p[j] = pack2(h0, h1);
+        g[2 * j] = __float_as_uint(g0);
+        g[2 * j + 1] = __float_as_uint(g1);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st16(H, core_off(row, c1 + 8 * q, kCH), p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    tmem_st32(tl + cgp + c1, g);
     tmem_wait_st();
 }
 
-// Backward epilogue over the thread's 32 columns: dZ = dA * GELU'(Z) to the
-// operand rows (BF16).
+// Backward epilogue over the thread's 32 columns (the two TMEM loads in
+// flight together): dZ = dA * GELU'(Z) to the operand rows (BF16).
 __device__ __forceinline__ void train_dz(uint32_t tl, uint32_t cgp, int c1, uint8_t* DZ, int row)
 {
+    uint32_t a[32], g[32];
+    tmem_ld32(tl + cACC + c1, a);
+    tmem_ld32(tl + cgp + c1, g);
+    tmem_wait_ld32(a);
+    tmem_after_wait32(g);
+    uint32_t p[16];
 #pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-        const int c0 = c1 + c;
-        uint32_t a[16], g[16];
-        tmem_ld16(tl + cACC + c0, a);
-        tmem_wait_ld(a);
-        tmem_ld16(tl + cgp + c0, g);
-        tmem_wait_ld(g);
-        uint32_t p[8];
+    for (int j = 0; j < 16; ++j)
+        p[j] = pack2(__uint_as_float(a[2 * j]) * __uint_as_float(g[2 * j]),
+                     __uint_as_float(a[2 * j + 1]) * __uint_as_float(g[2 * j + 1]));
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            p[j] = pack2(__uint_as_float(a[2 * j]) * __uint_as_float(g[2 * j]),
-                         __uint_as_float(a[2 * j + 1]) * __uint_as_float(g[2 * j + 1]));
-        st16(DZ, core_off(row, c0, kCD), p[0], p[1], p[2], p[3]);
-        st16(DZ, core_off(row, c0 + 8, kCD), p[4], p[5], p[6], p[7]);
-    }
+    for (int q = 0; q < 4; ++q) st16(DZ, core_off(row, c1 + 8 * q, kCD), p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
 }
 
 // Gradient of -t log q_vMF(w) with respect to the 20 raw outputs of lobes
@@ -423,8 +415,8 @@ __device__ __forceinline__ float train_loss_half(uint32_t tl, const float* __res
         d[5 * j + 4] = -t * (resp - pi[j]);
     }
 #pragma unroll
-    for (int c = 0; c < 20; ++c)
-        *reinterpret_cast<__nv_bfloat16*>(DO + core_off(row, C0 + c, kCD)) = __float2bfloat16_rn(d[c]);
+    for (int c = 0; c < 20; c += 2)      // even columns: a pair never crosses a core matrix
+        *reinterpret_cast<uint32_t*>(DO + core_off(row, C0 + c, kCD)) = pack2(d[c], d[c + 1]);
     return (h == 0 && t != 0.0f) ? -t * __logf(qs) : 0.0f;
 }
 
@@ -503,18 +495,29 @@ __global__ void __launch_bounds__(kTrThreads, 1) mlp_train_tc5_kernel(const __nv
     uint32_t acc_g = 0u;              // 0 on a CTA's first tile: the gradient blocks start from zero
     float lsum = 0.0f;
     const int tiles = (n + kRows - 1) / kRows;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int r = tile * kRows + row;
-        uint4 fq = make_uint4(0u, 0u, 0u, 0u);
-        float w[3] = {0.0f, 0.0f, 1.0f}, t = 0.0f;
-        if (r < n) {
+    // the row's record of a tile: its half of the features (the one of
+    // feature 9 set: bias of layer 1), the sampled direction, the target
+    auto load_record = [&](int tl_, uint4& fq, float (&w)[3], float& t) {
+        const int r = tl_ * kRows + row;
+        fq = make_uint4(0u, 0u, 0u, 0u);
+        w[0] = 0.0f; w[1] = 0.0f; w[2] = 1.0f;
+        t = 0.0f;
+        if (tl_ < tiles && r < n) {
             fq = __ldg(reinterpret_cast<const uint4*>(feat + (size_t)r * 16) + half);
-            if (half) fq.x = (fq.x & 0xFFFFu) | (0x3F80u << 16);      // feature 9 := 1 (bias of layer 1)
+            if (half) fq.x = (fq.x & 0xFFFFu) | (0x3F80u << 16);
             w[0] = __ldg(dirs + 3 * (size_t)r);
             w[1] = __ldg(dirs + 3 * (size_t)r + 1);
             w[2] = __ldg(dirs + 3 * (size_t)r + 2);
             t = __ldg(tgt + r) * scale;
         }
+    };
+    uint4 nfq;
+    float nw[3], nt;
+    load_record(blockIdx.x, nfq, nw, nt);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint4 fq = nfq;
+        const float w[3] = {nw[0], nw[1], nw[2]}, t = nt;
+        load_record(tile + gridDim.x, nfq, nw, nt);     // the next tile's, in flight during this one
         *reinterpret_cast<uint4*>(sm + kOffSX + core_off(row, 8 * half, kCX)) = fq;
         // ---- forward
         to_mma();
