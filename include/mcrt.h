@@ -268,7 +268,7 @@ typedef struct {
     int32_t count_events;      /* 1: also count collisions and leaf steps       */
     int32_t rare_batch;        /* GPU lanes of a warp that must be waiting for  */
                                /* a path start, ray start or vertex before that */
-                               /* work runs (1..32; 0 = default 8).  Launch     */
+                               /* work runs (1..32; 0 = default 10).  Launch    */
                                /* shape only: results do not depend on it       */
     struct mcrt_proposal* proposal; /* NULL: plain HG sampling.  Else the first */
                                /* n_learned volume vertices of every path draw  */

@@ -738,8 +738,7 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     P.max_order = o->max_order;
     P.sun_mode = o->sun_mode;
     P.max_steps = 1u << 22;
-    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
-    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+    set_rare_batch(P, o->rare_batch);
     cudaEvent_t e0, e1;
     CK(ctx, cudaEventCreate(&e0));
     CK(ctx, cudaEventCreate(&e1));
@@ -1013,8 +1012,7 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
         P.max_order = o->max_order;
         P.sun_mode = o->sun_mode;
         P.max_steps = 1u << 22;
-        P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
-        P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+        set_rare_batch(P, o->rare_batch);
         P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
         return run_learned(sc, P, kCamera, o, t, spp, who);
     }
@@ -1082,8 +1080,7 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
         P.max_order = o->max_order;
         P.sun_mode = o->sun_mode;
         P.max_steps = 1u << 22;
-        P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
-        P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+        set_rare_batch(P, o->rare_batch);
         P.s1 = t->d_s1; P.s2 = t->d_s2; P.counters = t->d_counters; P.work = static_cast<WorkState*>(t->d_work);
         return run_learned(sc, P, kFlux, o, t, 1ull, who);
     }
@@ -1171,8 +1168,7 @@ TraceParams batch_params(const std::vector<BatchItem>& h, const BatchItem* d_ite
     P.max_order = o->max_order;
     P.sun_mode = o->sun_mode;
     P.max_steps = 1u << 22;
-    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
-    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+    set_rare_batch(P, o->rare_batch);
     return P;
 }
 

@@ -199,6 +199,16 @@ struct TraceParams {
     const volatile int* cancel;
 };
 
+// Rare phases (path start, ray start, vertex) of a warp run once this many
+// of its lanes wait for them (the default when a caller passes 0), or when
+// fewer than 33 - that many lanes are stepping.  Launch shape only.
+constexpr int kDefaultRareBatch = 10;
+inline void set_rare_batch(TraceParams& P, int requested)
+{
+    P.rare_batch = requested > 0 ? requested : kDefaultRareBatch;
+    P.min_steppers = 33 - P.rare_batch;
+}
+
 enum Sensor { kCamera = 0, kFlux = 1 };
 
 // Launchers (return cudaError of the launch).

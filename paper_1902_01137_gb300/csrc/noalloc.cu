@@ -180,8 +180,7 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     P.max_order = o->max_order;
     P.sun_mode = o->sun_mode;
     P.max_steps = 1u << 22;
-    P.rare_batch = o->rare_batch > 0 ? o->rare_batch : 8;
-    P.min_steppers = o->rare_batch > 0 ? 33 - o->rare_batch : 25;
+    set_rare_batch(P, o->rare_batch);
     const bool bf16 = sc->storage == MCRT_STORAGE_BF16;
     const bool count = o->count_events != 0;
     const int block = o->block_size ? o->block_size : 128;

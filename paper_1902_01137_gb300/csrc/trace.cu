@@ -27,9 +27,10 @@
 //
 // Loop structure (one iteration): flush finished chunks and claim new ones
 // (convergent); one Philox block per lane; one phase of work per lane (path
-// start, ray start, traversal step or vertex); one 8-byte load (the voxel of
-// a tentative collision or the leaf-map entry of the leaf entered); the leaf
-// set-up; the end of a ray or path.
+// start, traversal step, vertex, ray start -- a path start or a vertex goes
+// on into the ray start it sets up, with that ray start's own block); one
+// 8-byte load (the voxel of a tentative collision or the leaf-map entry of
+// the leaf entered); the leaf set-up; the end of a ray or path.
 #include <cuda_bf16.h>
 
 #include "mcrt_internal.h"
@@ -70,9 +71,11 @@ constexpr int kOcc = 8;
 
 // Each lane is in one phase per iteration: it starts a path, starts a ray
 // (flight or sun ray), takes one traversal step, or handles the vertex that
-// ended a flight.  Every lane evaluates exactly one Philox block per
-// iteration at one site, whose counter depends on the phase; the voxel /
-// leaf-entry load and the leaf set-up also run at one site each.
+// ended a flight.  Every lane evaluates one Philox block per iteration at
+// one site, whose counter depends on the phase (a path start or vertex that
+// continues into its ray start also draws that ray start's block, the one a
+// later iteration would have drawn); the voxel / leaf-entry load and the
+// leaf set-up also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
 // EXTRA: the variants that also handle decomposition tracking of sun rays
@@ -239,8 +242,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         if (COUNT) { __syncwarp(); tclk = clock64(); }
 
         // ---- rare phases (path start, ray start, vertex) run in batches: a
-        //      lane waits until enough lanes of its warp need the same kind of
-        //      work, or until no lane is stepping -------------------------------
+        //      lane waits until enough lanes of its warp need one, or until
+        //      few lanes are stepping ------------------------------------------
         // (heightfield: a flight whose current leaf reaches down into the relief
         //  layer first finds its ground hit, a rare phase of its own)
         if (TERRAIN && phase == PH_STEP && R.texit >= tpend) phase = PH_TERRAIN;
@@ -249,14 +252,14 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
-        // of the rare kinds (ray start, vertex, the rest) only the one most
-        // lanes wait for runs in this iteration: the warp then executes one
-        // rare branch with more lanes instead of several with few
-        const int nb_ = __popc(__ballot_sync(kFull, phase == PH_BEGIN));
-        const int nv_ = __popc(__ballot_sync(kFull, phase == PH_VERTEX));
-        const int ns_ = __popc(rare_mask) - nb_ - nv_;
-        const int sel = (nb_ >= nv_ && nb_ >= ns_) ? PH_BEGIN : (nv_ >= ns_ ? PH_VERTEX : -1);
-        const bool mine = sel < 0 ? (phase != PH_BEGIN && phase != PH_VERTEX) : phase == sel;
+        // path starts and vertices go on into their ray start in the same
+        // iteration, so those three kinds run together (the ray-start branch
+        // then executes once with all their lanes); the other rare kinds
+        // (learned resume, ground walk) run in iterations of their own, when
+        // more lanes wait for them
+        const bool in_ray = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX;
+        const int n_ray = __popc(__ballot_sync(kFull, in_ray));
+        const bool mine = (2 * n_ray >= __popc(rare_mask)) ? in_ray : !in_ray;
         const int ph = (phase == PH_STEP || (rare && run_rare && mine)) ? phase : PH_IDLE;
 
         // ---- the scene of the lane's chunk (one per batch item) ---------------
@@ -294,6 +297,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         int st = kInside;
         bool setup = false;          // enter a leaf after the load
         bool walk = false;           // heightfield: find this ray's ground hit now
+        bool merge = false;          // a path start or vertex whose ray starts in this iteration too
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
             if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; sa = 0.0f; dal = 0.0f; }
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 for (int a = 0; a < 3; ++a) { vx[a] = q[a]; nd[a] = d[a]; }
                 kind = kMain;
                 c2 = 0u;
-                if (enters) phase = PH_BEGIN;
+                if (enters) { phase = PH_BEGIN; merge = true; }
                 else evc = EV_ESCAPE;          // a path that misses the field scores 0
             } else {
                 vx[0] = (1.0f - u01(x.x)) * S.Lper[0];
@@ -343,6 +347,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 c2 = 3u;
                 Ts = 1.0f;
                 phase = PH_BEGIN;
+                merge = true;
                 if constexpr (TERRAIN) {
                     // the surface point above (x, y), lifted along its normal;
                     // directions cosine-weighted about the normal; the direct
@@ -369,7 +374,89 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
         mark(2);
-        if (ph == PH_BEGIN) {
+        if (ph == PH_VERTEX) {
+            // weight, estimate factor toward the sun, new direction, roulette
+            const float xi1 = u01(x.x), xi2 = u01(x.y), xr = u01(x.z);
+            const int order = (int)ev + 1;
+            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
+            if (!vground) {
+                const float om = omega_at(S, vk);
+                const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
+                float ph = hg_pdf(S.g, mu);
+                float mu_new;
+                if (EXTRA && S.rayleigh) {
+                    // Rayleigh clear air: the mixture phase function in the estimate;
+                    // the species sampled with word 3 of the vertex block
+                    const float pc = cloud_scatter_share(S, vk);
+                    ph = pc * ph + (1.0f - pc) * rayleigh_pdf(mu);
+                    mu_new = u01(x.w) > pc ? rayleigh_sample_mu(xi1) : hg_sample_mu(S.g, xi1);
+                } else {
+                    mu_new = hg_sample_mu(S.g, xi1);
+                }
+                cf = score_it ? w * om * ph : 0.0f;
+                w *= om;
+                rotate_dir(R.d, mu_new, xi2, nd);
+                if (BATCH) {
+                    cfs = hg_dlog_dg(S.g, mu);
+                    sv_pending = hg_dlog_dg(S.g, mu_new);
+                    // d ln omega / d alpha = -k_cloud / (k omega) at this vertex
+                    if (EXTRA && om > 0.0f) sa -= __fdividef(fmaxf(vk - S.k_gas - S.k_clear, 0.0f), vk * om);
+                }
+                if (COUNT) cnt[C_REAL]++;
+            } else if constexpr (TERRAIN) {
+                // tilted ground: leave the surface along its normal, estimate
+                // with n.s, scatter cosine-weighted about n
+                float n[3];
+                hf_height(S, vx[0], vx[1], n);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vx[a] += kTerrainOffset * n[a];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    if (vx[a] < 0.0f) vx[a] += S.Lper[a];
+                    if (!(vx[a] < S.Lper[a])) vx[a] -= S.Lper[a];
+                    if (!(vx[a] >= 0.0f && vx[a] < S.Lper[a])) vx[a] = 0.0f;
+                }
+                const float ns = n[0] * S.sun[0] + n[1] * S.sun[1] + n[2] * S.sun[2];
+                cf = (score_it && ns > 0.0f) ? w * (S.albedo * (1.0f / kPi)) * ns : 0.0f;
+                w *= S.albedo;
+                cosine_about(n, xi1, xi2, nd);
+                if (COUNT) cnt[C_GROUND]++;
+            } else {
+                cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
+                w *= S.albedo;
+                cosine_up(xi1, xi2, nd);
+                if (BATCH) { cfs = 0.0f; sv_pending = 0.0f; }
+                if (COUNT) cnt[C_GROUND]++;
+            }
+            term_after = (P.max_order > 0) && (order >= P.max_order);
+            if (!term_after && w < 0.01f) {
+                if (xr * 0.01f <= w) w = 0.01f;
+                else term_after = true;
+            }
+            // (a ground facet turned away from the sun sends no sun ray)
+            if (score_it && (!TERRAIN || !vground || cf > 0.0f)) {
+                kind = kSunLocal;
+                c2 = (ev << 2) | 1u;
+                Ts = 1.0f;
+                phase = PH_BEGIN;
+                merge = true;
+            } else {
+                Ts = 0.0f;
+                evc = EV_SUN_END;
+            }
+        }
+
+        mark(5);
+        // a lane whose path start or vertex set up a ray starts it now, with
+        // the ray start's own Philox block (the one a later iteration would
+        // have drawn), so it skips one rare iteration and its wait
+        const bool any_merge = __any_sync(kFull, merge);
+        uint4 xb = x;
+        if (any_merge) {
+            const uint4 y = draw_block(pid, c2, 0u, rkey);
+            if (merge) xb = y;
+        }
+        if (ph == PH_BEGIN || merge) {
             // start a ray: the flight from vx along nd, or the sun ray from vx
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -383,7 +470,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             R.steps = 0;
             ptr = leaf_entry(S, R.v);
             setup = true;
-            tau = -__logf(u01(x.x));
+            tau = -__logf(u01(xb.x));
             blk = 1;
             if constexpr (TERRAIN) {
                 // a sun ray that meets the surface is shadowed (found now: sun rays
@@ -488,77 +575,6 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
         mark(4);
-        if (ph == PH_VERTEX) {
-            // weight, estimate factor toward the sun, new direction, roulette
-            const float xi1 = u01(x.x), xi2 = u01(x.y), xr = u01(x.z);
-            const int order = (int)ev + 1;
-            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
-            if (!vground) {
-                const float om = omega_at(S, vk);
-                const float mu = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
-                float ph = hg_pdf(S.g, mu);
-                float mu_new;
-                if (EXTRA && S.rayleigh) {
-                    // Rayleigh clear air: the mixture phase function in the estimate;
-                    // the species sampled with word 3 of the vertex block
-                    const float pc = cloud_scatter_share(S, vk);
-                    ph = pc * ph + (1.0f - pc) * rayleigh_pdf(mu);
-                    mu_new = u01(x.w) > pc ? rayleigh_sample_mu(xi1) : hg_sample_mu(S.g, xi1);
-                } else {
-                    mu_new = hg_sample_mu(S.g, xi1);
-                }
-                cf = score_it ? w * om * ph : 0.0f;
-                w *= om;
-                rotate_dir(R.d, mu_new, xi2, nd);
-                if (BATCH) {
-                    cfs = hg_dlog_dg(S.g, mu);
-                    sv_pending = hg_dlog_dg(S.g, mu_new);
-                    // d ln omega / d alpha = -k_cloud / (k omega) at this vertex
-                    if (EXTRA && om > 0.0f) sa -= __fdividef(fmaxf(vk - S.k_gas - S.k_clear, 0.0f), vk * om);
-                }
-                if (COUNT) cnt[C_REAL]++;
-            } else if constexpr (TERRAIN) {
-                // tilted ground: leave the surface along its normal, estimate
-                // with n.s, scatter cosine-weighted about n
-                float n[3];
-                hf_height(S, vx[0], vx[1], n);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) vx[a] += kTerrainOffset * n[a];
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    if (vx[a] < 0.0f) vx[a] += S.Lper[a];
-                    if (!(vx[a] < S.Lper[a])) vx[a] -= S.Lper[a];
-                    if (!(vx[a] >= 0.0f && vx[a] < S.Lper[a])) vx[a] = 0.0f;
-                }
-                const float ns = n[0] * S.sun[0] + n[1] * S.sun[1] + n[2] * S.sun[2];
-                cf = (score_it && ns > 0.0f) ? w * (S.albedo * (1.0f / kPi)) * ns : 0.0f;
-                w *= S.albedo;
-                cosine_about(n, xi1, xi2, nd);
-                if (COUNT) cnt[C_GROUND]++;
-            } else {
-                cf = score_it ? w * (S.albedo * (1.0f / kPi)) * fmaxf(S.sun[2], 0.0f) : 0.0f;
-                w *= S.albedo;
-                cosine_up(xi1, xi2, nd);
-                if (BATCH) { cfs = 0.0f; sv_pending = 0.0f; }
-                if (COUNT) cnt[C_GROUND]++;
-            }
-            term_after = (P.max_order > 0) && (order >= P.max_order);
-            if (!term_after && w < 0.01f) {
-                if (xr * 0.01f <= w) w = 0.01f;
-                else term_after = true;
-            }
-            // (a ground facet turned away from the sun sends no sun ray)
-            if (score_it && (!TERRAIN || !vground || cf > 0.0f)) {
-                kind = kSunLocal;
-                c2 = (ev << 2) | 1u;
-                Ts = 1.0f;
-                phase = PH_BEGIN;
-            } else {
-                Ts = 0.0f;
-                evc = EV_SUN_END;
-            }
-        }
-
         if (LEARNED && ph == PH_RESUME) {
             // resume a path stopped at a learned vertex: state, network output,
             // one-sample MIS direction, weight p_HG / q
@@ -654,7 +670,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         // ---- after the load ----------------------------------------------------
         if (setup) {
             finish_leaf<BF16>(S, R, val);
-            if (ph == PH_BEGIN) phase = PH_STEP;
+            if (ph == PH_BEGIN || merge) phase = PH_STEP;
             else if (R.steps > P.max_steps) evc = EV_ABORT;
         } else if (tent) {
             float kv;
