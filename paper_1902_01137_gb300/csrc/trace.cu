@@ -27,10 +27,11 @@
 //
 // Loop structure (one iteration): flush finished chunks and claim new ones
 // (convergent); one Philox block per lane; one phase of work per lane (path
-// start, traversal step, vertex, ray start -- a path start or a vertex goes
-// on into the ray start it sets up, with that ray start's own block); one
-// 8-byte load (the voxel of a tentative collision or the leaf-map entry of
-// the leaf entered); the leaf set-up; the end of a ray or path.
+// start, traversal step, vertex, ray start -- a path start or a vertex,
+// learned or not, goes on into the ray start it sets up, with that ray
+// start's own block); one 8-byte load (the voxel of a tentative collision
+// or the leaf-map entry of the leaf entered); the leaf set-up; the end of a
+// ray or path.
 #include <cuda_bf16.h>
 
 #include "mcrt_internal.h"
@@ -252,12 +253,12 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
-        // path starts and vertices go on into their ray start in the same
-        // iteration, so those three kinds run together (the ray-start branch
-        // then executes once with all their lanes); the other rare kinds
-        // (learned resume, ground walk) run in iterations of their own, when
-        // more lanes wait for them
-        const bool in_ray = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX;
+        // path starts and vertices (learned ones resumed too) go on into their
+        // ray start in the same iteration, so these kinds run together (the
+        // ray-start branch then executes once with all their lanes); the
+        // ground walk runs in iterations of its own, when more lanes wait for it
+        const bool in_ray = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX ||
+                            (LEARNED && phase == PH_RESUME);
         const int n_ray = __popc(__ballot_sync(kFull, in_ray));
         const bool mine = (2 * n_ray >= __popc(rare_mask)) ? in_ray : !in_ray;
         const int ph = (phase == PH_STEP || (rare && run_rare && mine)) ? phase : PH_IDLE;
@@ -446,10 +447,97 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
 
+        if (LEARNED && ph == PH_RESUME) {
+            // resume a path stopped at a learned vertex: state, network output,
+            // one-sample MIS direction, weight p_HG / q
+            const uint32_t slot = (uint32_t)pid;
+            const uint4 q0 = P.qin[4 * (size_t)slot], q1 = P.qin[4 * (size_t)slot + 1];
+            const uint4 q2 = P.qin[4 * (size_t)slot + 2], q3 = P.qin[4 * (size_t)slot + 3];
+            pid = (unsigned long long)q0.x | ((unsigned long long)q0.y << 32);
+            pend = pid + 1;
+            ev = q0.z;
+            lv = q0.w;
+            vx[0] = __uint_as_float(q1.x); vx[1] = __uint_as_float(q1.y); vx[2] = __uint_as_float(q1.z);
+            vk = __uint_as_float(q1.w);
+            R.d[0] = __uint_as_float(q2.x); R.d[1] = __uint_as_float(q2.y); R.d[2] = __uint_as_float(q2.z);
+            w = __uint_as_float(q2.w);
+            score = __uint_as_float(q3.x);
+            tdir = __uint_as_float(q3.y);
+            term_after = false;
+            if constexpr (SENSOR == kCamera) cell = (unsigned)(pid / P.spp);
+            kind = kMain;
+            c2 = ev << 2;
+            const uint4 xv = draw_block(pid, ev << 2, kBlockVertex, P.key);
+            const uint4 xl = draw_block(pid, ev << 2, kBlockVertex - 1u, P.key);
+            const float xi1 = u01(xv.x), xi2 = u01(xv.y), xr = u01(xv.z), xc = u01(xv.w), xlobe = u01(xl.x);
+            const int order = (int)ev + 1;
+            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
+            const float om = omega_at(S, vk);
+            const float mu_s = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
+            cf = score_it ? w * om * hg_pdf(S.g, mu_s) : 0.0f;
+            const float* mix = P.qin_mix + 48 * (size_t)slot;
+            if (xc <= P.mis_alpha) {
+                rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
+            } else {
+                int j = 7;
+#pragma unroll
+                for (int i = 0; i < 7; ++i)
+                    if (j == 7 && xlobe <= __ldg(mix + 6 * i + 4)) j = i;
+                const float mu_l[3] = {__ldg(mix + 6 * j), __ldg(mix + 6 * j + 1), __ldg(mix + 6 * j + 2)};
+                const float kap = __ldg(mix + 6 * j + 3);
+                float cw = 1.0f + __logf(xi1 + (1.0f - xi1) * __expf(-2.0f * kap)) / kap;
+                cw = fminf(fmaxf(cw, -1.0f), 1.0f);
+                rotate_dir(mu_l, cw, xi2, nd);
+            }
+            const float phg = hg_pdf(S.g, R.d[0] * nd[0] + R.d[1] * nd[1] + R.d[2] * nd[2]);
+            // mixture density: sum of pi_j C(kappa_j) exp(kappa_j (mu_j . w - 1))
+            float qv = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float c = __ldg(mix + 6 * i) * nd[0] + __ldg(mix + 6 * i + 1) * nd[1] + __ldg(mix + 6 * i + 2) * nd[2];
+                qv += __ldg(mix + 6 * i + 5) * __expf(__ldg(mix + 6 * i + 3) * (c - 1.0f));
+            }
+            const float qmix = P.mis_alpha * phg + (1.0f - P.mis_alpha) * qv;
+            // training record: features, direction, score so far, w * omega
+            if (P.rec_count && slot < P.rec_slots) {
+                const unsigned idx = atomicAdd(P.rec_count, 1u);
+                if (idx < P.rec_cap) {
+                    P.rec_feat[2 * (size_t)idx] = P.qin_feat[2 * (size_t)slot];
+                    P.rec_feat[2 * (size_t)idx + 1] = P.qin_feat[2 * (size_t)slot + 1];
+                    P.rec_dir[3 * (size_t)idx] = nd[0];
+                    P.rec_dir[3 * (size_t)idx + 1] = nd[1];
+                    P.rec_dir[3 * (size_t)idx + 2] = nd[2];
+                    P.rec_val[4 * (size_t)idx] = score;
+                    P.rec_val[4 * (size_t)idx + 1] = w * om;
+                    P.rec_val[4 * (size_t)idx + 2] = 0.0f;
+                    P.rec_val[4 * (size_t)idx + 3] = __uint_as_float((uint32_t)(pid - P.path_base));
+                    cur_rec = idx;
+                }
+            }
+            w *= om * __fdividef(phg, fmaxf(qmix, 1e-30f));
+            ++lv;
+            if (COUNT) cnt[C_REAL]++;
+            term_after = (P.max_order > 0) && (order >= P.max_order);
+            if (!term_after && w < 0.01f) {
+                if (xr * 0.01f <= w) w = 0.01f;
+                else term_after = true;
+            }
+            if (score_it) {
+                kind = kSunLocal;
+                c2 = (ev << 2) | 1u;
+                Ts = 1.0f;
+                phase = PH_BEGIN;
+                merge = true;
+            } else {
+                Ts = 0.0f;
+                evc = EV_SUN_END;
+            }
+        }
         mark(5);
-        // a lane whose path start or vertex set up a ray starts it now, with
-        // the ray start's own Philox block (the one a later iteration would
-        // have drawn), so it skips one rare iteration and its wait
+        // a lane whose path start, vertex or resumed vertex set up a ray
+        // starts it now, with the ray start's own Philox block (the one a
+        // later iteration would have drawn), so it skips one rare iteration
+        // and its wait
         const bool any_merge = __any_sync(kFull, merge);
         uint4 xb = x;
         if (any_merge) {
@@ -575,92 +663,6 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
         mark(4);
-        if (LEARNED && ph == PH_RESUME) {
-            // resume a path stopped at a learned vertex: state, network output,
-            // one-sample MIS direction, weight p_HG / q
-            const uint32_t slot = (uint32_t)pid;
-            const uint4 q0 = P.qin[4 * (size_t)slot], q1 = P.qin[4 * (size_t)slot + 1];
-            const uint4 q2 = P.qin[4 * (size_t)slot + 2], q3 = P.qin[4 * (size_t)slot + 3];
-            pid = (unsigned long long)q0.x | ((unsigned long long)q0.y << 32);
-            pend = pid + 1;
-            ev = q0.z;
-            lv = q0.w;
-            vx[0] = __uint_as_float(q1.x); vx[1] = __uint_as_float(q1.y); vx[2] = __uint_as_float(q1.z);
-            vk = __uint_as_float(q1.w);
-            R.d[0] = __uint_as_float(q2.x); R.d[1] = __uint_as_float(q2.y); R.d[2] = __uint_as_float(q2.z);
-            w = __uint_as_float(q2.w);
-            score = __uint_as_float(q3.x);
-            tdir = __uint_as_float(q3.y);
-            term_after = false;
-            if constexpr (SENSOR == kCamera) cell = (unsigned)(pid / P.spp);
-            kind = kMain;
-            c2 = ev << 2;
-            const uint4 xv = draw_block(pid, ev << 2, kBlockVertex, P.key);
-            const uint4 xl = draw_block(pid, ev << 2, kBlockVertex - 1u, P.key);
-            const float xi1 = u01(xv.x), xi2 = u01(xv.y), xr = u01(xv.z), xc = u01(xv.w), xlobe = u01(xl.x);
-            const int order = (int)ev + 1;
-            const bool score_it = (P.max_order == 0) || (order <= P.max_order);
-            const float om = omega_at(S, vk);
-            const float mu_s = R.d[0] * S.sun[0] + R.d[1] * S.sun[1] + R.d[2] * S.sun[2];
-            cf = score_it ? w * om * hg_pdf(S.g, mu_s) : 0.0f;
-            const float* mix = P.qin_mix + 48 * (size_t)slot;
-            if (xc <= P.mis_alpha) {
-                rotate_dir(R.d, hg_sample_mu(S.g, xi1), xi2, nd);
-            } else {
-                int j = 7;
-#pragma unroll
-                for (int i = 0; i < 7; ++i)
-                    if (j == 7 && xlobe <= __ldg(mix + 6 * i + 4)) j = i;
-                const float mu_l[3] = {__ldg(mix + 6 * j), __ldg(mix + 6 * j + 1), __ldg(mix + 6 * j + 2)};
-                const float kap = __ldg(mix + 6 * j + 3);
-                float cw = 1.0f + __logf(xi1 + (1.0f - xi1) * __expf(-2.0f * kap)) / kap;
-                cw = fminf(fmaxf(cw, -1.0f), 1.0f);
-                rotate_dir(mu_l, cw, xi2, nd);
-            }
-            const float phg = hg_pdf(S.g, R.d[0] * nd[0] + R.d[1] * nd[1] + R.d[2] * nd[2]);
-            // mixture density: sum of pi_j C(kappa_j) exp(kappa_j (mu_j . w - 1))
-            float qv = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float c = __ldg(mix + 6 * i) * nd[0] + __ldg(mix + 6 * i + 1) * nd[1] + __ldg(mix + 6 * i + 2) * nd[2];
-                qv += __ldg(mix + 6 * i + 5) * __expf(__ldg(mix + 6 * i + 3) * (c - 1.0f));
-            }
-            const float qmix = P.mis_alpha * phg + (1.0f - P.mis_alpha) * qv;
-            // training record: features, direction, score so far, w * omega
-            if (P.rec_count && slot < P.rec_slots) {
-                const unsigned idx = atomicAdd(P.rec_count, 1u);
-                if (idx < P.rec_cap) {
-                    P.rec_feat[2 * (size_t)idx] = P.qin_feat[2 * (size_t)slot];
-                    P.rec_feat[2 * (size_t)idx + 1] = P.qin_feat[2 * (size_t)slot + 1];
-                    P.rec_dir[3 * (size_t)idx] = nd[0];
-                    P.rec_dir[3 * (size_t)idx + 1] = nd[1];
-                    P.rec_dir[3 * (size_t)idx + 2] = nd[2];
-                    P.rec_val[4 * (size_t)idx] = score;
-                    P.rec_val[4 * (size_t)idx + 1] = w * om;
-                    P.rec_val[4 * (size_t)idx + 2] = 0.0f;
-                    P.rec_val[4 * (size_t)idx + 3] = __uint_as_float((uint32_t)(pid - P.path_base));
-                    cur_rec = idx;
-                }
-            }
-            w *= om * __fdividef(phg, fmaxf(qmix, 1e-30f));
-            ++lv;
-            if (COUNT) cnt[C_REAL]++;
-            term_after = (P.max_order > 0) && (order >= P.max_order);
-            if (!term_after && w < 0.01f) {
-                if (xr * 0.01f <= w) w = 0.01f;
-                else term_after = true;
-            }
-            if (score_it) {
-                kind = kSunLocal;
-                c2 = (ev << 2) | 1u;
-                Ts = 1.0f;
-                phase = PH_BEGIN;
-            } else {
-                Ts = 0.0f;
-                evc = EV_SUN_END;
-            }
-        }
-        mark(5);
         // ---- the one load: voxel word or leaf-map entry ---------------------
         uint2 val = make_uint2(0u, 0u);
         if (ptr) val = __ldg(ptr);
