@@ -253,15 +253,11 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         const unsigned rare_mask = __ballot_sync(kFull, rare);
         const unsigned step_mask = __ballot_sync(kFull, phase == PH_STEP);
         const bool run_rare = __popc(rare_mask) >= P.rare_batch || __popc(step_mask) < P.min_steppers;
-        // path starts and vertices (learned ones resumed too) go on into their
-        // ray start in the same iteration, so these kinds run together (the
-        // ray-start branch then executes once with all their lanes); the
-        // ground walk runs in iterations of its own, when more lanes wait for it
-        const bool in_ray = phase == PH_START || phase == PH_BEGIN || phase == PH_VERTEX ||
-                            (LEARNED && phase == PH_RESUME);
-        const int n_ray = __popc(__ballot_sync(kFull, in_ray));
-        const bool mine = (2 * n_ray >= __popc(rare_mask)) ? in_ray : !in_ray;
-        const int ph = (phase == PH_STEP || (rare && run_rare && mine)) ? phase : PH_IDLE;
+        // every rare kind runs in the same iteration: path starts and
+        // vertices (learned ones resumed too) go on into their ray start, and
+        // ground walks start there as well, so the ray-start and walk
+        // branches execute once with all their lanes
+        const int ph = (phase == PH_STEP || (rare && run_rare)) ? phase : PH_IDLE;
 
         // ---- the scene of the lane's chunk (one per batch item) ---------------
         const DevScene& S = BATCH ? P.items[item].S : P.S;
