@@ -70,14 +70,14 @@ PROFILED_DRAM_BYTES_PER_PATH = 23.73
 # locate it against its real ceiling: 152 SMs x 4 schedulers x 1 warp
 # instruction per cycle
 PROFILED_ISSUE_ACTIVE = 0.7097
-PROFILED_THREADS_PER_INST = 17.06
-PROFILED_WARP_INST_PER_PATH = 5103.1
+PROFILED_THREADS_PER_INST = 17.04
+PROFILED_WARP_INST_PER_PATH = 5079.2
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_1024px64spp_launches.md"
 # the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
 PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 39.44
 # one-pass count of the bench's octree launches (same profile as the pyramid's)
-PROFILED_OCTREE_WARP_INST_PER_PATH = 3896.3
-PROFILED_OCTREE_THREADS_PER_INST = 16.01
+PROFILED_OCTREE_WARP_INST_PER_PATH = 3870.5
+PROFILED_OCTREE_THREADS_PER_INST = 15.98
 
 
 def trace_sources_sha() -> str:

@@ -260,9 +260,9 @@ typedef struct {
                                /* order <= n and stop after order n             */
     int32_t sun_mode;          /* MCRT_SUN_RATIO (default), _DELTA or _DECOMP   */
     int32_t chunk;             /* paths a GPU thread claims at once; 0 = auto:  */
-                               /* 1, 2 or 4 as the paths per resident thread    */
-                               /* pass 48 and 160 (camera: dividing spp; batch: */
-                               /* 4).  Launch shape only                        */
+                               /* 1, 2, 4 or 8 as the paths per                 */
+                               /* resident thread pass 48, 160 and 400 (camera: */
+                               /* dividing spp; batch: 4).  Launch shape only   */
     int32_t block_size;        /* threads per block; 0 = auto                   */
     int32_t grid_size;         /* blocks; 0 = SMs x resident blocks             */
     int32_t count_events;      /* 1: also count collisions and leaf steps       */

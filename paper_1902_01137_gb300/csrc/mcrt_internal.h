@@ -237,11 +237,12 @@ cudaError_t launch_finalize(const double* s1, const double* s2, double n, int co
 // lane long chunks stretch the launch's tail (a chunk of one cloudy pixel
 // holds several long random walks); with many, short chunks cost claims.
 // Thresholds from GB300 measurements on the cumulus field: chunk 1 below
-// 48 paths per lane, 2 below 160, else 4; camera chunks divide spp.
+// 48 paths per lane, 2 below 160, 4 below 400, else 8 (the most the FP32
+// chunk sums are bounded for); camera chunks divide spp.
 inline uint32_t auto_chunk(unsigned long long total, unsigned long long lanes, uint32_t spp)
 {
     const double per_lane = lanes ? (double)total / (double)lanes : 0.0;
-    uint32_t c = per_lane < 48.0 ? 1u : (per_lane < 160.0 ? 2u : 4u);
+    uint32_t c = per_lane < 48.0 ? 1u : (per_lane < 160.0 ? 2u : (per_lane < 400.0 ? 4u : 8u));
     if (spp) {
         if (c > spp) c = spp;
         while (spp % c) --c;
