@@ -75,16 +75,23 @@ void orc_philox_batch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, i
 /* Random numbers.  Every draw is addressed: stream s of event e of path p
  * evaluates Philox at counter (p low, p high, (e << 2) | s, block) and the
  * key (seed low, seed high), and takes a fixed word of that block:
- *   block 0, word 0            first optical depth of a ray
+ *   block 0, word 0            first optical depth of a flight (stream 0)
+ *                              or of a flux path's direct sun ray (stream 3)
  *   block j >= 1, words 0, 1   j-th tentative collision of the ray: the
  *                              collision test (or roulette) draw, then the
  *                              next optical depth
- *   block VERTEX, words 0-2    scattering/reflection direction (two draws)
- *                              and Russian roulette at the vertex that ends
- *                              the flight of event e (stream 0)
+ *   stream 1, block 0          the vertex that ends the flight of event e:
+ *                              scattering/reflection direction (words 0, 1),
+ *                              Russian roulette (word 2), and the first
+ *                              optical depth of its sun ray (word 3)
  *   stream 2, block 0          path start (jitter, or ground point and
- *                              direction)
- * Streams: 0 free flight, 1 sun ray of the vertex, 2 path start, 3 direct
+ *                              direction); word 2 of a camera path's: the
+ *                              first optical depth of its first flight
+ *   stream 0, blocks VERTEX    a learned vertex (direction, roulette and MIS
+ *   and VERTEX - 1             draws; word 1 of block VERTEX - 1: its sun
+ *                              ray's first optical depth); word 0 of block
+ *                              VERTEX: the species at a Rayleigh vertex
+ * Streams: 0 free flight, 1 vertex and its sun ray, 2 path start, 3 direct
  * sun ray of a flux path (event 0). */
 #define BLOCK_VERTEX 0xFFFFFFFFu
 
@@ -971,7 +978,7 @@ static void wrap_xy(const orc_scene* S, double p[3]);
  * cut there, and a flight that spends none of its optical depth before it
  * is a ground event with the triangle's normal in n_ground. */
 static int free_flight(const orc_scene* S, double p[3], const double d[3], const rng_t* r,
-                       double* k_at, int vox_at[3], orc_counts* C, double n_ground[3])
+                       double* k_at, int vox_at[3], orc_counts* C, double n_ground[3], double tau0)
 {
     const double p0[3] = {p[0], p[1], p[2]};
     double tg = INFINITY, ng[3] = {0.0, 0.0, 1.0};
@@ -981,8 +988,11 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
     trav64 T;
     trav_begin(S, &T, p, d);
     double u[4];
-    rng_block(r, 0, u);
-    double tau = -log(u[0]);
+    double tau = tau0;                  /* given by the caller (>= 0), else word 0 of block 0 */
+    if (!(tau >= 0.0)) {
+        rng_block(r, 0, u);
+        tau = -log(u[0]);
+    }
     for (uint32_t j = 1;;) {
         double seg = T.seg;
         const int ground_here = has_tg && dist + seg >= tg;
@@ -1036,7 +1046,7 @@ static int free_flight(const orc_scene* S, double p[3], const double d[3], const
  * Roulette below 0.1 as in ratio tracking; at a leaf crossing it draws
  * word 3 of the next block (the block is then used up). */
 static double transmissivity(const orc_scene* S, const double p[3], const double s[3], const rng_t* r,
-                             orc_counts* C)
+                             orc_counts* C, double tau0)
 {
     if (S->hf) {                        /* shadow of the terrain */
         double tg;
@@ -1046,8 +1056,11 @@ static double transmissivity(const orc_scene* S, const double p[3], const double
     trav_begin(S, &T, p, s);
     double t = 1.0;
     double u[4];
-    rng_block(r, 0, u);
-    double tau = -log(u[0]);
+    double tau = tau0;                  /* given by the caller (>= 0), else word 0 of block 0 */
+    if (!(tau >= 0.0)) {
+        rng_block(r, 0, u);
+        tau = -log(u[0]);
+    }
     const int decomp = S->sun_mode == 2;
     for (uint32_t j = 1;;) {
         double Mt = decomp ? T.M - T.m : T.M;      /* tracking majorant */
@@ -1090,7 +1103,7 @@ double orc_transmissivity(const orc_scene* S, const double p[3], const double s[
 {
     rng_t r;
     rng_init(&r, seed, path, 0, 1);
-    return transmissivity(S, p, s, &r, NULL);
+    return transmissivity(S, p, s, &r, NULL, -1.0);
 }
 
 /* Distance to the first real collision (for the mean-free-path pin). */
@@ -1131,8 +1144,7 @@ double orc_first_collision_distance(const orc_scene* S, const double p[3], const
 /* omega (or rho), a new direction is sampled (HG about d, or cosine      */
 /* about +z), and Russian roulette applies below w = 0.01.  The path ends */
 /* at the top of atmosphere.  The flight of event e draws from stream     */
-/* (e, 0), its vertex from block VERTEX of that stream, and the vertex's  */
-/* sun ray from stream (e, 1).                                            */
+/* (e, 0); its vertex and the vertex's sun ray from stream (e, 1).        */
 /* ===================================================================== */
 #define MLP_IN 9
 #define MLP_OUT 40
@@ -1228,12 +1240,12 @@ double orc_hg_dlog_dg(double g, double mu)
  * derivative as the weight it replaces.) */
 static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                                orc_counts* C, int64_t* aborted, double* dscore, double* dalpha,
-                               orc_rec_sink* sink);
+                               orc_rec_sink* sink, double tau_first);
 
 static double trace_backward_d(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                                orc_counts* C, int64_t* aborted, double* dscore, double* dalpha)
 {
-    return trace_backward_r(S, p, d, seed, path, C, aborted, dscore, dalpha, NULL);
+    return trace_backward_r(S, p, d, seed, path, C, aborted, dscore, dalpha, NULL, -1.0);
 }
 
 static double trace_backward(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
@@ -1242,10 +1254,12 @@ static double trace_backward(const orc_scene* S, double p[3], double d[3], uint6
     return trace_backward_d(S, p, d, seed, path, C, aborted, NULL, NULL);
 }
 
-/* sink (may be NULL): receives one record per learned vertex of the path. */
+/* sink (may be NULL): receives one record per learned vertex of the path.
+ * tau_first >= 0: the first flight's optical depth (a camera path draws it
+ * with its start); else the flight draws it from its own stream. */
 static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uint64_t seed, uint64_t path,
                                orc_counts* C, int64_t* aborted, double* dscore, double* dalpha,
-                               orc_rec_sink* sink)
+                               orc_rec_sink* sink, double tau_first)
 {
     const int64_t rec0 = sink ? sink->n : 0;   /* this path's first record */
     double sg = 0.0, ds = 0.0;
@@ -1259,15 +1273,27 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
         double k;
         int vox[3] = {0, 0, 0};
         double ng[3];
-        int ev = free_flight(S, p, d, &r, &k, vox, C, ng);
+        int ev = free_flight(S, p, d, &r, &k, vox, C, ng, e == 0 ? tau_first : -1.0);
         if (ev == EV_ESCAPE) break;
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; break; }
         int order = (int)e + 1;
         int score_it = (S->max_order == 0 || order <= S->max_order);
         rng_t rs;
         rng_init(&rs, seed, path, e, 1);
-        double uv[4];
-        rng_block(&r, BLOCK_VERTEX, uv);
+        /* the vertex draws from block 0 of its sun ray's stream (e, 1):
+         * direction (words 0, 1), roulette (word 2) and the sun ray's first
+         * optical depth (word 3); a learned vertex from blocks VERTEX and
+         * VERTEX - 1 of the flight's stream (e, 0), its sun ray's first
+         * optical depth from word 1 of the latter */
+        const int learned_v = ev == EV_VOLUME && S->mlp && lv < S->n_learned;
+        double uv[4], ul[4] = {0.0, 0.0, 0.0, 0.0};
+        if (learned_v) {
+            rng_block(&r, BLOCK_VERTEX, uv);
+            rng_block(&r, BLOCK_VERTEX - 1u, ul);
+        } else {
+            rng_block(&rs, 0, uv);
+        }
+        const double sun_tau0 = -log(learned_v ? ul[1] : uv[3]);
         if (ev == EV_VOLUME) {
             const double before = score, w_vertex = w;
             double own = 0.0;
@@ -1280,10 +1306,11 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
             /* clear air with a Rayleigh phase function: the vertex's phase
              * function is the scattering-weighted mixture (used whole in
              * the local estimate); the new direction samples the species
-             * first (word 3 of the vertex block), then its phase function */
+             * first (word 0 of block VERTEX of the flight's stream), then
+             * its phase function */
             const double pc = S->clear_phase == 1 ? cloud_scatter_share(S, k) : 1.0;
             if (score_it) {
-                double Ts = transmissivity(S, p, s, &rs, C);
+                double Ts = transmissivity(S, p, s, &rs, C, sun_tau0);
                 double mu = d[0] * s[0] + d[1] * s[1] + d[2] * s[2];
                 double phg = orc_hg_pdf(S->g, mu);
                 double ph = S->clear_phase == 1 ? pc * phg + (1.0 - pc) * orc_rayleigh_pdf(mu) : phg;
@@ -1296,12 +1323,11 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
             }
             w *= om;
             double nd[3];
-            if (S->mlp && lv < S->n_learned) {
+            if (learned_v) {
                 /* learned proposal: features, network, one-sample MIS */
-                double x[MLP_IN], raw[MLP_OUT], ul[4];
+                double x[MLP_IN], raw[MLP_OUT];
                 vertex_features(S, p, d, k, vox, x);
                 orc_mlp_forward(S->mlp, x, 1, raw);
-                rng_block(&r, BLOCK_VERTEX - 1u, ul);
                 double um[4] = {uv[0], uv[1], uv[3], ul[0]};
                 w *= orc_mis_sample(raw, S->g, S->mis_alpha, d, um, nd, NULL, NULL);
                 if (sink) {
@@ -1321,7 +1347,9 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
                 }
             } else if (S->clear_phase == 1) {
                 /* the direction's density is the mixture; its g-score too */
-                double mu = uv[3] > pc ? orc_rayleigh_sample_mu(uv[0]) : orc_hg_sample_mu(S->g, uv[0]);
+                double us[4];
+                rng_block(&r, BLOCK_VERTEX, us);
+                double mu = us[0] > pc ? orc_rayleigh_sample_mu(uv[0]) : orc_hg_sample_mu(S->g, uv[0]);
                 rotate_dir(d, mu, 2.0 * ORC_PI * uv[1], nd);
                 double phg = orc_hg_pdf(S->g, mu);
                 sg += pc * phg * orc_hg_dlog_dg(S->g, mu) / (pc * phg + (1.0 - pc) * orc_rayleigh_pdf(mu));
@@ -1335,7 +1363,7 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
             d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
         } else if (!S->hf) { /* flat ground */
             if (score_it) {
-                double Ts = transmissivity(S, p, s, &rs, C);
+                double Ts = transmissivity(S, p, s, &rs, C, sun_tau0);
                 double c = w * (S->ground_albedo / ORC_PI) * fmax(s[2], 0.0) * Ts;
                 score += c;
                 ds += c * sg;
@@ -1348,7 +1376,7 @@ static double trace_backward_r(const orc_scene* S, double p[3], double d[3], uin
             wrap_xy(S, p);
             if (score_it) {
                 double ns = ng[0] * s[0] + ng[1] * s[1] + ng[2] * s[2];
-                double Ts = ns > 0.0 ? transmissivity(S, p, s, &rs, C) : 0.0;
+                double Ts = ns > 0.0 ? transmissivity(S, p, s, &rs, C, sun_tau0) : 0.0;
                 double c = w * (S->ground_albedo / ORC_PI) * fmax(ns, 0.0) * Ts;
                 score += c;
                 ds += c * sg;
@@ -1451,7 +1479,8 @@ static double camera_path_r(const orc_scene* S, const orc_camera* C, uint32_t sp
         return 0.0;
     }
     wrap_xy(S, p);
-    return trace_backward_r(S, p, d, seed, path, cnt, aborted, NULL, NULL, sink);
+    /* the first flight's optical depth: word 2 of the path-start block */
+    return trace_backward_r(S, p, d, seed, path, cnt, aborted, NULL, NULL, sink, -log(uj[2]));
 }
 
 /* One ground-flux path: uniform ground point, cosine-weighted upward
@@ -1492,7 +1521,7 @@ static void flux_path_r(const orc_scene* S, uint64_t seed, uint64_t path, double
         cosine_about(n, u2, u3, d);
         double ns = n[0] * S->sun[0] + n[1] * S->sun[1] + n[2] * S->sun[2];
         double q[3] = {p[0], p[1], p[2]};
-        double Tdir = ns > 0.0 ? transmissivity(S, q, S->sun, &rd, cnt) : 0.0;
+        double Tdir = ns > 0.0 ? transmissivity(S, q, S->sun, &rd, cnt, -1.0) : 0.0;
         double dsc = 0.0, dal = 0.0;
         double score = trace_backward_d(S, p, d, seed, path, cnt, aborted, &dsc, &dal);
         out[0] = fmax(ns, 0.0) / (n[2] * mu0) * Tdir;
@@ -1503,9 +1532,9 @@ static void flux_path_r(const orc_scene* S, uint64_t seed, uint64_t path, double
     }
     cosine_up(u2, u3, d);
     double q[3] = {p[0], p[1], p[2]};
-    double Tdir = transmissivity(S, q, S->sun, &rd, cnt);
+    double Tdir = transmissivity(S, q, S->sun, &rd, cnt, -1.0);
     double dsc = 0.0, dal = 0.0;
-    double score = trace_backward_r(S, p, d, seed, path, cnt, aborted, &dsc, &dal, sink);
+    double score = trace_backward_r(S, p, d, seed, path, cnt, aborted, &dsc, &dal, sink, -1.0);
     out[0] = Tdir;
     out[1] = ORC_PI / mu0 * score;
     out[2] = ORC_PI / mu0 * dsc;
@@ -1538,7 +1567,7 @@ static void forward_photon(const orc_scene* S, uint64_t seed, uint64_t path, dou
         rng_t r;
         rng_init(&r, seed, path, e, 0);
         double k;
-        int ev = free_flight(S, p, d, &r, &k, NULL, NULL, NULL);
+        int ev = free_flight(S, p, d, &r, &k, NULL, NULL, NULL, -1.0);
         if (ev == EV_ESCAPE) { out[0] += w; return; }
         if (ev == EV_ABORT) { if (aborted) (*aborted)++; out[5] += w; return; }
         double uv[4];

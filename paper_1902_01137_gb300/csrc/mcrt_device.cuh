@@ -63,11 +63,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 
 // Random numbers are addressed: stream s of event e of path p evaluates
 // Philox at counter (p lo, p hi, (e << 2) | s, block) and uses fixed words of
-// the block -- block 0 word 0: first optical depth of a ray; block j >= 1:
-// the j-th tentative collision (test or roulette draw, next optical depth);
-// block kBlockVertex: the vertex ending the flight of event e (two direction
-// draws, roulette); stream 2 block 0: path start.  Streams: 0 flight, 1 sun
-// ray of a vertex, 2 path start, 3 direct sun ray of a flux path.
+// the block -- block 0 word 0: first optical depth of a flight or a flux
+// path's direct sun ray; block j >= 1: the j-th tentative collision (test or
+// roulette draw, next optical depth); stream 1 block 0: the vertex ending the
+// flight of event e (two direction draws, roulette) and, word 3, the first
+// optical depth of its sun ray; stream 2 block 0: path start (and, word 2, a
+// camera path's first optical depth); blocks kBlockVertex and kBlockVertex - 1
+// of stream 0: a learned vertex (and a Rayleigh vertex's species).  Streams:
+// 0 flight, 1 vertex and its sun ray, 2 path start, 3 direct sun ray of a
+// flux path.
 constexpr uint32_t kBlockVertex = 0xFFFFFFFFu;
 
 __device__ __forceinline__ float u01(uint32_t w)

@@ -20,10 +20,17 @@
 //     (t *= 1 - k/M, Russian roulette below 0.1) or delta tracking.
 //   events: HG scattering with weight omega, Lambertian ground with weight
 //     albedo, Russian roulette below w = 0.01; escape at the top.
-// Random numbers: path id p, event e: stream (e, 0) for the flight (block j
-// for its j-th tentative collision, a fixed block for the vertex ending it);
-// (e, 1) for that vertex's sun ray; (0, 2) for the camera jitter / ground
-// point; (0, 3) for the direct sun ray of a flux path.
+// Random numbers: path id p, event e: stream (e, 0) for the flight (block 0
+// word 0 its first optical depth -- the camera's first flight takes word 2
+// of the path-start block instead -- and block j its j-th tentative
+// collision); (e, 1) for the vertex ending that flight and its sun ray
+// (block 0: two direction draws, roulette and, in word 3, the sun ray's
+// first optical depth; block j the sun ray's j-th tentative collision);
+// (0, 2) for the camera jitter / ground point; (0, 3) for the direct sun ray
+// of a flux path.  A learned vertex draws from blocks kBlockVertex and
+// kBlockVertex - 1 of stream (e, 0) (word 1 of the latter: its sun ray's
+// first optical depth), a Rayleigh vertex its species from word 0 of block
+// kBlockVertex.
 //
 // Loop structure (one iteration): flush finished chunks and claim new ones
 // (convergent); one Philox block per lane; one phase of work per lane (path
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         uint32_t xc2 = c2, xblk = 0u;
         if (ph == PH_START) xc2 = 2u;
         else if (ph == PH_STEP) xblk = blk;
-        else if (ph == PH_VERTEX) { xc2 = ev << 2; xblk = kBlockVertex; }
+        else if (ph == PH_VERTEX) { xc2 = (ev << 2) | 1u; xblk = 0u; }   // the sun ray's block 0
         mark(0);
         const uint4 x = draw_block(pid, xc2, xblk, rkey);
         mark(1);
@@ -295,6 +302,8 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         bool setup = false;          // enter a leaf after the load
         bool walk = false;           // heightfield: find this ray's ground hit now
         bool merge = false;          // a path start or vertex whose ray starts in this iteration too
+        uint32_t mword = 0u;         // ... the word giving that ray's first optical depth
+        bool mdraw = false;          // ... or draw it from the ray's own block 0 (flux path start)
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
             if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; sa = 0.0f; dal = 0.0f; }
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 for (int a = 0; a < 3; ++a) { vx[a] = q[a]; nd[a] = d[a]; }
                 kind = kMain;
                 c2 = 0u;
-                if (enters) { phase = PH_BEGIN; merge = true; }
+                if (enters) { phase = PH_BEGIN; merge = true; mword = x.z; }
                 else evc = EV_ESCAPE;          // a path that misses the field scores 0
             } else {
                 vx[0] = (1.0f - u01(x.x)) * S.Lper[0];
@@ -345,6 +354,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 Ts = 1.0f;
                 phase = PH_BEGIN;
                 merge = true;
+                mdraw = true;
                 if constexpr (TERRAIN) {
                     // the surface point above (x, y), lifted along its normal;
                     // directions cosine-weighted about the normal; the direct
@@ -383,10 +393,11 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 float mu_new;
                 if (EXTRA && S.rayleigh) {
                     // Rayleigh clear air: the mixture phase function in the estimate;
-                    // the species sampled with word 3 of the vertex block
+                    // the species sampled with word 0 of the flight's vertex block
                     const float pc = cloud_scatter_share(S, vk);
                     ph = pc * ph + (1.0f - pc) * rayleigh_pdf(mu);
-                    mu_new = u01(x.w) > pc ? rayleigh_sample_mu(xi1) : hg_sample_mu(S.g, xi1);
+                    const uint4 xs = draw_block(pid, ev << 2, kBlockVertex, rkey);
+                    mu_new = u01(xs.x) > pc ? rayleigh_sample_mu(xi1) : hg_sample_mu(S.g, xi1);
                 } else {
                     mu_new = hg_sample_mu(S.g, xi1);
                 }
@@ -437,6 +448,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 Ts = 1.0f;
                 phase = PH_BEGIN;
                 merge = true;
+                mword = x.w;     // word 3 of the vertex block
             } else {
                 Ts = 0.0f;
                 evc = EV_SUN_END;
@@ -524,6 +536,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 Ts = 1.0f;
                 phase = PH_BEGIN;
                 merge = true;
+                mword = xl.y;    // word 1 of the lobe block
             } else {
                 Ts = 0.0f;
                 evc = EV_SUN_END;
@@ -531,14 +544,15 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         }
         mark(5);
         // a lane whose path start, vertex or resumed vertex set up a ray
-        // starts it now, with the ray start's own Philox block (the one a
-        // later iteration would have drawn), so it skips one rare iteration
-        // and its wait
-        const bool any_merge = __any_sync(kFull, merge);
-        uint4 xb = x;
-        if (any_merge) {
+        // starts it now, so it skips one rare iteration and its wait; the
+        // ray's first optical depth comes from a word of the block that set
+        // it up (a flux path start, which uses all four, draws the ray's own
+        // block 0)
+        const bool any_draw = __any_sync(kFull, mdraw);
+        uint32_t tw = merge ? mword : x.x;
+        if (any_draw) {
             const uint4 y = draw_block(pid, c2, 0u, rkey);
-            if (merge) xb = y;
+            if (mdraw) tw = y.x;
         }
         if (ph == PH_BEGIN || merge) {
             // start a ray: the flight from vx along nd, or the sun ray from vx
@@ -554,7 +568,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             R.steps = 0;
             ptr = leaf_entry(S, R.v);
             setup = true;
-            tau = -__logf(u01(xb.x));
+            tau = -__logf(u01(tw));
             blk = 1;
             if constexpr (TERRAIN) {
                 // a sun ray that meets the surface is shadowed (found now: sun rays
