@@ -35,10 +35,10 @@
 // Loop structure (one iteration): flush finished chunks and claim new ones
 // (convergent); one Philox block per lane; one phase of work per lane (path
 // start, traversal step, vertex, ray start -- a path start or a vertex,
-// learned or not, goes on into the ray start it sets up, with that ray
-// start's own block); one 8-byte load (the voxel of a tentative collision
-// or the leaf-map entry of the leaf entered); the leaf set-up; the end of a
-// ray or path.
+// learned or not, goes on into the ray start it sets up, whose first
+// optical depth is a word of the block already drawn); one 8-byte load (the
+// voxel of a tentative collision or the leaf-map entry of the leaf entered);
+// the leaf set-up; the end of a ray or path.
 #include <cuda_bf16.h>
 
 #include "mcrt_internal.h"
@@ -81,9 +81,10 @@ constexpr int kOcc = 8;
 // (flight or sun ray), takes one traversal step, or handles the vertex that
 // ended a flight.  Every lane evaluates one Philox block per iteration at
 // one site, whose counter depends on the phase (a path start or vertex that
-// continues into its ray start also draws that ray start's block, the one a
-// later iteration would have drawn); the voxel / leaf-entry load and the
-// leaf set-up also run at one site each.
+// continues into its ray start takes that ray's first optical depth from a
+// word of it; only a flux path start, which uses all four words, draws the
+// ray's own block too); the voxel / leaf-entry load and the leaf set-up also
+// run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
 // EXTRA: the variants that also handle decomposition tracking of sun rays
