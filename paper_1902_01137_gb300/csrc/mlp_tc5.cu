@@ -58,20 +58,27 @@ __device__ __forceinline__ float tanh_fast(float x)
     return y;
 }
 
-// GELU (tanh form) and its derivative.
+// GELU (tanh form), h = x/2 (1 + tanh u) with u = c (x + a x^3), and its
+// derivative h' = (1 + t)/2 + x/2 (1 - t^2) c (1 + 3 a x^2), t = tanh u,
+// written as a chain of fused multiply-adds.
+constexpr float kGeluC = 0.7978845608028654f;                 // sqrt(2 / pi)
+constexpr float kGeluAC = 0.044715f * 0.7978845608028654f;      // a c
+constexpr float kGelu3AC = 3.0f * 0.044715f * 0.7978845608028654f;
+
 __device__ __forceinline__ void gelu2(float x, float& h, float& gp)
 {
-    const float c = 0.7978845608028654f;
     const float x2 = x * x;
-    const float t = tanh_fast(c * fmaf(0.044715f * x2, x, x));
-    h = 0.5f * x * (1.0f + t);
-    gp = 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * c * fmaf(3.0f * 0.044715f, x2, 1.0f);
+    const float t = tanh_fast(x * fmaf(kGeluAC, x2, kGeluC));
+    const float hx = 0.5f * x;
+    h = fmaf(hx, t, hx);
+    gp = fmaf(hx * fmaf(-t, t, 1.0f), fmaf(kGelu3AC, x2, kGeluC), fmaf(0.5f, t, 0.5f));
 }
 
 __device__ __forceinline__ float gelu1(float x)
 {
-    const float c = 0.7978845608028654f;
-    return 0.5f * x * (1.0f + tanh_fast(c * fmaf(0.044715f * x * x, x, x)));
+    const float t = tanh_fast(x * fmaf(kGeluAC, x * x, kGeluC));
+    const float hx = 0.5f * x;
+    return fmaf(hx, t, hx);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
