@@ -232,6 +232,36 @@ def test_launch_shape_does_not_change_results(m, small):
     np.testing.assert_allclose(c.mean, d.mean, rtol=4e-6, atol=1e-12)
 
 
+def test_rare_phase_batching_does_not_change_results(m, ctx, small):
+    """When a lane's path start, ray start or vertex runs (how many lanes of
+    its warp must be waiting for one) is launch shape only: a path start or
+    vertex that runs on into its ray start takes the same numbers it would
+    take in a later iteration, so every path's score is the same and only
+    the order of the FP64 adds of the chunk sums differs.  Covers the plain
+    kernel, decomposition tracking (its own variant) and a heightfield
+    (whose ground walks are a rare kind of their own)."""
+    sp, sc = small
+    cam = scenes.nadir_camera(sp, 32, 32)
+    for kw in ({}, {"sun_mode": m.MCRT_SUN_DECOMP}):
+        ref = sc.trace_flux(40000, seed=11, **kw)
+        for rb in (1, 4, 32):
+            r = sc.trace_flux(40000, seed=11, rare_batch=rb, **kw)
+            np.testing.assert_allclose(r.mean, ref.mean, rtol=1e-10, atol=1e-14)
+    ci = sc.trace_camera(cam, 16, seed=12)
+    for rb in (1, 32):
+        r = sc.trace_camera(cam, 16, seed=12, rare_batch=rb)
+        np.testing.assert_allclose(r.mean, ci.mean, rtol=1e-10, atol=1e-14)
+    ts = m.Scene.from_spec(ctx, sp)
+    try:
+        ts.set_heightfield(scenes.heightfield(128, 0.3, seed=5), sp.ground_albedo)
+        ref = ts.trace_flux(20000, seed=13)
+        for rb in (1, 32):
+            r = ts.trace_flux(20000, seed=13, rare_batch=rb)
+            np.testing.assert_allclose(r.mean, ref.mean, rtol=1e-10, atol=1e-14)
+    finally:
+        ts.close()
+
+
 def test_event_counters(m, small):
     sp, sc = small
     r = sc.trace_flux(20000, seed=4, count_events=1)
