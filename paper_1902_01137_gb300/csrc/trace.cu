@@ -34,8 +34,8 @@
 //
 // Loop structure (one iteration): flush finished chunks and claim new ones
 // (convergent); one Philox block per lane; one phase of work per lane (path
-// start, traversal step, vertex, ray start -- a path start or a vertex,
-// learned or not, goes on into the ray start it sets up, whose first
+// start, traversal step, vertex, ray start -- a camera path start or a
+// vertex, learned or not, goes on into the ray start it sets up, whose first
 // optical depth is a word of the block already drawn); one 8-byte load (the
 // voxel of a tentative collision or the leaf-map entry of the leaf entered);
 // the leaf set-up; the end of a ray or path.
@@ -80,11 +80,10 @@ constexpr int kOcc = 8;
 // Each lane is in one phase per iteration: it starts a path, starts a ray
 // (flight or sun ray), takes one traversal step, or handles the vertex that
 // ended a flight.  Every lane evaluates one Philox block per iteration at
-// one site, whose counter depends on the phase (a path start or vertex that
-// continues into its ray start takes that ray's first optical depth from a
-// word of it; only a flux path start, which uses all four words, draws the
-// ray's own block too); the voxel / leaf-entry load and the leaf set-up also
-// run at one site each.
+// one site, whose counter depends on the phase (a camera path start or a
+// vertex that continues into its ray start takes that ray's first optical
+// depth from a word of it); the voxel / leaf-entry load and the leaf set-up
+// also run at one site each.
 enum Phase { PH_IDLE = 0, PH_START, PH_BEGIN, PH_STEP, PH_VERTEX, PH_RESUME, PH_TERRAIN };
 
 // EXTRA: the variants that also handle decomposition tracking of sun rays
@@ -304,7 +303,6 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
         bool walk = false;           // heightfield: find this ray's ground hit now
         bool merge = false;          // a path start or vertex whose ray starts in this iteration too
         uint32_t mword = 0u;         // ... the word giving that ray's first optical depth
-        bool mdraw = false;          // ... or draw it from the ray's own block 0 (flux path start)
         if (ph == PH_START) {
             w = 1.0f; score = 0.0f; ev = 0; tdir = 0.0f; term_after = false;
             if (BATCH) { sg = 0.0f; sv_pending = 0.0f; cfs = 0.0f; dscore = 0.0f; sa = 0.0f; dal = 0.0f; }
@@ -353,9 +351,7 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
                 kind = kSunDirect;
                 c2 = 3u;
                 Ts = 1.0f;
-                phase = PH_BEGIN;
-                merge = true;
-                mdraw = true;
+                phase = PH_BEGIN;      // (its four words used up: the ray starts next time)
                 if constexpr (TERRAIN) {
                     // the surface point above (x, y), lifted along its normal;
                     // directions cosine-weighted about the normal; the direct
@@ -544,17 +540,12 @@ __global__ void __launch_bounds__(128, MCRT_TRACE_MIN_BLOCKS) trace_kernel(const
             }
         }
         mark(5);
-        // a lane whose path start, vertex or resumed vertex set up a ray
-        // starts it now, so it skips one rare iteration and its wait; the
-        // ray's first optical depth comes from a word of the block that set
-        // it up (a flux path start, which uses all four, draws the ray's own
-        // block 0)
-        const bool any_draw = __any_sync(kFull, mdraw);
-        uint32_t tw = merge ? mword : x.x;
-        if (any_draw) {
-            const uint4 y = draw_block(pid, c2, 0u, rkey);
-            if (mdraw) tw = y.x;
-        }
+        // a lane whose camera path start, vertex or resumed vertex set up a
+        // ray starts it now, so it skips one rare iteration and its wait;
+        // the ray's first optical depth comes from a word of the block that
+        // set it up (a flux path start uses all four words of its block, so
+        // its direct sun ray starts in a later iteration, from its own block)
+        const uint32_t tw = merge ? mword : x.x;
         if (ph == PH_BEGIN || merge) {
             // start a ray: the flight from vx along nd, or the sun ray from vx
 #pragma unroll
