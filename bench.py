@@ -62,22 +62,22 @@ WORKLOAD = "cumulus 512x512x160 @25m, 3-level majorants, 1024x1024 nadir image x
 W, H, SPP = CUMULUS.image.width, CUMULUS.image.height, CUMULUS.image.spp
 # DRAM traffic of the trace kernel from the last full ncu capture (profiles/),
 # valid only while the kernel's sources are the ones that were captured
-PROFILED_TRACE_SHA = "0201f140b7ad0ddc"
+PROFILED_TRACE_SHA = "a98ee57872041750"
 PROFILED_DRAM_BYTES_PER_PATH = 23.62
 # issue figures: warp instructions per path and threads per warp instruction
 # from a one-pass count of a bench launch (1024^2 x 64 spp), the small
 # capture's issue-active fraction; the kernel is issue-bound, so these
 # locate it against its real ceiling: 152 SMs x 4 schedulers x 1 warp
 # instruction per cycle
-PROFILED_ISSUE_ACTIVE = 0.7235
-PROFILED_THREADS_PER_INST = 16.64
-PROFILED_WARP_INST_PER_PATH = 4911.3
+PROFILED_ISSUE_ACTIVE = 0.7237
+PROFILED_THREADS_PER_INST = 16.53
+PROFILED_WARP_INST_PER_PATH = 4877.3
 PROFILED_SOURCE = "profiles/trace_kernel_cumulus_1024px64spp_launches.md"
 # the same capture over the octree (profiles/trace_kernel_octree_cumulus_512px16spp_ncu_full.md)
-PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 39.75
+PROFILED_OCTREE_DRAM_BYTES_PER_PATH = 39.87
 # one-pass count of the bench's octree launches (same profile as the pyramid's)
-PROFILED_OCTREE_WARP_INST_PER_PATH = 3728.5
-PROFILED_OCTREE_THREADS_PER_INST = 15.46
+PROFILED_OCTREE_WARP_INST_PER_PATH = 3704.2
+PROFILED_OCTREE_THREADS_PER_INST = 15.35
 
 
 def trace_sources_sha() -> str:
