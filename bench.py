@@ -19,11 +19,16 @@ per pixel (67,108,864 paths), mean/SE finalize.
              by a separate counting run with the same seed) / kernel time,
              over measured HBM
   cpu_baseline  the CPU oracle on a bounded pixel sample of the same image
+  octree     the same steps over the paper's 2^L octree (built in each step)
+  wavefront  the same steps (same seeds, same path scores) scheduled as a
+             wavefront: SoA queues of flights and vertices, one kernel per
+             stage and round, instead of the persistent loop
 
   fom        1/(relative variance x time) of the learned proposal against
-             plain HG sampling on the small blob field at sun zenith 60 deg:
-             domain-mean ground flux T_tot and a 512 x 512 image, with the
-             network's online training time counted and, separately, frozen
+             plain HG sampling on the bench field at sun zenith 60 deg, each
+             run until its median pixel relative SE is 1 %: a 512 x 512
+             image and the domain-mean ground flux T_tot, frozen network and
+             with its online training time counted
 
 ``--workload batch``: 96 flux problems (fields 64^2x32 ... 1024^2x160 with
 1-16 gas bands each, sun zenith 0-75 deg) in one persistent launch, launch
@@ -459,6 +464,33 @@ def run_gpu(args):
                                  PROFILED_OCTREE_WARP_INST_PER_PATH, PROFILED_OCTREE_THREADS_PER_INST)
         octree["roofline"] = o_issue or octree["roofline_hbm"]
 
+    # the same steps (same seeds, so the same path scores) scheduled as a
+    # wavefront: SoA queues of flights and vertices in device memory, one
+    # kernel per stage and round, instead of the persistent loop
+    wavefront = None
+    if not args.no_wavefront and world == 1:
+        wopts = m.mcrt_trace_opts_default()
+        wopts.schedule = m.MCRT_SCHEDULE_WAVEFRONT
+        for i in range(args.warmup):
+            step(base_seed + 600 + i, k_dev, o=wopts)
+        torch.cuda.synchronize()
+        wf_step_ms, wf_kern_ms = [], []
+        for i in range(args.steps):
+            flush_buf.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wf_kern_ms.append(step(base_seed + 100 + i, k_dev, o=wopts))
+            e1.record(stream)
+            e1.synchronize()
+            wf_step_ms.append(e0.elapsed_time(e1))
+        wf_total = sum(wf_step_ms)
+        wavefront = {"value": paths_per_step * args.steps / (wf_total / 1e3), "unit": "paths/s",
+                     "ms_per_step": wf_total / args.steps, "kernel_ms": statistics.mean(wf_kern_ms),
+                     "schedule": "wavefront: SoA queues, flight / vertex+sun ray / start kernels per round, "
+                                 "2^21 paths in flight", "steps": args.steps, "l2": "flushed between steps",
+                     "persistent_kernel_ms": statistics.mean(kern_ms)}
+
     # e2e: pinned host field in, image mean/SE out, through the C ABI
     e2e_val = None
     h2d = spec.k.nbytes
@@ -523,7 +555,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_val, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk,
             "collision_events_per_s": events / (kavg / 1e3),
-            "octree": octree,
+            "octree": octree, "wavefront": wavefront,
             "fom": fom,
             "counters": cnt}
     if rank == 0:
@@ -1077,18 +1109,29 @@ def run_fom_sweep(args):
     return 0
 
 
-def run_profile_case(grid="pyramid"):
+def run_profile_case(grid="pyramid", schedule="persistent"):
     """A small case of the bench kernel for ncu: the same 512x512x160 field
     (160 MiB, larger than L2), a 512 x 512 image at 16 spp (4,194,304
     paths), two launches; over the 8^L pyramid (the bench line) or over the
-    paper's 2^L octree (the line's `octree` figure: tau~ 1, finest level 1)."""
+    paper's 2^L octree (the line's `octree` figure: tau~ 1, finest level 1).
+    schedule "wavefront": one trace of the bench image itself (1024 x 1024
+    x 64 spp) with the wavefront schedule, whose round count is set by the
+    longest path rather than by the image size."""
     import torch
     import paper_1902_01137_gb300 as m
-    spec, _ = make_workload()
+    spec, bench_cam = make_workload()
     import scenes
     cam = scenes.nadir_camera(spec, 512, 512)
     ctx = m.Context(0)
     sc = m.Scene.from_spec(ctx, spec, k=torch.from_numpy(spec.k).cuda())
+    if schedule == "wavefront":
+        l0 = ctx.launches
+        r = sc.trace_camera(bench_cam, SPP, seed=7, schedule=m.MCRT_SCHEDULE_WAVEFRONT)
+        print("wavefront kernel_ms", r.kernel_ms, "launches", ctx.launches - l0, "mean", float(r.mean.mean()),
+              flush=True)
+        sc.close()
+        ctx.close()
+        return 0
     kw = dict(chunk=4)            # the bench launch's claim size (the default at its size)
     if grid == "octree":
         sc.build_octree()
@@ -1161,6 +1204,7 @@ def main():
     ap.add_argument("--sweep-paths", type=int, default=100_000_000)
     ap.add_argument("--no-fom", action="store_true")
     ap.add_argument("--no-octree", action="store_true")
+    ap.add_argument("--no-wavefront", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="trace one 512x512 x 16 spp image of the cumulus field twice and exit (for ncu captures)")
     ap.add_argument("--profile-learned", action="store_true",
@@ -1169,6 +1213,8 @@ def main():
                     help="run the network's training kernels on 2^20 synthetic records and exit (for ncu)")
     ap.add_argument("--profile-grid", default="pyramid", choices=["pyramid", "octree"],
                     help="grid the profile case traces over")
+    ap.add_argument("--profile-schedule", default="persistent", choices=["persistent", "wavefront"],
+                    help="schedule the profile case traces with")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per trace launch, if captured for this kernel version")
     args = ap.parse_args()
@@ -1177,7 +1223,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
-        return run_profile_case(args.profile_grid)
+        return run_profile_case(args.profile_grid, args.profile_schedule)
     if args.profile_learned:
         return run_profile_learned()
     if args.profile_train:

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define MCRT_ABI_VERSION 1
+#define MCRT_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define MCRT_API __attribute__((visibility("default")))
@@ -83,6 +83,19 @@ enum { MCRT_GRID_PYRAMID = 0, MCRT_GRID_OCTREE = 1 };
 
 /* Order in which a camera trace claims its pixels (mcrt_trace_opts.pixel_order). */
 enum { MCRT_ORDER_COST = 0, MCRT_ORDER_RASTER = 1 };
+
+/* How a camera trace schedules its paths on the GPU (mcrt_trace_opts.schedule).
+ * PERSISTENT: one loop per GPU thread that takes one step of one path per
+ * iteration, path state in registers (the default).  WAVEFRONT: paths wait
+ * in structure-of-arrays queues in device memory between stages (flight
+ * tracking; vertex and sun ray; path start), one kernel per stage and round.
+ * Both compute the same path scores bit for bit (Philox counters and FP32
+ * steps are the same); only the order of the FP64 tally additions differs.
+ * The wavefront form serves plain camera images only: no proposal, shards,
+ * decomposition tracking, Rayleigh clear air, heightfield ground, event
+ * counts, deadline or cancel flag (MCRT_ERR_UNSUPPORTED), and not through
+ * mcrt_trace_flux, mcrt_trace_batch or the no-allocation call. */
+enum { MCRT_SCHEDULE_PERSISTENT = 0, MCRT_SCHEDULE_WAVEFRONT = 1 };
 
 /* Library version and the ABI version it was built with. */
 MCRT_API int mcrt_version(int32_t* abi_version);
@@ -315,6 +328,11 @@ typedef struct {
                                /* whole path count.  0 or 1: no sharding.  Not  */
                                /* with a proposal, in batches or without        */
                                /* allocation (MCRT_ERR_UNSUPPORTED)             */
+    int32_t schedule;          /* MCRT_SCHEDULE_PERSISTENT (default) or         */
+                               /* MCRT_SCHEDULE_WAVEFRONT (camera traces)       */
+    int32_t wavefront_slots;   /* wavefront: paths in flight (queue entries per */
+                               /* stage, 56 B each, three queues); 0 = 2^21,    */
+                               /* at most 2^26.  Launch shape only              */
 } mcrt_trace_opts;
 
 /* Fill `opts` with the defaults listed above. */

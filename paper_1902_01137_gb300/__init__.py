@@ -46,6 +46,10 @@ MCRT_GRID_PYRAMID = 0
 MCRT_GRID_OCTREE = 1
 MCRT_ORDER_COST = 0
 MCRT_ORDER_RASTER = 1
+# the struct layouts below match include/mcrt.h at this ABI version
+ABI_VERSION = 2
+MCRT_SCHEDULE_PERSISTENT = 0
+MCRT_SCHEDULE_WAVEFRONT = 1
 
 COUNTER_NAMES = ("paths", "tentative", "real", "ground", "leaf_steps", "sun_tentative", "sun_leaf_steps",
                  "sun_rays", "aborted", "flights", "max_path_iters", "warp_ns_to_dry", "warp_ns_total",
@@ -91,7 +95,9 @@ class TraceOpts(C.Structure):
                 ("grid", C.c_int32),
                 ("pixel_order", C.c_int32),
                 ("shard_index", C.c_int32),
-                ("shard_count", C.c_int32)]
+                ("shard_count", C.c_int32),
+                ("schedule", C.c_int32),
+                ("wavefront_slots", C.c_int32)]
 
 
 _lib = None
@@ -172,6 +178,10 @@ def _load():
         fn.restype = C.c_int
     L.mcrt_status_string.restype = C.c_char_p
     L.mcrt_last_error.restype = C.c_char_p
+    abi = C.c_int32()
+    L.mcrt_version(C.byref(abi))
+    if abi.value != ABI_VERSION:
+        raise ImportError("libmcrt.so has ABI version %d, this binding expects %d: rebuild it" % (abi.value, ABI_VERSION))
     _lib = L
     return L
 

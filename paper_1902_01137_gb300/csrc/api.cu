@@ -612,6 +612,16 @@ int check_opts(mcrt_scene* sc, const mcrt_trace_opts* o, const char* who)
         return fail(ctx, MCRT_ERR_ARG, "%s: shard_index %d of %d", who, o->shard_index, o->shard_count);
     if (o->shard_count > 1 && o->proposal)
         return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: sharding with a proposal", who);
+    if (o->schedule != MCRT_SCHEDULE_PERSISTENT && o->schedule != MCRT_SCHEDULE_WAVEFRONT)
+        return fail(ctx, MCRT_ERR_ARG, "%s: bad schedule", who);
+    if (o->wavefront_slots < 0 || o->wavefront_slots > (1 << 26))
+        return fail(ctx, MCRT_ERR_ARG, "%s: wavefront_slots must be in [0, 2^26]", who);
+    if (o->schedule == MCRT_SCHEDULE_WAVEFRONT &&
+        (o->proposal || o->shard_count > 1 || o->sun_mode == MCRT_SUN_DECOMP || sc->clear_phase == MCRT_PHASE_RAYLEIGH ||
+         sc->d_hf || o->count_events || o->deadline_ms > 0.0 || o->cancel_flag))
+        return fail(ctx, MCRT_ERR_UNSUPPORTED,
+                    "%s: the wavefront schedule traces plain images only (no proposal, shards, decomposition "
+                    "tracking, Rayleigh air, heightfield, event counts, deadline or cancel flag)", who);
     return MCRT_OK;
 }
 
@@ -759,6 +769,31 @@ int run_trace(mcrt_scene* sc, TraceParams& P, int sensor, const mcrt_trace_opts*
     t->kernel_ms = ms;
     if (ws.status == 1) return fail(ctx, MCRT_ERR_TIMEOUT, "%s: deadline of %g ms expired", who, o->deadline_ms);
     if (ws.status == 2) return fail(ctx, MCRT_ERR_CANCELLED, "%s: cancelled", who);
+    return MCRT_OK;
+}
+
+// The camera trace as a wavefront of stage kernels over SoA queues.
+int run_wavefront(mcrt_scene* sc, TraceParams& P, const mcrt_trace_opts* o, mcrt_tally* t, const char* who)
+{
+    mcrt_ctx* ctx = sc->ctx;
+    P.s1 = t->d_s1;
+    P.s2 = t->d_s2;
+    P.counters = t->d_counters;
+    P.work = static_cast<WorkState*>(t->d_work);
+    P.max_order = o->max_order;
+    P.sun_mode = o->sun_mode;
+    P.max_steps = 1u << 22;
+    unsigned long long slots = o->wavefront_slots ? (unsigned long long)o->wavefront_slots : (1ull << 21);
+    if (slots > P.total) slots = P.total ? P.total : 1ull;
+    WavefrontStats ws{};
+    const cudaError_t e = wavefront_camera(P, sc->storage == MCRT_STORAGE_BF16, (unsigned)slots, ctx->sm_count,
+                                           ctx->stream, &ws);
+    ctx->launches += ws.launches;
+    if (e != cudaSuccess)
+        return fail(ctx, e == cudaErrorMemoryAllocation ? MCRT_ERR_OOM : MCRT_ERR_CUDA, "%s: wavefront: %s", who,
+                    cudaGetErrorString(e));
+    if (ws.overflow) return fail(ctx, MCRT_ERR_CUDA, "%s: wavefront queue overflow (%u)", who, ws.overflow);
+    t->kernel_ms = ws.ms;
     return MCRT_OK;
 }
 
@@ -1022,6 +1057,11 @@ int mcrt_trace_camera(mcrt_scene* sc, const mcrt_camera_desc* cam, uint32_t spp,
         if (rc) return rc;
         P.pix_order = d_order;
     }
+    if (o->schedule == MCRT_SCHEDULE_WAVEFRONT) {
+        rc = run_wavefront(sc, P, o, t, who);
+        dfree(ctx, d_order);
+        return rc;
+    }
     if (o->shard_count > 1) {
         // this shard's pixels: every shard_count-th position of the claim order
         const uint32_t nsh = (uint32_t)o->shard_count, idx = (uint32_t)o->shard_index, npix = (uint32_t)ncells;
@@ -1059,6 +1099,8 @@ int mcrt_trace_flux(mcrt_scene* sc, uint64_t npaths, uint64_t seed, const mcrt_t
     const mcrt_trace_opts* o = opts ? opts : &dflt;
     int rc = check_opts(sc, o, who);
     if (rc) return rc;
+    if (o->schedule != MCRT_SCHEDULE_PERSISTENT)
+        return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the wavefront schedule traces camera images only", who);
     if (npaths < 1) return fail(ctx, MCRT_ERR_ARG, "%s: npaths must be >= 1", who);
     CK(ctx, cudaSetDevice(ctx->device));
     rc = ensure_leaf(sc, o->tau_merge, o->finest_level, o->grid);
@@ -1112,6 +1154,8 @@ int prepare_batch(mcrt_ctx* ctx, const mcrt_batch_item* items, int32_t n, const 
     if (o->proposal) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: learned proposal in batches", who);
     if (o->shard_count > 1) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: sharding in batches (items are the unit)", who);
     if (o->sun_mode == MCRT_SUN_DECOMP) return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: decomposition tracking in batches", who);
+    if (o->schedule != MCRT_SCHEDULE_PERSISTENT)
+        return fail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the wavefront schedule traces camera images only", who);
     const uint32_t chunk = o->chunk ? (uint32_t)o->chunk : 4u;
     h.assign((size_t)n, BatchItem{});
     unsigned long long begin = 0;

@@ -265,6 +265,19 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32
 
 DevScene make_dev_scene(const mcrt_scene* sc, float k_gas);
 
+// Camera trace scheduled as a wavefront (wavefront.cu): `slots` queue
+// entries per stage, rounds of flight, vertex and start kernels until every
+// path has ended.  ms: device time from the first to the last kernel.
+struct WavefrontStats {
+    float ms;
+    unsigned rounds;
+    unsigned overflow;             // 1: a queue was full; 2: too many rounds
+    unsigned long long launches;
+};
+cudaError_t wavefront_camera(const TraceParams& P, bool bf16, unsigned slots, int sm_count, cudaStream_t st,
+                             WavefrontStats* stats);
+int wavefront_blocks_per_sm(bool bf16);
+
 // Option checks shared by the trace entry points (status and message as
 // mcrt_trace_camera reports them), and the leaf map of (tau~, finest level,
 // grid), rebuilt in place when another one is current.

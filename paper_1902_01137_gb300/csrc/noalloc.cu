@@ -95,6 +95,8 @@ extern "C" int mcrt_trace_camera_noalloc(mcrt_scene* sc, const mcrt_camera_desc*
     const mcrt_trace_opts* o = opts ? opts : &dflt;
     int rc = check_opts(sc, o, who);
     if (rc != MCRT_OK) return rc;
+    if (o->schedule != MCRT_SCHEDULE_PERSISTENT)
+        return nfail(ctx, MCRT_ERR_UNSUPPORTED, "%s: the wavefront schedule allocates its queues", who);
     if (cam->width < 1 || cam->height < 1)
         return nfail(ctx, MCRT_ERR_ARG, "%s: bad image size %d x %d", who, cam->width, cam->height);
     if ((long long)cam->width * cam->height > kNoAllocMaxPixels)

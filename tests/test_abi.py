@@ -55,8 +55,37 @@ def test_binding_argument_checks_without_gpu(built):
     assert L.mcrt_tally_read(None, None, None, None, 0) == m.MCRT_ERR_ARG
     o = m.mcrt_trace_opts_default()
     assert o.tau_merge == 1.0 and o.finest_level == 0 and o.sun_mode == m.MCRT_SUN_RATIO
+    assert o.schedule == m.MCRT_SCHEDULE_PERSISTENT and o.wavefront_slots == 0
     v = C.c_int32()
-    assert L.mcrt_version(C.byref(v)) == 0 and v.value == 1
+    assert L.mcrt_version(C.byref(v)) == 0 and v.value == m.ABI_VERSION
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures have the C structures' sizes and field offsets
+    (gcc compiles a probe against include/mcrt.h)."""
+    import shutil
+    import subprocess
+    import paper_1902_01137_gb300 as m
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    structs = {"mcrt_trace_opts": m.TraceOpts, "mcrt_camera_desc": m.CameraDesc,
+               "mcrt_field_desc": m.FieldDesc, "mcrt_batch_item": m.BatchItem}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcrt.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[cname + "." + f]) == getattr(py, f).offset, (cname, f)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
