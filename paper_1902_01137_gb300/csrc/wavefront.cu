@@ -14,12 +14,17 @@
 //           then ends or queues its next flight for the next round;
 //   start   new camera paths fill the flight queue's free slots;
 // and a one-thread kernel closes the round (queue counts, slots to fill,
-// the end of the trace).  A thread takes one queue entry from its load to
-// its push; pushes take one atomic per warp.  Every random number comes
-// from the Philox counter the persistent kernel uses for it, and every step
-// calls the same device functions in the same order, so each path scores
-// the same value bit for bit; only the order of the FP64 tally additions
-// differs.
+// the end of the trace).  Stage threads are persistent: a lane tracks one
+// queue entry up to its push, then takes the next; pushes take one atomic
+// per warp.  Every random number comes from the Philox counter the
+// persistent kernel uses for it, and every step calls the same device
+// functions in the same order, so each path scores the same value bit for
+// bit; only the order of the FP64 tally additions differs.
+//
+// A trace takes as many rounds as its longest path has events, and every
+// stage kernel ends with its longest entry, so with the long random walks
+// of optically thick clouds this schedule is slower than the persistent
+// loop, where a lane on a long walk holds up no other lane.
 #include <algorithm>
 
 #include "mcrt_internal.h"
