@@ -348,9 +348,11 @@ MCRT_API int mcrt_trace_opts_default(mcrt_trace_opts* opts);
  * cosine law; Russian roulette below w = 0.01.  Radiance is in units of the
  * solar irradiance per sr.  The tally has width*height cells, 1 quantity.
  * *tally_inout: NULL to create a new tally, or an existing tally of the same
- * shape to reuse (its sums are reset).  Requires majorants.  Errors:
+ * shape to reuse (its sums are reset).  Requires majorants.  The paths run
+ * in one persistent kernel, or with opts->schedule = MCRT_SCHEDULE_WAVEFRONT
+ * as stage kernels over device queues (same path scores).  Errors:
  * MCRT_ERR_ARG, MCRT_ERR_STATE, MCRT_ERR_TIMEOUT, MCRT_ERR_CANCELLED,
- * MCRT_ERR_CUDA, MCRT_ERR_OOM. */
+ * MCRT_ERR_UNSUPPORTED, MCRT_ERR_CUDA, MCRT_ERR_OOM. */
 MCRT_API int mcrt_trace_camera(mcrt_scene* scene, const mcrt_camera_desc* camera, uint32_t spp, uint64_t seed,
                       const mcrt_trace_opts* opts, mcrt_tally** tally_inout);
 
