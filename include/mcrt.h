@@ -331,7 +331,7 @@ typedef struct {
     int32_t schedule;          /* MCRT_SCHEDULE_PERSISTENT (default) or         */
                                /* MCRT_SCHEDULE_WAVEFRONT (camera traces)       */
     int32_t wavefront_slots;   /* wavefront: paths in flight (queue entries per */
-                               /* stage, 56 B each, three queues); 0 = 2^21,    */
+                               /* stage, 80 B each, three queues); 0 = 2^21,    */
                                /* at most 2^26.  Launch shape only              */
 } mcrt_trace_opts;
 

@@ -48,6 +48,14 @@ struct WfQueue {
     float* x[3];
     float* d[3];
     float* aux;
+    // flight entries: 0 for a flight not started yet, else the Philox block
+    // of its next tentative collision, with the ray's current voxel, distance
+    // along it and leaves entered (x: its current origin) -- a flight that
+    // reached its step budget for the round goes on from there
+    uint32_t* blk;
+    uint32_t* vox[3];
+    float* t;
+    uint32_t* steps;
 };
 
 struct WfState {
@@ -131,6 +139,11 @@ __device__ __forceinline__ void wf_ray_start(const DevScene& S, Ray& R, const fl
 // idle (or all are), with one atomic per warp on the queue's read head.
 constexpr int kRefillLanes = 8;
 
+// Steps a flight takes in one round before it waits for the next round, so
+// that no round waits long for one flight (one close to horizontal can wrap
+// around the periodic domain for thousands of leaves).
+constexpr uint32_t kStepsPerRound = 128;
+
 // Queue entries for the idle lanes of the calling warp (all 32 lanes call
 // it): true in a lane that got entry *i; *exhausted once the queue's n
 // entries are all taken.
@@ -181,10 +194,11 @@ __global__ void __launch_bounds__(kWfBlock) wf_flight_kernel(const __grid_consta
     const TraceParams& P = W.P;
     const DevScene& S = P.S;
     const WfQueue& F = W.F[in];
+    const WfQueue& G = W.F[in ^ 1];       // flights of the next round
     const unsigned n = min(W.st->nf[in], W.cap);
     bool have = false, exhausted = false;
     unsigned long long pid = 0;
-    uint32_t cell = 0, ev = 0, blk = 1;
+    uint32_t cell = 0, ev = 0, blk = 1, budget = 0;
     float w = 0.0f, score = 0.0f, tau = 0.0f;
     Ray R;
     for (;;) {
@@ -202,8 +216,26 @@ __global__ void __launch_bounds__(kWfBlock) wf_flight_kernel(const __grid_consta
                 d[a] = F.d[a][i];
             }
             tau = F.aux[i];
-            wf_ray_start<BF16>(S, R, o, d);
-            blk = 1;
+            blk = F.blk[i];
+            if (blk == 0u) {
+                wf_ray_start<BF16>(S, R, o, d);
+                blk = 1;
+            } else {
+                // a flight suspended at its step budget: re-entering its
+                // leaf from the same voxel at the same distance gives the
+                // same leaf, majorant and exit as before
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    R.o[a] = o[a];
+                    R.d[a] = d[a];
+                    R.inv_d[a] = (d[a] != 0.0f) ? __frcp_rn(d[a]) : 0.0f;
+                    R.v[a] = (int)F.vox[a][i];
+                }
+                R.t = F.t[i];
+                R.steps = F.steps[i];
+                finish_leaf<BF16>(S, R, __ldg(leaf_entry(S, R.v)));
+            }
+            budget = kStepsPerRound;
             have = true;
         }
         if (!__any_sync(kFull, have)) break;
@@ -242,12 +274,27 @@ __global__ void __launch_bounds__(kWfBlock) wf_flight_kernel(const __grid_consta
                 outcome = 1;
             }
         }
+        // a flight that used up its steps for this round goes on in the next
+        if (have && outcome == 0 && --budget == 0u) outcome = 3;
         const unsigned slot = wf_reserve(&W.st->nv, outcome == 1);
         if (outcome == 1) {
             if (slot < W.cap) wf_put(W.V, slot, pid, cell, ev, ground, w, score, vx, R.d, vk);
             else atomicOr(&W.st->overflow, 1u);
         } else if (outcome == 2) {
             wf_tally(P, cell, score);
+        }
+        const unsigned gslot = wf_reserve(&W.st->nf[in ^ 1], outcome == 3);
+        if (outcome == 3) {
+            if (gslot < W.cap) {
+                wf_put(G, gslot, pid, cell, ev, 0u, w, score, R.o, R.d, tau);
+                G.blk[gslot] = blk;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) G.vox[a][gslot] = (uint32_t)R.v[a];
+                G.t[gslot] = R.t;
+                G.steps[gslot] = R.steps;
+            } else {
+                atomicOr(&W.st->overflow, 1u);
+            }
         }
         if (outcome) have = false;
     }
@@ -371,8 +418,12 @@ __global__ void __launch_bounds__(kWfBlock) wf_vertex_kernel(const __grid_consta
         }
         const unsigned slot = wf_reserve(&W.st->nf[out], outcome == 1);
         if (outcome == 1) {
-            if (slot < W.cap) wf_put(W.F[out], slot, pid, cell, ev, 0u, w, score, vx, nd, tau_next);
-            else atomicOr(&W.st->overflow, 1u);
+            if (slot < W.cap) {
+                wf_put(W.F[out], slot, pid, cell, ev, 0u, w, score, vx, nd, tau_next);
+                W.F[out].blk[slot] = 0u;
+            } else {
+                atomicOr(&W.st->overflow, 1u);
+            }
         } else if (outcome == 2) {
             wf_tally(P, cell, score);
         }
@@ -448,8 +499,12 @@ __global__ void __launch_bounds__(kWfBlock) wf_start_kernel(const __grid_constan
         }
         const unsigned slot = wf_reserve(&W.st->nf[out], enters);
         if (enters) {
-            if (slot < W.cap) wf_put(W.F[out], slot, pid, cell, 0u, 0u, 1.0f, 0.0f, q, d, tau);
-            else atomicOr(&W.st->overflow, 1u);
+            if (slot < W.cap) {
+                wf_put(W.F[out], slot, pid, cell, 0u, 0u, 1.0f, 0.0f, q, d, tau);
+                W.F[out].blk[slot] = 0u;
+            } else {
+                atomicOr(&W.st->overflow, 1u);
+            }
         }
     }
 }
@@ -484,10 +539,10 @@ __global__ void wf_close_kernel(WfState* st, int in, unsigned cap, unsigned long
     }
 }
 
-// Bytes of one queue: the 8-byte ids, then 3 uint32 and 9 float arrays
-// (56 B per entry, a multiple of 8, so every queue and the state after them
+// Bytes of one queue: the 8-byte ids, then 8 uint32 and 10 float arrays
+// (80 B per entry, a multiple of 8, so every queue and the state after them
 // stay 8-byte aligned for any capacity).
-constexpr size_t kEntryBytes = 8 + 3 * 4 + 9 * 4;
+constexpr size_t kEntryBytes = 8 + 8 * 4 + 10 * 4;
 static_assert(kEntryBytes % 8 == 0, "queue entries keep 8-byte alignment");
 size_t queue_bytes(unsigned cap) { return (size_t)cap * kEntryBytes; }
 
@@ -495,14 +550,10 @@ void carve(WfQueue& Q, char* p, unsigned cap)
 {
     Q.pid = reinterpret_cast<unsigned long long*>(p);
     p += (size_t)cap * 8;
-    uint32_t** u[3] = {&Q.cell, &Q.ev, &Q.ground};
+    uint32_t** u[8] = {&Q.cell, &Q.ev, &Q.ground, &Q.blk, &Q.vox[0], &Q.vox[1], &Q.vox[2], &Q.steps};
     for (auto* f : u) { *f = reinterpret_cast<uint32_t*>(p); p += (size_t)cap * 4; }
-    float** fl[10] = {&Q.w, &Q.score, &Q.x[0], &Q.x[1], &Q.x[2], &Q.d[0], &Q.d[1], &Q.d[2], &Q.aux, nullptr};
-    for (auto* f : fl) {
-        if (!f) break;
-        *f = reinterpret_cast<float*>(p);
-        p += (size_t)cap * 4;
-    }
+    float** fl[10] = {&Q.w, &Q.score, &Q.x[0], &Q.x[1], &Q.x[2], &Q.d[0], &Q.d[1], &Q.d[2], &Q.aux, &Q.t};
+    for (auto* f : fl) { *f = reinterpret_cast<float*>(p); p += (size_t)cap * 4; }
 }
 
 }  // namespace
