@@ -19,7 +19,11 @@
 // per warp.  Every random number comes from the Philox counter the
 // persistent kernel uses for it, and every step calls the same device
 // functions in the same order, so each path scores the same value bit for
-// bit; only the order of the FP64 tally additions differs.
+// bit; only the order of the FP64 tally additions differs.  The traversal
+// is the shared device code of mcrt_device.cuh; the camera path start and
+// the vertex are restated here from trace.cu's phases, statement for
+// statement, and tests/test_gpu_wavefront.py holds the two schedules to
+// the same images.
 //
 // A trace takes as many rounds as its longest path has events, and every
 // stage kernel ends with its longest entry, so with the long random walks
